@@ -1,0 +1,171 @@
+"""Seeded synthetic inputs shaped like the paper's workloads.
+
+This module only generates inputs: grids, initial conditions, source samples
+and per-instance parameters.  It holds none of the method's arithmetic (no
+difference operator, no shift by the initial condition, no Krylov step), so the
+oracle and the CUDA path can both draw their inputs from here while sharing no
+computation.
+
+Shapes follow the paper's experiments: 1D periodic advection-diffusion on
+[0, 1) with second-order central differences (Sec. 3.1, Sec. 3.2), the viscous
+Burgers equation by waveform relaxation (Sec. 4), and output/sample times on a
+uniform grid over [0, T].
+
+Array conventions: a state vector is a length-n float array; a time series of
+n-vectors (sources G, solutions Y) is an array of shape (n_out, n) in C order,
+so that the n values at one output time are contiguous ("time-major").
+"""
+from __future__ import annotations
+
+import math
+from dataclasses import dataclass, field, asdict
+from typing import Optional
+
+import numpy as np
+
+SEED_BASE = 20150915
+
+BC_PERIODIC = 0
+BC_DIRICHLET0 = 1
+
+
+@dataclass
+class Problem:
+    """One linear problem u' = A u + g(t), u(0) = u0 on [0, T] (eq. ivp2).
+
+    ``op`` describes A: dim (1 or 2), nx, ny, bc, advection velocities ax, ay,
+    diffusivity nu and domain lengths Lx, Ly.  ``opts`` holds the solver
+    options (T, P, n_out, tol, ...).  ``u0`` and ``G`` are float64 arrays;
+    ``G`` has shape (n_out, n) or is None for a zero source.
+    """
+    name: str
+    op: dict
+    opts: dict
+    u0: np.ndarray
+    G: Optional[np.ndarray]
+    meta: dict = field(default_factory=dict)
+
+    @property
+    def n(self) -> int:
+        return int(self.op["nx"] * (self.op["ny"] if self.op["dim"] == 2 else 1))
+
+
+def default_opts(**kw) -> dict:
+    o = dict(T=1.0, P=1, n_out=2, tol=1e-8, svd_tol=1e-12, max_rank=16,
+             restart_len=20, max_restarts=0, krylov=1, sai_gamma=0.1,
+             precision=0, wr_max_iter=50, wr_tol=1e-6, burgers_form=0)
+    o.update(kw)
+    return o
+
+
+def make_op(nx, nu, ax=0.0, bc=BC_PERIODIC, dim=1, ny=1, ay=0.0, Lx=1.0, Ly=1.0) -> dict:
+    return dict(dim=dim, nx=int(nx), ny=int(ny), bc=int(bc), ax=float(ax), ay=float(ay),
+                nu=float(nu), Lx=float(Lx), Ly=float(Ly))
+
+
+def grid_1d(n: int, L: float = 1.0, bc: int = BC_PERIODIC) -> np.ndarray:
+    """Grid points of the 1D mesh: x_i = i*dx on [0, L) for periodic meshes,
+    interior points x_i = (i+1)*dx with dx = L/(n+1) for homogeneous Dirichlet."""
+    if bc == BC_PERIODIC:
+        return np.arange(n, dtype=np.float64) * (L / n)
+    return (np.arange(n, dtype=np.float64) + 1.0) * (L / (n + 1))
+
+
+def out_times(T: float, n_out: int) -> np.ndarray:
+    return np.arange(n_out, dtype=np.float64) * (T / (n_out - 1))
+
+
+def adv_diff_1d(n=1024, nu=1e-2, a=1.0, T=1.0, P=8, n_out=101, tol=1e-8,
+                svd_tol=1e-12, max_rank=16, with_source=True, **kw) -> Problem:
+    """1D periodic advection-diffusion, u0 = sin(2 pi x) + exp(-100 (x-0.5)^2),
+    g(x,t) = sin(4 pi x) cos(2 pi t).  At n=1024, nu=1e-2, P=8, n_out=101 this is
+    the small case; at n=2^20, nu=1e-3, P=64, n_out=1025 the large one."""
+    x = grid_1d(n)
+    u0 = np.sin(2 * np.pi * x) + np.exp(-100.0 * (x - 0.5) ** 2)
+    t = out_times(T, n_out)
+    G = None
+    if with_source:
+        G = np.cos(2 * np.pi * t)[:, None] * np.sin(4 * np.pi * x)[None, :]
+    return Problem(name=f"adv_diff_1d_n{n}", op=make_op(n, nu, a),
+                   opts=default_opts(T=T, P=P, n_out=n_out, tol=tol, svd_tol=svd_tol,
+                                     max_rank=max_rank, **kw),
+                   u0=u0, G=G)
+
+
+def pulse_ade(n=256, nu=1e-2, a=1.0, T=1.0, P=8, n_out=33, tol=1e-8, **kw) -> Problem:
+    """Homogeneous pulse problem of Sec. 3.1 (eq. pulseADE): u0 = sin^20(pi x), no source."""
+    x = grid_1d(n)
+    u0 = np.sin(np.pi * x) ** 20
+    return Problem(name=f"pulse_ade_n{n}", op=make_op(n, nu, a),
+                   opts=default_opts(T=T, P=P, n_out=n_out, tol=tol, **kw), u0=u0, G=None)
+
+
+def travelling_pulses(n=1000, nu=1e-2, a=1.0, T=1.0, P=2, n_out=201, tol=1e-4,
+                      max_rank=2, **kw) -> Problem:
+    """Manufactured travelling pulses of Sec. 3.2 (eq. manusol), u = 1/2 - 1/2 cos(10 pi (x - t));
+    the PDE source is f = u_t + a u_x - nu u_xx evaluated analytically."""
+    x = grid_1d(n)
+    t = out_times(T, n_out)
+    ph = 10 * np.pi * (x[None, :] - t[:, None])
+    ut = -5 * np.pi * np.sin(ph)
+    ux = 5 * np.pi * np.sin(ph)
+    uxx = 50 * np.pi ** 2 * np.cos(ph)
+    G = ut + a * ux - nu * uxx
+    u0 = 0.5 - 0.5 * np.cos(10 * np.pi * x)
+    return Problem(name=f"travelling_pulses_n{n}", op=make_op(n, nu, a),
+                   opts=default_opts(T=T, P=P, n_out=n_out, tol=tol, max_rank=max_rank, **kw),
+                   u0=u0, G=G, meta=dict(exact=lambda tt: 0.5 - 0.5 * np.cos(10 * np.pi * (x - tt))))
+
+
+def burgers_1d(n=65536, nu=5e-3, T=0.5, P=32, n_out=513, tol=1e-8, svd_tol=1e-8,
+               max_rank=16, wr_tol=1e-6, wr_max_iter=200, **kw) -> Problem:
+    """Viscous Burgers u_t + u u_x = nu u_xx (Sec. 4), periodic, u0 = 0.5 + sin(2 pi x), no forcing."""
+    x = grid_1d(n)
+    u0 = 0.5 + np.sin(2 * np.pi * x)
+    return Problem(name=f"burgers_n{n}", op=make_op(n, nu, 0.0),
+                   opts=default_opts(T=T, P=P, n_out=n_out, tol=tol, svd_tol=svd_tol,
+                                     max_rank=max_rank, wr_tol=wr_tol, wr_max_iter=wr_max_iter, **kw),
+                   u0=u0, G=None)
+
+
+def batched_instance(i: int, n_min_log2=12, n_max_log2=18, tol=1e-7) -> Problem:
+    """Instance i of the batched workload: n log-uniform in [2^12, 2^18] rounded to a
+    multiple of 64, nu log-uniform in [1e-4, 1e-1], a uniform in [0.5, 2], a random
+    16-mode Fourier u0, P = 2^U{2..6}, T = 1, n_out = 16 P + 1,
+    g = gamma sin(4 pi x) cos(2 pi t) with gamma ~ U(0, 1)."""
+    rng = np.random.default_rng(SEED_BASE + i)
+    n = int(round(2.0 ** rng.uniform(n_min_log2, n_max_log2) / 64.0)) * 64
+    n = max(n, 64)
+    nu = 10.0 ** rng.uniform(-4, -1)
+    a = rng.uniform(0.5, 2.0)
+    al = rng.uniform(-1, 1, 16)
+    be = rng.uniform(-1, 1, 16)
+    P = 2 ** int(rng.integers(2, 7))
+    gam = rng.uniform(0, 1)
+    x = grid_1d(n)
+    k = np.arange(1, 17)[:, None]
+    u0 = ((al[:, None] * np.cos(2 * np.pi * k * x) + be[:, None] * np.sin(2 * np.pi * k * x)) / k).sum(0)
+    n_out = 16 * P + 1
+    t = out_times(1.0, n_out)
+    G = gam * np.cos(2 * np.pi * t)[:, None] * np.sin(4 * np.pi * x)[None, :]
+    return Problem(name=f"batched_{i}", op=make_op(n, nu, a),
+                   opts=default_opts(T=1.0, P=P, n_out=n_out, tol=tol, svd_tol=1e-10, max_rank=8),
+                   u0=u0, G=G)
+
+
+def random_block(n: int, b: int, seed: int) -> np.ndarray:
+    """Seeded Gaussian n x b block (column-major in the (n, b) numpy sense)."""
+    return np.random.default_rng(SEED_BASE + seed).standard_normal((n, b))
+
+
+def smooth_block(n: int, b: int, seed: int, modes: int = 12) -> np.ndarray:
+    """Seeded smooth periodic n x b block: random combinations of the first `modes`
+    Fourier modes (the kind of vector the Krylov process works on)."""
+    rng = np.random.default_rng(SEED_BASE + 7919 * seed + 1)
+    x = grid_1d(n)
+    out = np.zeros((n, b))
+    for c in range(b):
+        for k in range(modes + 1):
+            out[:, c] += rng.standard_normal() * np.cos(2 * np.pi * k * x) / (1 + k)
+            out[:, c] += rng.standard_normal() * np.sin(2 * np.pi * k * x) / (1 + k)
+    return out

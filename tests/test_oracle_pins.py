@@ -1,0 +1,376 @@
+"""Pins of the FP64 CPU oracle against what the paper and the mathematics fix.
+
+Each test checks one oracle function against something other than itself: a
+closed form, a dense brute-force solution, an invariant, a special case, or a
+number the paper prints.  A plausible mistake (a dropped term, a wrong sign or
+index, a transposed operand) in any oracle step fails at least one of them.
+"""
+import math
+import os
+
+import numpy as np
+import pytest
+import scipy.integrate as sint
+import scipy.linalg as sla
+
+import closed_forms as cf
+import oracle.pebk as ob
+from paper_1509_04567_gb300 import workloads as wl
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+
+
+# ---------------------------------------------------------------- operator (Sec. 3.1)
+@pytest.mark.parametrize("n,a,nu", [(16, 1.0, 1e-2), (33, -0.7, 3e-3), (64, 0.0, 1e-1)])
+def test_operator_fourier_symbol_periodic(n, a, nu):
+    """A e_k = lambda_k e_k for the Fourier modes of the periodic mesh (circulant symbol)."""
+    op = wl.make_op(n, nu, a)
+    A = ob.operator_matrix(op).toarray()
+    lam = cf.circulant_eigs(n, a, nu)
+    x = np.arange(n)
+    for k in range(n):
+        e = np.exp(2j * np.pi * k * x / n)
+        np.testing.assert_allclose(A @ e, lam[k] * e, rtol=0, atol=1e-9 * max(1.0, abs(lam).max()))
+
+
+def test_operator_dirichlet_eigs_and_2d_sum():
+    n, nu = 20, 2e-2
+    op = wl.make_op(n, nu, 0.0, bc=wl.BC_DIRICHLET0)
+    A = ob.operator_matrix(op).toarray()
+    dx = 1.0 / (n + 1)
+    ref = np.sort(-(4 * nu / dx ** 2) * np.sin(np.arange(1, n + 1) * np.pi / (2 * (n + 1))) ** 2)
+    np.testing.assert_allclose(np.sort(np.linalg.eigvalsh(A)), ref, rtol=1e-12)
+    # 2D periodic: product Fourier modes have the sum of the 1D symbols
+    nx, ny, ax, ay = 8, 6, 1.0, 0.5
+    op2 = wl.make_op(nx, nu, ax, dim=2, ny=ny, ay=ay)
+    A2 = ob.operator_matrix(op2).toarray()
+    lx, ly = cf.circulant_eigs(nx, ax, nu), cf.circulant_eigs(ny, ay, nu)
+    ix, iy = np.meshgrid(np.arange(nx), np.arange(ny))
+    for kx, ky in [(1, 0), (2, 3), (7, 5)]:
+        e = (np.exp(2j * np.pi * kx * ix / nx) * np.exp(2j * np.pi * ky * iy / ny)).ravel()
+        np.testing.assert_allclose(A2 @ e, (lx[kx] + ly[ky]) * e, atol=1e-9 * abs(lx).max())
+
+
+# ---------------------------------------------------------------- partition (Sec. 2.2)
+def test_partition_golden():
+    ref = np.loadtxt(os.path.join(GOLDEN, "partition_n101_P8.txt"), dtype=int)
+    assert ob.partition(101, 8) == list(ref)
+    assert ob.partition(1025, 64) == list(range(0, 1025, 16))
+    with pytest.raises(ValueError):
+        ob.partition(5, 8)
+
+
+# ---------------------------------------------------------------- source model (Sec. 2.1)
+def test_compress_source_exact_rank_two():
+    """The small advection-diffusion source A u0 + sin(4 pi x) cos(2 pi t) has rank 2."""
+    pr = wl.adv_diff_1d(n=1024, P=8, n_out=101)
+    A = ob.operator_matrix(pr.op)
+    t = wl.out_times(1.0, 101)[:13]
+    Ghat = (A @ pr.u0)[:, None] + pr.G[:13].T
+    U, C, sig = ob.compress_source(Ghat, 1e-12, 16)
+    assert U.shape[1] == 2
+    assert sig[2] / sig[0] < 1e-14
+    np.testing.assert_allclose(U.T @ U, np.eye(2), atol=1e-14)
+    assert np.linalg.norm(Ghat - U @ C) <= 1e-13 * np.linalg.norm(Ghat)
+    # singular values agree with the square roots of the Gram eigenvalues (independent route)
+    ev = np.sort(np.linalg.eigvalsh(Ghat.T @ Ghat))[::-1]
+    np.testing.assert_allclose(sig[:2], np.sqrt(ev[:2]), rtol=1e-12)
+
+
+def test_compress_source_eckart_young_and_cap():
+    """Truncation error equals sqrt(sum of dropped sigma^2) for a matrix of known SVD."""
+    rng = np.random.default_rng(3)
+    n, s = 300, 9
+    Q1, _ = np.linalg.qr(rng.standard_normal((n, s)))
+    Q2, _ = np.linalg.qr(rng.standard_normal((s, s)))
+    sv = 10.0 ** -np.arange(s, dtype=float)
+    Gm = (Q1 * sv) @ Q2.T
+    U, C, sig = ob.compress_source(Gm, 2e-4, 16)
+    assert U.shape[1] == 4
+    np.testing.assert_allclose(sig, sv, rtol=1e-10, atol=1e-15)
+    np.testing.assert_allclose(np.linalg.norm(Gm - U @ C), np.sqrt(np.sum(sv[4:] ** 2)), rtol=1e-6)
+    U2, _, _ = ob.compress_source(Gm, 0.0, 3)
+    assert U2.shape[1] == 3
+    Uz, Cz, _ = ob.compress_source(np.zeros((n, s)), 1e-12, 16)
+    assert Uz.shape[1] == 0 and Cz.shape == (0, s)
+
+
+def test_theorem1_singular_value_decay():
+    """Thm 1: sigma_{j+1} = sqrt(s-j) O(dT^j): halving dT divides sigma_{j+1}/sigma_1 by ~2^j."""
+    n, s = 400, 17
+    x = np.arange(n) / n
+    def sig_of(dT):
+        t = np.linspace(0.3, 0.3 + dT, s)
+        Gm = (np.sin(2 * np.pi * x[:, None] + 3 * t[None, :]) + np.cos(4 * np.pi * x[:, None] - 5 * t[None, :])
+              + np.exp(-t[None, :]) * np.sin(6 * np.pi * x[:, None]))
+        return ob.compress_source(Gm, 0.0, s)[2]
+    a, b = sig_of(0.05), sig_of(0.025)
+    for j in (1, 2, 3):
+        ratio = (a[j] / a[0]) / (b[j] / b[0])
+        assert 0.6 * 2 ** j < ratio < 1.6 * 2 ** j, (j, ratio)
+
+
+def test_spline_reproduces_cubics_and_not_a_knot():
+    tau = np.linspace(0.0, 0.2, 9) + 0.01 * np.sin(np.arange(9))
+    c = np.array([[0.3, -1.0, 2.5, 4.0], [1.0, 0.0, -3.0, 0.5]])
+    C = np.array([[np.polyval(cc[::-1], tt) for tt in tau] for cc in c])
+    coef = ob.spline_segments(tau, C)
+    for i in range(tau.size - 1):
+        for r in range(2):
+            th = 0.37 * (tau[i + 1] - tau[i])
+            ref = np.polyval(c[r][::-1], tau[i] + th)
+            assert abs(sum(coef[i, l, r] * th ** l for l in range(4)) - ref) < 1e-12
+    # not-a-knot on generic data: third derivative continuous across tau_1 and tau_{s-2}
+    D = np.vstack([np.sin(7 * tau), np.exp(tau)])
+    cf_ = ob.spline_segments(tau, D)
+    np.testing.assert_allclose(cf_[0, 3], cf_[1, 3], rtol=1e-9)
+    np.testing.assert_allclose(cf_[-1, 3], cf_[-2, 3], rtol=1e-9)
+    # interpolation and C2 continuity
+    for i in range(tau.size - 1):
+        h = tau[i + 1] - tau[i]
+        np.testing.assert_allclose(cf_[i, 0], D[:, i], rtol=1e-14)
+        end = sum(cf_[i, l] * h ** l for l in range(4))
+        np.testing.assert_allclose(end, D[:, i + 1], rtol=1e-12)
+        if i < tau.size - 2:
+            d2 = 2 * cf_[i, 2] + 6 * cf_[i, 3] * h
+            np.testing.assert_allclose(d2, 2 * cf_[i + 1, 2], rtol=1e-8, atol=1e-10)
+    # two samples -> straight line, three -> parabola
+    c2 = ob.spline_segments(np.array([0.0, 0.5]), np.array([[1.0, 2.0]]))
+    np.testing.assert_allclose(c2[0, :, 0], [1.0, 2.0, 0.0, 0.0], atol=1e-14)
+    t3 = np.array([0.0, 0.1, 0.3])
+    c3 = ob.spline_segments(t3, np.array([[1.0, 1.0 + 0.1 - 0.01, 1.0 + 0.3 - 0.09]]))
+    np.testing.assert_allclose(c3[0, :, 0], [1.0, 1.0, -1.0, 0.0], atol=1e-12)
+
+
+# ---------------------------------------------------------------- block Krylov (eq. blockKrylovSubspace)
+@pytest.mark.parametrize("krylov", [0, 1])
+def test_block_krylov_orthonormal_and_spans_power_basis(krylov):
+    n, b, steps = 48, 2, 4
+    op = wl.make_op(n, 2e-3, 0.8)
+    A = ob.operator_matrix(op)
+    gamma = 0.01
+    kop = ob.KrylovOperator(op, A, krylov, gamma)
+    U, _ = np.linalg.qr(wl.smooth_block(n, b, 1, modes=6))
+    V, last = U.copy(), U
+    for _ in range(steps - 1):
+        new = ob.block_krylov_step(kop, V, last)
+        V = np.hstack([V, new])
+        last = new
+    assert V.shape[1] == steps * b
+    np.testing.assert_allclose(V.T @ V, np.eye(V.shape[1]), atol=1e-13)
+    Ad = A.toarray()
+    Op = Ad if krylov == 0 else np.linalg.inv(np.eye(n) - gamma * Ad)
+    blocks, X = [U], U
+    for _ in range(steps - 1):
+        X = Op @ X
+        blocks.append(X / np.linalg.norm(X))
+    Pw, _ = np.linalg.qr(np.hstack(blocks))
+    cosines = sla.svdvals(Pw.T @ V)
+    np.testing.assert_allclose(cosines, 1.0, atol=1e-9)
+
+
+def test_block_krylov_deflation():
+    """An invariant direction in the start block deflates instead of being normalised."""
+    n = 64
+    op = wl.make_op(n, 1e-2, 1.0)
+    A = ob.operator_matrix(op)
+    x = np.arange(n) / n
+    U, _ = np.linalg.qr(np.column_stack([np.cos(2 * np.pi * x), np.sin(2 * np.pi * x)]))
+    kop = ob.KrylovOperator(op, A, 1, 0.01)
+    new = ob.block_krylov_step(kop, U, U)
+    assert new.shape[1] == 0  # span{cos, sin} is invariant under the circulant A
+
+
+# ---------------------------------------------------------------- projected problem
+def test_projected_source_window_vs_ode_integrator():
+    rng = np.random.default_rng(5)
+    K, m = 6, 2
+    H = rng.standard_normal((K, K)) - 3 * np.eye(K)
+    B = rng.standard_normal((K, m))
+    tau = np.linspace(0, 0.4, 6)
+    C = rng.standard_normal((m, tau.size))
+    coef = ob.spline_segments(tau, C)
+    Y = ob.projected_source_window(H, B, tau, coef)
+    def p(t):
+        i = min(int(np.searchsorted(tau, t, side="right")) - 1, tau.size - 2)
+        th = t - tau[i]
+        return sum(coef[i, l] * th ** l for l in range(4))
+    sol = sint.solve_ivp(lambda t, y: H @ y + B @ p(t), (0, 0.4), np.zeros(K), t_eval=tau,
+                         method="DOP853", rtol=1e-13, atol=1e-15, max_step=0.005)
+    np.testing.assert_allclose(Y, sol.y.T, atol=1e-11)
+
+
+def test_projected_homogeneous_matches_eigendecomposition():
+    rng = np.random.default_rng(6)
+    K = 5
+    S = rng.standard_normal((K, K))
+    d = -np.arange(1, K + 1, dtype=float)
+    H = S @ np.diag(d) @ np.linalg.inv(S)
+    tau = np.array([0.0, 0.1, 0.7])
+    Y = ob.projected_homogeneous(H, 2.0, tau)
+    e1 = np.zeros(K); e1[0] = 2.0
+    for i, t in enumerate(tau):
+        np.testing.assert_allclose(Y[i], S @ (np.exp(d * t) * np.linalg.solve(S, e1)), atol=1e-12)
+
+
+def test_dense_reference_expm_vs_longdouble_taylor():
+    """The dense brute-force reference's expm agrees with a long-double Taylor series."""
+    n, m = 12, 2
+    A = ob.operator_matrix(wl.make_op(n, 1e-2, 1.0, bc=wl.BC_DIRICHLET0)).toarray()
+    h = 0.05
+    M = np.zeros((n + 4 * m, n + 4 * m))
+    M[:n, :n] = h * A
+    M[:n, n:n + m] = h * wl.random_block(n, m, 2)
+    for l in range(3):
+        M[n + l * m:n + (l + 1) * m, n + (l + 1) * m:n + (l + 2) * m] = np.eye(m)
+    np.testing.assert_allclose(sla.expm(M), cf.taylor_expm_longdouble(M).astype(float), atol=1e-13)
+
+
+# ---------------------------------------------------------------- whole method (Sec. 2.2, Fig. 3)
+def test_oracle_matches_circulant_closed_form_small_case():
+    """P1: the oracle's PEBK equals the exact semi-discrete solution with the same source model."""
+    pr = wl.adv_diff_1d(n=1024, P=8, n_out=101, tol=1e-12, restart_len=30)
+    Y, rep = ob.solve_linear(pr.op, pr.opts, pr.u0, pr.G)
+    assert all(rep["conv_nh"]) and all(all(c) for c in rep["conv_hom"])
+    t, wins = cf.fourier_windows_from_oracle_model(pr.op, pr.opts, pr.u0, pr.G, ob.compress_source,
+                                                   ob.spline_segments, ob.partition)
+    Yx = cf.exact_piecewise_cubic(cf.circulant_eigs(pr.n, 1.0, 1e-2), pr.u0, t, wins)
+    err = np.max(np.linalg.norm(Y - Yx, axis=1) / np.linalg.norm(Yx, axis=1))
+    assert err < 2e-11, err
+
+
+@pytest.mark.parametrize("krylov", [0, 1])
+def test_oracle_matches_dense_bruteforce_dirichlet(krylov):
+    """P2: n <= 64, homogeneous Dirichlet, both Krylov operators, vs the full augmented expm."""
+    n = 40
+    op = wl.make_op(n, 1e-2, 0.5, bc=wl.BC_DIRICHLET0)
+    x = wl.grid_1d(n, bc=wl.BC_DIRICHLET0)
+    u0 = np.sin(np.pi * x) * (1 + x)
+    t = wl.out_times(0.5, 17)
+    G = np.cos(3 * t)[:, None] * (x * (1 - x))[None, :] + t[:, None] ** 2 * np.sin(2 * np.pi * x)[None, :]
+    opts = wl.default_opts(T=0.5, P=4, n_out=17, tol=1e-13, krylov=krylov, restart_len=40)
+    Y, rep = ob.solve_linear(op, opts, u0, G)
+    tt, wins = cf.fourier_windows_from_oracle_model(op, opts, u0, G, ob.compress_source,
+                                                    ob.spline_segments, ob.partition)
+    Yx = cf.dense_exact(ob.operator_matrix(op).toarray(), u0, tt, wins)
+    err = np.max(np.linalg.norm(Y - Yx, axis=1) / np.linalg.norm(Yx, axis=1))
+    assert err < 1e-10, err
+
+
+def test_superposition_partition_invariance():
+    """P3: with a source exactly cubic in time (so every partition models it exactly) the
+    sum of P subsolutions equals the single-interval solve, and parts add up."""
+    n = 128
+    x = wl.grid_1d(n)
+    op = wl.make_op(n, 5e-3, 1.0)
+    u0 = np.cos(2 * np.pi * x) + 0.3 * np.sin(6 * np.pi * x)
+    t = wl.out_times(0.4, 33)
+    G = (1 + t - 2 * t ** 3)[:, None] * np.sin(4 * np.pi * x)[None, :] + (t ** 2)[:, None] * np.cos(8 * np.pi * x)[None, :]
+    res = []
+    for P in (1, 4):
+        opts = wl.default_opts(T=0.4, P=P, n_out=33, tol=1e-13, restart_len=40)
+        Y, rep, parts = ob.solve_linear(op, opts, u0, G, return_parts=True)
+        np.testing.assert_allclose(sum(parts.values()) + u0, Y, atol=1e-13)
+        res.append(Y)
+    np.testing.assert_allclose(res[0], res[1], atol=1e-10 * np.abs(res[0]).max())
+
+
+def test_single_mode_homogeneous_closed_form():
+    """P6: g = 0 and u0 a Fourier mode: u(t) = Re(exp(lambda_k t) e^{2 pi i k x})."""
+    n, k = 256, 3
+    x = wl.grid_1d(n)
+    op = wl.make_op(n, 1e-2, 1.0)
+    u0 = np.cos(2 * np.pi * k * x)
+    opts = wl.default_opts(T=1.0, P=8, n_out=17, tol=1e-13, restart_len=30)
+    Y, _ = ob.solve_linear(op, opts, u0, None)
+    lam = cf.circulant_eigs(n, 1.0, 1e-2)[k]
+    for i, tt in enumerate(wl.out_times(1.0, 17)):
+        np.testing.assert_allclose(Y[i], np.real(np.exp(lam * tt) * np.exp(2j * np.pi * k * x)), atol=1e-11)
+
+
+def test_skew_symmetric_norm_preservation():
+    """P6: nu = 0 makes A skew-symmetric, so ||u(t)|| = ||u0|| for g = 0."""
+    n = 200
+    x = wl.grid_1d(n)
+    u0 = np.exp(-50 * (x - 0.5) ** 2)
+    opts = wl.default_opts(T=0.5, P=4, n_out=9, tol=1e-12, restart_len=40)
+    Y, _ = ob.solve_linear(wl.make_op(n, 0.0, 1.0), opts, u0, None)
+    np.testing.assert_allclose(np.linalg.norm(Y, axis=1), np.linalg.norm(u0), rtol=1e-9)
+
+
+def test_constant_source_phi1_closed_form():
+    """P6: u0 = 0 and a constant source c: u(t) = t phi_1(tA) c, per Fourier mode."""
+    n = 128
+    x = wl.grid_1d(n)
+    c = np.exp(np.sin(2 * np.pi * x))
+    t = wl.out_times(0.5, 9)
+    G = np.tile(c, (9, 1))
+    opts = wl.default_opts(T=0.5, P=4, n_out=9, tol=1e-13, restart_len=40)
+    Y, _ = ob.solve_linear(wl.make_op(n, 1e-2, 1.0), opts, np.zeros(n), G)
+    lam = cf.circulant_eigs(n, 1.0, 1e-2)
+    ch = np.fft.fft(c)
+    for i, tt in enumerate(t):
+        ref = np.real(np.fft.ifft(tt * cf.phi_functions(lam * tt, 1)[1] * ch))
+        np.testing.assert_allclose(Y[i], ref, atol=1e-10 * np.abs(ref).max() + 1e-14)
+
+
+def test_pulse_problem_second_order_in_dx():
+    """P8: Sec. 3.1 pulse problem -- error at t = 1 vs the Fourier series is O(dx^2)."""
+    errs = []
+    for n in (64, 128, 256):
+        pr = wl.pulse_ade(n=n, nu=1e-2, a=1.0, T=1.0, P=8, n_out=9, tol=1e-10)
+        Y, _ = ob.solve_linear(pr.op, pr.opts, pr.u0, None)
+        ex = cf.pulse_series(wl.grid_1d(n), 1.0, 1.0, 1e-2)
+        errs.append(np.linalg.norm(Y[-1] - ex) / np.linalg.norm(ex))
+    r1, r2 = errs[0] / errs[1], errs[1] / errs[2]
+    assert 3.5 < r1 < 4.5 and 3.5 < r2 < 4.5, errs
+
+
+def test_table1_serial_error_golden():
+    """P8: the paper's Table 1 PEBK serial error 3.05e-4 (n = 1000, tol 1e-4, m = 2)."""
+    ref = np.loadtxt(os.path.join(GOLDEN, "table1_pebk_serial_error.txt"))
+    pr = wl.travelling_pulses(n=1000, T=1.0, P=2, n_out=201, tol=1e-4)
+    Y, rep = ob.solve_linear(pr.op, pr.opts, pr.u0, pr.G)
+    assert rep["m"] == [2, 2]
+    ex = pr.meta["exact"](1.0)
+    err = np.linalg.norm(Y[-1] - ex) / np.linalg.norm(ex)
+    assert abs(err - ref[0, 1]) < 0.03 * ref[0, 1], err
+
+
+# ---------------------------------------------------------------- Burgers by waveform relaxation (Sec. 2.3-2.4)
+def test_burgers_source_forms():
+    n = 64
+    op = wl.make_op(n, 1e-2, 0.0)
+    x = wl.grid_1d(n)
+    u = 0.5 + np.sin(2 * np.pi * x)
+    dx = 1.0 / n
+    g0 = ob.burgers_source(op, u, 0)
+    g1 = ob.burgers_source(op, u, 1)
+    i = 10
+    assert abs(g0[i] + (u[i + 1] ** 2 - u[i - 1] ** 2) / (4 * dx)) < 1e-12
+    assert abs(g1[i] + u[i] * (u[i + 1] - u[i - 1]) / (2 * dx)) < 1e-12
+    assert abs(g0.sum()) < 1e-10  # conservative form: discrete mean is conserved
+    # both approximate -u u_x to second order
+    ex = -u * 2 * np.pi * np.cos(2 * np.pi * x)
+    assert np.max(np.abs(g0 - ex)) < 0.05 and np.max(np.abs(g1 - ex)) < 0.05
+
+
+def test_burgers_wr_converges_to_fine_implicit_reference_and_conserves_mean():
+    """P7: the WR fixed point agrees with a tight-tolerance ODE integration of the same
+    semi-discrete Burgers system to the level of the cubic source model, and the discrete
+    mean is conserved (conservative form)."""
+    n = 64
+    op = wl.make_op(n, 5e-2, 0.0)
+    x = wl.grid_1d(n)
+    u0 = 0.5 + np.sin(2 * np.pi * x)
+    opts = wl.default_opts(T=0.1, P=4, n_out=41, tol=1e-13, svd_tol=1e-13, max_rank=16,
+                           wr_tol=1e-10, wr_max_iter=60, restart_len=40)
+    U, rep = ob.solve_burgers(op, opts, u0)
+    assert rep["converged"], rep["deltas"][-3:]
+    A = ob.operator_matrix(op)
+    f = lambda t, u: A @ u + ob.burgers_source(op, u, 0)
+    t = wl.out_times(0.1, 41)
+    sol = sint.solve_ivp(f, (0, 0.1), u0, t_eval=t, method="Radau", rtol=1e-12, atol=1e-13)
+    err = np.max(np.abs(U - sol.y.T))
+    assert err < 2e-6, err
+    np.testing.assert_allclose(U.mean(axis=1), u0.mean(), atol=1e-10)
