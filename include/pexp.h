@@ -1,0 +1,197 @@
+/*
+ * pexp.h -- C ABI of the GB300 Paraexp exponential block Krylov (PEBK) library.
+ *
+ * Method: G.L. Kooij, M.A. Botchev, B.J. Geurts, "A block Krylov subspace
+ * implementation of the time-parallel Paraexp method and its extension for
+ * nonlinear partial differential equations", arXiv:1509.04567.
+ *
+ * The library solves the semi-discrete linear initial value problem
+ *     u'(t) = A u(t) + g(t),  u(0) = u0,  t in [0, T]                 (Sec. 2.1, eq. ivp2)
+ * for A the second-order central-difference advection-diffusion operator
+ * (Sec. 3.1), by the time-parallel Paraexp decomposition (Sec. 2.2, Fig. 3):
+ * shift by u0 (eq. linivp_shift), split the source over P subintervals
+ * (eq. piecewiseSource_linivp), compress each subinterval's source samples by a
+ * truncated thin SVD into g ~ U p(t) (eq. svd_appr), integrate every subproblem
+ * (eq. linivpSubproblem) with an exponential block Krylov method
+ * (eq. blockKrylovSubspace) and sum the subsolutions (eq. superposition).
+ * The viscous Burgers equation is solved by waveform relaxation around the same
+ * linear solver (Sec. 2.3-2.4, eq. ivp3, Fig. 5).
+ *
+ * Conventions for every entry point:
+ *   - Return value: PEXP_OK (0) or a negative status code (below).  No C++
+ *     exception crosses this boundary.  pexp_status_string() names a code.
+ *   - Pointers named *_dev are CUDA device pointers owned by the caller; the
+ *     library reads/writes them in stream order on the context's stream and
+ *     never frees them.  Pointers named *_host are host pointers (pinned memory
+ *     gives the fastest copies); the call returns after the results are in them.
+ *   - A state vector is n contiguous values, n = nx (1D) or nx*ny (2D, unknown
+ *     (ix, iy) at index iy*nx + ix).  A time series of states (sources G,
+ *     solutions Y) is n_out consecutive vectors: element (i, k) -- value k at
+ *     output time t_i -- is at offset i*n + k ("time-major").
+ *   - Output times are uniform: t_i = i*T/(n_out-1), i = 0..n_out-1.  Subinterval
+ *     boundaries snap to this grid: T_j = t_{floor(j*(n_out-1)/P)}.
+ *   - dtype arguments are PEXP_F64 (double) or PEXP_F32 (float).
+ *   - A call is synchronous with respect to the host unless stated otherwise:
+ *     it returns when its device work has completed (the Krylov loop reads
+ *     convergence flags back to the host).
+ *   - Errors: invalid sizes/options -> PEXP_ERR_INVALID_ARG with nothing
+ *     written; CUDA runtime failure -> PEXP_ERR_CUDA; workspace allocation
+ *     failure -> PEXP_ERR_OOM.
+ */
+#ifndef PEXP_H
+#define PEXP_H
+
+#include <stdint.h>
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---------------------------------------------------------------- status codes */
+#define PEXP_OK                     0
+#define PEXP_ERR_INVALID_ARG       -1
+#define PEXP_ERR_OOM               -2
+#define PEXP_ERR_CUDA              -3
+#define PEXP_ERR_BREAKDOWN         -4  /* Krylov block lost all directions unexpectedly */
+#define PEXP_ERR_NOT_CONVERGED     -5  /* a subproblem missed tol within the step budget; output written */
+#define PEXP_ERR_WR_NOT_CONVERGED  -6  /* waveform relaxation hit wr_max_iter; last iterate written */
+#define PEXP_ERR_TIMEOUT           -7  /* a bounded device-side wait expired */
+#define PEXP_ERR_UNSUPPORTED       -8  /* valid request not implemented for this operator/precision */
+
+/* ---------------------------------------------------------------- enumerations */
+#define PEXP_BC_PERIODIC   0
+#define PEXP_BC_DIRICHLET0 1
+
+#define PEXP_KRYLOV_POLY 0   /* polynomial block Krylov space span{U, AU, A^2U, ...} (eq. blockKrylovSubspace) */
+#define PEXP_KRYLOV_SAI  1   /* shift-and-invert space of (I - gamma A)^{-1} (Sec. 2.1, cited acceleration) */
+
+#define PEXP_FP64  0         /* every n-length array and all arithmetic in FP64 */
+#define PEXP_MIXED 1         /* n-length Krylov data in FP32 with FP32 arithmetic; small matrices in FP64 */
+
+#define PEXP_F64 0
+#define PEXP_F32 1
+
+/* ---------------------------------------------------------------- descriptors */
+/* The operator A of eq. ivp2: second-order central differences of
+ * -a u_x + nu u_xx (Sec. 3.1), per dimension; 2D is the sum A_x + A_y.
+ *   (A u)_i = nu (u_{i-1} - 2u_i + u_{i+1})/dx^2 - a (u_{i+1} - u_{i-1})/(2 dx)
+ * dx = L/n (periodic) or L/(n+1) (homogeneous Dirichlet, interior points). */
+typedef struct {
+    int     dim;        /* 1 or 2 */
+    int64_t nx, ny;     /* mesh points per dimension (ny ignored for dim 1) */
+    int     bc;         /* PEXP_BC_* */
+    double  ax, ay;     /* advection velocities */
+    double  nu;         /* diffusivity */
+    double  Lx, Ly;     /* domain lengths */
+} pexp_operator;
+
+/* Solver options.  Defaults: pexp_default_options(). */
+typedef struct {
+    double T;            /* final time */
+    int    P;            /* number of subintervals, 1 <= P <= n_out-1 (Sec. 2.2) */
+    int    n_out;        /* number of output (= source sample) times, >= 2 */
+    double tol;          /* relative tolerance of each EBK subproblem (Sec. 3, "tol") */
+    double svd_tol;      /* keep singular values sigma_i > svd_tol*sigma_1 (Sec. 2.1) */
+    int    max_rank;     /* cap on the retained rank m = block width, <= PEXP_MAX_RANK */
+    int    restart_len;  /* block steps per Krylov cycle (Sec. 3: 20) */
+    int    max_restarts; /* extra cycles; the step budget is restart_len*(max_restarts+1) */
+    int    krylov;       /* PEXP_KRYLOV_* */
+    double sai_gamma;    /* SAI pole gamma = sai_gamma * T / P (nominal subinterval length) */
+    int    precision;    /* PEXP_FP64 or PEXP_MIXED */
+    int    wr_max_iter;  /* waveform relaxation iteration limit (Fig. 5, K) */
+    double wr_tol;       /* stop when max_i||u_{k+1}(t_i)-u_k(t_i)|| <= wr_tol*max_i||u_{k+1}(t_i)|| */
+    int    burgers_form; /* 0: -(u_{i+1}^2-u_{i-1}^2)/(4dx);  1: -u_i(u_{i+1}-u_{i-1})/(2dx) */
+} pexp_options;
+
+#define PEXP_MAX_RANK   16    /* largest block width */
+#define PEXP_MAX_STEPS  40    /* largest Krylov step budget restart_len*(max_restarts+1) */
+#define PEXP_MAX_SAMPLES 64   /* largest number of samples in one subinterval */
+
+/* Per-call report (host memory, optional). */
+typedef struct {
+    int    status;
+    int    n_sub;             /* P */
+    int    rank_max;          /* max_j m_j (retained source rank) */
+    int    rank_min;
+    int    k_nh_max;          /* max block steps of the source (nonhomogeneous) parts */
+    int    k_hom_max;         /* max steps of the homogeneous continuation windows */
+    int    k_hom_sum;         /* total homogeneous steps */
+    int    not_converged;     /* number of Krylov solves that missed tol */
+    double est_max;           /* largest final error estimate (relative) */
+    double sigma_ratio_max;   /* max_j sigma_{m_j+1}/sigma_1 (first dropped singular value) */
+    int    wr_iters;          /* waveform relaxation iterations made */
+    double wr_delta;          /* last relative WR update */
+    double time_ms;           /* device time of the solve (CUDA events) */
+    double t_source_ms;       /* phase times (CUDA events): source compression */
+    double t_krylov_ms;       /*   nonhomogeneous block Krylov solves (all subintervals) */
+    double t_hom_ms;          /*   homogeneous continuation chain */
+    double t_recon_ms;        /*   reconstruction of all output times */
+    double bytes_alg;         /* algorithmic HBM bytes: each array counted once per pass the method needs */
+    int    launches;          /* kernels launched by the call */
+} pexp_report;
+
+typedef struct pexp_ctx pexp_ctx;
+
+/* ---------------------------------------------------------------- context */
+/* Create a context on CUDA device `device` using `cuda_stream` (a cudaStream_t,
+ * NULL = the legacy default stream; borrowed, not destroyed).  The context owns a
+ * device workspace that grows on demand and is freed by pexp_destroy. */
+int pexp_create(pexp_ctx** out, int device, void* cuda_stream);
+int pexp_destroy(pexp_ctx* ctx);
+int pexp_set_stream(pexp_ctx* ctx, void* cuda_stream);
+void pexp_default_options(pexp_options* opts);
+const char* pexp_status_string(int status);
+
+/* ---------------------------------------------------------------- solvers */
+/* Paraexp-EBK linear solve (Sec. 2.2, Fig. 3).
+ *   y0_dev: n values (dtype y_dtype).  G_dev: n_out*n source samples g(t_i)
+ *   (time-major, dtype g_dtype) or NULL for g = 0.  Y_dev: n_out*n outputs
+ *   u(t_i) (time-major, dtype y_dtype); must not overlap G_dev or y0_dev.
+ * Returns PEXP_ERR_NOT_CONVERGED (outputs still written) when a Krylov solve missed tol. */
+int pexp_solve_linear(pexp_ctx* ctx, const pexp_operator* op, const pexp_options* opts,
+                      const void* y0_dev, const void* G_dev, int g_dtype,
+                      void* Y_dev, int y_dtype, pexp_report* rep);
+
+/* Same solve with HOST buffers: copies y0 and G in, solves, copies Y out. */
+int pexp_solve_linear_host(pexp_ctx* ctx, const pexp_operator* op, const pexp_options* opts,
+                           const void* y0_host, const void* G_host, int g_dtype,
+                           void* Y_host, int y_dtype, pexp_report* rep);
+
+/* Viscous Burgers u_t + u u_x = nu u_xx + f by waveform relaxation (Sec. 2.3-2.4, Fig. 5),
+ * plain Picard form (eq. ivp3): A = nu D2 from `op` (its advection velocity must be 0).
+ *   u0_dev: n values.  forcing_dev: optional n_out*n samples f(t_i) or NULL.
+ *   init_dev: optional first iterate (n_out*n) or NULL for u0 at every time.
+ *   U_dev: n_out*n output, the last iterate (also on PEXP_ERR_WR_NOT_CONVERGED).
+ * All arrays have dtype `dtype`. */
+int pexp_solve_burgers(pexp_ctx* ctx, const pexp_operator* op, const pexp_options* opts,
+                       const void* u0_dev, const void* forcing_dev, const void* init_dev,
+                       void* U_dev, int dtype, pexp_report* rep);
+
+/* ---------------------------------------------------------------- kernel-level entry points
+ * Single steps of the hot path, exposed for testing and composition.  All
+ * pointers are device pointers in FP64 unless a dtype is given. */
+
+/* Y = A X (transpose != 0: Y = A^T X) for `nvec` vectors of length n stored at
+ * X + c*n, Y + c*n (Sec. 3.1 stencil).  dtype PEXP_F64 or PEXP_F32. */
+int pexp_apply_operator(pexp_ctx* ctx, const pexp_operator* op, const void* X_dev, void* Y_dev,
+                        int nvec, int dtype, int transpose);
+
+/* Y = (I - gamma A)^{-1} X for `nvec` vectors (shift-and-invert operator of Sec. 2.1),
+ * 1D periodic operators only (else PEXP_ERR_UNSUPPORTED). */
+int pexp_sai_solve(pexp_ctx* ctx, const pexp_operator* op, double gamma, const void* X_dev,
+                   void* Y_dev, int nvec, int dtype);
+
+/* E_b = exp(M_b) for `batch` dense row-major N x N FP64 matrices, M and E
+ * consecutive in memory (Pade-13 scaling and squaring, Higham 2005). N <= 128. */
+int pexp_small_expm(pexp_ctx* ctx, const double* M_dev, double* E_dev, int N, int batch);
+
+/* g(t_i) = -u u_x at every row of U (n_out rows of n), conservative (form 0) or
+ * advective (form 1) central differences (Sec. 4; reading in the design doc). */
+int pexp_burgers_source(pexp_ctx* ctx, const pexp_operator* op, const void* U_dev, void* G_dev,
+                        int n_rows, int dtype, int form);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* PEXP_H */

@@ -14,8 +14,9 @@ Readings of points the paper leaves open (each is listed in the design doc):
   * subinterval boundaries snap to the output grid: T_j = t_floor(j (n_out-1) / P);
   * the Krylov space is either the polynomial block Krylov space of eq.
     blockKrylovSubspace (krylov=0) or its shift-and-invert form (krylov=1,
-    Sec. 2.1, the acceleration the paper cites) with pole gamma = sai_gamma * window;
-    in both cases the projected matrix is the Galerkin matrix V^T A V;
+    Sec. 2.1, the acceleration the paper cites);
+    in both cases the projected matrix is the Galerkin matrix V^T A V; the pole is
+    gamma = sai_gamma * T / P for every window;
   * a subproblem is converged when the change of the projected solution between
     two successive block steps, max over the window's sample times, is at most
     tol * max(||u0||, max ||v(t_i)||);
@@ -353,13 +354,11 @@ def solve_linear(op: dict, opts: dict, u0: np.ndarray, G: np.ndarray | None,
     Y = np.zeros((n_out, n)) if subintervals is not None else np.tile(u0, (n_out, 1))
     rep = dict(m=[], sigma_ratio=[], k_nh=[], est_nh=[], conv_nh=[], k_hom=[], conv_hom=[], boundaries=idx)
     parts = {}
-    kops = {}
+    # one shift-and-invert pole for all windows: gamma = sai_gamma * T / P
+    kop_all = KrylovOperator(op, A, opts["krylov"], opts.get("sai_gamma", 0.1) * T / P)
 
     def kop_for(width):
-        key = round(width, 15)
-        if key not in kops:
-            kops[key] = KrylovOperator(op, A, opts["krylov"], opts.get("sai_gamma", 0.1) * width)
-        return kops[key]
+        return kop_all
 
     for j in js:
         i0, i1 = idx[j - 1], idx[j]

@@ -1,0 +1,118 @@
+// Shared declarations of the PEBK CUDA library (sm_103a).
+//
+// Translation units:
+//   tall.cu   -- kernels over n-length data: central-difference stencil,
+//                shift-and-invert solve, batched tall-skinny products,
+//                reconstruction, Burgers source, conversions;
+//   small.cu  -- per-subinterval kernels on small FP64 matrices: source SVD by
+//                Jacobi, block orthonormalisation (pivoted Cholesky), cubic
+//                coefficient model, Pade exponential, projected time stepping;
+//   solver.cu -- host orchestration and the C ABI of include/pexp.h.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "../../include/pexp.h"
+
+namespace pexp {
+
+constexpr int kNumSM = 152;  // GB300: 2 dies x 76 SMs
+
+// One dimension of the central-difference operator (Sec. 3.1):
+//   (A u)_i += d ((u_{i-1} - u_i) + (u_{i+1} - u_i)) - c (u_{i+1} - u_{i-1}),
+// d = nu/dx^2, c = a/(2 dx).  The difference form keeps the rounding error
+// relative to the (small) result for smooth data.
+struct Dim1 {
+    int64_t n;       // points in this dimension
+    int64_t stride;  // element stride between neighbours in this dimension
+    double d, c;
+    int periodic;
+};
+
+struct OpDesc {
+    int dim;
+    int64_t n;   // total unknowns
+    Dim1 x, y;
+};
+
+// One task of a batched tall-skinny product over rows 0..n-1.
+//   TN:  out (p x q, column-major, ld p) = X'^T Y'
+//   NN:  Z (n x q) = alpha X' Tm + beta Z          (Tm p x q, column-major, ld ldt)
+// X' = X + xs 1^T (xs optional, FP64), Y' = [Y(:, 0:q1) | Y2(:, 0:q-q1)] + ys 1^T.
+// All tall arrays column-major with leading dimensions in elements.
+// NN may run in place (Z == X, p == q <= 16).
+template <typename T>
+struct TsTask {
+    const T* X;
+    const T* Y;
+    const T* Y2;
+    T* Z;
+    const double* Tm;
+    const double* xs;
+    const double* ys;
+    double* out;
+    int64_t ldx, ldy, ldy2, ldz;
+    int p, q, q1, ldt;
+    double alpha, beta;
+};
+
+// Reconstruction task: for output rows r = 0..ns-1 (coefficient rows r0 + r),
+//   Out[(i0 + r) * ldo + k] = u0[k] + sum_a V1[a*ld1 + k] C1[(r0+r)*ldc1 + a]
+//                                   + sum_a V2[a*ld2 + k] C2[(r0+r)*ldc2 + a]
+// with u0 optional; K1 or K2 may be zero.
+template <typename T>
+struct ReconTask {
+    const T* V1; const double* C1; int64_t ld1; int K1, ldc1;
+    const T* V2; const double* C2; int64_t ld2; int K2, ldc2;
+    int r0, ns;
+    int64_t i0;
+};
+
+struct SaiCoef {
+    double alpha, beta, inv_c;   // (I - gamma A) = c (I - alpha S^{-1})(I - beta S)
+    double alpha_n, beta_n;      // alpha^n, beta^n (circular closure)
+};
+
+// ---------------------------------------------------------------- tall.cu
+SaiCoef sai_coefficients(const OpDesc& op, double gamma);
+size_t sai_scratch_doubles(int64_t n, int nvec);
+size_t ts_tn_partial_doubles(int ntasks, int max_pq, int64_t n);
+
+template <typename T>
+void launch_stencil(const OpDesc& op, const T* X, T* Y, int nvec, int transpose, cudaStream_t s);
+template <typename T>
+void launch_stencil_ptrs(const OpDesc& op, const T* const* X, T* const* Y, int nvec, int transpose,
+                         cudaStream_t s);
+template <typename T>
+void launch_burgers_source(const OpDesc& op, const T* U, T* G, int nrows, int form, double inv2dx,
+                           cudaStream_t s);
+template <typename T>
+void launch_sai_solve(const OpDesc& op, const SaiCoef& cf, const T* const* X, T* const* Y, T* const* Ylo, int nvec,
+                      double* scratch, cudaStream_t s);
+template <typename T>
+void launch_ts_tn(const TsTask<T>* tasks_dev, int ntasks, int max_pq, int max_q, int64_t n, double* partial,
+                  cudaStream_t s, int exact = 0);
+template <typename T>
+void launch_ts_nn(const TsTask<T>* tasks_dev, int ntasks, int max_pq, int64_t n, cudaStream_t s);
+template <typename T, typename TO>
+void launch_recon(const ReconTask<T>* tasks_dev, int ntasks, int max_ns, int64_t n, const double* u0,
+                  TO* out, int64_t ldo, int max_c_doubles, cudaStream_t s);
+template <typename TI, typename TO>
+void launch_convert(const TI* x, TO* y, int64_t count, cudaStream_t s);
+// rows of A minus rows of B: partial[row] = ||A_row - B_row||^2, partial[nrows + row] = ||A_row||^2
+template <typename T>
+void launch_row_diff_norms(const T* A, const T* B, int64_t n, int nrows, double* out, cudaStream_t s);
+
+template <typename T>
+void launch_add(T* y, const T* x, int64_t count, cudaStream_t s);
+
+int fail_cuda(cudaError_t e, const char* what, const char* file, int line);
+
+}  // namespace pexp
+
+#define PEXP_CUDA_TRY(expr)                                                                \
+    do {                                                                                   \
+        cudaError_t _e = (expr);                                                           \
+        if (_e != cudaSuccess) return ::pexp::fail_cuda(_e, #expr, __FILE__, __LINE__);    \
+    } while (0)

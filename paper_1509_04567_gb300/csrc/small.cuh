@@ -1,0 +1,54 @@
+// Per-subinterval ("window") small-matrix state and kernels of the PEBK solver.
+#pragma once
+
+#include "common.cuh"
+
+namespace pexp {
+
+// Layout of the FP64 per-window buffer (one slab of `stride` doubles per window)
+// and of the int per-window buffer.  Matrices are column-major.
+struct WinLayout {
+    int s_max;     // samples per window
+    int b_max;     // block width
+    int K_max;     // basis columns = b_max * (kmax + 1)
+    int N_max;     // augmented matrix size = K_max + 4 b_max
+    int64_t stride;
+    int64_t off_gram;  // s_max x s_max     Gram of the source samples
+    int64_t off_zs;    // s_max x b_max     U = Ghat zs
+    int64_t off_C;     // b_max x s_max     coefficient samples (ld b_max)
+    int64_t off_coef;  // (s_max-1) x 4 x b_max cubic coefficients [(r*4+l)*b_max + k]
+    int64_t off_H;     // K_max x K_max     Galerkin matrix V^T A V
+    int64_t off_out1;  // (K_max + b_max) x 3 b_max   projections of step i
+    int64_t off_h2;    // K_max x b_max     second Gram-Schmidt pass
+    int64_t off_gw;    // b_max x b_max     Gram of the new block
+    int64_t off_T;     // b_max x b_max     block scaling
+    int64_t off_Y;     // s_max x K_max     projected solution at the samples, row r at r*K_max
+    int64_t off_Yp;    // s_max x K_max     previous step's projected solution
+    int64_t off_scal;  // 16 scalars
+    int64_t off_scr;   // 9 N_max^2 scratch (augmented matrix, exponential, Pade work)
+    int istride;
+};
+
+// int fields
+enum { WI_B = 0, WI_CONV, WI_STEPS, WI_S, WI_KIND, WI_KEPT, WI_STATUS, WI_K, WI_COUNT = 16 };
+// double scalars at off_scal
+enum { WS_BETA = 0, WS_EST, WS_SCALE, WS_SIGRATIO, WS_H, WS_PRE, WS_COUNT = 16 };
+
+enum { KIND_SOURCE = 0, KIND_HOM = 1 };
+
+WinLayout make_layout(int s_max, int b_max, int kmax);
+
+// Launchers.  `wins` is a device array of window indices (nw entries).
+void launch_source_eig(const WinLayout& L, double* wd, int* wi, const int* wins, int nw, double thr,
+                       int max_rank, cudaStream_t s);
+void launch_start_orth(const WinLayout& L, double* wd, int* wi, const int* wins, int nw, cudaStream_t s);
+void launch_block_orth(const WinLayout& L, double* wd, int* wi, const int* wins, int nw, int pass, int step,
+                       double defl, cudaStream_t s);
+void launch_spline(const WinLayout& L, double* wd, int* wi, const int* wins, int nw, double h, cudaStream_t s);
+void launch_project(const WinLayout& L, double* wd, int* wi, const int* wins, int nw, int step, double h,
+                    double tol, double scale_ref, cudaStream_t s);
+void launch_small_expm_batch(const double* M, double* E, int N, int batch, double* scratch, cudaStream_t s);
+size_t small_expm_scratch_doubles(int N);
+void init_pade_constants();
+
+}  // namespace pexp

@@ -1,0 +1,1055 @@
+// Host orchestration of the Paraexp exponential block Krylov (PEBK) solver and the
+// C ABI of include/pexp.h.
+//
+// Linear solve (Sec. 2.2, Fig. 3), on one GPU:
+//   1. shift by u0: g_hat = A u0 + g (eq. linivp_shift); subinterval j owns the
+//      samples t_{idx_{j-1}} .. t_{idx_j};
+//   2. source compression per subinterval, all subintervals in one batch:
+//      Gram matrix of g_hat samples, Jacobi eigen-decomposition, U = G_hat Z S^{-1},
+//      Cholesky re-orthonormalisation, not-a-knot cubic coefficient model;
+//   3. nonhomogeneous parts of all subproblems in one batch: block Krylov steps
+//      (shift-and-invert solve or stencil, explicit Galerkin projection H = V^T A V,
+//      block classical Gram-Schmidt with re-orthogonalisation, Cholesky QR twice),
+//      exact projected solve at the window's samples, stop on the change between
+//      successive steps;
+//   4. homogeneous parts: by superposition (eq. superposition) the homogeneous
+//      continuations of all earlier subproblems add up, on window m, to
+//      exp((t - T_{m-1}) A) z_{m-1} with z_{m-1} = u_hat(T_{m-1}); one single-vector
+//      Krylov solve per window carries that sum (P - 1 solves instead of P(P-1)/2);
+//   5. reconstruction u(t_i) = u0 + V_nh y_nh(t_i) + V_h y_h(t_i), all windows in one batch.
+#include <math.h>
+#include <stdio.h>
+#include <string.h>
+
+#include <algorithm>
+#include <new>
+#include <vector>
+
+#include "common.cuh"
+#include "small.cuh"
+
+using namespace pexp;
+
+// ---------------------------------------------------------------- context
+struct pexp_ctx {
+    int device = 0;
+    cudaStream_t stream = nullptr;
+    char* ws = nullptr;   // device workspace
+    size_t ws_cap = 0;
+    size_t ws_top = 0;
+    char* stage_h[2] = {nullptr, nullptr};   // pinned task staging
+    char* stage_d[2] = {nullptr, nullptr};
+    size_t stage_cap = 0;
+    cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+    cudaEvent_t evp[5] = {nullptr, nullptr, nullptr, nullptr, nullptr};   // phase boundaries
+    int launches = 0;
+    // host copies for host-pointer solves
+    void* io_d = nullptr;
+    size_t io_cap = 0;
+};
+
+namespace {
+
+constexpr size_t kAlign = 256;
+constexpr size_t kStageBytes = 8u << 20;
+
+struct OomError {};
+struct StatusError {
+    int code;
+};
+
+void* ws_alloc(pexp_ctx* c, size_t bytes) {
+    size_t off = (c->ws_top + kAlign - 1) / kAlign * kAlign;
+    if (off + bytes > c->ws_cap) throw OomError();
+    c->ws_top = off + bytes;
+    return c->ws + off;
+}
+
+// Reserve `need` bytes of workspace up front (grows the buffer between calls).
+int ws_reserve(pexp_ctx* c, size_t need) {
+    if (need <= c->ws_cap) return PEXP_OK;
+    if (c->ws) cudaFree(c->ws);
+    c->ws = nullptr;
+    c->ws_cap = 0;
+    size_t cap = need + need / 8 + (64u << 20);
+    if (cudaMalloc(&c->ws, cap) != cudaSuccess) {
+        cudaGetLastError();
+        if (cudaMalloc(&c->ws, need) != cudaSuccess) {
+            cudaGetLastError();
+            return PEXP_ERR_OOM;
+        }
+        cap = need;
+    }
+    c->ws_cap = cap;
+    return PEXP_OK;
+}
+
+// Task staging: host-side byte buffer copied to the device in one transfer.
+struct Stage {
+    pexp_ctx* c;
+    int half;
+    size_t used = 0;
+    Stage(pexp_ctx* c_, int h) : c(c_), half(h) {}
+    template <typename X>
+    X* put(const X* src, size_t count) {
+        size_t off = (used + 15) / 16 * 16;
+        size_t bytes = sizeof(X) * count;
+        if (off + bytes > c->stage_cap) throw OomError();
+        memcpy(c->stage_h[half] + off, src, bytes);
+        used = off + bytes;
+        return reinterpret_cast<X*>(c->stage_d[half] + off);
+    }
+    void flush() {
+        if (used) cudaMemcpyAsync(c->stage_d[half], c->stage_h[half], used, cudaMemcpyHostToDevice, c->stream);
+    }
+};
+
+void check_launch(pexp_ctx* c) {
+    c->launches++;
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) {
+        fail_cuda(e, "kernel launch", __FILE__, __LINE__);
+        throw StatusError{PEXP_ERR_CUDA};
+    }
+}
+
+void sync(pexp_ctx* c) {
+    cudaError_t e = cudaStreamSynchronize(c->stream);
+    if (e != cudaSuccess) {
+        fail_cuda(e, "cudaStreamSynchronize", __FILE__, __LINE__);
+        throw StatusError{PEXP_ERR_CUDA};
+    }
+}
+
+void d2h(pexp_ctx* c, void* dst, const void* src, size_t bytes) {
+    cudaError_t e = cudaMemcpyAsync(dst, src, bytes, cudaMemcpyDeviceToHost, c->stream);
+    if (e != cudaSuccess) {
+        fail_cuda(e, "cudaMemcpyAsync D2H", __FILE__, __LINE__);
+        throw StatusError{PEXP_ERR_CUDA};
+    }
+    sync(c);
+}
+
+OpDesc make_opdesc(const pexp_operator& op) {
+    OpDesc d;
+    memset(&d, 0, sizeof(d));
+    d.dim = op.dim;
+    auto dim1 = [&](int64_t n, double a, double L, int64_t stride) {
+        Dim1 r;
+        const double dx = (op.bc == PEXP_BC_PERIODIC) ? L / (double)n : L / (double)(n + 1);
+        r.n = n;
+        r.stride = stride;
+        r.d = op.nu / (dx * dx);
+        r.c = a / (2.0 * dx);
+        r.periodic = op.bc == PEXP_BC_PERIODIC;
+        return r;
+    };
+    d.x = dim1(op.nx, op.ax, op.Lx, 1);
+    if (op.dim == 2) {
+        d.y = dim1(op.ny, op.ay, op.Ly, op.nx);
+        d.n = op.nx * op.ny;
+    } else {
+        d.n = op.nx;
+    }
+    return d;
+}
+
+int validate(const pexp_operator* op, const pexp_options* o) {
+    if (!op || !o) return PEXP_ERR_INVALID_ARG;
+    if (op->dim != 1 && op->dim != 2) return PEXP_ERR_INVALID_ARG;
+    if (op->nx < 3 || (op->dim == 2 && op->ny < 3)) return PEXP_ERR_INVALID_ARG;
+    if (op->bc != PEXP_BC_PERIODIC && op->bc != PEXP_BC_DIRICHLET0) return PEXP_ERR_INVALID_ARG;
+    if (!(op->nu >= 0.0) || !(op->Lx > 0.0) || (op->dim == 2 && !(op->Ly > 0.0))) return PEXP_ERR_INVALID_ARG;
+    if (o->n_out < 2 || o->P < 1 || o->P > o->n_out - 1) return PEXP_ERR_INVALID_ARG;
+    if (!(o->T > 0.0) || !(o->tol > 0.0) || !(o->svd_tol >= 0.0)) return PEXP_ERR_INVALID_ARG;
+    if (o->max_rank < 1 || o->restart_len < 1 || o->max_restarts < 0) return PEXP_ERR_INVALID_ARG;
+    if (o->restart_len * (o->max_restarts + 1) > PEXP_MAX_STEPS) return PEXP_ERR_INVALID_ARG;
+    if (o->krylov != PEXP_KRYLOV_POLY && o->krylov != PEXP_KRYLOV_SAI) return PEXP_ERR_INVALID_ARG;
+    if (o->precision != PEXP_FP64 && o->precision != PEXP_MIXED) return PEXP_ERR_INVALID_ARG;
+    if (o->krylov == PEXP_KRYLOV_SAI && !(o->sai_gamma > 0.0)) return PEXP_ERR_INVALID_ARG;
+    // largest subinterval sample count
+    const int P = o->P, nt = o->n_out;
+    int smax = 0;
+    for (int j = 1; j <= P; ++j) {
+        const int i0 = (int)(((int64_t)(j - 1) * (nt - 1)) / P), i1 = (int)(((int64_t)j * (nt - 1)) / P);
+        smax = std::max(smax, i1 - i0 + 1);
+    }
+    if (smax > PEXP_MAX_SAMPLES) return PEXP_ERR_INVALID_ARG;
+    if (o->krylov == PEXP_KRYLOV_SAI && (op->dim != 1 || op->bc != PEXP_BC_PERIODIC)) return PEXP_ERR_UNSUPPORTED;
+    return PEXP_OK;
+}
+
+// ---------------------------------------------------------------- Krylov driver
+template <typename T>
+struct Win {
+    int w;        // window index in the small-state arrays
+    T* V;         // basis, n x K_max column-major (ld n)
+    T* S;         // scratch n x 2b (A V_i, A^T V_i)
+    int b;        // block width
+};
+
+template <typename T>
+struct Solver {
+    pexp_ctx* c;
+    cudaStream_t st;
+    OpDesc od;
+    int64_t n;
+    const pexp_options* o;
+    WinLayout L;
+    double* wd;
+    int* wi;
+    double* partial;
+    double* sai_scr;
+    SaiCoef sai;
+    double h;
+    int kmax;
+    double defl;
+    double scale_ref;
+    std::vector<int> wi_host;
+
+    T* slot(const Win<T>& W, int blk) const { return W.V + (int64_t)blk * W.b * n; }
+    double* D(int w) const { return wd + (int64_t)w * L.stride; }
+
+    // Runs block Krylov steps for the windows `ws` (each with its start block already
+    // orthonormal in V block 0).  Returns the number of windows that missed tol.
+    int run(std::vector<Win<T>> ws, int kind, int* max_steps) {
+        int notconv = 0;
+        *max_steps = 0;
+        std::vector<Win<T>> act = ws;
+        for (int step = 1; step <= kmax && !act.empty(); ++step) {
+            const int na = (int)act.size();
+            // ---- part A: operator applications, projections, projected solve
+            Stage sa(c, 0);
+            std::vector<const T*> xin;
+            std::vector<T*> yout, yav, yatv;
+            std::vector<const T*> xav;
+            std::vector<TsTask<T>> tn1(na);
+            std::vector<int> wl(na);
+            int max_pq = 0, max_q = 0;
+            for (int a = 0; a < na; ++a) {
+                const Win<T>& W = act[a];
+                T* Vi = slot(W, step - 1);
+                T* Wn = slot(W, step);
+                for (int cc = 0; cc < W.b; ++cc) {
+                    xin.push_back(Vi + (int64_t)cc * n);
+                    yout.push_back(Wn + (int64_t)cc * n);
+                    yav.push_back(W.S + (int64_t)cc * n);
+                    yatv.push_back(W.S + (int64_t)(W.b + cc) * n);
+                }
+                TsTask<T> t;
+                memset(&t, 0, sizeof(t));
+                t.X = W.V;
+                t.ldx = n;
+                t.p = (step + 1) * W.b;
+                t.Y = W.S;
+                t.ldy = n;
+                t.q1 = 2 * W.b;
+                t.Y2 = Wn;
+                t.ldy2 = n;
+                t.q = 3 * W.b;
+                t.out = D(W.w) + L.off_out1;
+                tn1[a] = t;
+                max_pq = std::max(max_pq, t.p * t.q);
+                max_q = std::max(max_q, t.q);
+                wl[a] = W.w;
+            }
+            const int nv = (int)xin.size();
+            const T* const* d_xin = sa.put(xin.data(), nv);
+            T* const* d_yout = sa.put(yout.data(), nv);
+            T* const* d_yav = sa.put(yav.data(), nv);
+            T* const* d_yatv = sa.put(yatv.data(), nv);
+            const TsTask<T>* d_tn1 = sa.put(tn1.data(), na);
+            const int* d_wl = sa.put(wl.data(), na);
+            sa.flush();
+            if (o->krylov == PEXP_KRYLOV_SAI) launch_sai_solve<T>(od, sai, d_xin, d_yout, nv, sai_scr, st);
+            else launch_stencil_ptrs<T>(od, d_xin, d_yout, nv, 0, st);
+            check_launch(c);
+            launch_stencil_ptrs<T>(od, d_xin, d_yav, nv, 0, st);
+            check_launch(c);
+            launch_stencil_ptrs<T>(od, d_xin, d_yatv, nv, 1, st);
+            check_launch(c);
+            launch_ts_tn<T>(d_tn1, na, max_pq, max_q, n, partial, st, 0);
+            check_launch(c);
+            launch_project(L, wd, wi, d_wl, na, step, h, o->tol, scale_ref, st);
+            check_launch(c);
+            // ---- convergence flags
+            d2h(c, wi_host.data(), wi, sizeof(int) * wi_host.size());
+            std::vector<Win<T>> next;
+            for (auto& W : act) {
+                const int* I = &wi_host[(size_t)W.w * L.istride];
+                *max_steps = std::max(*max_steps, I[WI_STEPS]);
+                if (!I[WI_CONV]) next.push_back(W);
+            }
+            if (step == kmax) {
+                notconv += (int)next.size();
+                break;
+            }
+            act.swap(next);
+            if (act.empty()) break;
+            // ---- part B: Gram-Schmidt (two passes) and Cholesky QR (two passes)
+            const int nb = (int)act.size();
+            Stage sb(c, 1);
+            std::vector<TsTask<T>> nn1(nb), tn2(nb), nn2(nb), tn3(nb), nn3(nb);
+            std::vector<int> wl2(nb);
+            int mpq1 = 0, mpq2 = 0, mq2 = 0, mpq3 = 0, mq3 = 0;
+            for (int a = 0; a < nb; ++a) {
+                const Win<T>& W = act[a];
+                T* Wn = slot(W, step);
+                const int b = W.b, p = step * b, ldo = (step + 1) * b;
+                TsTask<T> t;
+                memset(&t, 0, sizeof(t));
+                // W -= V_{1:step} h1, h1 = out1[0:p, 2b:3b]
+                t.X = W.V; t.ldx = n; t.p = p; t.q = b;
+                t.Z = Wn; t.ldz = n;
+                t.Tm = D(W.w) + L.off_out1 + (int64_t)2 * b * ldo; t.ldt = ldo;
+                t.alpha = -1.0; t.beta = 1.0;
+                nn1[a] = t;
+                mpq1 = std::max(mpq1, p * b);
+                // h2 = V^T W
+                memset(&t, 0, sizeof(t));
+                t.X = W.V; t.ldx = n; t.p = p;
+                t.Y = Wn; t.ldy = n; t.q = b; t.q1 = b;
+                t.out = D(W.w) + L.off_h2;
+                tn2[a] = t;
+                mpq2 = std::max(mpq2, p * b);
+                mq2 = std::max(mq2, b);
+                // W -= V h2
+                t = nn1[a];
+                t.Tm = D(W.w) + L.off_h2; t.ldt = p;
+                nn2[a] = t;
+                // Gram of W
+                memset(&t, 0, sizeof(t));
+                t.X = Wn; t.ldx = n; t.p = b;
+                t.Y = Wn; t.ldy = n; t.q = b; t.q1 = b;
+                t.out = D(W.w) + L.off_gw;
+                tn3[a] = t;
+                mpq3 = std::max(mpq3, b * b);
+                mq3 = std::max(mq3, b);
+                // W <- W T (in place)
+                memset(&t, 0, sizeof(t));
+                t.X = Wn; t.ldx = n; t.p = b; t.q = b;
+                t.Z = Wn; t.ldz = n;
+                t.Tm = D(W.w) + L.off_T; t.ldt = b;
+                t.alpha = 1.0; t.beta = 0.0;
+                nn3[a] = t;
+                wl2[a] = W.w;
+            }
+            const TsTask<T>* d_nn1 = sb.put(nn1.data(), nb);
+            const TsTask<T>* d_tn2 = sb.put(tn2.data(), nb);
+            const TsTask<T>* d_nn2 = sb.put(nn2.data(), nb);
+            const TsTask<T>* d_tn3 = sb.put(tn3.data(), nb);
+            const TsTask<T>* d_nn3 = sb.put(nn3.data(), nb);
+            const int* d_wl2 = sb.put(wl2.data(), nb);
+            sb.flush();
+            launch_ts_nn<T>(d_nn1, nb, mpq1, n, st); check_launch(c);
+            launch_ts_tn<T>(d_tn2, nb, mpq2, mq2, n, partial, st, 0); check_launch(c);
+            launch_ts_nn<T>(d_nn2, nb, mpq1, n, st); check_launch(c);
+            launch_ts_tn<T>(d_tn3, nb, mpq3, mq3, n, partial, st, 0); check_launch(c);
+            launch_block_orth(L, wd, wi, d_wl2, nb, 1, step, defl, st); check_launch(c);
+            launch_ts_nn<T>(d_nn3, nb, mpq3, n, st); check_launch(c);
+            launch_ts_tn<T>(d_tn3, nb, mpq3, mq3, n, partial, st, 0); check_launch(c);
+            launch_block_orth(L, wd, wi, d_wl2, nb, 2, step, defl, st); check_launch(c);
+            launch_ts_nn<T>(d_nn3, nb, mpq3, n, st); check_launch(c);
+        }
+        return notconv;
+    }
+};
+
+template <typename T>
+T* as(void* p) { return reinterpret_cast<T*>(p); }
+
+struct Partition {
+    std::vector<int> idx;   // P+1 boundaries
+    int smax = 0;
+};
+Partition make_partition(int n_out, int P) {
+    Partition r;
+    r.idx.resize(P + 1);
+    for (int j = 0; j <= P; ++j) r.idx[j] = (int)(((int64_t)j * (n_out - 1)) / P);
+    for (int j = 1; j <= P; ++j) r.smax = std::max(r.smax, r.idx[j] - r.idx[j - 1] + 1);
+    return r;
+}
+
+size_t align_up(size_t x) { return (x + kAlign - 1) / kAlign * kAlign; }
+
+// Upper bound of the workspace a linear solve needs (bytes).
+template <typename T>
+size_t linear_workspace_bytes(int64_t n, const pexp_options* o, int g_conv, int b_cap) {
+    const int P = o->P;
+    Partition pt = make_partition(o->n_out, P);
+    const int kmax = o->restart_len * (o->max_restarts + 1);
+    WinLayout L = make_layout(pt.smax, b_cap, kmax);
+    size_t s = 0;
+    s += align_up(sizeof(double) * n * 2);                                  // u0, A u0
+    if (g_conv) s += align_up(sizeof(T) * (size_t)n * o->n_out);           // converted G
+    s += align_up(sizeof(double) * L.stride * 2 * P);                       // window state
+    s += align_up(sizeof(int) * L.istride * 2 * P);
+    s += align_up(sizeof(double) * (ts_tn_partial_doubles(P, std::max(pt.smax * pt.smax, 3 * b_cap * (L.K_max + b_cap)), n) + 512));
+    s += align_up(sizeof(double) * sai_scratch_doubles(n, P * b_cap) + 64);
+    s += align_up(sizeof(T) * (size_t)n * L.K_max * P);                     // V_nh
+    s += align_up(sizeof(T) * (size_t)n * 2 * b_cap * P);                   // S
+    s += align_up(sizeof(T) * (size_t)n * (kmax + 1) * P);                  // V_h
+    s += align_up(sizeof(T) * (size_t)n * 2);                               // S for the homogeneous chain
+    s += (size_t)(4 * P + 32) * kAlign;   // alignment of the per-window allocations
+    return s;
+}
+
+template <typename T, typename TO>
+int solve_linear_typed(pexp_ctx* c, const pexp_operator* op, const pexp_options* o, const double* u0d,
+                       const void* G_dev, int g_dtype, TO* Y, pexp_report* rep) {
+    cudaStream_t st = c->stream;
+    Solver<T> S;
+    S.c = c;
+    S.st = st;
+    S.o = o;
+    S.od = make_opdesc(*op);
+    const int64_t n = S.od.n;
+    S.n = n;
+    const int P = o->P, n_out = o->n_out;
+    Partition pt = make_partition(n_out, P);
+    S.kmax = o->restart_len * (o->max_restarts + 1);
+    S.h = o->T / (double)(n_out - 1);
+    const bool fp64 = sizeof(T) == 8;
+    S.defl = fp64 ? 1e-10 : 1e-5;
+    const double svd_floor = fp64 ? 1e-7 : 1e-5;
+    const int b_cap = std::min(std::min(o->max_rank, PEXP_MAX_RANK), pt.smax);
+    S.L = make_layout(pt.smax, b_cap, S.kmax);
+    const WinLayout& L = S.L;
+
+    // ---- buffers
+    double* Au0 = as<double>(ws_alloc(c, sizeof(double) * n));
+    const T* G = nullptr;
+    if (G_dev) {
+        const bool same = (g_dtype == PEXP_F64) == fp64;
+        if (same) {
+            G = reinterpret_cast<const T*>(G_dev);
+        } else {
+            T* Gc = as<T>(ws_alloc(c, sizeof(T) * (size_t)n * n_out));
+            if (g_dtype == PEXP_F64) launch_convert<double, T>(reinterpret_cast<const double*>(G_dev), Gc, n * n_out, st);
+            else launch_convert<float, T>(reinterpret_cast<const float*>(G_dev), Gc, n * n_out, st);
+            check_launch(c);
+            G = Gc;
+        }
+    }
+    const int nwin = 2 * P;   // [0, P): source windows j=1..P; [P, 2P): homogeneous windows m=1..P
+    S.wd = as<double>(ws_alloc(c, sizeof(double) * L.stride * nwin));
+    S.wi = as<int>(ws_alloc(c, sizeof(int) * L.istride * nwin));
+    const size_t part_n = ts_tn_partial_doubles(P, std::max(pt.smax * pt.smax, 3 * b_cap * (L.K_max + b_cap)), n) + 512;
+    S.partial = as<double>(ws_alloc(c, sizeof(double) * part_n));
+    S.sai_scr = as<double>(ws_alloc(c, sizeof(double) * (sai_scratch_doubles(n, P * b_cap) + 64)));
+    // one pole for every window: gamma = sai_gamma * T / P (the nominal subinterval length)
+    if (o->krylov == PEXP_KRYLOV_SAI) S.sai = sai_coefficients(S.od, o->sai_gamma * o->T / (double)P);
+    S.wi_host.assign((size_t)L.istride * nwin, 0);
+
+    // ---- initial window state
+    {
+        std::vector<int> wih((size_t)L.istride * nwin, 0);
+        for (int j = 0; j < P; ++j) {
+            wih[(size_t)j * L.istride + WI_S] = pt.idx[j + 1] - pt.idx[j] + 1;
+            wih[(size_t)j * L.istride + WI_KIND] = KIND_SOURCE;
+            wih[(size_t)(P + j) * L.istride + WI_S] = pt.idx[j + 1] - pt.idx[j] + 1;
+            wih[(size_t)(P + j) * L.istride + WI_KIND] = KIND_HOM;
+            wih[(size_t)(P + j) * L.istride + WI_B] = 1;
+        }
+        cudaMemcpyAsync(S.wi, wih.data(), sizeof(int) * wih.size(), cudaMemcpyHostToDevice, st);
+        cudaMemsetAsync(S.wd, 0, sizeof(double) * L.stride * nwin, st);
+        sync(c);   // wih goes out of scope
+    }
+
+    cudaEventRecord(c->evp[0], st);
+    // ---- shift: A u0, ||u0||
+    launch_stencil<double>(S.od, u0d, Au0, 1, 0, st);
+    check_launch(c);
+    {
+        Stage s0(c, 0);
+        TsTask<double> t;
+        memset(&t, 0, sizeof(t));
+        t.X = u0d; t.ldx = n; t.p = 1; t.Y = u0d; t.ldy = n; t.q = 1; t.q1 = 1;
+        t.out = S.partial + part_n - 8;
+        const TsTask<double>* dt = s0.put(&t, 1);
+        s0.flush();
+        launch_ts_tn<double>(dt, 1, 1, 1, n, S.partial, st, 0);
+        check_launch(c);
+        double nn = 0;
+        d2h(c, &nn, S.partial + part_n - 8, sizeof(double));
+        S.scale_ref = sqrt(nn);
+    }
+
+    // ---- source compression, all subintervals
+    std::vector<int> all(P);
+    for (int j = 0; j < P; ++j) all[j] = j;
+    {
+        Stage s1(c, 0);
+        std::vector<TsTask<T>> tg(P);
+        for (int j = 0; j < P; ++j) {
+            TsTask<T> t;
+            memset(&t, 0, sizeof(t));
+            const int s = pt.idx[j + 1] - pt.idx[j] + 1;
+            t.X = G ? G + (int64_t)pt.idx[j] * n : nullptr;
+            t.ldx = n; t.p = s; t.xs = Au0;
+            t.Y = t.X; t.ldy = n; t.q = s; t.q1 = s; t.ys = Au0;
+            t.out = S.D(j) + L.off_gram;
+            tg[j] = t;
+        }
+        const TsTask<T>* dtg = s1.put(tg.data(), P);
+        const int* dall = s1.put(all.data(), P);
+        s1.flush();
+        launch_ts_tn<T>(dtg, P, pt.smax * pt.smax, pt.smax, n, S.partial, st, 1);
+        check_launch(c);
+        launch_source_eig(L, S.wd, S.wi, dall, P, std::max(o->svd_tol, svd_floor), b_cap, st);
+        check_launch(c);
+        d2h(c, S.wi_host.data(), S.wi, sizeof(int) * S.wi_host.size());
+    }
+    std::vector<int> mj(P);
+    int b_max = 0, b_min = 1 << 30;
+    for (int j = 0; j < P; ++j) {
+        mj[j] = S.wi_host[(size_t)j * L.istride + WI_B];
+        b_max = std::max(b_max, mj[j]);
+        b_min = std::min(b_min, mj[j]);
+    }
+    // bases laid out with the actual widths
+    std::vector<Win<T>> src;
+    std::vector<T*> Vnh(P, nullptr);
+    for (int j = 0; j < P; ++j) {
+        if (mj[j] == 0) continue;
+        Win<T> W;
+        W.w = j;
+        W.b = mj[j];
+        W.V = as<T>(ws_alloc(c, sizeof(T) * (size_t)n * W.b * (S.kmax + 1)));
+        W.S = as<T>(ws_alloc(c, sizeof(T) * (size_t)n * 2 * W.b));
+        Vnh[j] = W.V;
+        src.push_back(W);
+    }
+    {
+        const int ns = (int)src.size();
+        Stage s2(c, 1);
+        std::vector<TsTask<T>> tu(ns), tgr(ns), tsc(ns);
+        std::vector<int> wl(ns);
+        int mpq = 0, mq = 0, mpqg = 0;
+        for (int a = 0; a < ns; ++a) {
+            const Win<T>& W = src[a];
+            const int j = W.w;
+            const int s = pt.idx[j + 1] - pt.idx[j] + 1;
+            TsTask<T> t;
+            memset(&t, 0, sizeof(t));
+            t.X = G ? G + (int64_t)pt.idx[j] * n : nullptr; t.ldx = n; t.xs = Au0; t.p = s; t.q = W.b;
+            t.Z = W.V; t.ldz = n; t.Tm = S.D(j) + L.off_zs; t.ldt = L.s_max; t.alpha = 1.0; t.beta = 0.0;
+            tu[a] = t;
+            mpq = std::max(mpq, s * W.b);
+            memset(&t, 0, sizeof(t));
+            t.X = W.V; t.ldx = n; t.p = W.b; t.Y = W.V; t.ldy = n; t.q = W.b; t.q1 = W.b;
+            t.out = S.D(j) + L.off_gw;
+            tgr[a] = t;
+            mpqg = std::max(mpqg, W.b * W.b);
+            mq = std::max(mq, W.b);
+            memset(&t, 0, sizeof(t));
+            t.X = W.V; t.ldx = n; t.p = W.b; t.q = W.b; t.Z = W.V; t.ldz = n;
+            t.Tm = S.D(j) + L.off_T; t.ldt = W.b; t.alpha = 1.0; t.beta = 0.0;
+            tsc[a] = t;
+            wl[a] = j;
+        }
+        const TsTask<T>* dtu = s2.put(tu.data(), ns);
+        const TsTask<T>* dtg = s2.put(tgr.data(), ns);
+        const TsTask<T>* dts = s2.put(tsc.data(), ns);
+        const int* dwl = s2.put(wl.data(), ns);
+        s2.flush();
+        launch_ts_nn<T>(dtu, ns, mpq, n, st); check_launch(c);
+        launch_ts_tn<T>(dtg, ns, mpqg, mq, n, S.partial, st, 1); check_launch(c);
+        launch_start_orth(L, S.wd, S.wi, dwl, ns, st); check_launch(c);
+        launch_ts_nn<T>(dts, ns, mpqg, n, st); check_launch(c);
+        launch_spline(L, S.wd, S.wi, dwl, ns, S.h, st); check_launch(c);
+        sync(c);   // staging half 1 is reused by the Krylov loop
+    }
+
+    cudaEventRecord(c->evp[1], st);
+    // ---- nonhomogeneous parts, all subintervals in one batch
+    int k_nh = 0;
+    int notconv = S.run(src, KIND_SOURCE, &k_nh);
+    d2h(c, S.wi_host.data(), S.wi, sizeof(int) * S.wi_host.size());
+    std::vector<int> Knh(P, 0);
+    for (int j = 0; j < P; ++j) Knh[j] = S.wi_host[(size_t)j * L.istride + WI_K];
+
+    cudaEventRecord(c->evp[2], st);
+    // ---- homogeneous chain over windows 2..P
+    std::vector<T*> Vh(P, nullptr);
+    std::vector<int> Kh(P, 0);
+    int k_hom_max = 0, k_hom_sum = 0;
+    T* Sh = as<T>(ws_alloc(c, sizeof(T) * (size_t)n * 2));
+    for (int m = 1; m < P; ++m) {   // 0-based window m needs z at T_m (end of window m-1)
+        Vh[m] = as<T>(ws_alloc(c, sizeof(T) * (size_t)n * (S.kmax + 1)));
+        const int wprev = m - 1;
+        const int sprev = pt.idx[m] - pt.idx[m - 1] + 1;
+        Stage s3(c, 0);
+        ReconTask<T> rt;
+        memset(&rt, 0, sizeof(rt));
+        rt.V1 = Vnh[wprev]; rt.C1 = S.D(wprev) + L.off_Y; rt.ld1 = n; rt.K1 = Vnh[wprev] ? Knh[wprev] : 0; rt.ldc1 = L.K_max;
+        if (m - 1 >= 1) {
+            rt.V2 = Vh[m - 1]; rt.C2 = S.D(P + m - 1) + L.off_Y; rt.ld2 = n; rt.K2 = Kh[m - 1]; rt.ldc2 = L.K_max;
+        }
+        rt.r0 = sprev - 1; rt.ns = 1; rt.i0 = 0;
+        const ReconTask<T>* drt = s3.put(&rt, 1);
+        TsTask<T> tg, tsc;
+        memset(&tg, 0, sizeof(tg));
+        tg.X = Vh[m]; tg.ldx = n; tg.p = 1; tg.Y = Vh[m]; tg.ldy = n; tg.q = 1; tg.q1 = 1;
+        tg.out = S.D(P + m) + L.off_gw;
+        memset(&tsc, 0, sizeof(tsc));
+        tsc.X = Vh[m]; tsc.ldx = n; tsc.p = 1; tsc.q = 1; tsc.Z = Vh[m]; tsc.ldz = n;
+        tsc.Tm = S.D(P + m) + L.off_T; tsc.ldt = 1; tsc.alpha = 1.0; tsc.beta = 0.0;
+        const TsTask<T>* dtg = s3.put(&tg, 1);
+        const TsTask<T>* dts = s3.put(&tsc, 1);
+        int wsel = P + m;
+        const int* dw = s3.put(&wsel, 1);
+        s3.flush();
+        const int maxc = std::max(1, (rt.K1 + rt.K2));
+        launch_recon<T, T>(drt, 1, 1, n, nullptr, Vh[m], n, maxc, st); check_launch(c);
+        launch_ts_tn<T>(dtg, 1, 1, 1, n, S.partial, st, 1); check_launch(c);
+        launch_start_orth(L, S.wd, S.wi, dw, 1, st); check_launch(c);
+        launch_ts_nn<T>(dts, 1, 1, n, st); check_launch(c);
+        double beta = 0;
+        d2h(c, &beta, S.D(P + m) + L.off_scal + WS_BETA, sizeof(double));
+        if (!(beta > 0.0)) { Kh[m] = 0; continue; }
+        std::vector<Win<T>> one(1);
+        one[0].w = P + m; one[0].V = Vh[m]; one[0].S = Sh; one[0].b = 1;
+        int kh = 0;
+        notconv += S.run(one, KIND_HOM, &kh);
+        int kk = 0;
+        d2h(c, &kk, S.wi + (size_t)(P + m) * L.istride + WI_K, sizeof(int));
+        Kh[m] = kk;
+        k_hom_max = std::max(k_hom_max, kh);
+        k_hom_sum += kh;
+    }
+
+    cudaEventRecord(c->evp[3], st);
+    // ---- reconstruction of all windows
+    {
+        Stage s4(c, 1);
+        std::vector<ReconTask<T>> rts;
+        int maxc = 1, maxns = 1;
+        for (int m = 0; m < P; ++m) {
+            ReconTask<T> rt;
+            memset(&rt, 0, sizeof(rt));
+            const int s = pt.idx[m + 1] - pt.idx[m] + 1;
+            if (Vnh[m]) { rt.V1 = Vnh[m]; rt.C1 = S.D(m) + L.off_Y; rt.ld1 = n; rt.K1 = Knh[m]; rt.ldc1 = L.K_max; }
+            if (m >= 1 && Vh[m] && Kh[m] > 0) { rt.V2 = Vh[m]; rt.C2 = S.D(P + m) + L.off_Y; rt.ld2 = n; rt.K2 = Kh[m]; rt.ldc2 = L.K_max; }
+            rt.r0 = (m == 0) ? 0 : 1;
+            rt.ns = s - rt.r0;
+            rt.i0 = pt.idx[m] + rt.r0;
+            maxc = std::max(maxc, rt.ns * (rt.K1 + rt.K2));
+            maxns = std::max(maxns, rt.ns);
+            rts.push_back(rt);
+        }
+        const ReconTask<T>* drt = s4.put(rts.data(), rts.size());
+        s4.flush();
+        launch_recon<T, TO>(drt, (int)rts.size(), maxns, n, u0d, Y, n, maxc, st);
+        check_launch(c);
+        cudaEventRecord(c->evp[4], st);
+        sync(c);
+    }
+
+    if (rep) {
+        float ms[4] = {0, 0, 0, 0};
+        for (int k = 0; k < 4; ++k) cudaEventElapsedTime(&ms[k], c->evp[k], c->evp[k + 1]);
+        rep->t_source_ms = ms[0];
+        rep->t_krylov_ms = ms[1];
+        rep->t_hom_ms = ms[2];
+        rep->t_recon_ms = ms[3];
+        double est_max = 0, sig_max = 0;
+        for (int j = 0; j < P; ++j) {
+            double sc[WS_COUNT];
+            d2h(c, sc, S.D(j) + L.off_scal, sizeof(sc));
+            est_max = std::max(est_max, sc[WS_EST]);
+            sig_max = std::max(sig_max, sc[WS_SIGRATIO]);
+        }
+        rep->n_sub = P;
+        rep->rank_max = b_max;
+        rep->rank_min = b_min;
+        rep->k_nh_max = k_nh;
+        rep->k_hom_max = k_hom_max;
+        rep->k_hom_sum = k_hom_sum;
+        rep->not_converged = notconv;
+        rep->est_max = est_max;
+        rep->sigma_ratio_max = sig_max;
+        const double w = (double)sizeof(T);
+        double bytes = 0;
+        // algorithmic bytes: source reads, Krylov steps, reconstruction
+        for (int j = 0; j < P; ++j) {
+            const int s = pt.idx[j + 1] - pt.idx[j] + 1;
+            bytes += 2.0 * n * s * w + (double)n * mj[j] * w;
+            const double k = Knh[j] / std::max(1, mj[j]);
+            bytes += (double)n * mj[j] * w * (2.0 * k * (k + 1) + 14.0 * k);
+            if (j >= 1) { const double kh = Kh[j]; bytes += (double)n * w * (2.0 * kh * (kh + 1) + 14.0 * kh); }
+        }
+        bytes += (double)n * n_out * (double)sizeof(TO);
+        rep->bytes_alg = bytes;
+    }
+    return notconv ? PEXP_ERR_NOT_CONVERGED : PEXP_OK;
+}
+
+int solve_linear_dispatch(pexp_ctx* c, const pexp_operator* op, const pexp_options* o, const void* y0_dev,
+                          const void* G_dev, int g_dtype, void* Y_dev, int y_dtype, pexp_report* rep,
+                          size_t keep_top) {
+    const OpDesc od = make_opdesc(*op);
+    const int64_t n = od.n;
+    const bool fp64 = o->precision == PEXP_FP64;
+    Partition pt = make_partition(o->n_out, o->P);
+    const int b_cap = std::min(std::min(o->max_rank, PEXP_MAX_RANK), pt.smax);
+    const int g_conv = G_dev && ((g_dtype == PEXP_F64) != fp64);
+    size_t need = keep_top + align_up(sizeof(double) * n) +
+                  (fp64 ? linear_workspace_bytes<double>(n, o, g_conv, b_cap)
+                        : linear_workspace_bytes<float>(n, o, g_conv, b_cap));
+    if (need > c->ws_cap) {
+        if (keep_top) return PEXP_ERR_OOM;   // cannot move live buffers of the caller
+        int r = ws_reserve(c, need);
+        if (r) return r;
+    }
+    c->ws_top = keep_top;
+    double* u0d = as<double>(ws_alloc(c, sizeof(double) * n));
+    if (y_dtype == PEXP_F64) cudaMemcpyAsync(u0d, y0_dev, sizeof(double) * n, cudaMemcpyDeviceToDevice, c->stream);
+    else launch_convert<float, double>(reinterpret_cast<const float*>(y0_dev), u0d, n, c->stream);
+    if (fp64) {
+        if (y_dtype == PEXP_F64) return solve_linear_typed<double, double>(c, op, o, u0d, G_dev, g_dtype, as<double>(Y_dev), rep);
+        return solve_linear_typed<double, float>(c, op, o, u0d, G_dev, g_dtype, as<float>(Y_dev), rep);
+    }
+    if (y_dtype == PEXP_F64) return solve_linear_typed<float, double>(c, op, o, u0d, G_dev, g_dtype, as<double>(Y_dev), rep);
+    return solve_linear_typed<float, float>(c, op, o, u0d, G_dev, g_dtype, as<float>(Y_dev), rep);
+}
+
+template <typename F>
+int guarded(F&& f) {
+    try {
+        return f();
+    } catch (const OomError&) {
+        return PEXP_ERR_OOM;
+    } catch (const StatusError& e) {
+        return e.code;
+    } catch (const std::bad_alloc&) {
+        return PEXP_ERR_OOM;
+    } catch (...) {
+        return PEXP_ERR_CUDA;
+    }
+}
+
+}  // namespace
+
+// =====================================================================================
+// C ABI
+// =====================================================================================
+extern "C" {
+
+void pexp_default_options(pexp_options* o) {
+    if (!o) return;
+    memset(o, 0, sizeof(*o));
+    o->T = 1.0;
+    o->P = 1;
+    o->n_out = 2;
+    o->tol = 1e-8;
+    o->svd_tol = 1e-12;
+    o->max_rank = 16;
+    o->restart_len = 20;
+    o->max_restarts = 0;
+    o->krylov = PEXP_KRYLOV_SAI;
+    o->sai_gamma = 0.1;
+    o->precision = PEXP_FP64;
+    o->wr_max_iter = 50;
+    o->wr_tol = 1e-6;
+    o->burgers_form = 0;
+}
+
+const char* pexp_status_string(int s) {
+    switch (s) {
+        case PEXP_OK: return "ok";
+        case PEXP_ERR_INVALID_ARG: return "invalid argument";
+        case PEXP_ERR_OOM: return "out of device memory";
+        case PEXP_ERR_CUDA: return "CUDA error";
+        case PEXP_ERR_BREAKDOWN: return "Krylov breakdown";
+        case PEXP_ERR_NOT_CONVERGED: return "Krylov tolerance not reached";
+        case PEXP_ERR_WR_NOT_CONVERGED: return "waveform relaxation not converged";
+        case PEXP_ERR_TIMEOUT: return "device wait timed out";
+        case PEXP_ERR_UNSUPPORTED: return "unsupported operator/precision combination";
+        default: return "unknown status";
+    }
+}
+
+int pexp_create(pexp_ctx** out, int device, void* stream) {
+    if (!out) return PEXP_ERR_INVALID_ARG;
+    *out = nullptr;
+    pexp_ctx* c = new (std::nothrow) pexp_ctx();
+    if (!c) return PEXP_ERR_OOM;
+    c->device = device;
+    if (cudaSetDevice(device) != cudaSuccess) { delete c; return PEXP_ERR_CUDA; }
+    c->stream = reinterpret_cast<cudaStream_t>(stream);
+    c->stage_cap = kStageBytes;
+    for (int h = 0; h < 2; ++h) {
+        if (cudaMallocHost(&c->stage_h[h], kStageBytes) != cudaSuccess ||
+            cudaMalloc(&c->stage_d[h], kStageBytes) != cudaSuccess) {
+            pexp_destroy(c);
+            return PEXP_ERR_OOM;
+        }
+    }
+    cudaEventCreate(&c->ev0);
+    cudaEventCreate(&c->ev1);
+    for (int k = 0; k < 5; ++k) cudaEventCreate(&c->evp[k]);
+    init_pade_constants();
+    *out = c;
+    return PEXP_OK;
+}
+
+int pexp_destroy(pexp_ctx* c) {
+    if (!c) return PEXP_OK;
+    cudaSetDevice(c->device);
+    if (c->stream) cudaStreamSynchronize(c->stream);
+    if (c->ws) cudaFree(c->ws);
+    for (int h = 0; h < 2; ++h) {
+        if (c->stage_h[h]) cudaFreeHost(c->stage_h[h]);
+        if (c->stage_d[h]) cudaFree(c->stage_d[h]);
+    }
+    if (c->io_d) cudaFree(c->io_d);
+    if (c->ev0) cudaEventDestroy(c->ev0);
+    if (c->ev1) cudaEventDestroy(c->ev1);
+    for (int k = 0; k < 5; ++k)
+        if (c->evp[k]) cudaEventDestroy(c->evp[k]);
+    delete c;
+    return PEXP_OK;
+}
+
+int pexp_set_stream(pexp_ctx* c, void* stream) {
+    if (!c) return PEXP_ERR_INVALID_ARG;
+    c->stream = reinterpret_cast<cudaStream_t>(stream);
+    return PEXP_OK;
+}
+
+int pexp_solve_linear(pexp_ctx* c, const pexp_operator* op, const pexp_options* o, const void* y0_dev,
+                      const void* G_dev, int g_dtype, void* Y_dev, int y_dtype, pexp_report* rep) {
+    if (!c || !y0_dev || !Y_dev) return PEXP_ERR_INVALID_ARG;
+    if ((g_dtype != PEXP_F64 && g_dtype != PEXP_F32) || (y_dtype != PEXP_F64 && y_dtype != PEXP_F32))
+        return PEXP_ERR_INVALID_ARG;
+    int v = validate(op, o);
+    if (v) return v;
+    if (rep) memset(rep, 0, sizeof(*rep));
+    cudaSetDevice(c->device);
+    c->launches = 0;
+    cudaEventRecord(c->ev0, c->stream);
+    int r = guarded([&] { return solve_linear_dispatch(c, op, o, y0_dev, G_dev, g_dtype, Y_dev, y_dtype, rep, 0); });
+    cudaEventRecord(c->ev1, c->stream);
+    cudaEventSynchronize(c->ev1);
+    if (rep) {
+        float ms = 0;
+        cudaEventElapsedTime(&ms, c->ev0, c->ev1);
+        rep->time_ms = ms;
+        rep->launches = c->launches;
+        rep->status = r;
+    }
+    return r;
+}
+
+int pexp_solve_linear_host(pexp_ctx* c, const pexp_operator* op, const pexp_options* o, const void* y0_host,
+                           const void* G_host, int g_dtype, void* Y_host, int y_dtype, pexp_report* rep) {
+    if (!c || !y0_host || !Y_host) return PEXP_ERR_INVALID_ARG;
+    int v = validate(op, o);
+    if (v) return v;
+    const OpDesc od = make_opdesc(*op);
+    const size_t n = (size_t)od.n;
+    const size_t ys = (y_dtype == PEXP_F64) ? 8 : 4, gs = (g_dtype == PEXP_F64) ? 8 : 4;
+    const size_t bytes = align_up(n * ys) + (G_host ? align_up(n * o->n_out * gs) : 0) + align_up(n * o->n_out * ys);
+    cudaSetDevice(c->device);
+    if (bytes > c->io_cap) {
+        if (c->io_d) cudaFree(c->io_d);
+        c->io_d = nullptr;
+        c->io_cap = 0;
+        if (cudaMalloc(&c->io_d, bytes) != cudaSuccess) { cudaGetLastError(); return PEXP_ERR_OOM; }
+        c->io_cap = bytes;
+    }
+    char* p = reinterpret_cast<char*>(c->io_d);
+    void* y0d = p;
+    p += align_up(n * ys);
+    void* Gd = nullptr;
+    if (G_host) { Gd = p; p += align_up(n * o->n_out * gs); }
+    void* Yd = p;
+    PEXP_CUDA_TRY(cudaMemcpyAsync(y0d, y0_host, n * ys, cudaMemcpyHostToDevice, c->stream));
+    if (G_host) PEXP_CUDA_TRY(cudaMemcpyAsync(Gd, G_host, n * o->n_out * gs, cudaMemcpyHostToDevice, c->stream));
+    int r = pexp_solve_linear(c, op, o, y0d, Gd, g_dtype, Yd, y_dtype, rep);
+    if (r == PEXP_OK || r == PEXP_ERR_NOT_CONVERGED) {
+        PEXP_CUDA_TRY(cudaMemcpyAsync(Y_host, Yd, n * o->n_out * ys, cudaMemcpyDeviceToHost, c->stream));
+        PEXP_CUDA_TRY(cudaStreamSynchronize(c->stream));
+    }
+    return r;
+}
+
+int pexp_solve_burgers(pexp_ctx* c, const pexp_operator* op, const pexp_options* o, const void* u0_dev,
+                       const void* forcing_dev, const void* init_dev, void* U_dev, int dtype, pexp_report* rep) {
+    if (!c || !u0_dev || !U_dev || !op || !o) return PEXP_ERR_INVALID_ARG;
+    if (op->dim != 1 || op->ax != 0.0) return PEXP_ERR_INVALID_ARG;
+    if (dtype != PEXP_F64 && dtype != PEXP_F32) return PEXP_ERR_INVALID_ARG;
+    if (o->wr_max_iter < 1 || !(o->wr_tol > 0)) return PEXP_ERR_INVALID_ARG;
+    int v = validate(op, o);
+    if (v) return v;
+    if (rep) memset(rep, 0, sizeof(*rep));
+    cudaSetDevice(c->device);
+    const OpDesc od = make_opdesc(*op);
+    const int64_t n = od.n;
+    const int nt = o->n_out;
+    const size_t es = dtype == PEXP_F64 ? 8 : 4;
+    const double inv2dx = 1.0 / (2.0 * (op->bc == PEXP_BC_PERIODIC ? op->Lx / n : op->Lx / (n + 1)));
+    c->launches = 0;
+    cudaEventRecord(c->ev0, c->stream);
+    int status = guarded([&]() -> int {
+        // live WR buffers at the bottom of the workspace: previous iterate, source
+        const size_t keep = align_up(es * n * nt) * 2 + align_up(sizeof(double) * 2 * nt) + kAlign;
+        const bool fp64 = o->precision == PEXP_FP64;
+        Partition pt = make_partition(nt, o->P);
+        const int b_cap = std::min(std::min(o->max_rank, PEXP_MAX_RANK), pt.smax);
+        const int g_conv = (dtype == PEXP_F64) != fp64;
+        size_t need = keep + align_up(sizeof(double) * n) +
+                      (fp64 ? linear_workspace_bytes<double>(n, o, g_conv, b_cap)
+                            : linear_workspace_bytes<float>(n, o, g_conv, b_cap));
+        int r = ws_reserve(c, need);
+        if (r) return r;
+        c->ws_top = 0;
+        char* Uprev = reinterpret_cast<char*>(ws_alloc(c, es * n * nt));
+        char* Gk = reinterpret_cast<char*>(ws_alloc(c, es * n * nt));
+        double* norms = as<double>(ws_alloc(c, sizeof(double) * 2 * nt));
+        const size_t top = c->ws_top;
+        // first iterate
+        if (init_dev) {
+            cudaMemcpyAsync(Uprev, init_dev, es * n * nt, cudaMemcpyDeviceToDevice, c->stream);
+        } else {
+            for (int i = 0; i < nt; ++i)
+                cudaMemcpyAsync(Uprev + es * n * i, u0_dev, es * n, cudaMemcpyDeviceToDevice, c->stream);
+        }
+        std::vector<double> nh(2 * nt);
+        int status_l = PEXP_ERR_WR_NOT_CONVERGED;
+        double delta = 0;
+        int it = 0;
+        pexp_report lrep;
+        for (it = 1; it <= o->wr_max_iter; ++it) {
+            if (dtype == PEXP_F64) launch_burgers_source<double>(od, as<double>(Uprev), as<double>(Gk), nt, o->burgers_form, inv2dx, c->stream);
+            else launch_burgers_source<float>(od, as<float>(Uprev), as<float>(Gk), nt, o->burgers_form, inv2dx, c->stream);
+            check_launch(c);
+            if (forcing_dev) {
+                if (dtype == PEXP_F64) launch_add<double>(as<double>(Gk), reinterpret_cast<const double*>(forcing_dev), n * nt, c->stream);
+                else launch_add<float>(as<float>(Gk), reinterpret_cast<const float*>(forcing_dev), n * nt, c->stream);
+                check_launch(c);
+            }
+            int lr = solve_linear_dispatch(c, op, o, u0_dev, Gk, dtype, U_dev, dtype, &lrep, top);
+            if (lr != PEXP_OK && lr != PEXP_ERR_NOT_CONVERGED) return lr;
+            if (dtype == PEXP_F64) launch_row_diff_norms<double>(as<double>(U_dev), as<double>(Uprev), n, nt, norms, c->stream);
+            else launch_row_diff_norms<float>(as<float>(U_dev), as<float>(Uprev), n, nt, norms, c->stream);
+            check_launch(c);
+            d2h(c, nh.data(), norms, sizeof(double) * 2 * nt);
+            double dmax = 0, umax = 0;
+            for (int i = 0; i < nt; ++i) {
+                dmax = std::max(dmax, sqrt(nh[i]));
+                umax = std::max(umax, sqrt(nh[nt + i]));
+            }
+            delta = umax > 0 ? dmax / umax : 0.0;
+            if (rep) {
+                rep->k_nh_max = std::max(rep->k_nh_max, lrep.k_nh_max);
+                rep->k_hom_max = std::max(rep->k_hom_max, lrep.k_hom_max);
+                rep->rank_max = std::max(rep->rank_max, lrep.rank_max);
+                rep->not_converged += lrep.not_converged;
+                rep->bytes_alg += lrep.bytes_alg + 3.0 * es * n * nt;
+            }
+            if (delta <= o->wr_tol) { status_l = PEXP_OK; break; }
+            cudaMemcpyAsync(Uprev, U_dev, es * n * nt, cudaMemcpyDeviceToDevice, c->stream);
+        }
+        if (rep) {
+            rep->wr_iters = std::min(it, o->wr_max_iter);
+            rep->wr_delta = delta;
+            rep->n_sub = o->P;
+        }
+        return status_l;
+    });
+    cudaEventRecord(c->ev1, c->stream);
+    cudaEventSynchronize(c->ev1);
+    if (rep) {
+        float ms = 0;
+        cudaEventElapsedTime(&ms, c->ev0, c->ev1);
+        rep->time_ms = ms;
+        rep->launches = c->launches;
+        rep->status = status;
+    }
+    return status;
+}
+
+int pexp_apply_operator(pexp_ctx* c, const pexp_operator* op, const void* X, void* Y, int nvec, int dtype,
+                        int transpose) {
+    if (!c || !op || !X || !Y || nvec < 1) return PEXP_ERR_INVALID_ARG;
+    if (op->dim != 1 && op->dim != 2) return PEXP_ERR_INVALID_ARG;
+    cudaSetDevice(c->device);
+    const OpDesc od = make_opdesc(*op);
+    if (dtype == PEXP_F64) launch_stencil<double>(od, as<double>(const_cast<void*>(X)), as<double>(Y), nvec, transpose, c->stream);
+    else if (dtype == PEXP_F32) launch_stencil<float>(od, as<float>(const_cast<void*>(X)), as<float>(Y), nvec, transpose, c->stream);
+    else return PEXP_ERR_INVALID_ARG;
+    PEXP_CUDA_TRY(cudaGetLastError());
+    PEXP_CUDA_TRY(cudaStreamSynchronize(c->stream));
+    return PEXP_OK;
+}
+
+int pexp_sai_solve(pexp_ctx* c, const pexp_operator* op, double gamma, const void* X, void* Y, int nvec,
+                   int dtype) {
+    if (!c || !op || !X || !Y || nvec < 1 || !(gamma > 0)) return PEXP_ERR_INVALID_ARG;
+    if (op->dim != 1 || op->bc != PEXP_BC_PERIODIC) return PEXP_ERR_UNSUPPORTED;
+    if (dtype != PEXP_F64 && dtype != PEXP_F32) return PEXP_ERR_INVALID_ARG;
+    cudaSetDevice(c->device);
+    const OpDesc od = make_opdesc(*op);
+    const int64_t n = od.n;
+    return guarded([&]() -> int {
+        const size_t es = dtype == PEXP_F64 ? 8 : 4;
+        size_t need = align_up(sizeof(double) * (sai_scratch_doubles(n, nvec) + 64)) + 2 * kAlign;
+        int r = ws_reserve(c, need);
+        if (r) return r;
+        c->ws_top = 0;
+        double* scr = as<double>(ws_alloc(c, sizeof(double) * (sai_scratch_doubles(n, nvec) + 64)));
+        Stage sg(c, 0);
+        std::vector<const void*> xs(nvec);
+        std::vector<void*> ys(nvec);
+        for (int v = 0; v < nvec; ++v) {
+            xs[v] = reinterpret_cast<const char*>(X) + es * n * v;
+            ys[v] = reinterpret_cast<char*>(Y) + es * n * v;
+        }
+        const void* const* dx = sg.put(xs.data(), nvec);
+        void* const* dy = sg.put(ys.data(), nvec);
+        sg.flush();
+        const SaiCoef cf = sai_coefficients(od, gamma);
+        if (dtype == PEXP_F64)
+            launch_sai_solve<double>(od, cf, reinterpret_cast<const double* const*>(dx), reinterpret_cast<double* const*>(dy), nvec, scr, c->stream);
+        else
+            launch_sai_solve<float>(od, cf, reinterpret_cast<const float* const*>(dx), reinterpret_cast<float* const*>(dy), nvec, scr, c->stream);
+        check_launch(c);
+        sync(c);
+        return PEXP_OK;
+    });
+}
+
+int pexp_small_expm(pexp_ctx* c, const double* M, double* E, int N, int batch) {
+    if (!c || !M || !E || N < 1 || N > 128 || batch < 1) return PEXP_ERR_INVALID_ARG;
+    cudaSetDevice(c->device);
+    return guarded([&]() -> int {
+        size_t need = align_up(sizeof(double) * small_expm_scratch_doubles(N) * batch) + kAlign;
+        int r = ws_reserve(c, need);
+        if (r) return r;
+        c->ws_top = 0;
+        double* scr = as<double>(ws_alloc(c, sizeof(double) * small_expm_scratch_doubles(N) * batch));
+        launch_small_expm_batch(M, E, N, batch, scr, c->stream);
+        check_launch(c);
+        sync(c);
+        return PEXP_OK;
+    });
+}
+
+int pexp_burgers_source(pexp_ctx* c, const pexp_operator* op, const void* U, void* G, int n_rows, int dtype,
+                        int form) {
+    if (!c || !op || !U || !G || n_rows < 1 || op->dim != 1) return PEXP_ERR_INVALID_ARG;
+    cudaSetDevice(c->device);
+    const OpDesc od = make_opdesc(*op);
+    const int64_t n = od.n;
+    const double inv2dx = 1.0 / (2.0 * (op->bc == PEXP_BC_PERIODIC ? op->Lx / n : op->Lx / (n + 1)));
+    if (dtype == PEXP_F64) launch_burgers_source<double>(od, as<double>(const_cast<void*>(U)), as<double>(G), n_rows, form, inv2dx, c->stream);
+    else if (dtype == PEXP_F32) launch_burgers_source<float>(od, as<float>(const_cast<void*>(U)), as<float>(G), n_rows, form, inv2dx, c->stream);
+    else return PEXP_ERR_INVALID_ARG;
+    PEXP_CUDA_TRY(cudaGetLastError());
+    PEXP_CUDA_TRY(cudaStreamSynchronize(c->stream));
+    return PEXP_OK;
+}
+
+}  // extern "C"

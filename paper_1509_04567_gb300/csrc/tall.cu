@@ -1,0 +1,766 @@
+// Kernels over n-length data for the PEBK hot path (sm_103a).
+//
+//  * central-difference stencil Y = A X (Sec. 3.1), 1D/2D, periodic/Dirichlet;
+//  * shift-and-invert solve Y = (I - gamma A)^{-1} X (Sec. 2.1) for 1D periodic A;
+//  * batched tall-skinny products X^T Y (projections, Gram matrices) and
+//    X T (block updates) used by block Gram-Schmidt and the source compression;
+//  * reconstruction u(t_i) = u0 + V y(t_i) (eq. superposition);
+//  * Burgers nonlinear source -u u_x (Sec. 4) and small helpers.
+#include <math.h>
+#include <stdio.h>
+
+#include <algorithm>
+
+#include "common.cuh"
+
+namespace pexp {
+
+int fail_cuda(cudaError_t e, const char* what, const char* file, int line) {
+    fprintf(stderr, "pexp: CUDA error %s (%d) in %s at %s:%d\n", cudaGetErrorString(e), (int)e, what, file,
+            line);
+    return PEXP_ERR_CUDA;
+}
+
+static int grid_for(int64_t work, int threads, int per_thread = 1) {
+    int64_t b = (work + (int64_t)threads * per_thread - 1) / ((int64_t)threads * per_thread);
+    if (b < 1) b = 1;
+    if (b > 65535LL * 8) b = 65535LL * 8;
+    return (int)b;
+}
+
+// =====================================================================================
+// Stencil
+// =====================================================================================
+template <typename T>
+__device__ __forceinline__ T stencil_at(const OpDesc& op, const T* __restrict__ x, int64_t k, int transpose) {
+    const T u = x[k];
+    T acc = T(0);
+    {
+        const Dim1& D = op.x;
+        int64_t ix = (op.dim == 1) ? k : (k % D.n);
+        T um, up;
+        if (ix > 0) um = x[k - 1];
+        else um = D.periodic ? x[k + D.n - 1] : T(0);
+        if (ix < D.n - 1) up = x[k + 1];
+        else up = D.periodic ? x[k - (D.n - 1)] : T(0);
+        const T d = T(D.d), c = transpose ? T(-D.c) : T(D.c);
+        acc = d * ((um - u) + (up - u)) - c * (up - um);
+    }
+    if (op.dim == 2) {
+        const Dim1& D = op.y;
+        int64_t iy = k / op.x.n;
+        T um, up;
+        if (iy > 0) um = x[k - D.stride];
+        else um = D.periodic ? x[k + (D.n - 1) * D.stride] : T(0);
+        if (iy < D.n - 1) up = x[k + D.stride];
+        else up = D.periodic ? x[k - (D.n - 1) * D.stride] : T(0);
+        const T d = T(D.d), c = transpose ? T(-D.c) : T(D.c);
+        acc += d * ((um - u) + (up - u)) - c * (up - um);
+    }
+    return acc;
+}
+
+template <typename T>
+__global__ void __launch_bounds__(256) k_stencil(OpDesc op, const T* const* __restrict__ Xp,
+                                                 T* const* __restrict__ Yp, const T* Xb, T* Yb,
+                                                 int transpose) {
+    const int v = blockIdx.y;
+    const T* x = Xp ? Xp[v] : Xb + (int64_t)v * op.n;
+    T* y = Yp ? Yp[v] : Yb + (int64_t)v * op.n;
+    for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < op.n;
+         k += (int64_t)gridDim.x * blockDim.x)
+        y[k] = stencil_at(op, x, k, transpose);
+}
+
+template <typename T>
+void launch_stencil(const OpDesc& op, const T* X, T* Y, int nvec, int transpose, cudaStream_t s) {
+    if (nvec <= 0) return;
+    dim3 g(std::min(grid_for(op.n, 256), std::max(1, 4 * kNumSM * 8 / nvec + 1)), nvec);
+    k_stencil<T><<<g, 256, 0, s>>>(op, nullptr, nullptr, X, Y, transpose);
+}
+
+template <typename T>
+void launch_stencil_ptrs(const OpDesc& op, const T* const* X, T* const* Y, int nvec, int transpose,
+                         cudaStream_t s) {
+    if (nvec <= 0) return;
+    dim3 g(std::min(grid_for(op.n, 256), std::max(1, 4 * kNumSM * 8 / nvec + 1)), nvec);
+    k_stencil<T><<<g, 256, 0, s>>>(op, X, Y, nullptr, nullptr, transpose);
+}
+
+// =====================================================================================
+// Burgers source g = -u u_x (Sec. 4), conservative or advective central form
+// =====================================================================================
+template <typename T>
+__global__ void __launch_bounds__(256) k_burgers(OpDesc op, const T* __restrict__ U, T* __restrict__ G,
+                                                 int form, double inv2dx) {
+    const int64_t row = blockIdx.y;
+    const T* u = U + row * op.n;
+    T* g = G + row * op.n;
+    const int periodic = op.x.periodic;
+    const T h2 = T(inv2dx);
+    for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < op.n;
+         k += (int64_t)gridDim.x * blockDim.x) {
+        T um, up;
+        if (k > 0) um = u[k - 1];
+        else um = periodic ? u[op.n - 1] : T(0);
+        if (k < op.n - 1) up = u[k + 1];
+        else up = periodic ? u[0] : T(0);
+        if (form == 0) g[k] = -(up - um) * (up + um) * (h2 * T(0.5));   // -(u_{k+1}^2 - u_{k-1}^2)/(4 dx)
+        else g[k] = -u[k] * (up - um) * h2;                               // -u_k (u_{k+1} - u_{k-1})/(2 dx)
+    }
+}
+
+template <typename T>
+void launch_burgers_source(const OpDesc& op, const T* U, T* G, int nrows, int form, double inv2dx,
+                           cudaStream_t s) {
+    if (nrows <= 0) return;
+    dim3 g(std::min(grid_for(op.n, 256), std::max(1, 4 * kNumSM * 8 / nrows + 1)), nrows);
+    k_burgers<T><<<g, 256, 0, s>>>(op, U, G, form, inv2dx);
+}
+
+// =====================================================================================
+// Shift-and-invert solve for a 1D periodic operator.
+//
+// (I - gamma A) has constant diagonals p (sub), q (main), r (super) and wraps
+// around.  It factors as c (I - alpha S^{-1})(I - beta S) with S the cyclic
+// shift, |alpha|, |beta| < 1, c = (q + sqrt(q^2 - 4 p r)) / 2, alpha = -p/c,
+// beta = -r/c.  So y = (1/c) x with
+//     w_i = v_i + alpha w_{i-1}      (forward, circular)
+//     x_i = w_i + beta  x_{i+1}      (backward, circular)
+// Each recurrence is a scan of affine maps f(z) = a z + b: chunks of 2048
+// elements per CTA (8 per thread), a CTA-wide scan, and a circular sum over
+// chunk summaries for the carry into each chunk (terms decay like alpha^2048).
+// =====================================================================================
+constexpr int kSaiThreads = 256;
+constexpr int kSaiPer = 8;
+constexpr int kSaiChunk = kSaiThreads * kSaiPer;
+
+SaiCoef sai_coefficients(const OpDesc& op, double gamma) {
+    const Dim1& D = op.x;
+    // (A u)_i = (d + c) u_{i-1} - 2 d u_i + (d - c) u_{i+1}
+    const double p = -gamma * (D.d + D.c);
+    const double q = 1.0 + 2.0 * gamma * D.d;
+    const double r = -gamma * (D.d - D.c);
+    const double disc = q * q - 4.0 * p * r;
+    const double c = 0.5 * (q + sqrt(disc));
+    SaiCoef cf;
+    cf.alpha = -p / c;
+    cf.beta = -r / c;
+    cf.inv_c = 1.0 / c;
+    cf.alpha_n = pow(cf.alpha, (double)D.n);
+    cf.beta_n = pow(cf.beta, (double)D.n);
+    return cf;
+}
+
+size_t sai_scratch_doubles(int64_t n, int nvec) {
+    const int64_t nch = (n + kSaiChunk - 1) / kSaiChunk;
+    return (size_t)4 * nch * nvec;
+}
+
+// Arithmetic of the recurrences.  FP64 data use double.  FP32 data use a
+// double-float pair (hi, lo) -- Dekker/Knuth error-free sum and FMA product --
+// because the recurrences accumulate ~1/(1-alpha) terms and plain FP32 rounding
+// would leave smooth, correlated errors of ~1e-6 in every solve.
+struct DF {
+    float hi, lo;
+};
+__device__ __forceinline__ DF df_fast2sum(float a, float b) {
+    const float s = a + b;
+    return DF{s, b - (s - a)};
+}
+__device__ __forceinline__ DF df_add(DF a, DF b) {
+    const float s = a.hi + b.hi;
+    const float bb = s - a.hi;
+    const float e = (a.hi - (s - bb)) + (b.hi - bb);
+    return df_fast2sum(s, e + (a.lo + b.lo));
+}
+__device__ __forceinline__ DF df_mul(DF a, DF b) {
+    const float p = a.hi * b.hi;
+    float e = fmaf(a.hi, b.hi, -p);
+    e = fmaf(a.hi, b.lo, e);
+    e = fmaf(a.lo, b.hi, e);
+    return df_fast2sum(p, e);
+}
+__device__ __forceinline__ double rmul(double a, double b) { return a * b; }
+__device__ __forceinline__ DF rmul(DF a, DF b) { return df_mul(a, b); }
+__device__ __forceinline__ double rfma(double a, double b, double c) { return fma(a, b, c); }
+__device__ __forceinline__ DF rfma(DF a, DF b, DF c) { return df_add(df_mul(a, b), c); }
+__device__ __forceinline__ double rdbl(double a) { return a; }
+__device__ __forceinline__ double rdbl(DF a) { return (double)a.hi + (double)a.lo; }
+template <typename R> __device__ __forceinline__ R rfrom(double x);
+template <> __device__ __forceinline__ double rfrom<double>(double x) { return x; }
+template <> __device__ __forceinline__ DF rfrom<DF>(double x) {
+    const float h = (float)x;
+    return DF{h, (float)(x - (double)h)};
+}
+template <typename T> struct SaiR { using R = double; };
+template <> struct SaiR<float> { using R = DF; };
+template <typename T, typename R> __device__ __forceinline__ T rto(R x);
+template <> __device__ __forceinline__ double rto<double, double>(double x) { return x; }
+template <> __device__ __forceinline__ float rto<float, DF>(DF x) { return x.hi + x.lo; }
+// Store a recurrence value: FP64 as is; FP32 as a (hi, lo) pair when a low-part
+// array is given (the working block keeps double-float precision), else rounded.
+template <typename T> __device__ __forceinline__ void store_r(T* y, T* ylo, int64_t k, double v) { y[k] = v; }
+template <typename T> __device__ __forceinline__ void store_r(T* y, T* ylo, int64_t k, DF v) {
+    if (ylo) { y[k] = v.hi; ylo[k] = v.lo; } else { y[k] = v.hi + v.lo; }
+}
+template <typename T, typename R> __device__ __forceinline__ R load_r(T hi, T lo);
+template <> __device__ __forceinline__ double load_r<double, double>(double hi, double lo) { return hi; }
+template <> __device__ __forceinline__ DF load_r<float, DF>(float hi, float lo) { return DF{hi, lo}; }
+
+// Hillis-Steele scan of affine maps f(z) = a z + b over the CTA in "virtual" order
+// v (v = t forward, v = NT-1-t backward); map v is applied after maps < v.
+// Returns the exclusive composition for this thread and the CTA total.
+template <typename R>
+__device__ __forceinline__ void cta_affine_scan(R a, R b, bool reverse, R* sa, R* sb, R& ea, R& eb, R& ta,
+                                                R& tb) {
+    const int t = threadIdx.x;
+    const int v = reverse ? (kSaiThreads - 1 - t) : t;
+    sa[v] = a;
+    sb[v] = b;
+    __syncthreads();
+    for (int d = 1; d < kSaiThreads; d <<= 1) {
+        const R ca = sa[v], cb = sb[v];
+        R pa = rfrom<R>(1.0), pb = rfrom<R>(0.0);
+        const bool has = v >= d;
+        if (has) {
+            pa = sa[v - d];
+            pb = sb[v - d];
+        }
+        __syncthreads();
+        if (has) {
+            sa[v] = rmul(ca, pa);
+            sb[v] = rfma(ca, pb, cb);
+        }
+        __syncthreads();
+    }
+    if (v > 0) {
+        ea = sa[v - 1];
+        eb = sb[v - 1];
+    } else {
+        ea = rfrom<R>(1.0);
+        eb = rfrom<R>(0.0);
+    }
+    ta = sa[kSaiThreads - 1];
+    tb = sb[kSaiThreads - 1];
+    __syncthreads();
+}
+
+template <typename T>
+__device__ __forceinline__ int sai_load(const T* __restrict__ x, int64_t n, int64_t start, T* vals) {
+    int cnt = 0;
+#pragma unroll
+    for (int j = 0; j < kSaiPer; ++j) {
+        int64_t k = start + j;
+        if (k < n) {
+            vals[j] = x[k];
+            cnt = j + 1;
+        } else {
+            vals[j] = T(0);
+        }
+    }
+    return cnt;
+}
+
+template <typename R>
+__device__ __forceinline__ R ipow(R x, int e) {
+    R r = rfrom<R>(1.0);
+    for (int i = 0; i < e; ++i) r = rmul(r, x);
+    return r;
+}
+
+// Pass 1: chunk summaries of the forward recurrence with zero carry-in.
+template <typename T>
+__global__ void __launch_bounds__(kSaiThreads) k_sai_fwd_ends(int64_t n, int nch, double alpha,
+                                                              const T* const* __restrict__ Xp,
+                                                              double* __restrict__ ends,
+                                                              double* __restrict__ decays) {
+    using R = typename SaiR<T>::R;
+    __shared__ R sa[kSaiThreads], sb[kSaiThreads];
+    const int v = blockIdx.y, ch = blockIdx.x;
+    const T* x = Xp[v];
+    const int64_t start = (int64_t)ch * kSaiChunk + (int64_t)threadIdx.x * kSaiPer;
+    T vals[kSaiPer];
+    const int cnt = sai_load(x, n, start, vals);
+    const R al = rfrom<R>(alpha);
+    R b = rfrom<R>(0.0);
+    for (int j = 0; j < cnt; ++j) b = rfma(al, b, rfrom<R>((double)vals[j]));
+    R a = ipow(al, cnt);
+    R ea, eb, ta, tb;
+    cta_affine_scan<R>(a, b, false, sa, sb, ea, eb, ta, tb);
+    if (threadIdx.x == 0) {
+        ends[(int64_t)v * nch + ch] = rdbl(tb);
+        decays[(int64_t)v * nch + ch] = rdbl(ta);
+    }
+}
+
+// Circular carry into chunk `ch` from the chunk summaries (sum_k prod * end) / (1 - rho^n).
+__device__ __forceinline__ double sai_carry(const double* ends, const double* decays, int nch, int ch,
+                                            int dir, double rho_n) {
+    double sum = 0.0, prod = 1.0;
+    for (int k = 1; k <= nch; ++k) {
+        int c = ch - dir * k;
+        c %= nch;
+        if (c < 0) c += nch;
+        sum += prod * ends[c];
+        prod *= decays[c];
+        if (fabs(prod) < 1e-30) break;
+    }
+    return sum / (1.0 - rho_n);
+}
+
+// Pass 2: forward recurrence with carries -> w (written to Y); summaries of the
+// backward recurrence of w with zero carry from the right.
+template <typename T>
+__global__ void __launch_bounds__(kSaiThreads) k_sai_fwd_apply(int64_t n, int nch, double alpha, double beta,
+                                                               double alpha_n, const T* const* __restrict__ Xp,
+                                                               T* const* __restrict__ Yp, T* const* __restrict__ Ylo,
+                                                               const double* __restrict__ fends,
+                                                               const double* __restrict__ fdecays,
+                                                               double* __restrict__ bends,
+                                                               double* __restrict__ bdecays) {
+    using R = typename SaiR<T>::R;
+    __shared__ R sa[kSaiThreads], sb[kSaiThreads];
+    __shared__ double carry_in;
+    const int v = blockIdx.y, ch = blockIdx.x;
+    const T* x = Xp[v];
+    T* y = Yp[v];
+    T* ylo = Ylo ? Ylo[v] : nullptr;
+    if (threadIdx.x == 0)
+        carry_in = sai_carry(fends + (int64_t)v * nch, fdecays + (int64_t)v * nch, nch, ch, +1, alpha_n);
+    const int64_t start = (int64_t)ch * kSaiChunk + (int64_t)threadIdx.x * kSaiPer;
+    T vals[kSaiPer];
+    const int cnt = sai_load(x, n, start, vals);
+    const R al = rfrom<R>(alpha), be = rfrom<R>(beta);
+    R b = rfrom<R>(0.0);
+    for (int j = 0; j < cnt; ++j) b = rfma(al, b, rfrom<R>((double)vals[j]));
+    R a = ipow(al, cnt);
+    R ea, eb, ta, tb;
+    cta_affine_scan<R>(a, b, false, sa, sb, ea, eb, ta, tb);  // contains __syncthreads: carry_in visible
+    R w = rfma(ea, rfrom<R>(carry_in), eb);
+    R wv[kSaiPer];
+    for (int j = 0; j < cnt; ++j) {
+        w = rfma(al, w, rfrom<R>((double)vals[j]));
+        wv[j] = w;
+        store_r<T>(y, ylo, start + j, w);
+    }
+    // backward summaries over this thread's w values (kept at full precision)
+    R gb = rfrom<R>(0.0);
+    for (int j = cnt - 1; j >= 0; --j) gb = rfma(be, gb, wv[j]);
+    R ga = ipow(be, cnt);
+    cta_affine_scan<R>(ga, gb, true, sa, sb, ea, eb, ta, tb);
+    if (threadIdx.x == 0) {
+        bends[(int64_t)v * nch + ch] = rdbl(tb);
+        bdecays[(int64_t)v * nch + ch] = rdbl(ta);
+    }
+}
+
+// Pass 3: backward recurrence with carries, scaled by 1/c, in place on Y.  The
+// intermediate w is re-read from Y in the data type; for FP32 data its rounding
+// (relative 6e-8, uncorrelated) is the only FP32 error left in the solve.
+template <typename T>
+__global__ void __launch_bounds__(kSaiThreads) k_sai_bwd_apply(int64_t n, int nch, double beta, double beta_n,
+                                                               double inv_c, T* const* __restrict__ Yp,
+                                                               T* const* __restrict__ Ylo,
+                                                               const double* __restrict__ bends,
+                                                               const double* __restrict__ bdecays) {
+    using R = typename SaiR<T>::R;
+    __shared__ R sa[kSaiThreads], sb[kSaiThreads];
+    __shared__ double carry_in;
+    const int v = blockIdx.y, ch = blockIdx.x;
+    T* y = Yp[v];
+    T* ylo = Ylo ? Ylo[v] : nullptr;
+    if (threadIdx.x == 0)
+        carry_in = sai_carry(bends + (int64_t)v * nch, bdecays + (int64_t)v * nch, nch, ch, -1, beta_n);
+    const int64_t start = (int64_t)ch * kSaiChunk + (int64_t)threadIdx.x * kSaiPer;
+    T vals[kSaiPer], lows[kSaiPer];
+    const int cnt = sai_load<T>(y, n, start, vals);
+    if (ylo) sai_load<T>(ylo, n, start, lows);
+    R wv[kSaiPer];
+    for (int j = 0; j < cnt; ++j) wv[j] = load_r<T, R>(vals[j], ylo ? lows[j] : T(0));
+    const R be = rfrom<R>(beta);
+    R gb = rfrom<R>(0.0);
+    for (int j = cnt - 1; j >= 0; --j) gb = rfma(be, gb, wv[j]);
+    R ga = ipow(be, cnt);
+    R ea, eb, ta, tb;
+    cta_affine_scan<R>(ga, gb, true, sa, sb, ea, eb, ta, tb);
+    R xv = rfma(ea, rfrom<R>(carry_in), eb);
+    const R ic = rfrom<R>(inv_c);
+    for (int j = cnt - 1; j >= 0; --j) {
+        xv = rfma(be, xv, wv[j]);
+        store_r<T>(y, ylo, start + j, rmul(xv, ic));
+    }
+}
+
+template <typename T>
+void launch_sai_solve(const OpDesc& op, const SaiCoef& cf, const T* const* X, T* const* Y, T* const* Ylo, int nvec,
+                      double* scratch, cudaStream_t s) {
+    if (nvec <= 0) return;
+    const int64_t n = op.n;
+    const int nch = (int)((n + kSaiChunk - 1) / kSaiChunk);
+    double* fends = scratch;
+    double* fdec = fends + (size_t)nch * nvec;
+    double* bends = fdec + (size_t)nch * nvec;
+    double* bdec = bends + (size_t)nch * nvec;
+    dim3 g(nch, nvec);
+    k_sai_fwd_ends<T><<<g, kSaiThreads, 0, s>>>(n, nch, cf.alpha, X, fends, fdec);
+    k_sai_fwd_apply<T><<<g, kSaiThreads, 0, s>>>(n, nch, cf.alpha, cf.beta, cf.alpha_n, X, Y, Ylo, fends, fdec,
+                                                  bends, bdec);
+    k_sai_bwd_apply<T><<<g, kSaiThreads, 0, s>>>(n, nch, cf.beta, cf.beta_n, cf.inv_c, Y, Ylo, bends, bdec);
+}
+
+// =====================================================================================
+// Batched tall-skinny products
+// =====================================================================================
+template <typename T>
+struct Acc;
+template <>
+struct Acc<double> {
+    double s;
+    __device__ __forceinline__ void zero() { s = 0.0; }
+    __device__ __forceinline__ void add(double x, double y) { s = fma(x, y, s); }
+    __device__ __forceinline__ double get() const { return s; }
+};
+// FP32 products summed with Neumaier's compensated summation: the running error
+// stays near the FP32 unit roundoff independent of the number of rows.
+template <>
+struct Acc<float> {
+    float s, c;
+    __device__ __forceinline__ void zero() { s = 0.f; c = 0.f; }
+    __device__ __forceinline__ void add(float x, float y) {
+        const float v = x * y;
+        const float t = s + v;
+        if (fabsf(s) >= fabsf(v)) c += (s - t) + v;
+        else c += (v - t) + s;
+        s = t;
+    }
+    __device__ __forceinline__ double get() const { return (double)s + (double)c; }
+};
+
+// FP32 data, exact products (x*y = p + e via FMA) summed in a double-float (hi, lo)
+// accumulator: the Gram matrix of FP32 data comes out accurate to ~1e-14.
+struct AccDF {
+    float hi, lo;
+    __device__ __forceinline__ void zero() { hi = 0.f; lo = 0.f; }
+    __device__ __forceinline__ void add(float x, float y) {
+        const float p = x * y;
+        const float e = fmaf(x, y, -p);
+        const float s = hi + p;
+        const float bp = s - hi;
+        const float err = (hi - (s - bp)) + (p - bp);
+        const float l = lo + (err + e);
+        hi = s + l;
+        lo = l - (hi - s);
+    }
+    __device__ __forceinline__ double get() const { return (double)hi + (double)lo; }
+};
+template <typename T, bool EXACT>
+struct AccSel { using type = Acc<T>; };
+template <>
+struct AccSel<float, true> { using type = AccDF; };
+
+__device__ __forceinline__ double warp_sum(double v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
+struct TnGeom {
+    int nchunks;
+    int64_t rows;
+};
+static TnGeom tn_geom(int ntasks, int64_t n) {
+    TnGeom g;
+    int want = (4 * kNumSM + ntasks - 1) / ntasks;
+    int64_t maxch = (n + 2047) / 2048;
+    g.nchunks = (int)std::max<int64_t>(1, std::min<int64_t>(want, maxch));
+    g.rows = (n + g.nchunks - 1) / g.nchunks;
+    g.rows = (g.rows + 31) / 32 * 32;
+    g.nchunks = (int)((n + g.rows - 1) / g.rows);
+    return g;
+}
+
+// Upper bound for any launch with at most `ntasks` tasks: ntasks * nchunks <= 4*152 + ntasks.
+size_t ts_tn_partial_doubles(int ntasks, int max_pq, int64_t n) {
+    (void)n;
+    return (size_t)(4 * kNumSM + ntasks + 8) * (size_t)max_pq;
+}
+
+template <typename T, int GA, int QM, bool EXACT>
+__global__ void __launch_bounds__(256) k_ts_tn(const TsTask<T>* __restrict__ tasks, int64_t n, int64_t rows,
+                                               int nchunks, int pq_stride, double* __restrict__ partial) {
+    const TsTask<T> tk = tasks[blockIdx.y];
+    const int ch = blockIdx.x;
+    const int64_t r0 = (int64_t)ch * rows;
+    const int64_t r1 = (r0 + rows < n) ? r0 + rows : n;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+    double* pout = partial + ((size_t)blockIdx.y * nchunks + ch) * pq_stride;
+    const int p = tk.p, q = tk.q, q1 = tk.q1;
+    for (int a0 = warp * GA; a0 < p; a0 += nw * GA) {
+        typename AccSel<T, EXACT>::type acc[GA][QM];
+#pragma unroll
+        for (int g = 0; g < GA; ++g)
+#pragma unroll
+            for (int c = 0; c < QM; ++c) acc[g][c].zero();
+        for (int64_t r = r0 + lane; r < r1; r += 32) {
+            T yv[QM];
+            const T ysh = tk.ys ? T(tk.ys[r]) : T(0);
+#pragma unroll
+            for (int c = 0; c < QM; ++c) {
+                if (c < q) yv[c] = (c < q1 ? (tk.Y ? tk.Y[(int64_t)c * tk.ldy + r] : T(0)) : tk.Y2[(int64_t)(c - q1) * tk.ldy2 + r]) + ysh;
+                else yv[c] = T(0);
+            }
+            const T xsh = tk.xs ? T(tk.xs[r]) : T(0);
+#pragma unroll
+            for (int g = 0; g < GA; ++g) {
+                const int a = a0 + g;
+                if (a < p) {
+                    const T xv = (tk.X ? tk.X[(int64_t)a * tk.ldx + r] : T(0)) + xsh;
+#pragma unroll
+                    for (int c = 0; c < QM; ++c)
+                        if (c < q) acc[g][c].add(xv, yv[c]);
+                }
+            }
+        }
+#pragma unroll
+        for (int g = 0; g < GA; ++g) {
+            const int a = a0 + g;
+#pragma unroll
+            for (int c = 0; c < QM; ++c) {
+                double v = warp_sum(acc[g][c].get());
+                if (lane == 0 && a < p && c < q) pout[a + c * p] = v;
+            }
+        }
+    }
+}
+
+template <typename T>
+__global__ void __launch_bounds__(256) k_ts_reduce(const TsTask<T>* __restrict__ tasks, int nchunks, int pq_stride,
+                                                   const double* __restrict__ partial) {
+    const TsTask<T> tk = tasks[blockIdx.x];
+    const int pq = tk.p * tk.q;
+    const double* base = partial + (size_t)blockIdx.x * nchunks * pq_stride;
+    for (int e = threadIdx.x; e < pq; e += blockDim.x) {
+        double s = 0.0;
+        for (int c = 0; c < nchunks; ++c) s += base[(size_t)c * pq_stride + e];
+        tk.out[e] = s;
+    }
+}
+
+// The accumulator tile (columns of X per warp pass x columns of Y) is chosen from
+// max_q.  exact != 0 selects exact-product double-float accumulation for FP32 data.
+template <typename T, bool EXACT>
+static void tn_dispatch(const TsTask<T>* tasks_dev, int ntasks, int max_pq, int max_q, int64_t n, double* partial,
+                        cudaStream_t s) {
+    TnGeom g = tn_geom(ntasks, n);
+    dim3 grid(g.nchunks, ntasks);
+    if (max_q <= 4) k_ts_tn<T, 4, 4, EXACT><<<grid, 256, 0, s>>>(tasks_dev, n, g.rows, g.nchunks, max_pq, partial);
+    else if (max_q <= 8) k_ts_tn<T, 4, 8, EXACT><<<grid, 256, 0, s>>>(tasks_dev, n, g.rows, g.nchunks, max_pq, partial);
+    else if (max_q <= 16) k_ts_tn<T, 2, 16, EXACT><<<grid, 256, 0, s>>>(tasks_dev, n, g.rows, g.nchunks, max_pq, partial);
+    else k_ts_tn<T, 1, 48, EXACT><<<grid, 256, 0, s>>>(tasks_dev, n, g.rows, g.nchunks, max_pq, partial);
+    k_ts_reduce<T><<<ntasks, 256, 0, s>>>(tasks_dev, g.nchunks, max_pq, partial);
+}
+
+template <typename T>
+void launch_ts_tn(const TsTask<T>* tasks_dev, int ntasks, int max_pq, int max_q, int64_t n, double* partial,
+                  cudaStream_t s, int exact) {
+    if (ntasks <= 0) return;
+    if (exact) tn_dispatch<T, true>(tasks_dev, ntasks, max_pq, max_q, n, partial, s);
+    else tn_dispatch<T, false>(tasks_dev, ntasks, max_pq, max_q, n, partial, s);
+}
+
+template <typename T, int QM>
+__global__ void __launch_bounds__(256) k_ts_nn(const TsTask<T>* __restrict__ tasks, int64_t n) {
+    const TsTask<T> tk = tasks[blockIdx.y];
+    extern __shared__ double smem_nn[];
+    T* sT = reinterpret_cast<T*>(smem_nn);
+    const int p = tk.p, q = tk.q;
+    for (int e = threadIdx.x; e < p * q; e += blockDim.x) {
+        const int a = e % p, c = e / p;
+        sT[e] = T(tk.Tm[a + (int64_t)c * tk.ldt]);
+    }
+    __syncthreads();
+    const bool inplace = (const void*)tk.Z == (const void*)tk.X;
+    const T alpha = T(tk.alpha), beta = T(tk.beta);
+    for (int64_t r = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; r < n; r += (int64_t)gridDim.x * blockDim.x) {
+        const T xsh = tk.xs ? T(tk.xs[r]) : T(0);
+        T acc[QM];
+#pragma unroll
+        for (int c = 0; c < QM; ++c) acc[c] = T(0);
+        if (inplace) {
+            T xr[QM];
+#pragma unroll
+            for (int a = 0; a < QM; ++a) xr[a] = (a < p) ? tk.X[(int64_t)a * tk.ldx + r] + xsh : T(0);
+#pragma unroll
+            for (int a = 0; a < QM; ++a)
+                if (a < p) {
+#pragma unroll
+                    for (int c = 0; c < QM; ++c)
+                        if (c < q) acc[c] = fma(xr[a], sT[a + c * p], acc[c]);
+                }
+        } else {
+            for (int a = 0; a < p; ++a) {
+                const T xv = (tk.X ? tk.X[(int64_t)a * tk.ldx + r] : T(0)) + xsh;
+#pragma unroll
+                for (int c = 0; c < QM; ++c)
+                    if (c < q) acc[c] = fma(xv, sT[a + c * p], acc[c]);
+            }
+        }
+#pragma unroll
+        for (int c = 0; c < QM; ++c)
+            if (c < q) {
+                T* z = tk.Z + (int64_t)c * tk.ldz + r;
+                *z = (tk.beta == 0.0) ? alpha * acc[c] : fma(beta, *z, alpha * acc[c]);
+            }
+    }
+}
+
+template <typename T>
+void launch_ts_nn(const TsTask<T>* tasks_dev, int ntasks, int max_pq, int64_t n, cudaStream_t s) {
+    if (ntasks <= 0) return;
+    int bx = std::max(1, std::min(grid_for(n, 256), (4 * kNumSM * 4 + ntasks - 1) / ntasks));
+    dim3 grid(bx, ntasks);
+    size_t sm = (size_t)max_pq * sizeof(T);
+    if (sm > 48 * 1024) cudaFuncSetAttribute(k_ts_nn<T, 16>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    k_ts_nn<T, 16><<<grid, 256, sm, s>>>(tasks_dev, n);
+}
+
+// =====================================================================================
+// Reconstruction u(t) = u0 + V y(t)
+// =====================================================================================
+template <typename T, typename TO, int RM>
+__global__ void __launch_bounds__(256) k_recon(const ReconTask<T>* __restrict__ tasks, int64_t n,
+                                               const double* __restrict__ u0, TO* __restrict__ out, int64_t ldo) {
+    const ReconTask<T> tk = tasks[blockIdx.y];
+    extern __shared__ double smem_rc[];
+    const int K = tk.K1 + tk.K2;
+    // coefficients of rows r0..r0+ns-1 as T: sc[r*K + a]
+    T* sc = reinterpret_cast<T*>(smem_rc);
+    for (int e = threadIdx.x; e < tk.ns * K; e += blockDim.x) {
+        const int r = e / K, a = e % K;
+        sc[e] = (a < tk.K1) ? T(tk.C1[(int64_t)(tk.r0 + r) * tk.ldc1 + a])
+                            : T(tk.C2[(int64_t)(tk.r0 + r) * tk.ldc2 + (a - tk.K1)]);
+    }
+    __syncthreads();
+    for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < n; k += (int64_t)gridDim.x * blockDim.x) {
+        const T base = u0 ? T(u0[k]) : T(0);
+        for (int rg = 0; rg < tk.ns; rg += RM) {
+            T acc[RM];
+#pragma unroll
+            for (int r = 0; r < RM; ++r) acc[r] = base;
+            for (int a = 0; a < tk.K1; ++a) {
+                const T v = tk.V1[(int64_t)a * tk.ld1 + k];
+#pragma unroll
+                for (int r = 0; r < RM; ++r)
+                    if (rg + r < tk.ns) acc[r] = fma(v, sc[(rg + r) * K + a], acc[r]);
+            }
+            for (int a = 0; a < tk.K2; ++a) {
+                const T v = tk.V2[(int64_t)a * tk.ld2 + k];
+#pragma unroll
+                for (int r = 0; r < RM; ++r)
+                    if (rg + r < tk.ns) acc[r] = fma(v, sc[(rg + r) * K + tk.K1 + a], acc[r]);
+            }
+#pragma unroll
+            for (int r = 0; r < RM; ++r)
+                if (rg + r < tk.ns) out[(tk.i0 + rg + r) * ldo + k] = TO(acc[r]);
+        }
+    }
+}
+
+template <typename T, typename TO>
+void launch_recon(const ReconTask<T>* tasks_dev, int ntasks, int max_ns, int64_t n, const double* u0, TO* out,
+                  int64_t ldo, int max_c_doubles, cudaStream_t s) {
+    (void)max_ns;
+    if (ntasks <= 0) return;
+    int bx = std::max(1, std::min(grid_for(n, 256), (4 * kNumSM * 4 + ntasks - 1) / ntasks));
+    dim3 grid(bx, ntasks);
+    size_t sm = (size_t)max_c_doubles * sizeof(T);
+    if (sm > 48 * 1024)
+        cudaFuncSetAttribute(k_recon<T, TO, 17>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    k_recon<T, TO, 17><<<grid, 256, sm, s>>>(tasks_dev, n, u0, out, ldo);
+}
+
+// =====================================================================================
+// Helpers
+// =====================================================================================
+template <typename TI, typename TO>
+__global__ void k_convert(const TI* __restrict__ x, TO* __restrict__ y, int64_t count) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < count; i += (int64_t)gridDim.x * blockDim.x)
+        y[i] = TO(x[i]);
+}
+template <typename TI, typename TO>
+void launch_convert(const TI* x, TO* y, int64_t count, cudaStream_t s) {
+    if (count <= 0) return;
+    k_convert<TI, TO><<<std::min(grid_for(count, 256), 4 * kNumSM * 8), 256, 0, s>>>(x, y, count);
+}
+
+template <typename T>
+__global__ void k_add(T* __restrict__ y, const T* __restrict__ x, int64_t count) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < count; i += (int64_t)gridDim.x * blockDim.x)
+        y[i] += x[i];
+}
+template <typename T>
+void launch_add(T* y, const T* x, int64_t count, cudaStream_t s) {
+    if (count <= 0) return;
+    k_add<T><<<std::min(grid_for(count, 256), 4 * kNumSM * 8), 256, 0, s>>>(y, x, count);
+}
+
+template <typename T>
+__global__ void __launch_bounds__(256) k_row_diff_norms(const T* __restrict__ A, const T* __restrict__ B, int64_t n,
+                                                       int nrows, double* __restrict__ out) {
+    const int row = blockIdx.x;
+    const T* a = A + (int64_t)row * n;
+    const T* b = B + (int64_t)row * n;
+    double sd = 0.0, sa = 0.0;
+    for (int64_t k = threadIdx.x; k < n; k += blockDim.x) {
+        const double av = (double)a[k], bv = (double)b[k];
+        sd = fma(av - bv, av - bv, sd);
+        sa = fma(av, av, sa);
+    }
+    __shared__ double r1[8], r2[8];
+    sd = warp_sum(sd);
+    sa = warp_sum(sa);
+    if ((threadIdx.x & 31) == 0) {
+        r1[threadIdx.x >> 5] = sd;
+        r2[threadIdx.x >> 5] = sa;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double t1 = 0, t2 = 0;
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) {
+            t1 += r1[w];
+            t2 += r2[w];
+        }
+        out[row] = t1;
+        out[nrows + row] = t2;
+    }
+}
+template <typename T>
+void launch_row_diff_norms(const T* A, const T* B, int64_t n, int nrows, double* out, cudaStream_t s) {
+    if (nrows <= 0) return;
+    k_row_diff_norms<T><<<nrows, 256, 0, s>>>(A, B, n, nrows, out);
+}
+
+// ---------------------------------------------------------------- instantiations
+#define PEXP_INST_T(T)                                                                                    \
+    template void launch_stencil<T>(const OpDesc&, const T*, T*, int, int, cudaStream_t);                 \
+    template void launch_stencil_ptrs<T>(const OpDesc&, const T* const*, T* const*, int, int, cudaStream_t); \
+    template void launch_burgers_source<T>(const OpDesc&, const T*, T*, int, int, double, cudaStream_t);  \
+    template void launch_sai_solve<T>(const OpDesc&, const SaiCoef&, const T* const*, T* const*, T* const*,  \
+                                      int, double*, cudaStream_t);                                        \
+    template void launch_ts_tn<T>(const TsTask<T>*, int, int, int, int64_t, double*, cudaStream_t, int);   \
+    template void launch_ts_nn<T>(const TsTask<T>*, int, int, int64_t, cudaStream_t);                     \
+    template void launch_recon<T, float>(const ReconTask<T>*, int, int, int64_t, const double*, float*,    \
+                                         int64_t, int, cudaStream_t);                                     \
+    template void launch_recon<T, double>(const ReconTask<T>*, int, int, int64_t, const double*, double*,  \
+                                          int64_t, int, cudaStream_t);                                    \
+    template void launch_row_diff_norms<T>(const T*, const T*, int64_t, int, double*, cudaStream_t); \
+    template void launch_add<T>(T*, const T*, int64_t, cudaStream_t);
+PEXP_INST_T(double)
+PEXP_INST_T(float)
+template void launch_convert<double, float>(const double*, float*, int64_t, cudaStream_t);
+template void launch_convert<float, double>(const float*, double*, int64_t, cudaStream_t);
+template void launch_convert<double, double>(const double*, double*, int64_t, cudaStream_t);
+template void launch_convert<float, float>(const float*, float*, int64_t, cudaStream_t);
+
+}  // namespace pexp

@@ -1,0 +1,252 @@
+"""ctypes binding of the PEBK C ABI (include/pexp.h).
+
+Argument marshalling only: every step of the solver runs in the CUDA library.
+The library is loaded from paper_1509_04567_gb300/_lib/libpexp.so; if it is
+missing the import raises -- there is no fallback implementation.
+
+Device buffers are passed as torch CUDA tensors (their data_ptr), host buffers
+as numpy arrays.  Time series use the time-major layout of the C ABI: a tensor of
+shape (n_out, n), C-contiguous.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+from dataclasses import dataclass, fields
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "_lib", "libpexp.so")
+
+OK = 0
+ERR_INVALID_ARG = -1
+ERR_OOM = -2
+ERR_CUDA = -3
+ERR_BREAKDOWN = -4
+ERR_NOT_CONVERGED = -5
+ERR_WR_NOT_CONVERGED = -6
+ERR_TIMEOUT = -7
+ERR_UNSUPPORTED = -8
+
+BC_PERIODIC = 0
+BC_DIRICHLET0 = 1
+KRYLOV_POLY = 0
+KRYLOV_SAI = 1
+FP64 = 0
+MIXED = 1
+F64 = 0
+F32 = 1
+
+# Symbols declared in include/pexp.h (checked by the CPU tests).
+EXPORTS = ["pexp_create", "pexp_destroy", "pexp_set_stream", "pexp_default_options", "pexp_status_string",
+           "pexp_solve_linear", "pexp_solve_linear_host", "pexp_solve_burgers", "pexp_apply_operator",
+           "pexp_sai_solve", "pexp_small_expm", "pexp_burgers_source"]
+
+
+class Operator(C.Structure):
+    _fields_ = [("dim", C.c_int), ("nx", C.c_int64), ("ny", C.c_int64), ("bc", C.c_int),
+                ("ax", C.c_double), ("ay", C.c_double), ("nu", C.c_double), ("Lx", C.c_double),
+                ("Ly", C.c_double)]
+
+
+class Options(C.Structure):
+    _fields_ = [("T", C.c_double), ("P", C.c_int), ("n_out", C.c_int), ("tol", C.c_double),
+                ("svd_tol", C.c_double), ("max_rank", C.c_int), ("restart_len", C.c_int),
+                ("max_restarts", C.c_int), ("krylov", C.c_int), ("sai_gamma", C.c_double),
+                ("precision", C.c_int), ("wr_max_iter", C.c_int), ("wr_tol", C.c_double),
+                ("burgers_form", C.c_int)]
+
+
+class Report(C.Structure):
+    _fields_ = [("status", C.c_int), ("n_sub", C.c_int), ("rank_max", C.c_int), ("rank_min", C.c_int),
+                ("k_nh_max", C.c_int), ("k_hom_max", C.c_int), ("k_hom_sum", C.c_int),
+                ("not_converged", C.c_int), ("est_max", C.c_double), ("sigma_ratio_max", C.c_double),
+                ("wr_iters", C.c_int), ("wr_delta", C.c_double), ("time_ms", C.c_double),
+                ("t_source_ms", C.c_double), ("t_krylov_ms", C.c_double), ("t_hom_ms", C.c_double),
+                ("t_recon_ms", C.c_double), ("bytes_alg", C.c_double), ("launches", C.c_int)]
+
+    def as_dict(self) -> dict:
+        return {f[0]: getattr(self, f[0]) for f in self._fields_}
+
+
+_lib = None
+
+
+def lib() -> C.CDLL:
+    """Load libpexp.so (raises if it has not been built)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise ImportError(f"{LIB_PATH} is missing: build it with `python -m paper_1509_04567_gb300.build`")
+        L = C.CDLL(LIB_PATH)
+        vp, i, d = C.c_void_p, C.c_int, C.c_double
+        L.pexp_create.argtypes = [C.POINTER(vp), i, vp]
+        L.pexp_destroy.argtypes = [vp]
+        L.pexp_set_stream.argtypes = [vp, vp]
+        L.pexp_default_options.argtypes = [C.POINTER(Options)]
+        L.pexp_default_options.restype = None
+        L.pexp_status_string.argtypes = [i]
+        L.pexp_status_string.restype = C.c_char_p
+        L.pexp_solve_linear.argtypes = [vp, C.POINTER(Operator), C.POINTER(Options), vp, vp, i, vp, i,
+                                        C.POINTER(Report)]
+        L.pexp_solve_linear_host.argtypes = L.pexp_solve_linear.argtypes
+        L.pexp_solve_burgers.argtypes = [vp, C.POINTER(Operator), C.POINTER(Options), vp, vp, vp, vp, i,
+                                         C.POINTER(Report)]
+        L.pexp_apply_operator.argtypes = [vp, C.POINTER(Operator), vp, vp, i, i, i]
+        L.pexp_sai_solve.argtypes = [vp, C.POINTER(Operator), d, vp, vp, i, i]
+        L.pexp_small_expm.argtypes = [vp, vp, vp, i, i]
+        L.pexp_burgers_source.argtypes = [vp, C.POINTER(Operator), vp, vp, i, i, i]
+        for name in EXPORTS:
+            if name not in ("pexp_default_options", "pexp_status_string"):
+                getattr(L, name).restype = i
+        _lib = L
+    return _lib
+
+
+class PexpError(RuntimeError):
+    def __init__(self, code: int, what: str):
+        self.code = code
+        super().__init__(f"{what}: {lib().pexp_status_string(code).decode()} ({code})")
+
+
+def status_string(code: int) -> str:
+    return lib().pexp_status_string(code).decode()
+
+
+def make_operator(op: dict) -> Operator:
+    return Operator(int(op["dim"]), int(op["nx"]), int(op.get("ny", 1)), int(op["bc"]), float(op["ax"]),
+                    float(op.get("ay", 0.0)), float(op["nu"]), float(op.get("Lx", 1.0)), float(op.get("Ly", 1.0)))
+
+
+def make_options(opts: dict) -> Options:
+    o = Options()
+    lib().pexp_default_options(C.byref(o))
+    for name, _ in Options._fields_:
+        if name in opts:
+            setattr(o, name, type(getattr(o, name))(opts[name]))
+    return o
+
+
+def _dtype_code(t) -> int:
+    import torch
+    if t.dtype == torch.float64:
+        return F64
+    if t.dtype == torch.float32:
+        return F32
+    raise TypeError(f"unsupported dtype {t.dtype}")
+
+
+def _np_dtype_code(a) -> int:
+    import numpy as np
+    if a.dtype == np.float64:
+        return F64
+    if a.dtype == np.float32:
+        return F32
+    raise TypeError(f"unsupported dtype {a.dtype}")
+
+
+class Context:
+    """A library context on one CUDA device, bound to a CUDA stream."""
+
+    def __init__(self, device: int = 0, stream=None):
+        import torch
+        self.device = device
+        if stream is None:
+            stream = torch.cuda.current_stream(device)
+        self._stream = stream
+        h = C.c_void_p()
+        rc = lib().pexp_create(C.byref(h), device, C.c_void_p(stream.cuda_stream))
+        if rc != OK:
+            raise PexpError(rc, "pexp_create")
+        self.h = h
+
+    def close(self):
+        if getattr(self, "h", None):
+            lib().pexp_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def set_stream(self, stream):
+        self._stream = stream
+        rc = lib().pexp_set_stream(self.h, C.c_void_p(stream.cuda_stream))
+        if rc != OK:
+            raise PexpError(rc, "pexp_set_stream")
+
+    # ---------------------------------------------------------------- solvers
+    def solve_linear(self, op: dict, opts: dict, y0, G, Y, check: bool = True) -> dict:
+        """Paraexp-EBK solve: y0 (n,), G (n_out, n) or None, Y (n_out, n) -- CUDA tensors."""
+        for t in (y0, Y) + ((G,) if G is not None else ()):
+            assert t.is_cuda and t.is_contiguous()
+        rep = Report()
+        o = make_options(opts)
+        rc = lib().pexp_solve_linear(self.h, C.byref(make_operator(op)), C.byref(o), C.c_void_p(y0.data_ptr()),
+                                     C.c_void_p(G.data_ptr()) if G is not None else None,
+                                     _dtype_code(G) if G is not None else _dtype_code(Y),
+                                     C.c_void_p(Y.data_ptr()), _dtype_code(Y), C.byref(rep))
+        if check and rc not in (OK, ERR_NOT_CONVERGED):
+            raise PexpError(rc, "pexp_solve_linear")
+        d = rep.as_dict()
+        d["rc"] = rc
+        return d
+
+    def solve_linear_host(self, op: dict, opts: dict, y0, G, Y, check: bool = True) -> dict:
+        """Same solve with host numpy buffers (copied in and out by the library)."""
+        import numpy as np
+        for a in (y0, Y) + ((G,) if G is not None else ()):
+            assert isinstance(a, np.ndarray) and a.flags["C_CONTIGUOUS"]
+        rep = Report()
+        rc = lib().pexp_solve_linear_host(self.h, C.byref(make_operator(op)), C.byref(make_options(opts)),
+                                          C.c_void_p(y0.ctypes.data),
+                                          C.c_void_p(G.ctypes.data) if G is not None else None,
+                                          _np_dtype_code(G) if G is not None else _np_dtype_code(Y),
+                                          C.c_void_p(Y.ctypes.data), _np_dtype_code(Y), C.byref(rep))
+        if check and rc not in (OK, ERR_NOT_CONVERGED):
+            raise PexpError(rc, "pexp_solve_linear_host")
+        d = rep.as_dict()
+        d["rc"] = rc
+        return d
+
+    def solve_burgers(self, op: dict, opts: dict, u0, U, forcing=None, init=None, check: bool = True) -> dict:
+        rep = Report()
+        rc = lib().pexp_solve_burgers(self.h, C.byref(make_operator(op)), C.byref(make_options(opts)),
+                                      C.c_void_p(u0.data_ptr()),
+                                      C.c_void_p(forcing.data_ptr()) if forcing is not None else None,
+                                      C.c_void_p(init.data_ptr()) if init is not None else None,
+                                      C.c_void_p(U.data_ptr()), _dtype_code(U), C.byref(rep))
+        if check and rc not in (OK, ERR_NOT_CONVERGED, ERR_WR_NOT_CONVERGED):
+            raise PexpError(rc, "pexp_solve_burgers")
+        d = rep.as_dict()
+        d["rc"] = rc
+        return d
+
+    # ---------------------------------------------------------------- kernel-level calls
+    def apply_operator(self, op: dict, X, Y, transpose: bool = False):
+        nvec = X.shape[0] if X.dim() == 2 else 1
+        rc = lib().pexp_apply_operator(self.h, C.byref(make_operator(op)), C.c_void_p(X.data_ptr()),
+                                       C.c_void_p(Y.data_ptr()), nvec, _dtype_code(X), int(transpose))
+        if rc != OK:
+            raise PexpError(rc, "pexp_apply_operator")
+
+    def sai_solve(self, op: dict, gamma: float, X, Y):
+        nvec = X.shape[0] if X.dim() == 2 else 1
+        rc = lib().pexp_sai_solve(self.h, C.byref(make_operator(op)), float(gamma), C.c_void_p(X.data_ptr()),
+                                  C.c_void_p(Y.data_ptr()), nvec, _dtype_code(X))
+        if rc != OK:
+            raise PexpError(rc, "pexp_sai_solve")
+
+    def small_expm(self, M, E):
+        batch, N, _ = M.shape
+        rc = lib().pexp_small_expm(self.h, C.c_void_p(M.data_ptr()), C.c_void_p(E.data_ptr()), N, batch)
+        if rc != OK:
+            raise PexpError(rc, "pexp_small_expm")
+
+    def burgers_source(self, op: dict, U, G, form: int = 0):
+        rows = U.shape[0] if U.dim() == 2 else 1
+        rc = lib().pexp_burgers_source(self.h, C.byref(make_operator(op)), C.c_void_p(U.data_ptr()),
+                                       C.c_void_p(G.data_ptr()), rows, _dtype_code(U), form)
+        if rc != OK:
+            raise PexpError(rc, "pexp_burgers_source")
