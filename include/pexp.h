@@ -102,7 +102,10 @@ typedef struct {
     int    wr_max_iter;  /* waveform relaxation iteration limit (Fig. 5, K) */
     double wr_tol;       /* stop when max_i||u_{k+1}(t_i)-u_k(t_i)|| <= wr_tol*max_i||u_{k+1}(t_i)|| */
     int    burgers_form; /* 0: -(u_{i+1}^2-u_{i-1}^2)/(4dx);  1: -u_i(u_{i+1}-u_{i-1})/(2dx) */
+    int    diagnostics;  /* bit 0: measure the orthogonality of every Krylov basis (report.orth_max) */
 } pexp_options;
+
+#define PEXP_DIAG_ORTH 1
 
 #define PEXP_MAX_RANK   16    /* largest block width */
 #define PEXP_MAX_STEPS  40    /* largest Krylov step budget restart_len*(max_restarts+1) */
@@ -127,6 +130,7 @@ typedef struct {
     double t_krylov_ms;       /*   nonhomogeneous block Krylov solves (all subintervals) */
     double t_hom_ms;          /*   homogeneous continuation chain */
     double t_recon_ms;        /*   reconstruction of all output times */
+    double orth_max;          /* max over bases of max|V^T V - I| (PEXP_DIAG_ORTH), else -1 */
     double bytes_alg;         /* algorithmic HBM bytes: each array counted once per pass the method needs */
     int    launches;          /* kernels launched by the call */
 } pexp_report;
@@ -145,7 +149,9 @@ const char* pexp_status_string(int status);
 
 /* ---------------------------------------------------------------- solvers */
 /* Paraexp-EBK linear solve (Sec. 2.2, Fig. 3).
- *   y0_dev: n values (dtype y_dtype).  G_dev: n_out*n source samples g(t_i)
+ *   y0_dev: n FP64 values (always FP64: the shift g_hat = A u0 + g of eq. linivp_shift
+ *   multiplies the rounding error of u0 by ||A||, up to ~4e9 on fine meshes, so u0 must
+ *   carry full precision whatever the precision of the solve).  G_dev: n_out*n source samples g(t_i)
  *   (time-major, dtype g_dtype) or NULL for g = 0.  Y_dev: n_out*n outputs
  *   u(t_i) (time-major, dtype y_dtype); must not overlap G_dev or y0_dev.
  * Returns PEXP_ERR_NOT_CONVERGED (outputs still written) when a Krylov solve missed tol. */
@@ -153,17 +159,17 @@ int pexp_solve_linear(pexp_ctx* ctx, const pexp_operator* op, const pexp_options
                       const void* y0_dev, const void* G_dev, int g_dtype,
                       void* Y_dev, int y_dtype, pexp_report* rep);
 
-/* Same solve with HOST buffers: copies y0 and G in, solves, copies Y out. */
+/* Same solve with HOST buffers (y0 FP64 as above): copies y0 and G in, solves, copies Y out. */
 int pexp_solve_linear_host(pexp_ctx* ctx, const pexp_operator* op, const pexp_options* opts,
                            const void* y0_host, const void* G_host, int g_dtype,
                            void* Y_host, int y_dtype, pexp_report* rep);
 
 /* Viscous Burgers u_t + u u_x = nu u_xx + f by waveform relaxation (Sec. 2.3-2.4, Fig. 5),
  * plain Picard form (eq. ivp3): A = nu D2 from `op` (its advection velocity must be 0).
- *   u0_dev: n values.  forcing_dev: optional n_out*n samples f(t_i) or NULL.
+ *   u0_dev: n FP64 values.  forcing_dev: optional n_out*n samples f(t_i) or NULL.
  *   init_dev: optional first iterate (n_out*n) or NULL for u0 at every time.
  *   U_dev: n_out*n output, the last iterate (also on PEXP_ERR_WR_NOT_CONVERGED).
- * All arrays have dtype `dtype`. */
+ * forcing, init and U have dtype `dtype`. */
 int pexp_solve_burgers(pexp_ctx* ctx, const pexp_operator* op, const pexp_options* opts,
                        const void* u0_dev, const void* forcing_dev, const void* init_dev,
                        void* U_dev, int dtype, pexp_report* rep);

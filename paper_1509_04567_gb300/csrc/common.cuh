@@ -57,6 +57,23 @@ struct TsTask {
     double alpha, beta;
 };
 
+// Double-float update task for FP32 data (see k_ts_nn_df):
+//   Z = alpha (X + xs 1^T) Tm [+ Z], X and Z given as (hi, lo) FP32 array pairs;
+//   the low array of X covers its first pl columns (pl = 0: all p columns).
+struct DfTask {
+    const float* Xh;
+    const float* Xl;
+    int pl;
+    const double* xs;
+    int64_t ldx;
+    float* Zh;
+    float* Zl;
+    int64_t ldz;
+    const double* Tm;
+    int ldt, p, q, accumulate;
+    double alpha;
+};
+
 // Reconstruction task: for output rows r = 0..ns-1 (coefficient rows r0 + r),
 //   Out[(i0 + r) * ldo + k] = u0[k] + sum_a V1[a*ld1 + k] C1[(r0+r)*ldc1 + a]
 //                                   + sum_a V2[a*ld2 + k] C2[(r0+r)*ldc2 + a]
@@ -84,6 +101,8 @@ void launch_stencil(const OpDesc& op, const T* X, T* Y, int nvec, int transpose,
 template <typename T>
 void launch_stencil_ptrs(const OpDesc& op, const T* const* X, T* const* Y, int nvec, int transpose,
                          cudaStream_t s);
+void launch_stencil_df(const OpDesc& op, const float* const* X, const float* const* Xl, float* const* Yh,
+                       float* const* Yl, int nvec, int transpose, cudaStream_t s);
 template <typename T>
 void launch_burgers_source(const OpDesc& op, const T* U, T* G, int nrows, int form, double inv2dx,
                            cudaStream_t s);
@@ -106,6 +125,9 @@ void launch_row_diff_norms(const T* A, const T* B, int64_t n, int nrows, double*
 
 template <typename T>
 void launch_add(T* y, const T* x, int64_t count, cudaStream_t s);
+void launch_ts_nn_df(const DfTask* tasks_dev, int ntasks, int max_pq, int64_t n, cudaStream_t s);
+template <typename T>
+void launch_row_dots(const double* u, const T* G, int64_t n, int nrows, double* out, cudaStream_t s);
 
 int fail_cuda(cudaError_t e, const char* what, const char* file, int line);
 

@@ -19,10 +19,11 @@
 
 namespace pexp {
 
-WinLayout make_layout(int s_max, int b_max, int kmax) {
+WinLayout make_layout(int s_max, int b_max, int kmax, int ycols) {
     WinLayout L;
     L.s_max = s_max;
     L.b_max = b_max;
+    L.ycols = ycols;
     L.K_max = b_max * (kmax + 1);
     L.N_max = L.K_max + 4 * b_max;
     int64_t o = 0;
@@ -36,7 +37,7 @@ WinLayout make_layout(int s_max, int b_max, int kmax) {
     L.off_C = take((int64_t)b_max * s_max);
     L.off_coef = take((int64_t)std::max(1, s_max - 1) * 4 * b_max);
     L.off_H = take((int64_t)L.K_max * L.K_max);
-    L.off_out1 = take((int64_t)(L.K_max + b_max) * 3 * b_max);
+    L.off_out1 = take((int64_t)(L.K_max + b_max) * ycols * b_max);
     L.off_h2 = take((int64_t)L.K_max * b_max);
     L.off_gw = take((int64_t)b_max * b_max);
     L.off_T = take((int64_t)b_max * b_max);
@@ -240,7 +241,8 @@ __device__ void cta_expm(double* A, int N, double* E, double* w) {
 // Source compression: Jacobi eigen-decomposition of the Gram matrix (Sec. 2.1)
 // =====================================================================================
 __global__ void __launch_bounds__(64) k_source_eig(WinLayout L, double* __restrict__ wd, int* __restrict__ wi,
-                                                   const int* __restrict__ wins, double thr, int max_rank) {
+                                                   const int* __restrict__ wins, double thr, int max_rank,
+                                                   const double* __restrict__ dots, const double* __restrict__ nrm2) {
     const int w = wins[blockIdx.x];
     double* D = wd + (int64_t)w * L.stride;
     int* I = wi + (int64_t)w * L.istride;
@@ -252,9 +254,13 @@ __global__ void __launch_bounds__(64) k_source_eig(WinLayout L, double* __restri
     __shared__ int order[PEXP_MAX_SAMPLES];
     __shared__ int s_more;
     const double* G = D + L.off_gram;
+    const int i0 = I[WI_I0];
+    const double na2 = *nrm2;
     for (int e = threadIdx.x; e < s * s; e += blockDim.x) {
-        A[e] = G[e];
-        Z[e] = (e % s == e / s) ? 1.0 : 0.0;
+        const int i = e % s, j = e / s;
+        // (A u0 + g_i) . (A u0 + g_j) = ||A u0||^2 + (A u0).g_i + (A u0).g_j + g_i . g_j
+        A[e] = na2 + (dots ? (dots[i0 + i] + dots[i0 + j]) + G[e] : 0.0);
+        Z[e] = (i == j) ? 1.0 : 0.0;
     }
     __syncthreads();
     for (int sweep = 0; sweep < 40; ++sweep) {
@@ -356,11 +362,11 @@ __global__ void __launch_bounds__(64) k_source_eig(WinLayout L, double* __restri
 }
 
 void launch_source_eig(const WinLayout& L, double* wd, int* wi, const int* wins, int nw, double thr, int max_rank,
-                       cudaStream_t s) {
+                       const double* dots, const double* nrm2, cudaStream_t s) {
     if (nw <= 0) return;
     size_t sm = (size_t)2 * L.s_max * L.s_max * sizeof(double);
     if (sm > 48 * 1024) cudaFuncSetAttribute(k_source_eig, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-    k_source_eig<<<nw, 64, sm, s>>>(L, wd, wi, wins, thr, max_rank);
+    k_source_eig<<<nw, 64, sm, s>>>(L, wd, wi, wins, thr, max_rank, dots, nrm2);
 }
 
 // =====================================================================================
@@ -446,11 +452,13 @@ __global__ void k_block_orth(WinLayout L, double* __restrict__ wd, int* __restri
     double lim2;
     int ncand = b;
     if (pass == 1) {
-        // pre-Gram-Schmidt norms: diagonal of W^T W stored in out1 rows [step*b, step*b+b), cols [2b, 3b)
+        // pre-Gram-Schmidt norms: diagonal of W^T W stored in out1 rows [step*b, step*b+b),
+        // in the last column block
         const int ldo = (step + 1) * b;
         const double* o1 = D + L.off_out1;
+        const int wc = (L.ycols - 1) * b;
         double pre = 0.0;
-        for (int c = 0; c < b; ++c) pre = fmax(pre, o1[(step * b + c) + (2 * b + c) * ldo]);
+        for (int c = 0; c < b; ++c) pre = fmax(pre, o1[(step * b + c) + (wc + c) * ldo]);
         lim2 = defl * defl * pre;
         D[L.off_scal + WS_PRE] = sqrt(pre);
     } else {
@@ -603,13 +611,20 @@ __global__ void __launch_bounds__(256) k_project(WinLayout L, double* __restrict
     const int KM = L.K_max;
     double* H = D + L.off_H;
     const double* o1 = D + L.off_out1;
+    // column blocks of out1: [0,b) V^T A V_i, [b,2b) V^T A^T V_i, and with ycols == 5 the
+    // low parts [2b,3b), [3b,4b) of the same products (FP32 data)
+    const bool lo = L.ycols == 5;
     for (int e = threadIdx.x; e < K * b; e += blockDim.x) {
         const int a = e % K, c = e / K;
-        H[a + ((step - 1) * b + c) * KM] = o1[a + c * ldo];
+        double v = o1[a + c * ldo];
+        if (lo) v += o1[a + (2 * b + c) * ldo];
+        H[a + ((step - 1) * b + c) * KM] = v;
     }
     for (int e = threadIdx.x; e < (step - 1) * b * b; e += blockDim.x) {
         const int a = e % ((step - 1) * b), c = e / ((step - 1) * b);
-        H[((step - 1) * b + c) + a * KM] = o1[a + (b + c) * ldo];
+        double v = o1[a + (b + c) * ldo];
+        if (lo) v += o1[a + (3 * b + c) * ldo];
+        H[((step - 1) * b + c) + a * KM] = v;
     }
     __syncthreads();
     const int N = (kind == KIND_SOURCE) ? K + 4 * b : K;

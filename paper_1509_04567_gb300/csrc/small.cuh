@@ -12,13 +12,14 @@ struct WinLayout {
     int b_max;     // block width
     int K_max;     // basis columns = b_max * (kmax + 1)
     int N_max;     // augmented matrix size = K_max + 4 b_max
+    int ycols;     // column blocks of the step projections: 3 (A V, A^T V, W) or 5 with low parts
     int64_t stride;
     int64_t off_gram;  // s_max x s_max     Gram of the source samples
     int64_t off_zs;    // s_max x b_max     U = Ghat zs
     int64_t off_C;     // b_max x s_max     coefficient samples (ld b_max)
     int64_t off_coef;  // (s_max-1) x 4 x b_max cubic coefficients [(r*4+l)*b_max + k]
     int64_t off_H;     // K_max x K_max     Galerkin matrix V^T A V
-    int64_t off_out1;  // (K_max + b_max) x 3 b_max   projections of step i
+    int64_t off_out1;  // (K_max + b_max) x ycols b_max   projections of step i
     int64_t off_h2;    // K_max x b_max     second Gram-Schmidt pass
     int64_t off_gw;    // b_max x b_max     Gram of the new block
     int64_t off_T;     // b_max x b_max     block scaling
@@ -30,17 +31,20 @@ struct WinLayout {
 };
 
 // int fields
-enum { WI_B = 0, WI_CONV, WI_STEPS, WI_S, WI_KIND, WI_KEPT, WI_STATUS, WI_K, WI_COUNT = 16 };
+enum { WI_B = 0, WI_CONV, WI_STEPS, WI_S, WI_KIND, WI_KEPT, WI_STATUS, WI_K, WI_I0, WI_COUNT = 16 };
 // double scalars at off_scal
 enum { WS_BETA = 0, WS_EST, WS_SCALE, WS_SIGRATIO, WS_H, WS_PRE, WS_COUNT = 16 };
 
 enum { KIND_SOURCE = 0, KIND_HOM = 1 };
 
-WinLayout make_layout(int s_max, int b_max, int kmax);
+WinLayout make_layout(int s_max, int b_max, int kmax, int ycols = 3);
 
 // Launchers.  `wins` is a device array of window indices (nw entries).
+// The Gram matrix of the shifted samples G_hat = A u0 1^T + G is assembled from its
+// parts: off_gram holds G^T G, dots[i] = (A u0) . g(t_i) (NULL: no source),
+// *nrm2 = ||A u0||^2.
 void launch_source_eig(const WinLayout& L, double* wd, int* wi, const int* wins, int nw, double thr,
-                       int max_rank, cudaStream_t s);
+                       int max_rank, const double* dots, const double* nrm2, cudaStream_t s);
 void launch_start_orth(const WinLayout& L, double* wd, int* wi, const int* wins, int nw, cudaStream_t s);
 void launch_block_orth(const WinLayout& L, double* wd, int* wi, const int* wins, int nw, int pass, int step,
                        double defl, cudaStream_t s);

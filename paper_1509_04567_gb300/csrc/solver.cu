@@ -23,6 +23,7 @@
 
 #include <algorithm>
 #include <new>
+#include <type_traits>
 #include <vector>
 
 #include "common.cuh"
@@ -34,9 +35,12 @@ using namespace pexp;
 struct pexp_ctx {
     int device = 0;
     cudaStream_t stream = nullptr;
-    char* ws = nullptr;   // device workspace
+    char* ws = nullptr;   // device workspace (small state, scratch)
     size_t ws_cap = 0;
     size_t ws_top = 0;
+    char* bs = nullptr;   // device pool of the Krylov bases, sized once the block widths are known
+    size_t bs_cap = 0;
+    size_t bs_top = 0;
     char* stage_h[2] = {nullptr, nullptr};   // pinned task staging
     char* stage_d[2] = {nullptr, nullptr};
     size_t stage_cap = 0;
@@ -51,6 +55,18 @@ struct pexp_ctx {
 namespace {
 
 constexpr size_t kAlign = 256;
+
+// Relative thresholds below which a new Krylov direction counts as already in the
+// space (block deflation), per precision of the n-length data.
+#ifndef PEXP_DEFL_FP64
+#define PEXP_DEFL_FP64 1e-10
+#endif
+#ifndef PEXP_DEFL_FP32
+#define PEXP_DEFL_FP32 1e-5
+#endif
+#ifndef PEXP_TN_EXACT_FP32
+#define PEXP_TN_EXACT_FP32 0
+#endif
 constexpr size_t kStageBytes = 8u << 20;
 
 struct OomError {};
@@ -81,6 +97,27 @@ int ws_reserve(pexp_ctx* c, size_t need) {
         cap = need;
     }
     c->ws_cap = cap;
+    return PEXP_OK;
+}
+
+void* bs_alloc(pexp_ctx* c, size_t bytes) {
+    size_t off = (c->bs_top + kAlign - 1) / kAlign * kAlign;
+    if (off + bytes > c->bs_cap) throw OomError();
+    c->bs_top = off + bytes;
+    return c->bs + off;
+}
+
+int bs_reserve(pexp_ctx* c, size_t need) {
+    c->bs_top = 0;
+    if (need <= c->bs_cap) return PEXP_OK;
+    if (c->bs) cudaFree(c->bs);
+    c->bs = nullptr;
+    c->bs_cap = 0;
+    if (cudaMalloc(&c->bs, need) != cudaSuccess) {
+        cudaGetLastError();
+        return PEXP_ERR_OOM;
+    }
+    c->bs_cap = need;
     return PEXP_OK;
 }
 
@@ -184,9 +221,12 @@ template <typename T>
 struct Win {
     int w;        // window index in the small-state arrays
     T* V;         // basis, n x K_max column-major (ld n)
-    T* S;         // scratch n x 2b (A V_i, A^T V_i)
+    T* S;         // scratch n x (ycols-1) b: A V_i, A^T V_i (and their low parts for FP32 data)
     int b;        // block width
+    float* Wlo;   // FP32 data: low parts of the working block (n x b); NULL for FP64
+    float* V1lo;  // FP32 data: low parts of the start block V_1 (n x b); NULL for FP64
 };
+
 
 template <typename T>
 struct Solver {
@@ -205,10 +245,40 @@ struct Solver {
     int kmax;
     double defl;
     double scale_ref;
+    double* diag = nullptr;   // K_max x 48 doubles for the orthogonality diagnostic
     std::vector<int> wi_host;
 
     T* slot(const Win<T>& W, int blk) const { return W.V + (int64_t)blk * W.b * n; }
     double* D(int w) const { return wd + (int64_t)w * L.stride; }
+
+    // max |V^T V - I| over the first K columns of V (diagnostic, one pass over V per 48 columns).
+    double orth_defect(const T* V, int K) {
+        if (K <= 0) return 0.0;
+        std::vector<double> G((size_t)K * K);
+        for (int c0 = 0; c0 < K; c0 += 48) {
+            const int q = std::min(48, K - c0);
+            Stage sg(c, 0);
+            TsTask<T> t;
+            memset(&t, 0, sizeof(t));
+            t.X = V; t.ldx = n; t.p = K; t.Y = V + (int64_t)c0 * n; t.ldy = n; t.q = q; t.q1 = q;
+            t.out = diag;
+            const TsTask<T>* dt = sg.put(&t, 1);
+            sg.flush();
+            launch_ts_tn<T>(dt, 1, K * q, q, n, partial, st, 1);
+            check_launch(c);
+            d2h(c, G.data() + (size_t)c0 * K, t.out, sizeof(double) * K * q);
+        }
+        double m = 0.0;
+        for (int j = 0; j < K; ++j) {
+            // zero columns (deflated directions) are skipped
+            if (G[(size_t)j * K + j] < 0.5) continue;
+            for (int i = 0; i < K; ++i) {
+                if (G[(size_t)i * K + i] < 0.5) continue;
+                m = std::max(m, fabs(G[(size_t)j * K + i] - (i == j ? 1.0 : 0.0)));
+            }
+        }
+        return m;
+    }
 
     // Runs block Krylov steps for the windows `ws` (each with its start block already
     // orthonormal in V block 0).  Returns the number of windows that missed tol.
@@ -221,11 +291,13 @@ struct Solver {
             // ---- part A: operator applications, projections, projected solve
             Stage sa(c, 0);
             std::vector<const T*> xin;
-            std::vector<T*> yout, yav, yatv;
-            std::vector<const T*> xav;
-            std::vector<TsTask<T>> tn1(na);
+            std::vector<T*> yout, ylo, yav, yatv, yavl, yatvl;
+            std::vector<const float*> xlo;
+            const int yc = L.ycols;   // 3 (FP64) or 5 (FP32 data: A V and A^T V carry low parts)
+            // TN1 over X = V_{1:step+1} (the working block W sits in slot step) and
+            // Y = [A V_i, A^T V_i, (low parts), W]; Y is split into launches of <= 48 columns
+            std::vector<std::vector<TsTask<T>>> tn1;
             std::vector<int> wl(na);
-            int max_pq = 0, max_q = 0;
             for (int a = 0; a < na; ++a) {
                 const Win<T>& W = act[a];
                 T* Vi = slot(W, step - 1);
@@ -233,43 +305,87 @@ struct Solver {
                 for (int cc = 0; cc < W.b; ++cc) {
                     xin.push_back(Vi + (int64_t)cc * n);
                     yout.push_back(Wn + (int64_t)cc * n);
+                    ylo.push_back(W.Wlo ? reinterpret_cast<T*>(W.Wlo) + (int64_t)cc * n : nullptr);
                     yav.push_back(W.S + (int64_t)cc * n);
                     yatv.push_back(W.S + (int64_t)(W.b + cc) * n);
+                    yavl.push_back(W.S + (int64_t)(2 * W.b + cc) * n);
+                    yatvl.push_back(W.S + (int64_t)(3 * W.b + cc) * n);
+                    xlo.push_back(step == 1 && W.V1lo ? W.V1lo + (int64_t)cc * n : nullptr);
                 }
-                TsTask<T> t;
-                memset(&t, 0, sizeof(t));
-                t.X = W.V;
-                t.ldx = n;
-                t.p = (step + 1) * W.b;
-                t.Y = W.S;
-                t.ldy = n;
-                t.q1 = 2 * W.b;
-                t.Y2 = Wn;
-                t.ldy2 = n;
-                t.q = 3 * W.b;
-                t.out = D(W.w) + L.off_out1;
-                tn1[a] = t;
-                max_pq = std::max(max_pq, t.p * t.q);
-                max_q = std::max(max_q, t.q);
+                const int ldo = (step + 1) * W.b;
+                const int qs = (yc - 1) * W.b;   // columns of S
+                int sl = 0;
+                for (int c0 = 0; c0 < qs + W.b; ++sl) {
+                    TsTask<T> t;
+                    memset(&t, 0, sizeof(t));
+                    t.X = W.V;
+                    t.ldx = n;
+                    t.p = ldo;
+                    t.out = D(W.w) + L.off_out1 + (int64_t)c0 * ldo;
+                    if (c0 < qs) {
+                        const int q = std::min(48, qs - c0);
+                        t.Y = W.S + (int64_t)c0 * n; t.ldy = n; t.q = q; t.q1 = q;
+                        // the working block joins the last S slice when it fits
+                        if (c0 + q == qs && q + W.b <= 48) { t.Y2 = Wn; t.ldy2 = n; t.q = q + W.b; }
+                        c0 += t.q;
+                    } else {
+                        t.Y = Wn; t.ldy = n; t.q = W.b; t.q1 = W.b;
+                        c0 += W.b;
+                    }
+                    if ((int)tn1.size() <= sl) tn1.emplace_back();
+                    tn1[sl].push_back(t);
+                }
                 wl[a] = W.w;
             }
             const int nv = (int)xin.size();
             const T* const* d_xin = sa.put(xin.data(), nv);
             T* const* d_yout = sa.put(yout.data(), nv);
+            T* const* d_ylo = std::is_same<T, float>::value ? sa.put(ylo.data(), nv) : nullptr;
             T* const* d_yav = sa.put(yav.data(), nv);
             T* const* d_yatv = sa.put(yatv.data(), nv);
-            const TsTask<T>* d_tn1 = sa.put(tn1.data(), na);
+            T* const* d_yavl = std::is_same<T, float>::value ? sa.put(yavl.data(), nv) : nullptr;
+            T* const* d_yatvl = std::is_same<T, float>::value ? sa.put(yatvl.data(), nv) : nullptr;
+            // at step 1 the Galerkin block V_1^T A V_1 uses the unrounded start block on one
+            // side: the FP32 rounding error d of V_1 would otherwise add d^T A d ~ |d|^2 ||A||
+            // to it, a spurious damping of the dominant component
+            const float* const* d_xlo = (std::is_same<T, float>::value && step == 1) ? sa.put(xlo.data(), nv) : nullptr;
+            std::vector<const TsTask<T>*> d_tn1(tn1.size());
+            std::vector<int> tn1_pq(tn1.size(), 0), tn1_q(tn1.size(), 0);
+            for (size_t sl = 0; sl < tn1.size(); ++sl) {
+                for (auto& t : tn1[sl]) {
+                    tn1_pq[sl] = std::max(tn1_pq[sl], t.p * t.q);
+                    tn1_q[sl] = std::max(tn1_q[sl], t.q);
+                }
+                d_tn1[sl] = sa.put(tn1[sl].data(), tn1[sl].size());
+            }
             const int* d_wl = sa.put(wl.data(), na);
             sa.flush();
-            if (o->krylov == PEXP_KRYLOV_SAI) launch_sai_solve<T>(od, sai, d_xin, d_yout, nv, sai_scr, st);
-            else launch_stencil_ptrs<T>(od, d_xin, d_yout, nv, 0, st);
+            if (o->krylov == PEXP_KRYLOV_SAI) {
+                launch_sai_solve<T>(od, sai, d_xin, d_yout, d_ylo, nv, sai_scr, st);
+            } else {
+                launch_stencil_ptrs<T>(od, d_xin, d_yout, nv, 0, st);
+                for (const auto& W : act)
+                    if (W.Wlo) cudaMemsetAsync(W.Wlo, 0, sizeof(float) * (size_t)n * W.b, st);
+            }
             check_launch(c);
-            launch_stencil_ptrs<T>(od, d_xin, d_yav, nv, 0, st);
-            check_launch(c);
-            launch_stencil_ptrs<T>(od, d_xin, d_yatv, nv, 1, st);
-            check_launch(c);
-            launch_ts_tn<T>(d_tn1, na, max_pq, max_q, n, partial, st, 0);
-            check_launch(c);
+            if constexpr (std::is_same<T, float>::value) {
+                launch_stencil_df(od, reinterpret_cast<const float* const*>(d_xin), d_xlo,
+                                  reinterpret_cast<float* const*>(d_yav), reinterpret_cast<float* const*>(d_yavl), nv, 0, st);
+                check_launch(c);
+                launch_stencil_df(od, reinterpret_cast<const float* const*>(d_xin), d_xlo,
+                                  reinterpret_cast<float* const*>(d_yatv), reinterpret_cast<float* const*>(d_yatvl), nv, 1, st);
+                check_launch(c);
+            } else {
+                launch_stencil_ptrs<T>(od, d_xin, d_yav, nv, 0, st);
+                check_launch(c);
+                launch_stencil_ptrs<T>(od, d_xin, d_yatv, nv, 1, st);
+                check_launch(c);
+            }
+            for (size_t sl = 0; sl < tn1.size(); ++sl) {
+                launch_ts_tn<T>(d_tn1[sl], (int)tn1[sl].size(), tn1_pq[sl], tn1_q[sl], n, partial, st,
+                                std::is_same<T, float>::value ? 1 : 0);
+                check_launch(c);
+            }
             launch_project(L, wd, wi, d_wl, na, step, h, o->tol, scale_ref, st);
             check_launch(c);
             // ---- convergence flags
@@ -334,22 +450,62 @@ struct Solver {
                 nn3[a] = t;
                 wl2[a] = W.w;
             }
-            const TsTask<T>* d_nn1 = sb.put(nn1.data(), nb);
             const TsTask<T>* d_tn2 = sb.put(tn2.data(), nb);
-            const TsTask<T>* d_nn2 = sb.put(nn2.data(), nb);
             const TsTask<T>* d_tn3 = sb.put(tn3.data(), nb);
-            const TsTask<T>* d_nn3 = sb.put(nn3.data(), nb);
             const int* d_wl2 = sb.put(wl2.data(), nb);
-            sb.flush();
-            launch_ts_nn<T>(d_nn1, nb, mpq1, n, st); check_launch(c);
-            launch_ts_tn<T>(d_tn2, nb, mpq2, mq2, n, partial, st, 0); check_launch(c);
-            launch_ts_nn<T>(d_nn2, nb, mpq1, n, st); check_launch(c);
-            launch_ts_tn<T>(d_tn3, nb, mpq3, mq3, n, partial, st, 0); check_launch(c);
-            launch_block_orth(L, wd, wi, d_wl2, nb, 1, step, defl, st); check_launch(c);
-            launch_ts_nn<T>(d_nn3, nb, mpq3, n, st); check_launch(c);
-            launch_ts_tn<T>(d_tn3, nb, mpq3, mq3, n, partial, st, 0); check_launch(c);
-            launch_block_orth(L, wd, wi, d_wl2, nb, 2, step, defl, st); check_launch(c);
-            launch_ts_nn<T>(d_nn3, nb, mpq3, n, st); check_launch(c);
+            if constexpr (std::is_same<T, float>::value) {
+                // FP32 data: the working block stays a double-float pair (slot = hi, Wlo = lo)
+                // through both Gram-Schmidt updates and both Cholesky scalings; the
+                // final scaling rounds the orthonormal block to FP32 in place.
+                std::vector<DfTask> d1(nb), d2(nb), d3(nb), d4(nb);
+                for (int a = 0; a < nb; ++a) {
+                    const Win<T>& W = act[a];
+                    float* Wn = slot(W, step);
+                    const int b = W.b, p = step * b, ldo = (step + 1) * b;
+                    DfTask t;
+                    memset(&t, 0, sizeof(t));
+                    t.Xh = W.V; t.ldx = n; t.Zh = Wn; t.Zl = W.Wlo; t.ldz = n;
+                    t.Tm = D(W.w) + L.off_out1 + (int64_t)(L.ycols - 1) * b * ldo; t.ldt = ldo;
+                    t.p = p; t.q = b; t.alpha = -1.0; t.accumulate = 1;
+                    d1[a] = t;
+                    t.Tm = D(W.w) + L.off_h2; t.ldt = p;
+                    d2[a] = t;
+                    memset(&t, 0, sizeof(t));
+                    t.Xh = Wn; t.Xl = W.Wlo; t.ldx = n; t.Zh = Wn; t.Zl = W.Wlo; t.ldz = n;
+                    t.Tm = D(W.w) + L.off_T; t.ldt = b; t.p = b; t.q = b; t.alpha = 1.0; t.accumulate = 0;
+                    d3[a] = t;
+                    t.Zl = nullptr;
+                    d4[a] = t;
+                }
+                const DfTask* dd1 = sb.put(d1.data(), nb);
+                const DfTask* dd2 = sb.put(d2.data(), nb);
+                const DfTask* dd3 = sb.put(d3.data(), nb);
+                const DfTask* dd4 = sb.put(d4.data(), nb);
+                sb.flush();
+                launch_ts_nn_df(dd1, nb, mpq1, n, st); check_launch(c);
+                launch_ts_tn<T>(d_tn2, nb, mpq2, mq2, n, partial, st, PEXP_TN_EXACT_FP32); check_launch(c);
+                launch_ts_nn_df(dd2, nb, mpq1, n, st); check_launch(c);
+                launch_ts_tn<T>(d_tn3, nb, mpq3, mq3, n, partial, st, 1); check_launch(c);
+                launch_block_orth(L, wd, wi, d_wl2, nb, 1, step, defl, st); check_launch(c);
+                launch_ts_nn_df(dd3, nb, mpq3, n, st); check_launch(c);
+                launch_ts_tn<T>(d_tn3, nb, mpq3, mq3, n, partial, st, 1); check_launch(c);
+                launch_block_orth(L, wd, wi, d_wl2, nb, 2, step, defl, st); check_launch(c);
+                launch_ts_nn_df(dd4, nb, mpq3, n, st); check_launch(c);
+            } else {
+                const TsTask<T>* d_nn1 = sb.put(nn1.data(), nb);
+                const TsTask<T>* d_nn2 = sb.put(nn2.data(), nb);
+                const TsTask<T>* d_nn3 = sb.put(nn3.data(), nb);
+                sb.flush();
+                launch_ts_nn<T>(d_nn1, nb, mpq1, n, st); check_launch(c);
+                launch_ts_tn<T>(d_tn2, nb, mpq2, mq2, n, partial, st, 0); check_launch(c);
+                launch_ts_nn<T>(d_nn2, nb, mpq1, n, st); check_launch(c);
+                launch_ts_tn<T>(d_tn3, nb, mpq3, mq3, n, partial, st, 0); check_launch(c);
+                launch_block_orth(L, wd, wi, d_wl2, nb, 1, step, defl, st); check_launch(c);
+                launch_ts_nn<T>(d_nn3, nb, mpq3, n, st); check_launch(c);
+                launch_ts_tn<T>(d_tn3, nb, mpq3, mq3, n, partial, st, 0); check_launch(c);
+                launch_block_orth(L, wd, wi, d_wl2, nb, 2, step, defl, st); check_launch(c);
+                launch_ts_nn<T>(d_nn3, nb, mpq3, n, st); check_launch(c);
+            }
         }
         return notconv;
     }
@@ -378,18 +534,16 @@ size_t linear_workspace_bytes(int64_t n, const pexp_options* o, int g_conv, int 
     const int P = o->P;
     Partition pt = make_partition(o->n_out, P);
     const int kmax = o->restart_len * (o->max_restarts + 1);
-    WinLayout L = make_layout(pt.smax, b_cap, kmax);
+    WinLayout L = make_layout(pt.smax, b_cap, kmax, sizeof(T) == 8 ? 3 : 5);
     size_t s = 0;
     s += align_up(sizeof(double) * n * 2);                                  // u0, A u0
     if (g_conv) s += align_up(sizeof(T) * (size_t)n * o->n_out);           // converted G
     s += align_up(sizeof(double) * L.stride * 2 * P);                       // window state
     s += align_up(sizeof(int) * L.istride * 2 * P);
-    s += align_up(sizeof(double) * (ts_tn_partial_doubles(P, std::max(pt.smax * pt.smax, 3 * b_cap * (L.K_max + b_cap)), n) + 512));
+    s += align_up(sizeof(double) * (ts_tn_partial_doubles(P, std::max(std::max(pt.smax * pt.smax, 48 * (L.K_max + b_cap)), 48 * L.K_max), n) + 512));
+    s += align_up(sizeof(double) * (size_t)L.K_max * 48);                   // orthogonality diagnostic
     s += align_up(sizeof(double) * sai_scratch_doubles(n, P * b_cap) + 64);
-    s += align_up(sizeof(T) * (size_t)n * L.K_max * P);                     // V_nh
-    s += align_up(sizeof(T) * (size_t)n * 2 * b_cap * P);                   // S
-    s += align_up(sizeof(T) * (size_t)n * (kmax + 1) * P);                  // V_h
-    s += align_up(sizeof(T) * (size_t)n * 2);                               // S for the homogeneous chain
+    s += align_up(sizeof(double) * o->n_out);                               // (A u0) . g(t_i)
     s += (size_t)(4 * P + 32) * kAlign;   // alignment of the per-window allocations
     return s;
 }
@@ -410,10 +564,10 @@ int solve_linear_typed(pexp_ctx* c, const pexp_operator* op, const pexp_options*
     S.kmax = o->restart_len * (o->max_restarts + 1);
     S.h = o->T / (double)(n_out - 1);
     const bool fp64 = sizeof(T) == 8;
-    S.defl = fp64 ? 1e-10 : 1e-5;
+    S.defl = fp64 ? PEXP_DEFL_FP64 : PEXP_DEFL_FP32;
     const double svd_floor = fp64 ? 1e-7 : 1e-5;
     const int b_cap = std::min(std::min(o->max_rank, PEXP_MAX_RANK), pt.smax);
-    S.L = make_layout(pt.smax, b_cap, S.kmax);
+    S.L = make_layout(pt.smax, b_cap, S.kmax, fp64 ? 3 : 5);
     const WinLayout& L = S.L;
 
     // ---- buffers
@@ -434,8 +588,9 @@ int solve_linear_typed(pexp_ctx* c, const pexp_operator* op, const pexp_options*
     const int nwin = 2 * P;   // [0, P): source windows j=1..P; [P, 2P): homogeneous windows m=1..P
     S.wd = as<double>(ws_alloc(c, sizeof(double) * L.stride * nwin));
     S.wi = as<int>(ws_alloc(c, sizeof(int) * L.istride * nwin));
-    const size_t part_n = ts_tn_partial_doubles(P, std::max(pt.smax * pt.smax, 3 * b_cap * (L.K_max + b_cap)), n) + 512;
+    const size_t part_n = ts_tn_partial_doubles(P, std::max(std::max(pt.smax * pt.smax, 48 * (L.K_max + b_cap)), 48 * L.K_max), n) + 512;
     S.partial = as<double>(ws_alloc(c, sizeof(double) * part_n));
+    S.diag = as<double>(ws_alloc(c, sizeof(double) * (size_t)L.K_max * 48));
     S.sai_scr = as<double>(ws_alloc(c, sizeof(double) * (sai_scratch_doubles(n, P * b_cap) + 64)));
     // one pole for every window: gamma = sai_gamma * T / P (the nominal subinterval length)
     if (o->krylov == PEXP_KRYLOV_SAI) S.sai = sai_coefficients(S.od, o->sai_gamma * o->T / (double)P);
@@ -447,6 +602,7 @@ int solve_linear_typed(pexp_ctx* c, const pexp_operator* op, const pexp_options*
         for (int j = 0; j < P; ++j) {
             wih[(size_t)j * L.istride + WI_S] = pt.idx[j + 1] - pt.idx[j] + 1;
             wih[(size_t)j * L.istride + WI_KIND] = KIND_SOURCE;
+            wih[(size_t)j * L.istride + WI_I0] = pt.idx[j];
             wih[(size_t)(P + j) * L.istride + WI_S] = pt.idx[j + 1] - pt.idx[j] + 1;
             wih[(size_t)(P + j) * L.istride + WI_KIND] = KIND_HOM;
             wih[(size_t)(P + j) * L.istride + WI_B] = 1;
@@ -457,25 +613,32 @@ int solve_linear_typed(pexp_ctx* c, const pexp_operator* op, const pexp_options*
     }
 
     cudaEventRecord(c->evp[0], st);
-    // ---- shift: A u0, ||u0||
+    // ---- shift: A u0, ||u0||, ||A u0||^2, (A u0) . g(t_i)
+    double* nrm = S.partial + part_n - 8;   // [0] = ||u0||^2, [1] = ||A u0||^2
+    double* dots = G ? as<double>(ws_alloc(c, sizeof(double) * n_out)) : nullptr;
     launch_stencil<double>(S.od, u0d, Au0, 1, 0, st);
     check_launch(c);
     {
         Stage s0(c, 0);
-        TsTask<double> t;
-        memset(&t, 0, sizeof(t));
-        t.X = u0d; t.ldx = n; t.p = 1; t.Y = u0d; t.ldy = n; t.q = 1; t.q1 = 1;
-        t.out = S.partial + part_n - 8;
-        const TsTask<double>* dt = s0.put(&t, 1);
+        TsTask<double> t[2];
+        memset(t, 0, sizeof(t));
+        t[0].X = u0d; t[0].ldx = n; t[0].p = 1; t[0].Y = u0d; t[0].ldy = n; t[0].q = 1; t[0].q1 = 1; t[0].out = nrm;
+        t[1].X = Au0; t[1].ldx = n; t[1].p = 1; t[1].Y = Au0; t[1].ldy = n; t[1].q = 1; t[1].q1 = 1; t[1].out = nrm + 1;
+        const TsTask<double>* dt = s0.put(t, 2);
         s0.flush();
-        launch_ts_tn<double>(dt, 1, 1, 1, n, S.partial, st, 0);
+        launch_ts_tn<double>(dt, 2, 1, 1, n, S.partial, st, 0);
         check_launch(c);
+        if (G) {
+            launch_row_dots<T>(Au0, G, n, n_out, dots, st);
+            check_launch(c);
+        }
         double nn = 0;
-        d2h(c, &nn, S.partial + part_n - 8, sizeof(double));
+        d2h(c, &nn, nrm, sizeof(double));
         S.scale_ref = sqrt(nn);
     }
 
-    // ---- source compression, all subintervals
+    // ---- source compression, all subintervals: Gram of g_hat = A u0 + g from
+    // G^T G (per window), (A u0) . g(t_i) and ||A u0||^2
     std::vector<int> all(P);
     for (int j = 0; j < P; ++j) all[j] = j;
     {
@@ -486,17 +649,19 @@ int solve_linear_typed(pexp_ctx* c, const pexp_operator* op, const pexp_options*
             memset(&t, 0, sizeof(t));
             const int s = pt.idx[j + 1] - pt.idx[j] + 1;
             t.X = G ? G + (int64_t)pt.idx[j] * n : nullptr;
-            t.ldx = n; t.p = s; t.xs = Au0;
-            t.Y = t.X; t.ldy = n; t.q = s; t.q1 = s; t.ys = Au0;
+            t.ldx = n; t.p = s;
+            t.Y = t.X; t.ldy = n; t.q = s; t.q1 = s;
             t.out = S.D(j) + L.off_gram;
             tg[j] = t;
         }
         const TsTask<T>* dtg = s1.put(tg.data(), P);
         const int* dall = s1.put(all.data(), P);
         s1.flush();
-        launch_ts_tn<T>(dtg, P, pt.smax * pt.smax, pt.smax, n, S.partial, st, 1);
-        check_launch(c);
-        launch_source_eig(L, S.wd, S.wi, dall, P, std::max(o->svd_tol, svd_floor), b_cap, st);
+        if (G) {
+            launch_ts_tn<T>(dtg, P, pt.smax * pt.smax, pt.smax, n, S.partial, st, 1);
+            check_launch(c);
+        }
+        launch_source_eig(L, S.wd, S.wi, dall, P, std::max(o->svd_tol, svd_floor), b_cap, dots, nrm + 1, st);
         check_launch(c);
         d2h(c, S.wi_host.data(), S.wi, sizeof(int) * S.wi_host.size());
     }
@@ -507,17 +672,32 @@ int solve_linear_typed(pexp_ctx* c, const pexp_operator* op, const pexp_options*
         b_max = std::max(b_max, mj[j]);
         b_min = std::min(b_min, mj[j]);
     }
-    // bases laid out with the actual widths
+    // bases laid out with the actual widths, in the basis pool
+    {
+        size_t need = 0;
+        for (int j = 0; j < P; ++j)
+            if (mj[j] > 0)
+                need += align_up(sizeof(T) * (size_t)n * mj[j] * (S.kmax + 1)) + align_up(sizeof(T) * (size_t)n * (L.ycols - 1) * mj[j]) +
+                        (std::is_same<T, float>::value ? 2 * align_up(sizeof(float) * (size_t)n * mj[j]) : 0);
+        need += (size_t)P * align_up(sizeof(T) * (size_t)n * (S.kmax + 1));   // homogeneous bases
+        need += align_up(sizeof(T) * (size_t)n * (L.ycols - 1)) + 3 * align_up(sizeof(float) * (size_t)n) + (size_t)(6 * P + 8) * kAlign;
+        const int r = bs_reserve(c, need);
+        if (r) throw StatusError{r};
+    }
     std::vector<Win<T>> src;
     std::vector<T*> Vnh(P, nullptr);
+    std::vector<float*> src_lo(P, nullptr);
     for (int j = 0; j < P; ++j) {
         if (mj[j] == 0) continue;
         Win<T> W;
         W.w = j;
         W.b = mj[j];
-        W.V = as<T>(ws_alloc(c, sizeof(T) * (size_t)n * W.b * (S.kmax + 1)));
-        W.S = as<T>(ws_alloc(c, sizeof(T) * (size_t)n * 2 * W.b));
+        W.V = as<T>(bs_alloc(c, sizeof(T) * (size_t)n * W.b * (S.kmax + 1)));
+        W.S = as<T>(bs_alloc(c, sizeof(T) * (size_t)n * (L.ycols - 1) * W.b));
+        W.Wlo = std::is_same<T, float>::value ? as<float>(bs_alloc(c, sizeof(float) * (size_t)n * W.b)) : nullptr;
+        W.V1lo = std::is_same<T, float>::value ? as<float>(bs_alloc(c, sizeof(float) * (size_t)n * W.b)) : nullptr;
         Vnh[j] = W.V;
+        src_lo[j] = W.V1lo;
         src.push_back(W);
     }
     {
@@ -552,11 +732,40 @@ int solve_linear_typed(pexp_ctx* c, const pexp_operator* op, const pexp_options*
         const TsTask<T>* dtg = s2.put(tgr.data(), ns);
         const TsTask<T>* dts = s2.put(tsc.data(), ns);
         const int* dwl = s2.put(wl.data(), ns);
+        const DfTask* ddu = nullptr;
+        const DfTask* dds = nullptr;
+        if constexpr (std::is_same<T, float>::value) {
+            // U = (A u0 1^T + G) Z S^{-1} in double-float: the columns of G_hat nearly
+            // cancel for the smaller singular values.
+            std::vector<DfTask> du(ns);
+            for (int a = 0; a < ns; ++a) {
+                DfTask t;
+                memset(&t, 0, sizeof(t));
+                t.Xh = tu[a].X; t.ldx = n; t.xs = Au0; t.Zh = tu[a].Z; t.Zl = src[a].V1lo; t.ldz = n;
+                t.Tm = tu[a].Tm; t.ldt = tu[a].ldt; t.p = tu[a].p; t.q = tu[a].q; t.alpha = 1.0;
+                du[a] = t;
+            }
+            ddu = s2.put(du.data(), ns);
+            // re-orthonormalisation of the start block keeps its low part
+            std::vector<DfTask> dsc(ns);
+            for (int a = 0; a < ns; ++a) {
+                DfTask t;
+                memset(&t, 0, sizeof(t));
+                t.Xh = src[a].V; t.Xl = src[a].V1lo; t.ldx = n; t.Zh = src[a].V; t.Zl = src[a].V1lo; t.ldz = n;
+                t.Tm = tsc[a].Tm; t.ldt = tsc[a].ldt; t.p = src[a].b; t.q = src[a].b; t.alpha = 1.0;
+                dsc[a] = t;
+            }
+            dds = s2.put(dsc.data(), ns);
+        }
         s2.flush();
-        launch_ts_nn<T>(dtu, ns, mpq, n, st); check_launch(c);
+        if (ddu) launch_ts_nn_df(ddu, ns, mpq, n, st);
+        else launch_ts_nn<T>(dtu, ns, mpq, n, st);
+        check_launch(c);
         launch_ts_tn<T>(dtg, ns, mpqg, mq, n, S.partial, st, 1); check_launch(c);
         launch_start_orth(L, S.wd, S.wi, dwl, ns, st); check_launch(c);
-        launch_ts_nn<T>(dts, ns, mpqg, n, st); check_launch(c);
+        if (dds) launch_ts_nn_df(dds, ns, mpqg, n, st);
+        else launch_ts_nn<T>(dts, ns, mpqg, n, st);
+        check_launch(c);
         launch_spline(L, S.wd, S.wi, dwl, ns, S.h, st); check_launch(c);
         sync(c);   // staging half 1 is reused by the Krylov loop
     }
@@ -568,15 +777,26 @@ int solve_linear_typed(pexp_ctx* c, const pexp_operator* op, const pexp_options*
     d2h(c, S.wi_host.data(), S.wi, sizeof(int) * S.wi_host.size());
     std::vector<int> Knh(P, 0);
     for (int j = 0; j < P; ++j) Knh[j] = S.wi_host[(size_t)j * L.istride + WI_K];
+    double orth_max = -1.0;
+    if (o->diagnostics & PEXP_DIAG_ORTH) {
+        orth_max = 0.0;
+        for (int j = 0; j < P; ++j)
+            if (Vnh[j]) orth_max = std::max(orth_max, S.orth_defect(Vnh[j], Knh[j]));
+    }
 
     cudaEventRecord(c->evp[2], st);
     // ---- homogeneous chain over windows 2..P
     std::vector<T*> Vh(P, nullptr);
     std::vector<int> Kh(P, 0);
     int k_hom_max = 0, k_hom_sum = 0;
-    T* Sh = as<T>(ws_alloc(c, sizeof(T) * (size_t)n * 2));
+    T* Sh = as<T>(bs_alloc(c, sizeof(T) * (size_t)n * (L.ycols - 1)));
+    float* Whlo = std::is_same<T, float>::value ? as<float>(bs_alloc(c, sizeof(float) * (size_t)n)) : nullptr;
+    // low parts of the homogeneous start vectors, two buffers used alternately along the chain
+    float* Vh1lo_buf[2] = {nullptr, nullptr};
+    if (std::is_same<T, float>::value)
+        for (int k = 0; k < 2; ++k) Vh1lo_buf[k] = as<float>(bs_alloc(c, sizeof(float) * (size_t)n));
     for (int m = 1; m < P; ++m) {   // 0-based window m needs z at T_m (end of window m-1)
-        Vh[m] = as<T>(ws_alloc(c, sizeof(T) * (size_t)n * (S.kmax + 1)));
+        Vh[m] = as<T>(bs_alloc(c, sizeof(T) * (size_t)n * (S.kmax + 1)));
         const int wprev = m - 1;
         const int sprev = pt.idx[m] - pt.idx[m - 1] + 1;
         Stage s3(c, 0);
@@ -599,22 +819,64 @@ int solve_linear_typed(pexp_ctx* c, const pexp_operator* op, const pexp_options*
         const TsTask<T>* dts = s3.put(&tsc, 1);
         int wsel = P + m;
         const int* dw = s3.put(&wsel, 1);
+        // FP32 data: z = u_hat(T_m) and its normalisation in double-float (z is the
+        // dominant direction of the window; see the note at step 1 of the Krylov loop)
+        const DfTask* dz = nullptr;
+        int nz = 0;
+        DfTask zt[3];
+        memset(zt, 0, sizeof(zt));
+        float* Vh1lo = Vh1lo_buf[m & 1];
+        float* Vh1lo_prev = Vh1lo_buf[(m - 1) & 1];
+        if constexpr (std::is_same<T, float>::value) {
+            // z carries the state from window to window: its dominant columns (the source
+            // start block and the previous homogeneous start vector) enter with their low
+            // parts, so the FP32 rounding of those columns is not re-applied every window
+            int acc = 0;
+            if (rt.K1 > 0) {
+                DfTask& t = zt[nz++];
+                t.Xh = rt.V1; t.Xl = src_lo[wprev]; t.pl = mj[wprev]; t.ldx = n; t.Zh = Vh[m]; t.Zl = Vh1lo; t.ldz = n;
+                t.Tm = rt.C1 + (int64_t)rt.r0 * rt.ldc1; t.ldt = rt.K1; t.p = rt.K1; t.q = 1; t.alpha = 1.0;
+                t.accumulate = acc;
+                acc = 1;
+            }
+            if (rt.K2 > 0) {
+                DfTask& t = zt[nz++];
+                t.Xh = rt.V2; t.Xl = Vh1lo_prev; t.pl = 1; t.ldx = n; t.Zh = Vh[m]; t.Zl = Vh1lo; t.ldz = n;
+                t.Tm = rt.C2 + (int64_t)rt.r0 * rt.ldc2; t.ldt = rt.K2;
+                t.p = rt.K2; t.q = 1; t.alpha = 1.0; t.accumulate = acc;
+            }
+            DfTask& t = zt[2];
+            t.Xh = Vh[m]; t.Xl = Vh1lo; t.ldx = n; t.Zh = Vh[m]; t.Zl = Vh1lo; t.ldz = n;
+            t.Tm = S.D(P + m) + L.off_T; t.ldt = 1; t.p = 1; t.q = 1; t.alpha = 1.0;
+            dz = s3.put(zt, 3);
+        }
         s3.flush();
         const int maxc = std::max(1, (rt.K1 + rt.K2));
-        launch_recon<T, T>(drt, 1, 1, n, nullptr, Vh[m], n, maxc, st); check_launch(c);
+        if (dz) {
+            if (nz == 0) cudaMemsetAsync(Vh[m], 0, sizeof(T) * (size_t)n, st);
+            for (int k = 0; k < nz; ++k) {
+                launch_ts_nn_df(dz + k, 1, std::max(rt.K1, rt.K2), n, st);
+                check_launch(c);
+            }
+        } else {
+            launch_recon<T, T>(drt, 1, 1, n, nullptr, Vh[m], n, maxc, st); check_launch(c);
+        }
         launch_ts_tn<T>(dtg, 1, 1, 1, n, S.partial, st, 1); check_launch(c);
         launch_start_orth(L, S.wd, S.wi, dw, 1, st); check_launch(c);
-        launch_ts_nn<T>(dts, 1, 1, n, st); check_launch(c);
+        if (dz) launch_ts_nn_df(dz + 2, 1, 1, n, st);
+        else launch_ts_nn<T>(dts, 1, 1, n, st);
+        check_launch(c);
         double beta = 0;
         d2h(c, &beta, S.D(P + m) + L.off_scal + WS_BETA, sizeof(double));
         if (!(beta > 0.0)) { Kh[m] = 0; continue; }
         std::vector<Win<T>> one(1);
-        one[0].w = P + m; one[0].V = Vh[m]; one[0].S = Sh; one[0].b = 1;
+        one[0].w = P + m; one[0].V = Vh[m]; one[0].S = Sh; one[0].b = 1; one[0].Wlo = Whlo; one[0].V1lo = Vh1lo;
         int kh = 0;
         notconv += S.run(one, KIND_HOM, &kh);
         int kk = 0;
         d2h(c, &kk, S.wi + (size_t)(P + m) * L.istride + WI_K, sizeof(int));
         Kh[m] = kk;
+        if (o->diagnostics & PEXP_DIAG_ORTH) orth_max = std::max(orth_max, S.orth_defect(Vh[m], kk));
         k_hom_max = std::max(k_hom_max, kh);
         k_hom_sum += kh;
     }
@@ -669,6 +931,7 @@ int solve_linear_typed(pexp_ctx* c, const pexp_operator* op, const pexp_options*
         rep->not_converged = notconv;
         rep->est_max = est_max;
         rep->sigma_ratio_max = sig_max;
+        rep->orth_max = orth_max;
         const double w = (double)sizeof(T);
         double bytes = 0;
         // algorithmic bytes: source reads, Krylov steps, reconstruction
@@ -694,7 +957,7 @@ int solve_linear_dispatch(pexp_ctx* c, const pexp_operator* op, const pexp_optio
     Partition pt = make_partition(o->n_out, o->P);
     const int b_cap = std::min(std::min(o->max_rank, PEXP_MAX_RANK), pt.smax);
     const int g_conv = G_dev && ((g_dtype == PEXP_F64) != fp64);
-    size_t need = keep_top + align_up(sizeof(double) * n) +
+    size_t need = keep_top +
                   (fp64 ? linear_workspace_bytes<double>(n, o, g_conv, b_cap)
                         : linear_workspace_bytes<float>(n, o, g_conv, b_cap));
     if (need > c->ws_cap) {
@@ -703,9 +966,8 @@ int solve_linear_dispatch(pexp_ctx* c, const pexp_operator* op, const pexp_optio
         if (r) return r;
     }
     c->ws_top = keep_top;
-    double* u0d = as<double>(ws_alloc(c, sizeof(double) * n));
-    if (y_dtype == PEXP_F64) cudaMemcpyAsync(u0d, y0_dev, sizeof(double) * n, cudaMemcpyDeviceToDevice, c->stream);
-    else launch_convert<float, double>(reinterpret_cast<const float*>(y0_dev), u0d, n, c->stream);
+    // the initial condition is FP64 in every precision (A u0 amplifies its rounding by ||A||)
+    const double* u0d = reinterpret_cast<const double*>(y0_dev);
     if (fp64) {
         if (y_dtype == PEXP_F64) return solve_linear_typed<double, double>(c, op, o, u0d, G_dev, g_dtype, as<double>(Y_dev), rep);
         return solve_linear_typed<double, float>(c, op, o, u0d, G_dev, g_dtype, as<float>(Y_dev), rep);
@@ -799,6 +1061,7 @@ int pexp_destroy(pexp_ctx* c) {
     cudaSetDevice(c->device);
     if (c->stream) cudaStreamSynchronize(c->stream);
     if (c->ws) cudaFree(c->ws);
+    if (c->bs) cudaFree(c->bs);
     for (int h = 0; h < 2; ++h) {
         if (c->stage_h[h]) cudaFreeHost(c->stage_h[h]);
         if (c->stage_d[h]) cudaFree(c->stage_d[h]);
@@ -850,7 +1113,7 @@ int pexp_solve_linear_host(pexp_ctx* c, const pexp_operator* op, const pexp_opti
     const OpDesc od = make_opdesc(*op);
     const size_t n = (size_t)od.n;
     const size_t ys = (y_dtype == PEXP_F64) ? 8 : 4, gs = (g_dtype == PEXP_F64) ? 8 : 4;
-    const size_t bytes = align_up(n * ys) + (G_host ? align_up(n * o->n_out * gs) : 0) + align_up(n * o->n_out * ys);
+    const size_t bytes = align_up(n * 8) + (G_host ? align_up(n * o->n_out * gs) : 0) + align_up(n * o->n_out * ys);
     cudaSetDevice(c->device);
     if (bytes > c->io_cap) {
         if (c->io_d) cudaFree(c->io_d);
@@ -861,11 +1124,11 @@ int pexp_solve_linear_host(pexp_ctx* c, const pexp_operator* op, const pexp_opti
     }
     char* p = reinterpret_cast<char*>(c->io_d);
     void* y0d = p;
-    p += align_up(n * ys);
+    p += align_up(n * 8);
     void* Gd = nullptr;
     if (G_host) { Gd = p; p += align_up(n * o->n_out * gs); }
     void* Yd = p;
-    PEXP_CUDA_TRY(cudaMemcpyAsync(y0d, y0_host, n * ys, cudaMemcpyHostToDevice, c->stream));
+    PEXP_CUDA_TRY(cudaMemcpyAsync(y0d, y0_host, n * 8, cudaMemcpyHostToDevice, c->stream));
     if (G_host) PEXP_CUDA_TRY(cudaMemcpyAsync(Gd, G_host, n * o->n_out * gs, cudaMemcpyHostToDevice, c->stream));
     int r = pexp_solve_linear(c, op, o, y0d, Gd, g_dtype, Yd, y_dtype, rep);
     if (r == PEXP_OK || r == PEXP_ERR_NOT_CONVERGED) {
@@ -913,8 +1176,12 @@ int pexp_solve_burgers(pexp_ctx* c, const pexp_operator* op, const pexp_options*
         if (init_dev) {
             cudaMemcpyAsync(Uprev, init_dev, es * n * nt, cudaMemcpyDeviceToDevice, c->stream);
         } else {
-            for (int i = 0; i < nt; ++i)
-                cudaMemcpyAsync(Uprev + es * n * i, u0_dev, es * n, cudaMemcpyDeviceToDevice, c->stream);
+            for (int i = 0; i < nt; ++i) {
+                if (dtype == PEXP_F64)
+                    cudaMemcpyAsync(Uprev + es * n * i, u0_dev, es * n, cudaMemcpyDeviceToDevice, c->stream);
+                else
+                    launch_convert<double, float>(reinterpret_cast<const double*>(u0_dev), as<float>(Uprev + es * n * i), n, c->stream);
+            }
         }
         std::vector<double> nh(2 * nt);
         int status_l = PEXP_ERR_WR_NOT_CONVERGED;
@@ -1012,9 +1279,9 @@ int pexp_sai_solve(pexp_ctx* c, const pexp_operator* op, double gamma, const voi
         sg.flush();
         const SaiCoef cf = sai_coefficients(od, gamma);
         if (dtype == PEXP_F64)
-            launch_sai_solve<double>(od, cf, reinterpret_cast<const double* const*>(dx), reinterpret_cast<double* const*>(dy), nvec, scr, c->stream);
+            launch_sai_solve<double>(od, cf, reinterpret_cast<const double* const*>(dx), reinterpret_cast<double* const*>(dy), nullptr, nvec, scr, c->stream);
         else
-            launch_sai_solve<float>(od, cf, reinterpret_cast<const float* const*>(dx), reinterpret_cast<float* const*>(dy), nvec, scr, c->stream);
+            launch_sai_solve<float>(od, cf, reinterpret_cast<const float* const*>(dx), reinterpret_cast<float* const*>(dy), nullptr, nvec, scr, c->stream);
         check_launch(c);
         sync(c);
         return PEXP_OK;

@@ -87,6 +87,89 @@ void launch_stencil_ptrs(const OpDesc& op, const T* const* X, T* const* Y, int n
     k_stencil<T><<<g, 256, 0, s>>>(op, X, Y, nullptr, nullptr, transpose);
 }
 
+// Double-float stencil for FP32 data: (hi, lo) = A x or A^T x to ~2^-48 relative,
+// from the exact FP32 values of x.  The Galerkin matrix V^T A V of the FP32 basis is
+// built from these: rounding A x to FP32 would perturb it by far more than the
+// basis rounding itself, because A amplifies the high-frequency part of x.
+struct DF2 {
+    float hi, lo;
+};
+__device__ __forceinline__ DF2 two_diff(float a, float b) {
+    const float s = a - b;
+    const float bb = s - a;
+    const float e = (a - (s - bb)) - (b + bb);
+    return DF2{s, e};
+}
+__device__ __forceinline__ DF2 df2_add(DF2 a, DF2 b) {
+    const float s = a.hi + b.hi;
+    const float bb = s - a.hi;
+    const float e = (a.hi - (s - bb)) + (b.hi - bb) + (a.lo + b.lo);
+    const float h = s + e;
+    return DF2{h, e - (h - s)};
+}
+__device__ __forceinline__ DF2 df2_mul(DF2 a, DF2 b) {
+    const float p = a.hi * b.hi;
+    float e = fmaf(a.hi, b.hi, -p);
+    e = fmaf(a.hi, b.lo, e);
+    e = fmaf(a.lo, b.hi, e);
+    const float h = p + e;
+    return DF2{h, e - (h - p)};
+}
+__device__ __forceinline__ DF2 df2_from(double v) {
+    const float h = (float)v;
+    return DF2{h, (float)(v - (double)h)};
+}
+
+__device__ __forceinline__ DF2 stencil_df_dim(const Dim1& D, const float* __restrict__ x, const float* __restrict__ xl,
+                                             int64_t k, int64_t idx, float u, float ul, int transpose) {
+    float um, up, uml = 0.f, upl = 0.f;
+    int64_t km = -1, kp = -1;
+    if (idx > 0) km = k - D.stride;
+    else if (D.periodic) km = k + (D.n - 1) * D.stride;
+    if (idx < D.n - 1) kp = k + D.stride;
+    else if (D.periodic) kp = k - (D.n - 1) * D.stride;
+    um = km >= 0 ? x[km] : 0.f;
+    up = kp >= 0 ? x[kp] : 0.f;
+    if (xl) {
+        uml = km >= 0 ? xl[km] : 0.f;
+        upl = kp >= 0 ? xl[kp] : 0.f;
+    }
+    // differences of (hi + lo) values: exact hi difference plus the lo difference
+    const DF2 dm = df2_add(two_diff(um, u), DF2{uml - ul, 0.f});
+    const DF2 dp = df2_add(two_diff(up, u), DF2{upl - ul, 0.f});
+    const DF2 dc = df2_add(two_diff(up, um), DF2{upl - uml, 0.f});
+    const DF2 d = df2_from(D.d), c = df2_from(transpose ? -D.c : D.c);
+    const DF2 t1 = df2_mul(d, df2_add(dm, dp));
+    const DF2 t2 = df2_mul(c, dc);
+    return df2_add(t1, DF2{-t2.hi, -t2.lo});
+}
+
+__global__ void __launch_bounds__(256) k_stencil_df(OpDesc op, const float* const* __restrict__ Xp,
+                                                   const float* const* __restrict__ Xl,
+                                                   float* const* __restrict__ Yh, float* const* __restrict__ Yl,
+                                                   int transpose) {
+    const int v = blockIdx.y;
+    const float* x = Xp[v];
+    const float* xl = Xl ? Xl[v] : nullptr;
+    float* yh = Yh[v];
+    float* yl = Yl[v];
+    for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < op.n; k += (int64_t)gridDim.x * blockDim.x) {
+        const float u = x[k];
+        const float ul = xl ? xl[k] : 0.f;
+        DF2 r = stencil_df_dim(op.x, x, xl, k, (op.dim == 1) ? k : (k % op.x.n), u, ul, transpose);
+        if (op.dim == 2) r = df2_add(r, stencil_df_dim(op.y, x, xl, k, k / op.x.n, u, ul, transpose));
+        yh[k] = r.hi;
+        yl[k] = r.lo;
+    }
+}
+
+void launch_stencil_df(const OpDesc& op, const float* const* X, const float* const* Xl, float* const* Yh,
+                       float* const* Yl, int nvec, int transpose, cudaStream_t s) {
+    if (nvec <= 0) return;
+    dim3 g(std::min(grid_for(op.n, 256), std::max(1, 4 * kNumSM * 8 / nvec + 1)), nvec);
+    k_stencil_df<<<g, 256, 0, s>>>(op, X, Xl, Yh, Yl, transpose);
+}
+
 // =====================================================================================
 // Burgers source g = -u u_x (Sec. 4), conservative or advective central form
 // =====================================================================================
@@ -625,6 +708,108 @@ void launch_ts_nn(const TsTask<T>* tasks_dev, int ntasks, int max_pq, int64_t n,
     k_ts_nn<T, 16><<<grid, 256, sm, s>>>(tasks_dev, n);
 }
 
+// Double-float block update for FP32 data (the working block of a Krylov step):
+//   Z = alpha (X + xs 1^T) T  [+ Z]
+// X and Z are (hi, lo) pairs of FP32 arrays (a missing lo array means 0, and for
+// Z means "round to FP32"); products and sums are error-free to ~2^-48, so the
+// cancellation of Gram-Schmidt leaves no FP32-sized noise in the new direction.
+__global__ void __launch_bounds__(256) k_ts_nn_df(const DfTask* __restrict__ tasks, int64_t n) {
+    const DfTask tk = tasks[blockIdx.y];
+    extern __shared__ float smem_df[];
+    const int p = tk.p, q = tk.q;
+    float* Th = smem_df;
+    float* Tl = smem_df + p * q;
+    for (int e = threadIdx.x; e < p * q; e += blockDim.x) {
+        const int a = e % p, c = e / p;
+        const double v = tk.alpha * tk.Tm[a + (int64_t)c * tk.ldt];
+        const float h = (float)v;
+        Th[e] = h;
+        Tl[e] = (float)(v - (double)h);
+    }
+    __syncthreads();
+    const bool inplace = tk.Zh == tk.Xh;
+    const int pl = (tk.Xl && tk.pl > 0) ? tk.pl : (tk.Xl ? p : 0);   // columns of X with a low part
+    for (int64_t r = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; r < n; r += (int64_t)gridDim.x * blockDim.x) {
+        DF xsh = DF{0.f, 0.f};
+        if (tk.xs) {
+            const double v = tk.xs[r];
+            const float h = (float)v;
+            xsh = DF{h, (float)(v - (double)h)};
+        }
+        DF acc[16];
+#pragma unroll
+        for (int c = 0; c < 16; ++c) acc[c] = DF{0.f, 0.f};
+        if (inplace) {
+            DF xr[16];
+#pragma unroll
+            for (int a = 0; a < 16; ++a)
+                if (a < p) xr[a] = DF{tk.Xh[(int64_t)a * tk.ldx + r], a < pl ? tk.Xl[(int64_t)a * tk.ldx + r] : 0.f};
+#pragma unroll
+            for (int a = 0; a < 16; ++a)
+                if (a < p) {
+                    const DF x = tk.xs ? df_add(xr[a], xsh) : xr[a];
+#pragma unroll
+                    for (int c = 0; c < 16; ++c)
+                        if (c < q) acc[c] = df_add(acc[c], df_mul(x, DF{Th[a + c * p], Tl[a + c * p]}));
+                }
+        } else {
+            for (int a = 0; a < p; ++a) {
+                DF x = DF{tk.Xh ? tk.Xh[(int64_t)a * tk.ldx + r] : 0.f, a < pl ? tk.Xl[(int64_t)a * tk.ldx + r] : 0.f};
+                if (tk.xs) x = df_add(x, xsh);
+#pragma unroll
+                for (int c = 0; c < 16; ++c)
+                    if (c < q) acc[c] = df_add(acc[c], df_mul(x, DF{Th[a + c * p], Tl[a + c * p]}));
+            }
+        }
+#pragma unroll
+        for (int c = 0; c < 16; ++c)
+            if (c < q) {
+                DF z = acc[c];
+                const int64_t o = (int64_t)c * tk.ldz + r;
+                if (tk.accumulate) z = df_add(z, DF{tk.Zh[o], tk.Zl ? tk.Zl[o] : 0.f});
+                if (tk.Zl) {
+                    tk.Zh[o] = z.hi;
+                    tk.Zl[o] = z.lo;
+                } else {
+                    tk.Zh[o] = z.hi + z.lo;
+                }
+            }
+    }
+}
+
+void launch_ts_nn_df(const DfTask* tasks_dev, int ntasks, int max_pq, int64_t n, cudaStream_t s) {
+    if (ntasks <= 0) return;
+    int bx = std::max(1, std::min(grid_for(n, 256), (4 * kNumSM * 4 + ntasks - 1) / ntasks));
+    dim3 grid(bx, ntasks);
+    size_t sm = (size_t)max_pq * 2 * sizeof(float);
+    if (sm > 48 * 1024) cudaFuncSetAttribute(k_ts_nn_df, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    k_ts_nn_df<<<grid, 256, sm, s>>>(tasks_dev, n);
+}
+
+// out[i] = sum_k u[k] * G[i*n + k] for the rows i < nrows (FP64 accumulation).
+template <typename T>
+__global__ void __launch_bounds__(256) k_row_dots(const double* __restrict__ u, const T* __restrict__ G, int64_t n,
+                                                 double* __restrict__ out) {
+    const int64_t row = blockIdx.x;
+    const T* g = G + row * n;
+    double s = 0.0;
+    for (int64_t k = threadIdx.x; k < n; k += blockDim.x) s = fma(u[k], (double)g[k], s);
+    __shared__ double red[8];
+    s = warp_sum(s);
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = s;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double t = 0;
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += red[w];
+        out[row] = t;
+    }
+}
+template <typename T>
+void launch_row_dots(const double* u, const T* G, int64_t n, int nrows, double* out, cudaStream_t s) {
+    if (nrows <= 0) return;
+    k_row_dots<T><<<nrows, 256, 0, s>>>(u, G, n, out);
+}
+
 // =====================================================================================
 // Reconstruction u(t) = u0 + V y(t)
 // =====================================================================================
@@ -755,7 +940,8 @@ void launch_row_diff_norms(const T* A, const T* B, int64_t n, int nrows, double*
     template void launch_recon<T, double>(const ReconTask<T>*, int, int, int64_t, const double*, double*,  \
                                           int64_t, int, cudaStream_t);                                    \
     template void launch_row_diff_norms<T>(const T*, const T*, int64_t, int, double*, cudaStream_t); \
-    template void launch_add<T>(T*, const T*, int64_t, cudaStream_t);
+    template void launch_add<T>(T*, const T*, int64_t, cudaStream_t);                                   \
+    template void launch_row_dots<T>(const double*, const T*, int64_t, int, double*, cudaStream_t);
 PEXP_INST_T(double)
 PEXP_INST_T(float)
 template void launch_convert<double, float>(const double*, float*, int64_t, cudaStream_t);

@@ -31,6 +31,7 @@ BC_PERIODIC = 0
 BC_DIRICHLET0 = 1
 KRYLOV_POLY = 0
 KRYLOV_SAI = 1
+DIAG_ORTH = 1
 FP64 = 0
 MIXED = 1
 F64 = 0
@@ -53,7 +54,7 @@ class Options(C.Structure):
                 ("svd_tol", C.c_double), ("max_rank", C.c_int), ("restart_len", C.c_int),
                 ("max_restarts", C.c_int), ("krylov", C.c_int), ("sai_gamma", C.c_double),
                 ("precision", C.c_int), ("wr_max_iter", C.c_int), ("wr_tol", C.c_double),
-                ("burgers_form", C.c_int)]
+                ("burgers_form", C.c_int), ("diagnostics", C.c_int)]
 
 
 class Report(C.Structure):
@@ -62,7 +63,8 @@ class Report(C.Structure):
                 ("not_converged", C.c_int), ("est_max", C.c_double), ("sigma_ratio_max", C.c_double),
                 ("wr_iters", C.c_int), ("wr_delta", C.c_double), ("time_ms", C.c_double),
                 ("t_source_ms", C.c_double), ("t_krylov_ms", C.c_double), ("t_hom_ms", C.c_double),
-                ("t_recon_ms", C.c_double), ("bytes_alg", C.c_double), ("launches", C.c_int)]
+                ("t_recon_ms", C.c_double), ("orth_max", C.c_double), ("bytes_alg", C.c_double),
+                ("launches", C.c_int)]
 
     def as_dict(self) -> dict:
         return {f[0]: getattr(self, f[0]) for f in self._fields_}
@@ -178,9 +180,12 @@ class Context:
 
     # ---------------------------------------------------------------- solvers
     def solve_linear(self, op: dict, opts: dict, y0, G, Y, check: bool = True) -> dict:
-        """Paraexp-EBK solve: y0 (n,), G (n_out, n) or None, Y (n_out, n) -- CUDA tensors."""
+        """Paraexp-EBK solve: y0 (n,) FP64, G (n_out, n) or None, Y (n_out, n) -- CUDA tensors."""
+        import torch
         for t in (y0, Y) + ((G,) if G is not None else ()):
             assert t.is_cuda and t.is_contiguous()
+        if y0.dtype != torch.float64:
+            raise TypeError("the initial condition must be FP64")
         rep = Report()
         o = make_options(opts)
         rc = lib().pexp_solve_linear(self.h, C.byref(make_operator(op)), C.byref(o), C.c_void_p(y0.data_ptr()),
@@ -198,6 +203,8 @@ class Context:
         import numpy as np
         for a in (y0, Y) + ((G,) if G is not None else ()):
             assert isinstance(a, np.ndarray) and a.flags["C_CONTIGUOUS"]
+        if y0.dtype != np.float64:
+            raise TypeError("the initial condition must be FP64")
         rep = Report()
         rc = lib().pexp_solve_linear_host(self.h, C.byref(make_operator(op)), C.byref(make_options(opts)),
                                           C.c_void_p(y0.ctypes.data),
@@ -211,6 +218,10 @@ class Context:
         return d
 
     def solve_burgers(self, op: dict, opts: dict, u0, U, forcing=None, init=None, check: bool = True) -> dict:
+        """Burgers waveform relaxation: u0 (n,) FP64; U, forcing, init (n_out, n) in one dtype."""
+        import torch
+        if u0.dtype != torch.float64:
+            raise TypeError("the initial condition must be FP64")
         rep = Report()
         rc = lib().pexp_solve_burgers(self.h, C.byref(make_operator(op)), C.byref(make_options(opts)),
                                       C.c_void_p(u0.data_ptr()),

@@ -22,7 +22,7 @@ def run_linear(c, pr, opts=None, dtype="f64", G=True):
     opts = dict(pr.opts if opts is None else opts)
     dt = torch.float64 if dtype == "f64" else torch.float32
     dev = torch.device("cuda:0")
-    y0 = torch.from_numpy(pr.u0).to(dev, dt)
+    y0 = torch.from_numpy(pr.u0).to(dev)
     Gt = torch.from_numpy(pr.G).to(dev, dt) if (G and pr.G is not None) else None
     Y = torch.zeros((opts["n_out"], pr.n), dtype=dt, device=dev)
     rep = c.solve_linear(pr.op, opts, y0, Gt, Y)
