@@ -1,0 +1,322 @@
+"""Benchmark of the GB300 Paraexp-EBK hot path.
+
+Workload: 1D periodic advection-diffusion, n = 2^20 points, nu = 1e-3, a = 1,
+u0 = sin(2 pi x) + exp(-100 (x-0.5)^2), g = sin(4 pi x) cos(2 pi t), T = 1,
+P = 64 subintervals, 1025 output times, source rank <= 8 (SVD cut 1e-10).
+One step = one full PEBK solve (source compression, nonhomogeneous block Krylov
+solves of all subintervals, homogeneous continuation, reconstruction of all
+1025 outputs).  The headline is the mixed-precision path; the FP64 GPU path is
+run on the same inputs for the accuracy comparison and the speedup.
+
+Prints one JSON line (rank 0).  `--impl reference` times the FP64 CPU oracle
+on a bounded sample of the same workload instead.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "Paraexp solves/s & HBM GB/s: mixed-prec vs FP64 GPU at 1e-6 rel err"
+N, NU, A, P, NT, T = 1 << 20, 1e-3, 1.0, 64, 1025, 1.0
+WORKLOAD = "adv_diff_1d_n1048576_P64_nout1025"
+
+
+def opts_for(precision: int, diag: int = 0) -> dict:
+    from paper_1509_04567_gb300 import workloads as wl
+    return wl.default_opts(T=T, P=P, n_out=NT, tol=1e-7 if precision else 1e-8, svd_tol=1e-10, max_rank=8,
+                           precision=precision, diagnostics=diag)
+
+
+def config(precision: str) -> dict:
+    return {"workload": WORKLOAD, "n": N, "nu": NU, "a": A, "P": P, "n_out": NT, "T": T,
+            "precision": precision, "krylov": "shift-and-invert", "tol": 1e-7 if precision == "mixed" else 1e-8,
+            "l2": "inputs larger than L2 (source 4.3 GB FP32 / 8.6 GB FP64, outputs 4.3 GB)"}
+
+
+def read_peaks() -> dict:
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        return json.load(open(p))
+    except Exception:
+        return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "fallback": True}
+
+
+def profile_traffic(kernel_class: str):
+    """Per-launch DRAM bytes of a kernel class from the committed ncu summary, or None."""
+    p = os.path.join(ROOT, "profiles", f"{kernel_class}_traffic.txt")
+    try:
+        for line in open(p):
+            if line.startswith("traffic_bytes_per_launch:"):
+                return float(line.split(":")[1])
+    except Exception:
+        pass
+    return None
+
+
+class Clocks:
+    """nvidia-smi sampling of SM clocks and throttle reasons during the timed region."""
+
+    def __init__(self, device: int):
+        self.f = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+        q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+        try:
+            self.p = subprocess.Popen(["nvidia-smi", f"--query-gpu={q}", "--format=csv,noheader,nounits",
+                                       "-i", str(device), "-lms", "200"], stdout=self.f, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.p = None
+
+    def stop(self) -> dict:
+        if self.p is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.p.terminate()
+        self.p.wait()
+        self.f.seek(0)
+        sm, mx, reasons = [], [], set()
+        for line in self.f.read().splitlines():
+            v = [x.strip() for x in line.split(",")]
+            if len(v) < 9:
+                continue
+            try:
+                sm.append(float(v[1]))
+                mx.append(float(v[2]))
+            except ValueError:
+                continue
+            for name, flag in zip(("hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"), v[5:9]):
+                if flag.lower() == "active":
+                    reasons.add(name)
+        os.unlink(self.f.name)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": sorted(reasons)}
+
+
+def cpu_sample(seconds_hint: float = 20.0) -> dict:
+    """Time the FP64 CPU oracle on a bounded sample of the workload: the nonhomogeneous
+    part of one subinterval and one homogeneous window; a full solve is 64 of the former
+    and 2016 (= 64*63/2) of the latter, so solves/s = 1 / (64 t_nh + 2016 t_hom)."""
+    import numpy as np
+    import oracle.pebk as ob
+    from paper_1509_04567_gb300 import workloads as wl
+    # the first subinterval's samples only (the full source would be 8.6 GB on the host)
+    pr = wl.adv_diff_1d(n=N, nu=NU, a=A, T=T, P=P, n_out=NT, tol=1e-8, svd_tol=1e-10, max_rank=8,
+                        with_source=False)
+    opts = dict(pr.opts)
+    A_ = ob.operator_matrix(pr.op)
+    t = np.arange(NT) * (T / (NT - 1))
+    idx = ob.partition(NT, P)
+    kop = ob.KrylovOperator(pr.op, A_, 1, opts["sai_gamma"] * T / P)
+    x = wl.grid_1d(N)
+    i0, i1 = idx[0], idx[1]
+    G1 = np.cos(2 * np.pi * t[i0:i1 + 1])[:, None] * np.sin(4 * np.pi * x)[None, :]
+    t0 = time.perf_counter()
+    tau = t[i0:i1 + 1] - t[i0]
+    Ghat = (A_ @ pr.u0)[:, None] + G1.T
+    U, C, _ = ob.compress_source(Ghat, opts["svd_tol"], opts["max_rank"])
+    coef = ob.spline_segments(tau, C)
+    V, Y, _ = ob.ebk_nonhomogeneous(kop, U, tau, coef, opts["tol"], float(np.linalg.norm(pr.u0)), 20)
+    t_nh = time.perf_counter() - t0
+    w = V @ Y[-1]
+    t1 = time.perf_counter()
+    ob.ebk_homogeneous(kop, w, tau, opts["tol"], float(np.linalg.norm(pr.u0)), 20)
+    t_hom = time.perf_counter() - t1
+    per_solve = P * t_nh + (P * (P - 1) // 2) * t_hom
+    try:
+        import threadpoolctl
+        cores = max(i.get("num_threads", 1) for i in threadpoolctl.threadpool_info()) if threadpoolctl.threadpool_info() else 1
+    except Exception:
+        cores = os.cpu_count()
+    return {"value": 1.0 / per_solve, "unit": "solves/s", "cores": cores, "kind": "oracle",
+            "sample": f"one nonhomogeneous subinterval ({t_nh:.2f} s) and one homogeneous window ({t_hom:.2f} s) "
+                      f"of the workload, extrapolated to 64 + 2016 per solve",
+            "sample_seconds": t_nh + t_hom}
+
+
+def run_reference(args) -> None:
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    for _ in range(min(args.warmup, 1)):
+        cpu_sample()
+    steps = [cpu_sample() for _ in range(args.steps)]
+    cb = steps[-1]
+    v = statistics.median(s["value"] for s in steps)
+    line = {"impl": "reference", "metric": METRIC, "value": v, "unit": "solves/s", "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 / v, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": config(args.precision), "cpu_baseline": dict(cb, value=v),
+            "e2e": {"value": v, "unit": "solves/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def main() -> None:
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=3)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--precision", default="mixed", choices=["mixed", "fp64"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.impl == "reference":
+        run_reference(args)
+        return
+
+    import numpy as np
+    import torch
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl")
+    dev = torch.device("cuda", local)
+    torch.cuda.set_device(dev)
+
+    import __graft_entry__
+    if rank == 0 or world == 1:
+        __graft_entry__.build()
+    if dist is not None:
+        dist.barrier()
+    from paper_1509_04567_gb300 import pexp, workloads as wl
+
+    prec = 1 if args.precision == "mixed" else 0
+    gdt = torch.float32 if prec else torch.float64
+    ctx = pexp.Context(local)
+    op = wl.make_op(N, NU, A)
+    # inputs on the device (same formulas as workloads.adv_diff_1d, evaluated on the GPU)
+    x = torch.arange(N, dtype=torch.float64, device=dev) / N
+    u0 = torch.sin(2 * np.pi * x) + torch.exp(-100.0 * (x - 0.5) ** 2)
+    tt = torch.arange(NT, dtype=torch.float64, device=dev) * (T / (NT - 1))
+    G = (torch.cos(2 * np.pi * tt)[:, None] * torch.sin(4 * np.pi * x)[None, :]).to(gdt).contiguous()
+    Y = torch.empty((NT, N), dtype=gdt, device=dev)
+    opts = opts_for(prec, diag=pexp.DIAG_KTIME)
+    stream = torch.cuda.current_stream(dev)
+
+    for _ in range(args.warmup):
+        ctx.solve_linear(op, opts, u0, G, Y)
+    torch.cuda.synchronize(dev)
+    if dist is not None:
+        dist.barrier()
+    clocks = Clocks(local)
+    torch.cuda.synchronize(dev)
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    reps = []
+    ev0.record(stream)
+    for _ in range(args.steps):
+        reps.append(ctx.solve_linear(op, opts, u0, G, Y))
+    ev1.record(stream)
+    torch.cuda.synchronize(dev)
+    ck = clocks.stop()
+    ms = ev0.elapsed_time(ev1) / args.steps
+    if dist is not None:
+        t = torch.tensor([ms], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+        dist.barrier()
+    value = world * 1e3 / ms
+
+    # kernel classes over the timed region: the dominant one sets the roofline line
+    k_ms = np.sum([r["k_ms"] for r in reps], axis=0)
+    k_n = np.sum([r["k_launches"] for r in reps], axis=0)
+    k_b = np.sum([r["k_bytes"] for r in reps], axis=0)
+    dom = int(np.argmax(k_ms))
+    peaks = read_peaks()
+    if prec:
+        achieved = k_b[dom] / (k_ms[dom] * 1e-3) / 1e9
+        roof = {"bound": "hbm", "kernel_class": pexp.KC_NAMES[dom], "achieved": achieved,
+                "peak": peaks.get("hbm_gbs"), "unit": "GB/s",
+                "frac": achieved / peaks.get("hbm_gbs", 6800.0),
+                "traffic": profile_traffic(pexp.KC_NAMES[dom]),
+                "peak_source": "measured" if "fallback" not in peaks else "fallback",
+                "launches": int(k_n[dom]), "avg_launch_us": 1e3 * k_ms[dom] / max(1, k_n[dom])}
+    else:
+        achieved = k_b[dom] / (k_ms[dom] * 1e-3) / 1e9
+        roof = {"bound": "alu", "kernel_class": pexp.KC_NAMES[dom], "achieved": achieved, "unit": "GB/s",
+                "peak": None, "frac": None, "traffic": None,
+                "note": "FP64 path: bound by the FP64 FMA rate (1.01 TFLOP/s measured), not HBM"}
+    kernel_split = {pexp.KC_NAMES[i]: {"ms_per_step": k_ms[i] / args.steps, "launches_per_step": k_n[i] / args.steps,
+                                        "GB_per_s": (k_b[i] / (k_ms[i] * 1e-3) / 1e9) if k_ms[i] > 0 else None}
+                    for i in range(8) if k_n[i] > 0}
+    rep = reps[-1]
+
+    extra = {}
+    if rank == 0:
+        # accuracy and speed of the other precision on the same inputs
+        oth = 0 if prec else 1
+        ot = opts_for(oth)
+        Go = G.to(torch.float64 if oth == 0 else torch.float32).contiguous()
+        Yo = torch.empty((NT, N), dtype=Go.dtype, device=dev)
+        ctx.solve_linear(op, ot, u0, Go, Yo)
+        torch.cuda.synchronize(dev)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        ctx.solve_linear(op, ot, u0, Go, Yo)
+        e1.record(stream)
+        torch.cuda.synchronize(dev)
+        ms_o = e0.elapsed_time(e1)
+        Yd = (Yo if oth == 0 else Y).double()
+        Ym = (Y if oth == 0 else Yo).double()
+        err = float(((Ym - Yd).norm(dim=1) / Yd.norm(dim=1)).max().item())
+        del Yd, Ym, Yo, Go
+        extra = {"fp64_ms_per_step": ms_o if prec else ms, "mixed_ms_per_step": ms if prec else ms_o,
+                 "speedup_mixed_vs_fp64": (ms_o / ms) if prec else (ms / ms_o),
+                 "rel_err_mixed_vs_fp64": err}
+
+        # end to end through the host-pointer entry: pinned host inputs/outputs, copies timed
+        u0h = u0.cpu().numpy()
+        Gh = torch.empty((NT, N), dtype=gdt, pin_memory=True)
+        Gh.copy_(G)
+        Yh = torch.empty((NT, N), dtype=gdt, pin_memory=True)
+        Gn, Yn = Gh.numpy(), Yh.numpy()
+        opts_e = opts_for(prec)
+        ctx.solve_linear_host(op, opts_e, u0h, Gn, Yn)
+        torch.cuda.synchronize(dev)
+        t0 = time.perf_counter()
+        for _ in range(args.steps):
+            ctx.solve_linear_host(op, opts_e, u0h, Gn, Yn)
+        torch.cuda.synchronize(dev)
+        e2e_s = (time.perf_counter() - t0) / args.steps
+        el = Gh.element_size()
+        extra["e2e"] = {"value": world / e2e_s, "unit": "solves/s",
+                        "h2d_bytes_per_step": int(N * 8 + NT * N * el), "d2h_bytes_per_step": int(NT * N * el)}
+        del Gh, Yh
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        cpu = cpu_sample()
+
+    if rank == 0:
+        line = {"metric": METRIC, "value": value, "unit": "solves/s", "n_gpus": world, "steps": args.steps,
+                "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+                "vs_baseline": None, "dtype": "f32" if prec else "f64", "data": "synthetic",
+                "config": config(args.precision), "hbm_gbs_alg": rep["bytes_alg"] / (ms * 1e-3) / 1e9,
+                "roofline": roof, "clocks": ck, "gpu_launches": int(sum(r["launches"] for r in reps)),
+                "krylov": {"k_nh_max": rep["k_nh_max"], "k_hom_max": rep["k_hom_max"], "k_hom_sum": rep["k_hom_sum"],
+                           "rank_max": rep["rank_max"], "not_converged": rep["not_converged"]},
+                "phases_ms": {k: rep[k] for k in ("t_source_ms", "t_krylov_ms", "t_hom_ms", "t_recon_ms")},
+                "kernel_classes": kernel_split}
+        line.update(extra)
+        if cpu is not None:
+            line["cpu_baseline"] = cpu
+        print(json.dumps(line), flush=True)
+    ctx.close()
+    if dist is not None:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -105,7 +105,18 @@ typedef struct {
     int    diagnostics;  /* bit 0: measure the orthogonality of every Krylov basis (report.orth_max) */
 } pexp_options;
 
-#define PEXP_DIAG_ORTH 1
+#define PEXP_DIAG_ORTH  1   /* measure the orthogonality of every Krylov basis */
+#define PEXP_DIAG_KTIME 2   /* time every kernel class with CUDA events (report.k_*) */
+
+/* kernel classes of report.k_ms / k_launches / k_bytes */
+#define PEXP_KC_SAI     0   /* shift-and-invert recurrence solve */
+#define PEXP_KC_STENCIL 1   /* operator stencil (A V, A^T V) */
+#define PEXP_KC_PROJ    2   /* tall-skinny projections X^T Y (Gram-Schmidt, Galerkin, Gram) */
+#define PEXP_KC_UPDATE  3   /* tall-skinny block updates X T */
+#define PEXP_KC_SMALL   4   /* per-subinterval small FP64 kernels */
+#define PEXP_KC_SOURCE  5   /* source Gram matrix and source block */
+#define PEXP_KC_RECON   6   /* reconstruction of the outputs */
+#define PEXP_KC_COUNT   8
 
 #define PEXP_MAX_RANK   16    /* largest block width */
 #define PEXP_MAX_STEPS  40    /* largest Krylov step budget restart_len*(max_restarts+1) */
@@ -131,6 +142,9 @@ typedef struct {
     double t_hom_ms;          /*   homogeneous continuation chain */
     double t_recon_ms;        /*   reconstruction of all output times */
     double orth_max;          /* max over bases of max|V^T V - I| (PEXP_DIAG_ORTH), else -1 */
+    double k_ms[PEXP_KC_COUNT];      /* PEXP_DIAG_KTIME: summed kernel time per class (ms) */
+    int    k_launches[PEXP_KC_COUNT];/*   launches per class */
+    double k_bytes[PEXP_KC_COUNT];   /*   algorithmic bytes per class (each array once per launch) */
     double bytes_alg;         /* algorithmic HBM bytes: each array counted once per pass the method needs */
     int    launches;          /* kernels launched by the call */
 } pexp_report;

@@ -31,6 +31,37 @@
 
 using namespace pexp;
 
+// ---------------------------------------------------------------- kernel-class timer
+// Optional CUDA-event timing of kernel classes: events recorded around launches on the
+// solve's stream, read back once the solve has completed.
+struct KTimer {
+    bool on = false;
+    std::vector<cudaEvent_t> pool;
+    size_t used = 0;
+    struct Rec {
+        int cls;
+        cudaEvent_t a, b;
+        double bytes;
+    };
+    std::vector<Rec> recs;
+    cudaEvent_t next() {
+        if (used == pool.size()) {
+            cudaEvent_t e;
+            cudaEventCreate(&e);
+            pool.push_back(e);
+        }
+        return pool[used++];
+    }
+    void reset(bool enable) {
+        on = enable;
+        used = 0;
+        recs.clear();
+    }
+    ~KTimer() {
+        for (auto e : pool) cudaEventDestroy(e);
+    }
+};
+
 // ---------------------------------------------------------------- context
 struct pexp_ctx {
     int device = 0;
@@ -50,6 +81,7 @@ struct pexp_ctx {
     // host copies for host-pointer solves
     void* io_d = nullptr;
     size_t io_cap = 0;
+    KTimer kt;
 };
 
 namespace {
@@ -140,6 +172,20 @@ struct Stage {
         if (used) cudaMemcpyAsync(c->stage_d[half], c->stage_h[half], used, cudaMemcpyHostToDevice, c->stream);
     }
 };
+
+// Time a launch sequence as kernel class `cls` moving `bytes` algorithmic bytes.
+template <typename F>
+void timed(pexp_ctx* c, int cls, double bytes, F&& f) {
+    if (!c->kt.on) {
+        f();
+        return;
+    }
+    cudaEvent_t a = c->kt.next(), b = c->kt.next();
+    cudaEventRecord(a, c->stream);
+    f();
+    cudaEventRecord(b, c->stream);
+    c->kt.recs.push_back({cls, a, b, bytes});
+}
 
 void check_launch(pexp_ctx* c) {
     c->launches++;
@@ -360,33 +406,42 @@ struct Solver {
             }
             const int* d_wl = sa.put(wl.data(), na);
             sa.flush();
+            const double w = sizeof(T);
+            const double wout = std::is_same<T, float>::value ? 8.0 : w;   // hi + lo for FP32 data
             if (o->krylov == PEXP_KRYLOV_SAI) {
-                launch_sai_solve<T>(od, sai, d_xin, d_yout, d_ylo, nv, sai_scr, st);
+                timed(c, PEXP_KC_SAI, (double)nv * n * (w + wout),
+                      [&] { launch_sai_solve<T>(od, sai, d_xin, d_yout, d_ylo, nv, sai_scr, st); });
             } else {
                 launch_stencil_ptrs<T>(od, d_xin, d_yout, nv, 0, st);
                 for (const auto& W : act)
                     if (W.Wlo) cudaMemsetAsync(W.Wlo, 0, sizeof(float) * (size_t)n * W.b, st);
             }
             check_launch(c);
-            if constexpr (std::is_same<T, float>::value) {
-                launch_stencil_df(od, reinterpret_cast<const float* const*>(d_xin), d_xlo,
-                                  reinterpret_cast<float* const*>(d_yav), reinterpret_cast<float* const*>(d_yavl), nv, 0, st);
-                check_launch(c);
-                launch_stencil_df(od, reinterpret_cast<const float* const*>(d_xin), d_xlo,
-                                  reinterpret_cast<float* const*>(d_yatv), reinterpret_cast<float* const*>(d_yatvl), nv, 1, st);
-                check_launch(c);
-            } else {
-                launch_stencil_ptrs<T>(od, d_xin, d_yav, nv, 0, st);
-                check_launch(c);
-                launch_stencil_ptrs<T>(od, d_xin, d_yatv, nv, 1, st);
-                check_launch(c);
-            }
+            timed(c, PEXP_KC_STENCIL, 2.0 * nv * n * (w + wout), [&] {
+                if constexpr (std::is_same<T, float>::value) {
+                    launch_stencil_df(od, reinterpret_cast<const float* const*>(d_xin), d_xlo,
+                                      reinterpret_cast<float* const*>(d_yav), reinterpret_cast<float* const*>(d_yavl), nv, 0, st);
+                    check_launch(c);
+                    launch_stencil_df(od, reinterpret_cast<const float* const*>(d_xin), d_xlo,
+                                      reinterpret_cast<float* const*>(d_yatv), reinterpret_cast<float* const*>(d_yatvl), nv, 1, st);
+                    check_launch(c);
+                } else {
+                    launch_stencil_ptrs<T>(od, d_xin, d_yav, nv, 0, st);
+                    check_launch(c);
+                    launch_stencil_ptrs<T>(od, d_xin, d_yatv, nv, 1, st);
+                    check_launch(c);
+                }
+            });
             for (size_t sl = 0; sl < tn1.size(); ++sl) {
-                launch_ts_tn<T>(d_tn1[sl], (int)tn1[sl].size(), tn1_pq[sl], tn1_q[sl], n, partial, st,
-                                std::is_same<T, float>::value ? 1 : 0);
-                check_launch(c);
+                double by = 0;
+                for (auto& t : tn1[sl]) by += (double)n * (t.p + t.q) * w;
+                timed(c, PEXP_KC_PROJ, by, [&] {
+                    launch_ts_tn<T>(d_tn1[sl], (int)tn1[sl].size(), tn1_pq[sl], tn1_q[sl], n, partial, st,
+                                    std::is_same<T, float>::value ? 1 : 0);
+                    check_launch(c);
+                });
             }
-            launch_project(L, wd, wi, d_wl, na, step, h, o->tol, scale_ref, st);
+            timed(c, PEXP_KC_SMALL, 0.0, [&] { launch_project(L, wd, wi, d_wl, na, step, h, o->tol, scale_ref, st); });
             check_launch(c);
             // ---- convergence flags
             d2h(c, wi_host.data(), wi, sizeof(int) * wi_host.size());
@@ -482,29 +537,35 @@ struct Solver {
                 const DfTask* dd3 = sb.put(d3.data(), nb);
                 const DfTask* dd4 = sb.put(d4.data(), nb);
                 sb.flush();
-                launch_ts_nn_df(dd1, nb, mpq1, n, st); check_launch(c);
-                launch_ts_tn<T>(d_tn2, nb, mpq2, mq2, n, partial, st, PEXP_TN_EXACT_FP32); check_launch(c);
-                launch_ts_nn_df(dd2, nb, mpq1, n, st); check_launch(c);
-                launch_ts_tn<T>(d_tn3, nb, mpq3, mq3, n, partial, st, 1); check_launch(c);
-                launch_block_orth(L, wd, wi, d_wl2, nb, 1, step, defl, st); check_launch(c);
-                launch_ts_nn_df(dd3, nb, mpq3, n, st); check_launch(c);
-                launch_ts_tn<T>(d_tn3, nb, mpq3, mq3, n, partial, st, 1); check_launch(c);
-                launch_block_orth(L, wd, wi, d_wl2, nb, 2, step, defl, st); check_launch(c);
-                launch_ts_nn_df(dd4, nb, mpq3, n, st); check_launch(c);
+                double pb = 0, bb = 0;   // sum of p*b and of b over the active windows
+                for (auto& W : act) { pb += (double)step * W.b; bb += W.b; }
+                const double nn = (double)n;
+                timed(c, PEXP_KC_UPDATE, nn * (pb * 4 + bb * 16), [&] { launch_ts_nn_df(dd1, nb, mpq1, n, st); }); check_launch(c);
+                timed(c, PEXP_KC_PROJ, nn * (pb + bb) * 4, [&] { launch_ts_tn<T>(d_tn2, nb, mpq2, mq2, n, partial, st, PEXP_TN_EXACT_FP32); }); check_launch(c);
+                timed(c, PEXP_KC_UPDATE, nn * (pb * 4 + bb * 16), [&] { launch_ts_nn_df(dd2, nb, mpq1, n, st); }); check_launch(c);
+                timed(c, PEXP_KC_PROJ, nn * bb * 4, [&] { launch_ts_tn<T>(d_tn3, nb, mpq3, mq3, n, partial, st, 1); }); check_launch(c);
+                timed(c, PEXP_KC_SMALL, 0.0, [&] { launch_block_orth(L, wd, wi, d_wl2, nb, 1, step, defl, st); }); check_launch(c);
+                timed(c, PEXP_KC_UPDATE, nn * bb * 16, [&] { launch_ts_nn_df(dd3, nb, mpq3, n, st); }); check_launch(c);
+                timed(c, PEXP_KC_PROJ, nn * bb * 4, [&] { launch_ts_tn<T>(d_tn3, nb, mpq3, mq3, n, partial, st, 1); }); check_launch(c);
+                timed(c, PEXP_KC_SMALL, 0.0, [&] { launch_block_orth(L, wd, wi, d_wl2, nb, 2, step, defl, st); }); check_launch(c);
+                timed(c, PEXP_KC_UPDATE, nn * bb * 12, [&] { launch_ts_nn_df(dd4, nb, mpq3, n, st); }); check_launch(c);
             } else {
                 const TsTask<T>* d_nn1 = sb.put(nn1.data(), nb);
                 const TsTask<T>* d_nn2 = sb.put(nn2.data(), nb);
                 const TsTask<T>* d_nn3 = sb.put(nn3.data(), nb);
                 sb.flush();
-                launch_ts_nn<T>(d_nn1, nb, mpq1, n, st); check_launch(c);
-                launch_ts_tn<T>(d_tn2, nb, mpq2, mq2, n, partial, st, 0); check_launch(c);
-                launch_ts_nn<T>(d_nn2, nb, mpq1, n, st); check_launch(c);
-                launch_ts_tn<T>(d_tn3, nb, mpq3, mq3, n, partial, st, 0); check_launch(c);
-                launch_block_orth(L, wd, wi, d_wl2, nb, 1, step, defl, st); check_launch(c);
-                launch_ts_nn<T>(d_nn3, nb, mpq3, n, st); check_launch(c);
-                launch_ts_tn<T>(d_tn3, nb, mpq3, mq3, n, partial, st, 0); check_launch(c);
-                launch_block_orth(L, wd, wi, d_wl2, nb, 2, step, defl, st); check_launch(c);
-                launch_ts_nn<T>(d_nn3, nb, mpq3, n, st); check_launch(c);
+                double pb = 0, bb = 0;
+                for (auto& W : act) { pb += (double)step * W.b; bb += W.b; }
+                const double nn = (double)n * 8.0;
+                timed(c, PEXP_KC_UPDATE, nn * (pb + 2 * bb), [&] { launch_ts_nn<T>(d_nn1, nb, mpq1, n, st); }); check_launch(c);
+                timed(c, PEXP_KC_PROJ, nn * (pb + bb), [&] { launch_ts_tn<T>(d_tn2, nb, mpq2, mq2, n, partial, st, 0); }); check_launch(c);
+                timed(c, PEXP_KC_UPDATE, nn * (pb + 2 * bb), [&] { launch_ts_nn<T>(d_nn2, nb, mpq1, n, st); }); check_launch(c);
+                timed(c, PEXP_KC_PROJ, nn * bb, [&] { launch_ts_tn<T>(d_tn3, nb, mpq3, mq3, n, partial, st, 0); }); check_launch(c);
+                timed(c, PEXP_KC_SMALL, 0.0, [&] { launch_block_orth(L, wd, wi, d_wl2, nb, 1, step, defl, st); }); check_launch(c);
+                timed(c, PEXP_KC_UPDATE, nn * 2 * bb, [&] { launch_ts_nn<T>(d_nn3, nb, mpq3, n, st); }); check_launch(c);
+                timed(c, PEXP_KC_PROJ, nn * bb, [&] { launch_ts_tn<T>(d_tn3, nb, mpq3, mq3, n, partial, st, 0); }); check_launch(c);
+                timed(c, PEXP_KC_SMALL, 0.0, [&] { launch_block_orth(L, wd, wi, d_wl2, nb, 2, step, defl, st); }); check_launch(c);
+                timed(c, PEXP_KC_UPDATE, nn * 2 * bb, [&] { launch_ts_nn<T>(d_nn3, nb, mpq3, n, st); }); check_launch(c);
             }
         }
         return notconv;
@@ -658,7 +719,8 @@ int solve_linear_typed(pexp_ctx* c, const pexp_operator* op, const pexp_options*
         const int* dall = s1.put(all.data(), P);
         s1.flush();
         if (G) {
-            launch_ts_tn<T>(dtg, P, pt.smax * pt.smax, pt.smax, n, S.partial, st, 1);
+            timed(c, PEXP_KC_SOURCE, (double)n * n_out * sizeof(T),
+                  [&] { launch_ts_tn<T>(dtg, P, pt.smax * pt.smax, pt.smax, n, S.partial, st, 1); });
             check_launch(c);
         }
         launch_source_eig(L, S.wd, S.wi, dall, P, std::max(o->svd_tol, svd_floor), b_cap, dots, nrm + 1, st);
@@ -902,7 +964,10 @@ int solve_linear_typed(pexp_ctx* c, const pexp_operator* op, const pexp_options*
         }
         const ReconTask<T>* drt = s4.put(rts.data(), rts.size());
         s4.flush();
-        launch_recon<T, TO>(drt, (int)rts.size(), maxns, n, u0d, Y, n, maxc, st);
+        double kt = 0;
+        for (auto& r : rts) kt += r.K1 + r.K2;
+        timed(c, PEXP_KC_RECON, (double)n * kt * sizeof(T) + (double)n * n_out * sizeof(TO),
+              [&] { launch_recon<T, TO>(drt, (int)rts.size(), maxns, n, u0d, Y, n, maxc, st); });
         check_launch(c);
         cudaEventRecord(c->evp[4], st);
         sync(c);
@@ -1091,10 +1156,20 @@ int pexp_solve_linear(pexp_ctx* c, const pexp_operator* op, const pexp_options* 
     if (rep) memset(rep, 0, sizeof(*rep));
     cudaSetDevice(c->device);
     c->launches = 0;
+    c->kt.reset((o->diagnostics & PEXP_DIAG_KTIME) != 0);
     cudaEventRecord(c->ev0, c->stream);
     int r = guarded([&] { return solve_linear_dispatch(c, op, o, y0_dev, G_dev, g_dtype, Y_dev, y_dtype, rep, 0); });
     cudaEventRecord(c->ev1, c->stream);
     cudaEventSynchronize(c->ev1);
+    if (rep && c->kt.on) {
+        for (auto& k : c->kt.recs) {
+            float ms = 0;
+            cudaEventElapsedTime(&ms, k.a, k.b);
+            rep->k_ms[k.cls] += ms;
+            rep->k_launches[k.cls] += 1;
+            rep->k_bytes[k.cls] += k.bytes;
+        }
+    }
     if (rep) {
         float ms = 0;
         cudaEventElapsedTime(&ms, c->ev0, c->ev1);

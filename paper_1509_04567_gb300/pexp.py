@@ -32,6 +32,8 @@ BC_DIRICHLET0 = 1
 KRYLOV_POLY = 0
 KRYLOV_SAI = 1
 DIAG_ORTH = 1
+DIAG_KTIME = 2
+KC_NAMES = ["sai", "stencil", "proj", "update", "small", "source", "recon", "other"]
 FP64 = 0
 MIXED = 1
 F64 = 0
@@ -63,11 +65,16 @@ class Report(C.Structure):
                 ("not_converged", C.c_int), ("est_max", C.c_double), ("sigma_ratio_max", C.c_double),
                 ("wr_iters", C.c_int), ("wr_delta", C.c_double), ("time_ms", C.c_double),
                 ("t_source_ms", C.c_double), ("t_krylov_ms", C.c_double), ("t_hom_ms", C.c_double),
-                ("t_recon_ms", C.c_double), ("orth_max", C.c_double), ("bytes_alg", C.c_double),
+                ("t_recon_ms", C.c_double), ("orth_max", C.c_double), ("k_ms", C.c_double * 8),
+                ("k_launches", C.c_int * 8), ("k_bytes", C.c_double * 8), ("bytes_alg", C.c_double),
                 ("launches", C.c_int)]
 
     def as_dict(self) -> dict:
-        return {f[0]: getattr(self, f[0]) for f in self._fields_}
+        d = {}
+        for f in self._fields_:
+            v = getattr(self, f[0])
+            d[f[0]] = list(v) if hasattr(v, "__len__") else v
+        return d
 
 
 _lib = None

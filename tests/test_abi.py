@@ -48,7 +48,7 @@ def test_struct_layouts_match_header_order():
                 continue
             parts = decl.split()
             names = " ".join(parts[1:]).replace(" ", "").split(",")
-            fields += names
+            fields += [re.sub(r"\[.*\]", "", nm) for nm in names]
         assert [f[0] for f in pycls._fields_] == fields, cname
 
 
