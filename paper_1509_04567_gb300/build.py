@@ -15,7 +15,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 OUT_DIR = os.path.join(HERE, "_lib")
 LIB = os.path.join(OUT_DIR, "libpexp.so")
-SOURCES = ["tall.cu", "small.cu", "solver.cu"]
+SOURCES = ["tall.cu", "small.cu", "krylov.cu", "solver.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-O2",
          "--expt-relaxed-constexpr", "-diag-suppress", "177"]
@@ -37,7 +37,7 @@ def _compile(src: str, obj: str) -> None:
 
 def build(force: bool = False, verbose: bool = False) -> str:
     os.makedirs(OUT_DIR, exist_ok=True)
-    srcs = [os.path.join(CSRC, s) for s in SOURCES] + [os.path.join(CSRC, h) for h in ("common.cuh", "small.cuh")]
+    srcs = [os.path.join(CSRC, s) for s in SOURCES] + [os.path.join(CSRC, h) for h in ("common.cuh", "small.cuh", "krylov.cuh")]
     hdr = os.path.join(os.path.dirname(HERE), "include", "pexp.h")
     newest = max(os.path.getmtime(p) for p in srcs + [hdr])
     if not force and os.path.exists(LIB) and os.path.getmtime(LIB) >= newest:

@@ -242,7 +242,8 @@ __device__ void cta_expm(double* A, int N, double* E, double* w) {
 // =====================================================================================
 __global__ void __launch_bounds__(64) k_source_eig(WinLayout L, double* __restrict__ wd, int* __restrict__ wi,
                                                    const int* __restrict__ wins, double thr, int max_rank,
-                                                   const double* __restrict__ dots, const double* __restrict__ nrm2) {
+                                                   const double* __restrict__ dots, const double* __restrict__ nrm2,
+                                                   Parts gp) {
     const int w = wins[blockIdx.x];
     double* D = wd + (int64_t)w * L.stride;
     int* I = wi + (int64_t)w * L.istride;
@@ -259,8 +260,15 @@ __global__ void __launch_bounds__(64) k_source_eig(WinLayout L, double* __restri
     for (int e = threadIdx.x; e < s * s; e += blockDim.x) {
         const int i = e % s, j = e / s;
         // (A u0 + g_i) . (A u0 + g_j) = ||A u0||^2 + (A u0).g_i + (A u0).g_j + g_i . g_j
-        A[e] = na2 + (dots ? (dots[i0 + i] + dots[i0 + j]) + G[e] : 0.0);
+        A[e] = na2 + (dots ? (dots[i0 + i] + dots[i0 + j]) + (gp.part ? 0.0 : G[e]) : 0.0);
         Z[e] = (i == j) ? 1.0 : 0.0;
+    }
+    if (dots && gp.part) {
+        __syncthreads();
+        for (int e = threadIdx.x >> 5; e < s * s; e += (int)(blockDim.x >> 5)) {
+            const double v = parts_sum_warp(gp, blockIdx.x, e);
+            if ((threadIdx.x & 31) == 0) A[e] += v;
+        }
     }
     __syncthreads();
     for (int sweep = 0; sweep < 40; ++sweep) {
@@ -362,11 +370,11 @@ __global__ void __launch_bounds__(64) k_source_eig(WinLayout L, double* __restri
 }
 
 void launch_source_eig(const WinLayout& L, double* wd, int* wi, const int* wins, int nw, double thr, int max_rank,
-                       const double* dots, const double* nrm2, cudaStream_t s) {
+                       const double* dots, const double* nrm2, cudaStream_t s, Parts gp) {
     if (nw <= 0) return;
     size_t sm = (size_t)2 * L.s_max * L.s_max * sizeof(double);
     if (sm > 48 * 1024) cudaFuncSetAttribute(k_source_eig, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-    k_source_eig<<<nw, 64, sm, s>>>(L, wd, wi, wins, thr, max_rank, dots, nrm2);
+    k_source_eig<<<nw, 64, sm, s>>>(L, wd, wi, wins, thr, max_rank, dots, nrm2, gp);
 }
 
 // =====================================================================================
@@ -438,27 +446,39 @@ void launch_start_orth(const WinLayout& L, double* wd, int* wi, const int* wins,
 //   pass 2: re-orthonormalise the kept columns (Cholesky of their Gram).
 // =====================================================================================
 __global__ void k_block_orth(WinLayout L, double* __restrict__ wd, int* __restrict__ wi, const int* __restrict__ wins,
-                             int pass, int step, double defl) {
+                             int pass, int step, double defl, Parts gp) {
     const int w = wins[blockIdx.x];
     double* D = wd + (int64_t)w * L.stride;
     int* I = wi + (int64_t)w * L.istride;
-    if (threadIdx.x != 0) return;
     const int b = I[WI_B];
+    __shared__ double sG[PEXP_MAX_RANK * PEXP_MAX_RANK];
+    if (gp.part) {
+        for (int e = 0; e < b * b; ++e) {
+            const double v = parts_sum_warp(gp, blockIdx.x, e);
+            if (threadIdx.x == 0) sG[e] = v;
+        }
+    }
+    __syncwarp();
+    if (threadIdx.x != 0) return;
     const double* G0 = D + L.off_gw;
     double G[PEXP_MAX_RANK * PEXP_MAX_RANK], R[PEXP_MAX_RANK * PEXP_MAX_RANK];
     int perm[PEXP_MAX_RANK];
-    for (int e = 0; e < b * b; ++e) { G[e] = G0[e]; R[e] = 0.0; }
+    for (int e = 0; e < b * b; ++e) {
+        G[e] = gp.part ? sG[e] : G0[e];
+        R[e] = 0.0;
+    }
     for (int k = 0; k < b; ++k) perm[k] = k;
     double lim2;
     int ncand = b;
     if (pass == 1) {
         // pre-Gram-Schmidt norms: diagonal of W^T W stored in out1 rows [step*b, step*b+b),
-        // in the last column block
+        // in the last column block (fused path: b values after h1 at out1)
         const int ldo = (step + 1) * b;
         const double* o1 = D + L.off_out1;
         const int wc = (L.ycols - 1) * b;
         double pre = 0.0;
-        for (int c = 0; c < b; ++c) pre = fmax(pre, o1[(step * b + c) + (wc + c) * ldo]);
+        for (int c = 0; c < b; ++c)
+            pre = fmax(pre, gp.part ? o1[step * b * b + c] : o1[(step * b + c) + (wc + c) * ldo]);
         lim2 = defl * defl * pre;
         D[L.off_scal + WS_PRE] = sqrt(pre);
     } else {
@@ -508,9 +528,9 @@ __global__ void k_block_orth(WinLayout L, double* __restrict__ wd, int* __restri
 }
 
 void launch_block_orth(const WinLayout& L, double* wd, int* wi, const int* wins, int nw, int pass, int step,
-                       double defl, cudaStream_t s) {
+                       double defl, cudaStream_t s, Parts gp) {
     if (nw <= 0) return;
-    k_block_orth<<<nw, 32, 0, s>>>(L, wd, wi, wins, pass, step, defl);
+    k_block_orth<<<nw, 32, 0, s>>>(L, wd, wi, wins, pass, step, defl, gp);
 }
 
 // =====================================================================================
@@ -599,7 +619,7 @@ void launch_spline(const WinLayout& L, double* wd, int* wi, const int* wins, int
 // =====================================================================================
 __global__ void __launch_bounds__(256) k_project(WinLayout L, double* __restrict__ wd, int* __restrict__ wi,
                                                  const int* __restrict__ wins, int step, double h, double tol,
-                                                 double scale_ref) {
+                                                 double scale_ref, Parts fp, double dcoef, double ccoef) {
     const int w = wins[blockIdx.x];
     double* D = wd + (int64_t)w * L.stride;
     int* I = wi + (int64_t)w * L.istride;
@@ -614,17 +634,42 @@ __global__ void __launch_bounds__(256) k_project(WinLayout L, double* __restrict
     // column blocks of out1: [0,b) V^T A V_i, [b,2b) V^T A^T V_i, and with ycols == 5 the
     // low parts [2b,3b), [3b,4b) of the same products (FP32 data)
     const bool lo = L.ycols == 5;
-    for (int e = threadIdx.x; e < K * b; e += blockDim.x) {
-        const int a = e % K, c = e / K;
-        double v = o1[a + c * ldo];
-        if (lo) v += o1[a + (2 * b + c) * ldo];
-        H[a + ((step - 1) * b + c) * KM] = v;
-    }
-    for (int e = threadIdx.x; e < (step - 1) * b * b; e += blockDim.x) {
-        const int a = e % ((step - 1) * b), c = e / ((step - 1) * b);
-        double v = o1[a + (b + c) * ldo];
-        if (lo) v += o1[a + (3 * b + c) * ldo];
-        H[((step - 1) * b + c) + a * KM] = v;
+    if (fp.part) {
+        // fused partials: E (K x b) | F (K x b) | h1 (K x b) | pre (b) per chunk
+        double* o1w = D + L.off_out1;
+        const int nfield = 3 * K * b + b;
+        const int nwarps = blockDim.x >> 5;
+        for (int e = threadIdx.x >> 5; e < nfield; e += nwarps) {
+            const double sacc = parts_sum_warp(fp, blockIdx.x, e);
+            if ((threadIdx.x & 31) != 0) continue;
+            if (e < 2 * K * b) {
+                // E and F: stage in the scratch area for the H assembly below
+                D[L.off_scr + e] = sacc;
+            } else {
+                o1w[e - 2 * K * b] = sacc;   // h1 (K x b) then pre (b)
+            }
+        }
+        __syncthreads();
+        const double* Es = D + L.off_scr;
+        const double* Fs = Es + K * b;
+        for (int e = threadIdx.x; e < K * b; e += blockDim.x) {
+            const int a = e % K, c = e / K;
+            H[a + ((step - 1) * b + c) * KM] = -dcoef * Es[e] - ccoef * Fs[e];
+            if (a < (step - 1) * b) H[((step - 1) * b + c) + a * KM] = -dcoef * Es[e] + ccoef * Fs[e];
+        }
+    } else {
+        for (int e = threadIdx.x; e < K * b; e += blockDim.x) {
+            const int a = e % K, c = e / K;
+            double v = o1[a + c * ldo];
+            if (lo) v += o1[a + (2 * b + c) * ldo];
+            H[a + ((step - 1) * b + c) * KM] = v;
+        }
+        for (int e = threadIdx.x; e < (step - 1) * b * b; e += blockDim.x) {
+            const int a = e % ((step - 1) * b), c = e / ((step - 1) * b);
+            double v = o1[a + (b + c) * ldo];
+            if (lo) v += o1[a + (3 * b + c) * ldo];
+            H[((step - 1) * b + c) + a * KM] = v;
+        }
     }
     __syncthreads();
     const int N = (kind == KIND_SOURCE) ? K + 4 * b : K;
@@ -706,9 +751,9 @@ __global__ void __launch_bounds__(256) k_project(WinLayout L, double* __restrict
 }
 
 void launch_project(const WinLayout& L, double* wd, int* wi, const int* wins, int nw, int step, double h, double tol,
-                    double scale_ref, cudaStream_t s) {
+                    double scale_ref, cudaStream_t s, Parts fp, double d, double cadv) {
     if (nw <= 0) return;
-    k_project<<<nw, 256, 0, s>>>(L, wd, wi, wins, step, h, tol, scale_ref);
+    k_project<<<nw, 256, 0, s>>>(L, wd, wi, wins, step, h, tol, scale_ref, fp, d, cadv);
 }
 
 // =====================================================================================

@@ -39,18 +39,42 @@ enum { KIND_SOURCE = 0, KIND_HOM = 1 };
 
 WinLayout make_layout(int s_max, int b_max, int kmax, int ycols = 3);
 
+// Partial sums of the fused Krylov kernels: window k of the launch list owns chunks
+// [k*nchunks, (k+1)*nchunks) of `part`, `pstride` doubles each (NULL: dense inputs).
+struct Parts {
+    const double* part;
+    int nchunks, pstride;
+};
+
+// Sum of entry e over the chunks of task `task`, computed by one warp (all lanes get it):
+// lanes take chunks lane, lane+32, ... and the lane sums meet in a fixed shuffle tree.
+__device__ __forceinline__ double parts_sum_warp(const Parts& p, int task, int e) {
+    const int lane = threadIdx.x & 31;
+    const double* base = p.part + (size_t)task * p.nchunks * p.pstride + e;
+    double s = 0.0;
+#pragma unroll 4
+    for (int c = lane; c < p.nchunks; c += 32) s += base[(size_t)c * p.pstride];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+    return s;
+}
+
 // Launchers.  `wins` is a device array of window indices (nw entries).
 // The Gram matrix of the shifted samples G_hat = A u0 1^T + G is assembled from its
 // parts: off_gram holds G^T G, dots[i] = (A u0) . g(t_i) (NULL: no source),
 // *nrm2 = ||A u0||^2.
 void launch_source_eig(const WinLayout& L, double* wd, int* wi, const int* wins, int nw, double thr,
-                       int max_rank, const double* dots, const double* nrm2, cudaStream_t s);
+                       int max_rank, const double* dots, const double* nrm2, cudaStream_t s,
+                       Parts gp = Parts{nullptr, 0, 0});
 void launch_start_orth(const WinLayout& L, double* wd, int* wi, const int* wins, int nw, cudaStream_t s);
 void launch_block_orth(const WinLayout& L, double* wd, int* wi, const int* wins, int nw, int pass, int step,
-                       double defl, cudaStream_t s);
+                       double defl, cudaStream_t s, Parts gp = Parts{nullptr, 0, 0});
 void launch_spline(const WinLayout& L, double* wd, int* wi, const int* wins, int nw, double h, cudaStream_t s);
+// With fused partials (E, F, h1, pre of the step) and the operator coefficients d, c:
+// H[a, i] = -d E - c F, H[i, a] = -d E + c F; h1 and pre are stored at out1.
 void launch_project(const WinLayout& L, double* wd, int* wi, const int* wins, int nw, int step, double h,
-                    double tol, double scale_ref, cudaStream_t s);
+                    double tol, double scale_ref, cudaStream_t s, Parts fp = Parts{nullptr, 0, 0}, double d = 0.0,
+                    double cadv = 0.0);
 void launch_small_expm_batch(const double* M, double* E, int N, int batch, double* scratch, cudaStream_t s);
 size_t small_expm_scratch_doubles(int N);
 void init_pade_constants();

@@ -27,6 +27,7 @@
 #include <vector>
 
 #include "common.cuh"
+#include "krylov.cuh"
 #include "small.cuh"
 
 using namespace pexp;
@@ -292,6 +293,8 @@ struct Solver {
     double defl;
     double scale_ref;
     double* diag = nullptr;   // K_max x 48 doubles for the orthogonality diagnostic
+    double* kpart[2] = {nullptr, nullptr};   // partial sums of the fused Krylov kernels
+    bool fused = false;                        // 1D operator and block widths <= kKrylovMaxB
     std::vector<int> wi_host;
 
     T* slot(const Win<T>& W, int blk) const { return W.V + (int64_t)blk * W.b * n; }
@@ -326,9 +329,172 @@ struct Solver {
         return m;
     }
 
+    // Fused block Krylov steps (1D operators, block widths <= kKrylovMaxB): per step one
+    // projection pass (Galerkin sums by parts, first Gram-Schmidt coefficients, norms),
+    // the projected solve, and three passes for Gram-Schmidt and Cholesky QR.
+    int run_fused(std::vector<Win<T>> ws, int* max_steps) {
+        int notconv = 0;
+        *max_steps = 0;
+        std::stable_sort(ws.begin(), ws.end(), [](const Win<T>& a, const Win<T>& b) { return a.b < b.b; });
+        std::vector<Win<T>> act = ws;
+        const int periodic = od.x.periodic;
+        for (int step = 1; step <= kmax && !act.empty(); ++step) {
+            const int na = (int)act.size();
+            int bmax = 0;
+            for (auto& W : act) bmax = std::max(bmax, W.b);
+            const KGeom g = krylov_geom(na, n);
+            const int ps1 = 3 * step * bmax * bmax + bmax;   // step_proj partial stride
+            // ---- part A
+            Stage sa(c, 0);
+            std::vector<const T*> xin;
+            std::vector<T*> yout, ylo;
+            std::vector<StepTask<T>> st1(na);
+            std::vector<int> wl(na);
+            for (int a = 0; a < na; ++a) {
+                const Win<T>& W = act[a];
+                T* Vi = slot(W, step - 1);
+                T* Wn = slot(W, step);
+                for (int cc = 0; cc < W.b; ++cc) {
+                    xin.push_back(Vi + (int64_t)cc * n);
+                    yout.push_back(Wn + (int64_t)cc * n);
+                    ylo.push_back(W.Wlo ? reinterpret_cast<T*>(W.Wlo) + (int64_t)cc * n : nullptr);
+                }
+                st1[a] = StepTask<T>{W.V, n, step * W.b};
+                wl[a] = W.w;
+            }
+            const int nv = (int)xin.size();
+            const T* const* d_xin = sa.put(xin.data(), nv);
+            T* const* d_yout = sa.put(yout.data(), nv);
+            T* const* d_ylo = std::is_same<T, float>::value ? sa.put(ylo.data(), nv) : nullptr;
+            const StepTask<T>* d_st1 = sa.put(st1.data(), na);
+            const int* d_wl = sa.put(wl.data(), na);
+            sa.flush();
+            const double w = sizeof(T);
+            const double wout = std::is_same<T, float>::value ? 8.0 : w;
+            if (o->krylov == PEXP_KRYLOV_SAI) {
+                timed(c, PEXP_KC_SAI, (double)nv * n * (w + wout),
+                      [&] { launch_sai_solve<T>(od, sai, d_xin, d_yout, d_ylo, nv, sai_scr, st); });
+            } else {
+                timed(c, PEXP_KC_STENCIL, (double)nv * n * (w + w), [&] { launch_stencil_ptrs<T>(od, d_xin, d_yout, nv, 0, st); });
+                for (const auto& W : act)
+                    if (W.Wlo) cudaMemsetAsync(W.Wlo, 0, sizeof(float) * (size_t)n * W.b, st);
+            }
+            check_launch(c);
+            double by1 = 0;
+            for (auto& W : act) by1 += (double)n * (step + 1) * W.b * w;
+            timed(c, PEXP_KC_PROJ, by1, [&] {
+                for (int a0 = 0; a0 < na;) {
+                    int a1 = a0;
+                    while (a1 < na && act[a1].b == act[a0].b) ++a1;
+                    launch_step_proj<T>(d_st1 + a0, a1 - a0, act[a0].b, n, periodic, g,
+                                        kpart[0] + (size_t)a0 * g.nchunks * ps1, ps1, st);
+                    check_launch(c);
+                    a0 = a1;
+                }
+            });
+            timed(c, PEXP_KC_SMALL, 0.0, [&] {
+                launch_project(L, wd, wi, d_wl, na, step, h, o->tol, scale_ref, st, Parts{kpart[0], g.nchunks, ps1},
+                               od.x.d, od.x.c);
+            });
+            check_launch(c);
+            d2h(c, wi_host.data(), wi, sizeof(int) * wi_host.size());
+            std::vector<Win<T>> next;
+            for (auto& W : act) {
+                const int* I = &wi_host[(size_t)W.w * L.istride];
+                *max_steps = std::max(*max_steps, I[WI_STEPS]);
+                if (!I[WI_CONV]) next.push_back(W);
+            }
+            if (step == kmax) {
+                notconv += (int)next.size();
+                break;
+            }
+            act.swap(next);
+            if (act.empty()) break;
+            // ---- part B: two Gram-Schmidt passes and two Cholesky QR passes
+            const int nb = (int)act.size();
+            const KGeom gb = krylov_geom(nb, n);
+            int bmb = 0;
+            for (auto& W : act) bmb = std::max(bmb, W.b);
+            const int ps2 = step * bmb * bmb;   // h2 partial stride
+            const int psg = bmb * bmb;          // Gram partial stride
+            Stage sb(c, 1);
+            std::vector<UpdTask<T>> u1(nb), u2(nb), u3(nb), u4(nb);
+            std::vector<int> wl2(nb);
+            for (int a = 0; a < nb; ++a) {
+                const Win<T>& W = act[a];
+                T* Wn = slot(W, step);
+                const int p = step * W.b;
+                UpdTask<T> t;
+                memset(&t, 0, sizeof(t));
+                t.V = W.V; t.Wh = Wn; t.Wl = W.Wlo; t.ld = n; t.p = p;
+                t.hm = D(W.w) + L.off_out1; t.ldh = p;                         // h1 from the projection pass
+                u1[a] = t;
+                t.hm = nullptr; t.hpart = kpart[1] + (size_t)a * gb.nchunks * ps2; t.hchunks = gb.nchunks; t.hstride = ps2;
+                u2[a] = t;                                                     // h2 summed from partials
+                memset(&t, 0, sizeof(t));
+                t.Wh = Wn; t.Wl = W.Wlo; t.ld = n; t.p = W.b; t.hm = D(W.w) + L.off_T; t.ldh = W.b;
+                u3[a] = t;                                                     // W <- W T1 (Gram)
+                t.out = Wn;
+                u4[a] = t;                                                     // final: round into the slot
+                wl2[a] = W.w;
+            }
+            const UpdTask<T>* d1 = sb.put(u1.data(), nb);
+            const UpdTask<T>* d2 = sb.put(u2.data(), nb);
+            const UpdTask<T>* d3 = sb.put(u3.data(), nb);
+            const UpdTask<T>* d4 = sb.put(u4.data(), nb);
+            const int* d_wl2 = sb.put(wl2.data(), nb);
+            sb.flush();
+            double pb = 0, bb = 0;
+            for (auto& W : act) { pb += (double)step * W.b; bb += W.b; }
+            const double wl_ = std::is_same<T, float>::value ? 8.0 : w;   // bytes per element of the working block
+            auto groups = [&](auto&& f) {
+                for (int a0 = 0; a0 < nb;) {
+                    int a1 = a0;
+                    while (a1 < nb && act[a1].b == act[a0].b) ++a1;
+                    f(a0, a1, act[a0].b);
+                    a0 = a1;
+                }
+            };
+            timed(c, PEXP_KC_UPDATE, (double)n * (pb * w + 2 * bb * wl_), [&] {
+                groups([&](int a0, int a1, int b) {
+                    launch_update<T>(d1 + a0, a1 - a0, b, step * b, n, 0, gb, kpart[1] + (size_t)a0 * gb.nchunks * ps2, ps2, st);
+                    check_launch(c);
+                });
+            });
+            timed(c, PEXP_KC_UPDATE, (double)n * (pb * w + 2 * bb * wl_), [&] {
+                groups([&](int a0, int a1, int b) {
+                    launch_update<T>(d2 + a0, a1 - a0, b, step * b, n, 1, gb, kpart[0] + (size_t)a0 * gb.nchunks * psg, psg, st);
+                    check_launch(c);
+                });
+            });
+            timed(c, PEXP_KC_SMALL, 0.0, [&] {
+                launch_block_orth(L, wd, wi, d_wl2, nb, 1, step, defl, st, Parts{kpart[0], gb.nchunks, psg});
+            });
+            check_launch(c);
+            timed(c, PEXP_KC_UPDATE, (double)n * 2 * bb * wl_, [&] {
+                groups([&](int a0, int a1, int b) {
+                    launch_scale<T>(d3 + a0, a1 - a0, b, n, 1, gb, kpart[1] + (size_t)a0 * gb.nchunks * psg, psg, st);
+                    check_launch(c);
+                });
+            });
+            timed(c, PEXP_KC_SMALL, 0.0, [&] {
+                launch_block_orth(L, wd, wi, d_wl2, nb, 2, step, defl, st, Parts{kpart[1], gb.nchunks, psg});
+            });
+            check_launch(c);
+            timed(c, PEXP_KC_UPDATE, (double)n * bb * (wl_ + w), [&] {
+                groups([&](int a0, int a1, int b) {
+                    launch_scale<T>(d4 + a0, a1 - a0, b, n, 0, gb, nullptr, psg, st);
+                    check_launch(c);
+                });
+            });
+        }
+        return notconv;
+    }
+
     // Runs block Krylov steps for the windows `ws` (each with its start block already
     // orthonormal in V block 0).  Returns the number of windows that missed tol.
     int run(std::vector<Win<T>> ws, int kind, int* max_steps) {
+        if (fused) return run_fused(ws, max_steps);
         int notconv = 0;
         *max_steps = 0;
         std::vector<Win<T>> act = ws;
@@ -603,6 +769,8 @@ size_t linear_workspace_bytes(int64_t n, const pexp_options* o, int g_conv, int 
     s += align_up(sizeof(int) * L.istride * 2 * P);
     s += align_up(sizeof(double) * (ts_tn_partial_doubles(P, std::max(std::max(pt.smax * pt.smax, 48 * (L.K_max + b_cap)), 48 * L.K_max), n) + 512));
     s += align_up(sizeof(double) * (size_t)L.K_max * 48);                   // orthogonality diagnostic
+    s += 2 * align_up(sizeof(double) * ((size_t)(8 * kNumSM + P + 8) *
+                                        std::max<size_t>((size_t)(3 * kmax * b_cap * b_cap + b_cap + b_cap * b_cap), (size_t)pt.smax * pt.smax) + 64));
     s += align_up(sizeof(double) * sai_scratch_doubles(n, P * b_cap) + 64);
     s += align_up(sizeof(double) * o->n_out);                               // (A u0) . g(t_i)
     s += (size_t)(4 * P + 32) * kAlign;   // alignment of the per-window allocations
@@ -652,6 +820,9 @@ int solve_linear_typed(pexp_ctx* c, const pexp_operator* op, const pexp_options*
     const size_t part_n = ts_tn_partial_doubles(P, std::max(std::max(pt.smax * pt.smax, 48 * (L.K_max + b_cap)), 48 * L.K_max), n) + 512;
     S.partial = as<double>(ws_alloc(c, sizeof(double) * part_n));
     S.diag = as<double>(ws_alloc(c, sizeof(double) * (size_t)L.K_max * 48));
+    const size_t kpart_n = (size_t)(8 * kNumSM + P + 8) *
+                           std::max<size_t>((size_t)(3 * S.kmax * b_cap * b_cap + b_cap + b_cap * b_cap), (size_t)pt.smax * pt.smax) + 64;
+    for (int k = 0; k < 2; ++k) S.kpart[k] = as<double>(ws_alloc(c, sizeof(double) * kpart_n));
     S.sai_scr = as<double>(ws_alloc(c, sizeof(double) * (sai_scratch_doubles(n, P * b_cap) + 64)));
     // one pole for every window: gamma = sai_gamma * T / P (the nominal subinterval length)
     if (o->krylov == PEXP_KRYLOV_SAI) S.sai = sai_coefficients(S.od, o->sai_gamma * o->T / (double)P);
@@ -715,15 +886,25 @@ int solve_linear_typed(pexp_ctx* c, const pexp_operator* op, const pexp_options*
             t.out = S.D(j) + L.off_gram;
             tg[j] = t;
         }
-        const TsTask<T>* dtg = s1.put(tg.data(), P);
+        std::vector<const T*> gx(P);
+        std::vector<int> gs(P);
+        for (int j = 0; j < P; ++j) {
+            gx[j] = G ? G + (int64_t)pt.idx[j] * n : nullptr;
+            gs[j] = pt.idx[j + 1] - pt.idx[j] + 1;
+        }
+        const T* const* dgx = s1.put(gx.data(), P);
+        const int* dgs = s1.put(gs.data(), P);
         const int* dall = s1.put(all.data(), P);
         s1.flush();
+        const KGeom gg = krylov_geom(P, n);
+        const int psg = pt.smax * pt.smax;
         if (G) {
             timed(c, PEXP_KC_SOURCE, (double)n * n_out * sizeof(T),
-                  [&] { launch_ts_tn<T>(dtg, P, pt.smax * pt.smax, pt.smax, n, S.partial, st, 1); });
+                  [&] { launch_source_gram<T>(dgx, dgs, P, pt.smax, n, gg, S.kpart[0], psg, st); });
             check_launch(c);
         }
-        launch_source_eig(L, S.wd, S.wi, dall, P, std::max(o->svd_tol, svd_floor), b_cap, dots, nrm + 1, st);
+        launch_source_eig(L, S.wd, S.wi, dall, P, std::max(o->svd_tol, svd_floor), b_cap, dots, nrm + 1, st,
+                          Parts{G ? S.kpart[0] : nullptr, gg.nchunks, psg});
         check_launch(c);
         d2h(c, S.wi_host.data(), S.wi, sizeof(int) * S.wi_host.size());
     }
@@ -734,6 +915,8 @@ int solve_linear_typed(pexp_ctx* c, const pexp_operator* op, const pexp_options*
         b_max = std::max(b_max, mj[j]);
         b_min = std::min(b_min, mj[j]);
     }
+    S.fused = (S.od.dim == 1) && (b_max <= kKrylovMaxB) &&
+              krylov_update_smem(S.kmax * b_max, b_max, sizeof(T)) <= 200u * 1024u;
     // bases laid out with the actual widths, in the basis pool
     {
         size_t need = 0;

@@ -377,17 +377,39 @@ __global__ void __launch_bounds__(kSaiThreads) k_sai_fwd_ends(int64_t n, int nch
     }
 }
 
-// Circular carry into chunk `ch` from the chunk summaries (sum_k prod * end) / (1 - rho^n).
-__device__ __forceinline__ double sai_carry(const double* ends, const double* decays, int nch, int ch,
-                                            int dir, double rho_n) {
-    double sum = 0.0, prod = 1.0;
-    for (int k = 1; k <= nch; ++k) {
-        int c = ch - dir * k;
-        c %= nch;
-        if (c < 0) c += nch;
-        sum += prod * ends[c];
-        prod *= decays[c];
-        if (fabs(prod) < 1e-30) break;
+// Circular carry into chunk `ch` from the chunk summaries: sum_k prod_k * end_{c_k} / (1 - rho^n),
+// c_k = ch - dir*k (circular), prod_k = product of the decays of c_1..c_{k-1}.  Evaluated by
+// one warp, 32 summaries at a time (decays multiply along a warp scan), until the running
+// product drops below 1e-30.  Must be called by all 32 lanes of warp 0.
+__device__ __forceinline__ double sai_carry_warp(const double* ends, const double* decays, int nch, int ch, int dir,
+                                                 double rho_n) {
+    const int lane = threadIdx.x & 31;
+    double sum = 0.0, base = 1.0;
+    for (int k0 = 1; k0 <= nch; k0 += 32) {
+        const int k = k0 + lane;
+        double e = 0.0, d = 1.0;
+        if (k <= nch) {
+            int cidx = ch - dir * k;
+            cidx %= nch;
+            if (cidx < 0) cidx += nch;
+            e = ends[cidx];
+            d = decays[cidx];
+        }
+        // exclusive prefix product of the decays within the warp
+        double incl = d;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const double up = __shfl_up_sync(0xffffffffu, incl, o);
+            if (lane >= o) incl *= up;
+        }
+        double excl = __shfl_up_sync(0xffffffffu, incl, 1);
+        if (lane == 0) excl = 1.0;
+        double term = base * excl * e;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) term += __shfl_xor_sync(0xffffffffu, term, o);
+        sum += term;
+        base *= __shfl_sync(0xffffffffu, incl, 31);
+        if (fabs(base) < 1e-30) break;
     }
     return sum / (1.0 - rho_n);
 }
@@ -409,8 +431,10 @@ __global__ void __launch_bounds__(kSaiThreads) k_sai_fwd_apply(int64_t n, int nc
     const T* x = Xp[v];
     T* y = Yp[v];
     T* ylo = Ylo ? Ylo[v] : nullptr;
-    if (threadIdx.x == 0)
-        carry_in = sai_carry(fends + (int64_t)v * nch, fdecays + (int64_t)v * nch, nch, ch, +1, alpha_n);
+    if (threadIdx.x < 32) {
+        const double cv = sai_carry_warp(fends + (int64_t)v * nch, fdecays + (int64_t)v * nch, nch, ch, +1, alpha_n);
+        if (threadIdx.x == 0) carry_in = cv;
+    }
     const int64_t start = (int64_t)ch * kSaiChunk + (int64_t)threadIdx.x * kSaiPer;
     T vals[kSaiPer];
     const int cnt = sai_load(x, n, start, vals);
@@ -453,8 +477,10 @@ __global__ void __launch_bounds__(kSaiThreads) k_sai_bwd_apply(int64_t n, int nc
     const int v = blockIdx.y, ch = blockIdx.x;
     T* y = Yp[v];
     T* ylo = Ylo ? Ylo[v] : nullptr;
-    if (threadIdx.x == 0)
-        carry_in = sai_carry(bends + (int64_t)v * nch, bdecays + (int64_t)v * nch, nch, ch, -1, beta_n);
+    if (threadIdx.x < 32) {
+        const double cv = sai_carry_warp(bends + (int64_t)v * nch, bdecays + (int64_t)v * nch, nch, ch, -1, beta_n);
+        if (threadIdx.x == 0) carry_in = cv;
+    }
     const int64_t start = (int64_t)ch * kSaiChunk + (int64_t)threadIdx.x * kSaiPer;
     T vals[kSaiPer], lows[kSaiPer];
     const int cnt = sai_load<T>(y, n, start, vals);
