@@ -58,6 +58,7 @@ extern "C" {
 #define PEXP_ERR_WR_NOT_CONVERGED  -6  /* waveform relaxation hit wr_max_iter; last iterate written */
 #define PEXP_ERR_TIMEOUT           -7  /* a bounded device-side wait expired */
 #define PEXP_ERR_UNSUPPORTED       -8  /* valid request not implemented for this operator/precision */
+#define PEXP_ERR_SCRATCH_LIMIT     -9  /* request needs more than the fixed scratch of pexp_sai_solve_noalloc */
 
 /* ---------------------------------------------------------------- enumerations */
 #define PEXP_BC_PERIODIC   0
@@ -210,6 +211,43 @@ int pexp_small_expm(pexp_ctx* ctx, const double* M_dev, double* E_dev, int N, in
  * advective (form 1) central differences (Sec. 4; reading in the design doc). */
 int pexp_burgers_source(pexp_ctx* ctx, const pexp_operator* op, const void* U_dev, void* G_dev,
                         int n_rows, int dtype, int form);
+
+/* ---------------------------------------------------------------- allocation-free entry point
+ * The paper has no counterpart: this is a deployment variant of pexp_sai_solve.
+ *
+ * Y = (I - gamma A)^{-1} X for `nvec` vectors, computed by the same kernels as
+ * pexp_sai_solve, but with no context and no allocation: the call makes no
+ * cudaMalloc, cudaFree or other allocating call of CUDA or any library.  It is
+ * for callers that cannot allocate device memory at the point of the call:
+ *   - code that runs under a fixed device-memory budget whose memory another
+ *     allocator (e.g. a framework's caching allocator) has already reserved, so a
+ *     cudaMalloc would fail or fragment that pool;
+ *   - code on latency-critical streams, where cudaMalloc/cudaFree may synchronise
+ *     the whole device and stall the other streams.
+ * Its scratch (chunk summaries of the two recurrences and the vector pointer
+ * tables) lives in one statically sized device array of PEXP_NOALLOC_SCRATCH_BYTES
+ * that every GPU which loads the library holds until the process exits.
+ *
+ *   op:     1D periodic operator (else PEXP_ERR_UNSUPPORTED); gamma > 0.
+ *   X_dev:  nvec input vectors of length n = op->nx at X_dev + k*n (device, read).
+ *   Y_dev:  nvec output vectors, same layout (device, written); must not overlap X_dev.
+ *   dtype:  PEXP_F64 or PEXP_F32 (the element type of X and Y).
+ *   cuda_stream: cudaStream_t of the current device (NULL = legacy default stream).
+ * Size limit: 8 * (2*nvec + 4*ceil(n/2048)*nvec) <= PEXP_NOALLOC_SCRATCH_BYTES
+ * (n = 2^20: nvec <= 127); larger requests return PEXP_ERR_SCRATCH_LIMIT before any
+ * CUDA call.  Invalid arguments return PEXP_ERR_INVALID_ARG; CUDA failures PEXP_ERR_CUDA.
+ *
+ * The call runs on the calling thread's current device and is asynchronous: it
+ * returns once its kernels are enqueued on cuda_stream; the caller synchronises.
+ * The first call on a device also looks up the device address of the scratch array
+ * (once per device, thread-safe); make that first call before any stream capture
+ * begins.  Every call, on any stream, shares the one array, which keeps the last
+ * call's contents; nothing in it needs to start at zero (each call writes every
+ * entry it reads).  Calls that overlap on the GPU (concurrent streams, or calls from
+ * several threads without ordering) race on the scratch and give wrong results. */
+#define PEXP_NOALLOC_SCRATCH_BYTES (2u << 20)
+int pexp_sai_solve_noalloc(const pexp_operator* op, double gamma, const void* X_dev, void* Y_dev,
+                           int nvec, int dtype, void* cuda_stream);
 
 #ifdef __cplusplus
 }

@@ -1276,6 +1276,7 @@ const char* pexp_status_string(int s) {
         case PEXP_ERR_WR_NOT_CONVERGED: return "waveform relaxation not converged";
         case PEXP_ERR_TIMEOUT: return "device wait timed out";
         case PEXP_ERR_UNSUPPORTED: return "unsupported operator/precision combination";
+        case PEXP_ERR_SCRATCH_LIMIT: return "request exceeds the fixed scratch of the allocation-free entry point";
         default: return "unknown status";
     }
 }

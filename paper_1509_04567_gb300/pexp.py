@@ -26,6 +26,7 @@ ERR_NOT_CONVERGED = -5
 ERR_WR_NOT_CONVERGED = -6
 ERR_TIMEOUT = -7
 ERR_UNSUPPORTED = -8
+ERR_SCRATCH_LIMIT = -9
 
 BC_PERIODIC = 0
 BC_DIRICHLET0 = 1
@@ -42,7 +43,7 @@ F32 = 1
 # Symbols declared in include/pexp.h (checked by the CPU tests).
 EXPORTS = ["pexp_create", "pexp_destroy", "pexp_set_stream", "pexp_default_options", "pexp_status_string",
            "pexp_solve_linear", "pexp_solve_linear_host", "pexp_solve_burgers", "pexp_apply_operator",
-           "pexp_sai_solve", "pexp_small_expm", "pexp_burgers_source"]
+           "pexp_sai_solve", "pexp_small_expm", "pexp_burgers_source", "pexp_sai_solve_noalloc"]
 
 
 class Operator(C.Structure):
@@ -104,6 +105,7 @@ def lib() -> C.CDLL:
         L.pexp_sai_solve.argtypes = [vp, C.POINTER(Operator), d, vp, vp, i, i]
         L.pexp_small_expm.argtypes = [vp, vp, vp, i, i]
         L.pexp_burgers_source.argtypes = [vp, C.POINTER(Operator), vp, vp, i, i, i]
+        L.pexp_sai_solve_noalloc.argtypes = [C.POINTER(Operator), d, vp, vp, i, i, vp]
         for name in EXPORTS:
             if name not in ("pexp_default_options", "pexp_status_string"):
                 getattr(L, name).restype = i
@@ -119,6 +121,20 @@ class PexpError(RuntimeError):
 
 def status_string(code: int) -> str:
     return lib().pexp_status_string(code).decode()
+
+
+def sai_solve_noalloc(op: dict, gamma: float, X, Y, stream=None) -> None:
+    """Y = (I - gamma A)^{-1} X through pexp_sai_solve_noalloc: no context and no
+    allocation; enqueued on `stream` (a torch.cuda.Stream; default: the current
+    stream of X's device) and asynchronous -- synchronise before reading Y."""
+    import torch
+    nvec = X.shape[0] if X.dim() == 2 else 1
+    st = stream if stream is not None else torch.cuda.current_stream(X.device)
+    with torch.cuda.device(X.device):
+        rc = lib().pexp_sai_solve_noalloc(C.byref(make_operator(op)), float(gamma), C.c_void_p(X.data_ptr()),
+                                          C.c_void_p(Y.data_ptr()), nvec, _dtype_code(X), C.c_void_p(st.cuda_stream))
+    if rc != OK:
+        raise PexpError(rc, "pexp_sai_solve_noalloc")
 
 
 def make_operator(op: dict) -> Operator:
