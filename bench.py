@@ -37,10 +37,12 @@ def opts_for(precision: int, diag: int = 0) -> dict:
                            precision=precision, diagnostics=diag)
 
 
-def config(precision: str) -> dict:
-    return {"workload": WORKLOAD, "n": N, "nu": NU, "a": A, "P": P, "n_out": NT, "T": T,
+def config(precision: str, n: int = N) -> dict:
+    wname = WORKLOAD if n == N else WORKLOAD.replace("n1048576", f"n{n}")
+    return {"workload": wname, "n": n, "nu": NU, "a": A, "P": P, "n_out": NT, "T": T,
             "precision": precision, "krylov": "shift-and-invert", "tol": 1e-7 if precision == "mixed" else 1e-8,
-            "l2": "inputs larger than L2 (source 4.3 GB FP32 / 8.6 GB FP64, outputs 4.3 GB)"}
+            "l2": f"inputs larger than L2 (source {NT * n * 4 / 1e9:.1f} GB FP32 / {NT * n * 8 / 1e9:.1f} GB FP64, "
+                  f"outputs {NT * n * 4 / 1e9:.1f} GB)"}
 
 
 def read_peaks() -> dict:
@@ -167,6 +169,9 @@ def main() -> None:
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--precision", default="mixed", choices=["mixed", "fp64"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--n", type=int, default=N, help="grid points (profiling cases; the bench line uses 2^20)")
+    ap.add_argument("--quick", action="store_true",
+                    help="timed solves only: no precision comparison, end-to-end leg or CPU baseline")
     args = ap.parse_args()
     if args.impl == "reference":
         run_reference(args)
@@ -196,13 +201,14 @@ def main() -> None:
     prec = 1 if args.precision == "mixed" else 0
     gdt = torch.float32 if prec else torch.float64
     ctx = pexp.Context(local)
-    op = wl.make_op(N, NU, A)
+    n = args.n
+    op = wl.make_op(n, NU, A)
     # inputs on the device (same formulas as workloads.adv_diff_1d, evaluated on the GPU)
-    x = torch.arange(N, dtype=torch.float64, device=dev) / N
+    x = torch.arange(n, dtype=torch.float64, device=dev) / n
     u0 = torch.sin(2 * np.pi * x) + torch.exp(-100.0 * (x - 0.5) ** 2)
     tt = torch.arange(NT, dtype=torch.float64, device=dev) * (T / (NT - 1))
     G = (torch.cos(2 * np.pi * tt)[:, None] * torch.sin(4 * np.pi * x)[None, :]).to(gdt).contiguous()
-    Y = torch.empty((NT, N), dtype=gdt, device=dev)
+    Y = torch.empty((NT, n), dtype=gdt, device=dev)
     opts = opts_for(prec, diag=pexp.DIAG_KTIME)
     stream = torch.cuda.current_stream(dev)
 
@@ -254,12 +260,12 @@ def main() -> None:
     rep = reps[-1]
 
     extra = {}
-    if rank == 0:
+    if rank == 0 and not args.quick:
         # accuracy and speed of the other precision on the same inputs
         oth = 0 if prec else 1
         ot = opts_for(oth)
         Go = G.to(torch.float64 if oth == 0 else torch.float32).contiguous()
-        Yo = torch.empty((NT, N), dtype=Go.dtype, device=dev)
+        Yo = torch.empty((NT, n), dtype=Go.dtype, device=dev)
         ctx.solve_linear(op, ot, u0, Go, Yo)
         torch.cuda.synchronize(dev)
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -278,9 +284,9 @@ def main() -> None:
 
         # end to end through the host-pointer entry: pinned host inputs/outputs, copies timed
         u0h = u0.cpu().numpy()
-        Gh = torch.empty((NT, N), dtype=gdt, pin_memory=True)
+        Gh = torch.empty((NT, n), dtype=gdt, pin_memory=True)
         Gh.copy_(G)
-        Yh = torch.empty((NT, N), dtype=gdt, pin_memory=True)
+        Yh = torch.empty((NT, n), dtype=gdt, pin_memory=True)
         Gn, Yn = Gh.numpy(), Yh.numpy()
         opts_e = opts_for(prec)
         ctx.solve_linear_host(op, opts_e, u0h, Gn, Yn)
@@ -292,18 +298,18 @@ def main() -> None:
         e2e_s = (time.perf_counter() - t0) / args.steps
         el = Gh.element_size()
         extra["e2e"] = {"value": world / e2e_s, "unit": "solves/s",
-                        "h2d_bytes_per_step": int(N * 8 + NT * N * el), "d2h_bytes_per_step": int(NT * N * el)}
+                        "h2d_bytes_per_step": int(n * 8 + NT * n * el), "d2h_bytes_per_step": int(NT * n * el)}
         del Gh, Yh
 
     cpu = None
-    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+    if rank == 0 and world == 1 and not args.no_cpu_baseline and not args.quick:
         cpu = cpu_sample()
 
     if rank == 0:
         line = {"metric": METRIC, "value": value, "unit": "solves/s", "n_gpus": world, "steps": args.steps,
                 "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
                 "vs_baseline": None, "dtype": "f32" if prec else "f64", "data": "synthetic",
-                "config": config(args.precision), "hbm_gbs_alg": rep["bytes_alg"] / (ms * 1e-3) / 1e9,
+                "config": config(args.precision, n), "hbm_gbs_alg": rep["bytes_alg"] / (ms * 1e-3) / 1e9,
                 "roofline": roof, "clocks": ck, "gpu_launches": int(sum(r["launches"] for r in reps)),
                 "krylov": {"k_nh_max": rep["k_nh_max"], "k_hom_max": rep["k_hom_max"], "k_hom_sum": rep["k_hom_sum"],
                            "rank_max": rep["rank_max"], "not_converged": rep["not_converged"]},
