@@ -109,6 +109,10 @@ void launch_burgers_source(const OpDesc& op, const T* U, T* G, int nrows, int fo
 template <typename T>
 void launch_sai_solve(const OpDesc& op, const SaiCoef& cf, const T* const* X, T* const* Y, T* const* Ylo, int nvec,
                       double* scratch, cudaStream_t s);
+// Same with input low parts (FP32 data: X + Xlo is a double-float input; NULL = none).
+template <typename T>
+void launch_sai_solve_lo(const OpDesc& op, const SaiCoef& cf, const T* const* X, const T* const* Xlo, T* const* Y,
+                         T* const* Ylo, int nvec, double* scratch, cudaStream_t s);
 template <typename T>
 void launch_ts_tn(const TsTask<T>* tasks_dev, int ntasks, int max_pq, int max_q, int64_t n, double* partial,
                   cudaStream_t s, int exact = 0);

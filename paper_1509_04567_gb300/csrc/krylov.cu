@@ -9,17 +9,33 @@
 // cancellation, so FP32 products are accurate to FP32 relative to H, whereas
 // v_a^T (A v_i) would multiply the rounding of A v_i by ||A||.
 //
-// Kernels (one CTA = 256 threads works on a row chunk of one window):
-//   k_step_proj     E = dV^T dV_i, F = V^T (S V_i - S^-1 V_i), h1 = V^T W, pre = diag(W^T W)
-//   k_update_proj   W <- W - V h1, then h2 = V^T W      (classical Gram-Schmidt, both passes)
-//   k_update_gram   W <- W - V h2, then G = W^T W
-//   k_scale_gram    W <- W T, then G = W^T W (optional); final pass rounds W into the basis
-// Partial sums of each CTA go to a buffer and are summed, in a fixed order, by
-// the small per-window kernels that consume them.
+// Kernels (CTA = 256 threads on a chunk of 2048-8192 rows of one window):
+//   k_step_proj  E = dV^T dV_i, F = V^T (S V_i - S^-1 V_i), h1 = V^T W, pre = diag(W^T W)
+//   k_update0    W <- W - V h1, then G = W^T W           (first Gram-Schmidt pass)
+//   k_scale_proj W <- W T1 (Cholesky QR), then h2 = V^T W
+//   k_update1    W <- W - V h2, then G = W^T W           (second pass)
+//   k_scale      W <- W T2; the final pass rounds W into the basis
+// i.e. block classical Gram-Schmidt with Cholesky QR, applied twice (BCGS2).
 //
-// FP32 data: products in FP32, per-lane sums compensated (Neumaier), lanes and
-// CTAs combined in FP64; the working block W is a (hi, lo) pair updated in
-// double-float so that Gram-Schmidt cancellation leaves no FP32-sized noise.
+// Memory-level parallelism: every thread owns rows and issues the loads of all the
+// columns it needs for a row before using any of them, so a CTA keeps tens of KB in
+// flight; the +-1 neighbours of the stencil sums come from adjacent lanes (warps
+// overlap by one row on each side).  Sums: each thread accumulates FP32 (FP64 data:
+// FP64) products of its rows; warps reduce in the data type; the 8 warps and the
+// CTAs are combined in FP64 (one partial per CTA, summed in a fixed order by the
+// consumer).  FP64 arithmetic runs at 1/64 of the FP32 rate on this GPU, so it is
+// kept out of the per-row work of the FP32 kernels.  The Galerkin sums E and F are
+// compensated (per-thread two-product/two-sum, two-sum warp tree): the projected
+// matrix multiplies their rounding by ||H|| over each subinterval, and plain FP32
+// sums left a solution error of several 1e-6 at 2^20 points.
+//
+// FP32 data: the working block W is a (hi, lo) pair updated in double-float, so that
+// Gram-Schmidt cancellation leaves no FP32-sized noise.  The first pass subtracts
+// V h1 with exact FP32 products x*h_hi (FMA) and a compensated sum; the second pass
+// coefficients h2 are at the orthogonality-error level, so FP32 products suffice.
+// The second pass works on the block normalised by the first Cholesky QR: a block
+// whose columns are nearly dependent (condition kappa) would otherwise turn the
+// ~1e-10 residual of the projections into a kappa-times larger loss of orthogonality.
 #include <algorithm>
 
 #include "common.cuh"
@@ -53,7 +69,8 @@ struct Sum<float> {
     __device__ __forceinline__ double get() const { return (double)s + (double)c; }
 };
 
-__device__ __forceinline__ double wsum(double v) {
+template <typename T>
+__device__ __forceinline__ T warp_sum(T v) {
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
     return v;
@@ -70,13 +87,6 @@ __device__ __forceinline__ F2 f2_add(F2 a, F2 b) {
     const float h = s + e;
     return F2{h, e - (h - s)};
 }
-__device__ __forceinline__ F2 f2_mulf(float a, F2 b) {   // a (FP32) * (hi, lo)
-    const float p = a * b.hi;
-    float e = fmaf(a, b.hi, -p);
-    e = fmaf(a, b.lo, e);
-    const float h = p + e;
-    return F2{h, e - (h - p)};
-}
 __device__ __forceinline__ F2 f2_mul(F2 a, F2 b) {
     const float p = a.hi * b.hi;
     float e = fmaf(a.hi, b.hi, -p);
@@ -91,371 +101,636 @@ __device__ __forceinline__ F2 f2_from(double v) {
 }
 
 constexpr int kThreads = 256;
-constexpr int kTile = 256;   // rows staged in shared memory per iteration
+constexpr int kWarps = kThreads / 32;
+constexpr int kTile = 256;    // rows per shared-memory tile of k_source_gram
+constexpr int kHalo = 30;     // active rows per warp in k_step_proj (lanes 1..30)
 
-__device__ __forceinline__ int64_t wrap(int64_t r, int64_t n) { return r < 0 ? r + n : (r >= n ? r - n : r); }
+// per-thread accumulator budget (registers) of the projection kernels
+// (two CTAs of 256 threads per SM: at most 128 registers per thread)
+template <typename T>
+struct Budget {
+    static constexpr int acc = 72;
+};
+template <>
+struct Budget<double> {
+    static constexpr int acc = 36;
+};
+template <typename T, int B>
+struct Group {
+    // columns per CTA of k_step_proj: FP32 data keep E and F as compensated (s, c) pairs
+    // (5 registers per column and block column), FP64 data plain sums (3 doubles)
+    static constexpr int step = sizeof(T) == 4 ? 16 / B : Budget<T>::acc / (3 * B);
+    static constexpr int vtw = Budget<T>::acc / (B + 1);     // columns per CTA of k_vtw
+};
+constexpr int kFuseP = 16;   // k_scale_proj keeps V^T W accumulators for up to 16 columns
+
+template <typename T>
+__device__ __forceinline__ T ldg(const T* p) { return __ldg(p); }
+
+// s + c += x * y: FP32 sums keep the rounding errors of the product and of the sum in c
+// (two-product by FMA, two-sum); FP64 sums are plain FMAs.
+__device__ __forceinline__ void comp_add(float& s, float& c, float x, float y) {
+    const float p = x * y;
+    const float pe = fmaf(x, y, -p);
+    const float t = s + p;
+    const float bp = t - s;
+    c += ((s - (t - bp)) + (p - bp)) + pe;
+    s = t;
+}
+__device__ __forceinline__ void comp_add(double& s, double&, double x, double y) { s = fma(x, y, s); }
+
+// Reduce per-thread values over the CTA: warp sums in the data type, then the 8 warp
+// results in FP64 by thread e for entry e.  sred: kWarps x ne doubles.
+template <typename T>
+__device__ __forceinline__ void warp_to_smem(T v, double* sred, int ne, int e) {
+    const T s = warp_sum(v);
+    if ((threadIdx.x & 31) == 0) sred[(threadIdx.x >> 5) * ne + e] = (double)s;
+}
+// Same for a compensated (hi, lo) pair: the warp tree adds with two-sum.
+__device__ __forceinline__ void warp_to_smem2(float hi, float lo, double* sred, int ne, int e) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        const float h2 = __shfl_xor_sync(0xffffffffu, hi, o), l2 = __shfl_xor_sync(0xffffffffu, lo, o);
+        const float sum = hi + h2;
+        const float bp = sum - hi;
+        const float err = (hi - (sum - bp)) + (h2 - bp);
+        hi = sum;
+        lo = lo + l2 + err;
+    }
+    if ((threadIdx.x & 31) == 0) sred[(threadIdx.x >> 5) * ne + e] = (double)hi + (double)lo;
+}
+__device__ __forceinline__ void warp_to_smem2(double hi, double lo, double* sred, int ne, int e) {
+    warp_to_smem(hi + lo, sred, ne, e);
+}
+__device__ __forceinline__ double cta_entry(const double* sred, int ne, int e) {
+    double s = 0.0;
+#pragma unroll
+    for (int w = 0; w < kWarps; ++w) s += sred[w * ne + e];
+    return s;
+}
 
 }  // namespace
 
 // =====================================================================================
-// k_step_proj
+// k_step_proj: grid (chunks, tasks, column groups).  Group z owns columns
+// [z*PG, z*PG + PG) of V_{1:p}; group 0 also sums diag(W^T W).
 // =====================================================================================
 template <typename T, int B>
-__global__ void __launch_bounds__(kThreads) k_step_proj(const StepTask<T>* __restrict__ tasks, int64_t n, int periodic,
+__global__ void __launch_bounds__(kThreads, 2) k_step_proj(const StepTask<T>* __restrict__ tasks, int64_t n, int periodic,
                                                         int64_t rows, int nchunks, int pstride,
                                                         double* __restrict__ partial) {
+    constexpr int PG = Group<T, B>::step;
+    constexpr int NE = 3 * PG * B + B;
+    __shared__ double sred[kWarps * NE];
     const StepTask<T> tk = tasks[blockIdx.y];
-    const int ch = blockIdx.x;
-    const int64_t r0 = (int64_t)ch * rows;
+    const int p = tk.p;
+    const int a0 = blockIdx.z * PG;
+    if (a0 >= p) return;
+    const int na = min(PG, p - a0);
+    const int64_t ld = tk.ld;
+    const T* __restrict__ Va = tk.V + (int64_t)a0 * ld;
+    const T* __restrict__ Vi = tk.V + (int64_t)(p - B) * ld;   // last block of V_{1:p}
+    const T* __restrict__ W = tk.V + (int64_t)p * ld;          // working block (slot p)
+    const int64_t r0 = (int64_t)blockIdx.x * rows;
     const int64_t r1 = (r0 + rows < n) ? r0 + rows : n;
-    const int p = tk.p;   // columns of V_{1:i}
-    const T* Vi = tk.V + (int64_t)(p - B) * tk.ld;   // last block of V_{1:i}
-    const T* W = tk.V + (int64_t)p * tk.ld;          // working block (slot i+1)
-    __shared__ T sD[B][kTile], sC[B][kTile], sW[B][kTile];
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    // each warp owns columns a = warp, warp + 8, ... (at most 8 per warp kept in registers)
-    constexpr int GMAX = 6;
-    Sum<T> E[GMAX][B], F[GMAX][B], Hh[GMAX][B];
-    Sum<T> pre[B];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const bool grp0 = blockIdx.z == 0;
+    T aE[PG][B], aF[PG][B], cE[PG][B], cF[PG][B], aH[PG][B], aP[B];
 #pragma unroll
-    for (int g = 0; g < GMAX; ++g)
+    for (int q = 0; q < PG; ++q)
+#pragma unroll
+        for (int c = 0; c < B; ++c) aE[q][c] = aF[q][c] = cE[q][c] = cF[q][c] = aH[q][c] = T(0);
+#pragma unroll
+    for (int c = 0; c < B; ++c) aP[c] = T(0);
+    // Dirichlet: the r = -1 term dv_{-1} = v_0 of the E sums, in the chunk holding row 0
+    if (!periodic && r0 == 0 && threadIdx.x == 0) {
+#pragma unroll
+        for (int q = 0; q < PG; ++q)
+#pragma unroll
+            for (int c = 0; c < B; ++c)
+                if (q < na) aE[q][c] = Va[(int64_t)q * ld] * Vi[(int64_t)c * ld];
+    }
+    // lanes 1..30 of each warp own rows; lanes 0 and 31 load the rows before and after
+    for (int64_t base = r0; base < r1; base += (int64_t)kHalo * kWarps) {
+        const int64_t r = base + (int64_t)warp * kHalo + lane - 1;
+        const bool act = lane >= 1 && lane <= kHalo && r < r1;
+        const bool need = r <= r1;   // r >= r0 - 1 holds by construction
+        bool ok;
+        int64_t rp;
+        if (periodic) {
+            ok = need;
+            rp = r < 0 ? r + n : (r >= n ? r - n : r);
+        } else {
+            ok = need && r >= 0 && r < n;
+            rp = r;
+        }
+        T x[PG], vi[B], w[B];
+#pragma unroll
+        for (int q = 0; q < PG; ++q) x[q] = (ok && q < na) ? ldg(Va + (int64_t)q * ld + rp) : T(0);
 #pragma unroll
         for (int c = 0; c < B; ++c) {
-            E[g][c].zero();
-            F[g][c].zero();
-            Hh[g][c].zero();
+            vi[c] = ok ? ldg(Vi + (int64_t)c * ld + rp) : T(0);
+            w[c] = act ? ldg(W + (int64_t)c * ld + rp) : T(0);
+        }
+        T D[B], C[B];
+#pragma unroll
+        for (int c = 0; c < B; ++c) {
+            const T vr = __shfl_down_sync(0xffffffffu, vi[c], 1);
+            const T vl = __shfl_up_sync(0xffffffffu, vi[c], 1);
+            D[c] = vr - vi[c];
+            C[c] = vr - vl;
         }
 #pragma unroll
-    for (int c = 0; c < B; ++c) pre[c].zero();
-    const int ng = (p + 7) / 8;   // columns per warp
-    double* pout = partial + ((size_t)blockIdx.y * nchunks + ch) * pstride;
-    // column groups beyond GMAX are handled in extra passes over the chunk
-    for (int g0 = 0; g0 < ng; g0 += GMAX) {
-        for (int64_t t0 = r0; t0 < r1; t0 += kTile) {
-            const int nt = (int)((t0 + kTile <= r1) ? kTile : (r1 - t0));
-            __syncthreads();
-            for (int e = threadIdx.x; e < B * kTile; e += kThreads) {
-                const int c = e / kTile, k = e % kTile;
-                if (k < nt) {
-                    const int64_t r = t0 + k;
-                    const T* v = Vi + (int64_t)c * tk.ld;
-                    const T vr = v[r];
-                    T vp, vm;
-                    if (periodic) {
-                        vp = v[wrap(r + 1, n)];
-                        vm = v[wrap(r - 1, n)];
-                    } else {
-                        vp = (r + 1 < n) ? v[r + 1] : T(0);
-                        vm = (r > 0) ? v[r - 1] : T(0);
-                    }
-                    sD[c][k] = vp - vr;
-                    sC[c][k] = vp - vm;
-                    sW[c][k] = W[(int64_t)c * tk.ld + r];
-                }
-            }
-            __syncthreads();
-            if (g0 == 0 && warp == 0) {
-                for (int k = lane; k < nt; k += 32)
+        for (int q = 0; q < PG; ++q) {
+            const T xr = __shfl_down_sync(0xffffffffu, x[q], 1);
+            if (act && q < na) {
+                const T dx = xr - x[q];
 #pragma unroll
-                    for (int c = 0; c < B; ++c) pre[c].add(sW[c][k], sW[c][k]);
-            }
-#pragma unroll
-            for (int g = 0; g < GMAX; ++g) {
-                const int a = (g0 + g) * 8 + warp;
-                if (g0 + g >= ng || a >= p) continue;
-                const T* va = tk.V + (int64_t)a * tk.ld;
-                for (int k = lane; k < nt; k += 32) {
-                    const int64_t r = t0 + k;
-                    const T x = va[r];
-                    T xn;
-                    if (periodic) xn = va[wrap(r + 1, n)];
-                    else xn = (r + 1 < n) ? va[r + 1] : T(0);
-                    const T dx = xn - x;
-#pragma unroll
-                    for (int c = 0; c < B; ++c) {
-                        E[g][c].add(dx, sD[c][k]);
-                        F[g][c].add(x, sC[c][k]);
-                        Hh[g][c].add(x, sW[c][k]);
-                    }
+                for (int c = 0; c < B; ++c) {
+                    comp_add(aE[q][c], cE[q][c], dx, D[c]);
+                    comp_add(aF[q][c], cF[q][c], x[q], C[c]);
+                    aH[q][c] = fma(x[q], w[c], aH[q][c]);
                 }
             }
         }
-        // Dirichlet: the ghost term dv_{-1} dv_{-1} = v_0 v_0 belongs to the chunk holding row 0
-        // warp reductions and partial output for this column group
+        if (act && grp0) {
 #pragma unroll
-        for (int g = 0; g < GMAX; ++g) {
-            const int a = (g0 + g) * 8 + warp;
-            if (g0 + g >= ng || a >= p) continue;
-            double extra[B];
+            for (int c = 0; c < B; ++c) aP[c] = fma(w[c], w[c], aP[c]);
+        }
+    }
 #pragma unroll
-            for (int c = 0; c < B; ++c) extra[c] = 0.0;
-            if (!periodic && r0 == 0 && lane == 0) {
-#pragma unroll
-                for (int c = 0; c < B; ++c) extra[c] = (double)tk.V[(int64_t)a * tk.ld] * (double)Vi[(int64_t)c * tk.ld];
-            }
+    for (int q = 0; q < PG; ++q) {
+        if (q < na) {
 #pragma unroll
             for (int c = 0; c < B; ++c) {
-                const double e = wsum(E[g][c].get() + extra[c]);
-                const double f = wsum(F[g][c].get());
-                const double hh = wsum(Hh[g][c].get());
-                if (lane == 0) {
-                    pout[a + c * p] = e;
-                    pout[p * B + a + c * p] = f;
-                    pout[2 * p * B + a + c * p] = hh;
-                }
-                E[g][c].zero();
-                F[g][c].zero();
-                Hh[g][c].zero();
+                warp_to_smem2(aE[q][c], cE[q][c], sred, NE, (q * B + c) * 3 + 0);
+                warp_to_smem2(aF[q][c], cF[q][c], sred, NE, (q * B + c) * 3 + 1);
+                warp_to_smem(aH[q][c], sred, NE, (q * B + c) * 3 + 2);
             }
         }
     }
-    if (warp == 0) {
+    if (grp0) {
 #pragma unroll
-        for (int c = 0; c < B; ++c) {
-            const double v = wsum(pre[c].get());
-            if (lane == 0) pout[3 * p * B + c] = v;
+        for (int c = 0; c < B; ++c) warp_to_smem(aP[c], sred, NE, 3 * PG * B + c);
+    }
+    __syncthreads();
+    double* pout = partial + ((size_t)blockIdx.y * nchunks + blockIdx.x) * pstride;
+    for (int e = threadIdx.x; e < NE; e += kThreads) {
+        if (e < 3 * PG * B) {
+            const int kind = e % 3, qc = e / 3, q = qc / B, c = qc % B;
+            if (q < na) pout[kind * p * B + (a0 + q) + c * p] = cta_entry(sred, NE, e);
+        } else if (grp0) {
+            pout[3 * p * B + (e - 3 * PG * B)] = cta_entry(sred, NE, e);
         }
     }
 }
 
 // =====================================================================================
-// Gram-Schmidt update fused with the next projection (mode 0) or Gram matrix (mode 1):
-//   W <- W - V h;   mode 0: partial h2 = V^T W;   mode 1: partial G = W^T W.
-// A row tile of V is staged in shared memory: rows update W (row-parallel), then
-// warps own columns of V for the projection (column-parallel), V read once.
+// Coefficients of the update kernels: dense FP64 (tk.hm, leading dimension tk.ldh),
+// staged in shared memory -- as (hi, lo) FP32 pairs for FP32 data.
+// =====================================================================================
+template <typename T>
+struct Coef;
+template <>
+struct Coef<float> {
+    using type = float2;
+    __device__ static type make(double v) {
+        const float h = (float)v;
+        return make_float2(h, (float)(v - (double)h));
+    }
+};
+template <>
+struct Coef<double> {
+    using type = double;
+    __device__ static type make(double v) { return v; }
+};
+
+template <typename T>
+__device__ __forceinline__ void stage_coeffs(const UpdTask<T>& tk, int rows_h, int cols, typename Coef<T>::type* sh) {
+    for (int e = threadIdx.x; e < rows_h * cols; e += kThreads) {
+        const int a = e % rows_h, c = e / rows_h;
+        sh[e] = Coef<T>::make(tk.hm[a + (int64_t)c * tk.ldh]);
+    }
+    __syncthreads();
+}
+
+// W <- W - V h for one row: FP32 data in double-float with exact products x*h_hi
+// (FMA) and a compensated sum; FP64 data with FMAs.  Columns [q0, q0 + Q) of V.
+template <int Q, int B>
+__device__ __forceinline__ void sub_vh(const float (&x)[Q], const float (&xl)[Q], const float2* sh, int p, int q0,
+                                       float (&sh_)[B], float (&sl_)[B]) {
+#pragma unroll
+    for (int c = 0; c < B; ++c) {
+        float s = sh_[c], l = sl_[c];
+#pragma unroll
+        for (int q = 0; q < Q; ++q) {
+            if (q0 + q < p) {
+                const float2 h = sh[(q0 + q) + c * p];
+                const float ph = x[q] * h.x;
+                float pe = fmaf(x[q], h.x, -ph);
+                pe = fmaf(x[q], h.y, pe);
+                pe = fmaf(xl[q], h.x, pe);
+                const float t = s + ph;
+                const float bp = t - s;
+                l += ((s - (t - bp)) + (ph - bp)) + pe;
+                s = t;
+            }
+        }
+        sh_[c] = s;
+        sl_[c] = l;
+    }
+}
+template <int Q, int B>
+__device__ __forceinline__ void sub_vh(const double (&x)[Q], const double (&)[Q], const double* sh, int p, int q0,
+                                       double (&sh_)[B], double (&)[B]) {
+#pragma unroll
+    for (int c = 0; c < B; ++c) {
+        double s = sh_[c];
+#pragma unroll
+        for (int q = 0; q < Q; ++q)
+            if (q0 + q < p) s = fma(x[q], sh[(q0 + q) + c * p], s);
+        sh_[c] = s;
+    }
+}
+
+// =====================================================================================
+// k_update0: W <- W - V h1 (first Gram-Schmidt pass) and partial G = W^T W.
 // =====================================================================================
 template <typename T, int B>
-__device__ __forceinline__ void load_coeffs(const UpdTask<T>& tk, int nc, double* sh) {
-    // nc = number of coefficient entries (p*B or B*B); summed over partial chunks if given
-    if (tk.hpart) {
-        const Parts pp{tk.hpart, tk.hchunks, tk.hstride};
-        for (int e = threadIdx.x >> 5; e < nc; e += kThreads / 32) {
-            const double v = parts_sum_warp(pp, 0, e);
-            if ((threadIdx.x & 31) == 0) sh[e] = v;
-        }
-        return;
-    }
-    for (int e = threadIdx.x; e < nc; e += kThreads) {
-        {
-            const int rows = (nc == B * B) ? B : tk.p;
-            const int a = e % rows, c = e / rows;
-            sh[e] = tk.hm[a + (int64_t)c * tk.ldh];
-        }
-    }
-}
-
-template <typename T, int B, int MODE>
-__global__ void __launch_bounds__(kThreads) k_update(const UpdTask<T>* __restrict__ tasks, int64_t n, int64_t rows,
-                                                     int nchunks, int pstride, double* __restrict__ partial) {
+__global__ void __launch_bounds__(kThreads, 2) k_update0(const UpdTask<T>* __restrict__ tasks, int64_t n, int64_t rows,
+                                                         int nchunks, int pstride, double* __restrict__ partial) {
+    using CT = typename Coef<T>::type;
+    constexpr int Q = 16;
+    constexpr int NE = B * B;
+    extern __shared__ double sh_dyn[];
+    CT* sh = reinterpret_cast<CT*>(sh_dyn);
+    __shared__ double sred[kWarps * NE];
     const UpdTask<T> tk = tasks[blockIdx.y];
-    const int ch = blockIdx.x;
-    const int64_t r0 = (int64_t)ch * rows;
-    const int64_t r1 = (r0 + rows < n) ? r0 + rows : n;
     const int p = tk.p;
-    extern __shared__ double sh_upd[];
-    double* sh = sh_upd;                                       // p x B coefficients
-    T* sV = reinterpret_cast<T*>(sh + ((p * B + 1) & ~1));    // p x kTile
-    T* sW = sV + (size_t)p * kTile;                            // B x kTile (rounded new W)
-    load_coeffs<T, B>(tk, p * B, sh);
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    constexpr int GMAX = 6;
-    const int ng = (p + 7) / 8;
-    Sum<T> acc[GMAX][B];
-    Sum<T> gram[B][B];
-#pragma unroll
-    for (int g = 0; g < GMAX; ++g)
-#pragma unroll
-        for (int c = 0; c < B; ++c) acc[g][c].zero();
+    stage_coeffs<T>(tk, p, B, sh);
+    const int64_t ld = tk.ld;
+    const int64_t r0 = (int64_t)blockIdx.x * rows;
+    const int64_t r1 = (r0 + rows < n) ? r0 + rows : n;
+    T g[B][B];
 #pragma unroll
     for (int i = 0; i < B; ++i)
 #pragma unroll
-        for (int j = 0; j < B; ++j) gram[i][j].zero();
-    double* pout = partial + ((size_t)blockIdx.y * nchunks + ch) * pstride;
-    for (int g0 = 0; g0 < (MODE == 0 ? ng : 1); g0 += GMAX) {
-        for (int64_t t0 = r0; t0 < r1; t0 += kTile) {
-            const int nt = (int)((t0 + kTile <= r1) ? kTile : (r1 - t0));
-            __syncthreads();
-            for (int e = threadIdx.x; e < p * kTile; e += kThreads) {
-                const int a = e / kTile, k = e % kTile;
-                if (k < nt) sV[(size_t)a * kTile + k] = tk.V[(int64_t)a * tk.ld + t0 + k];
+        for (int j = 0; j < B; ++j) g[i][j] = T(0);
+    for (int64_t base = r0; base < r1; base += kThreads) {
+        const int64_t r = base + threadIdx.x;
+        const bool act = r < r1;
+        T s[B], l[B];
+#pragma unroll
+        for (int c = 0; c < B; ++c) s[c] = l[c] = T(0);
+        for (int q0 = 0; q0 < p; q0 += Q) {
+            T x[Q], xl[Q];
+#pragma unroll
+            for (int q = 0; q < Q; ++q) {
+                const int a = q0 + q;
+                x[q] = (act && a < p) ? ldg(tk.V + (int64_t)a * ld + r) : T(0);
+                // low parts of the last block (the dominant direction of the step)
+                if constexpr (sizeof(T) == 4)
+                    xl[q] = (act && tk.Vlo && a < p && a >= p - B) ? ldg(tk.Vlo + (int64_t)(a - (p - B)) * ld + r) : 0.f;
+                else
+                    xl[q] = T(0);
             }
-            __syncthreads();
-            // row-parallel update (first column group only), or reload of the updated W
-            for (int k = threadIdx.x; k < nt; k += kThreads) {
-                const int64_t r = t0 + k;
-                if (g0 == 0) {
-                    if constexpr (sizeof(T) == 4) {
-                        F2 w[B];
+            sub_vh<Q, B>(x, xl, sh, p, q0, s, l);
+        }
+        T wr[B];
 #pragma unroll
-                        for (int c = 0; c < B; ++c) w[c] = F2{tk.Wh[(int64_t)c * tk.ld + r], tk.Wl[(int64_t)c * tk.ld + r]};
-                        for (int a = 0; a < p; ++a) {
-                            const float x = sV[(size_t)a * kTile + k];
-#pragma unroll
-                            for (int c = 0; c < B; ++c) w[c] = f2_add(w[c], f2_mulf(x, f2_from(-sh[a + c * p])));
-                        }
-#pragma unroll
-                        for (int c = 0; c < B; ++c) {
-                            tk.Wh[(int64_t)c * tk.ld + r] = w[c].hi;
-                            tk.Wl[(int64_t)c * tk.ld + r] = w[c].lo;
-                            sW[c * kTile + k] = w[c].hi + w[c].lo;
-                        }
-                    } else {
-                        double w[B];
-#pragma unroll
-                        for (int c = 0; c < B; ++c) w[c] = tk.Wh[(int64_t)c * tk.ld + r];
-                        for (int a = 0; a < p; ++a) {
-                            const double x = sV[(size_t)a * kTile + k];
-#pragma unroll
-                            for (int c = 0; c < B; ++c) w[c] = fma(-sh[a + c * p], x, w[c]);
-                        }
-#pragma unroll
-                        for (int c = 0; c < B; ++c) {
-                            tk.Wh[(int64_t)c * tk.ld + r] = w[c];
-                            sW[c * kTile + k] = w[c];
-                        }
-                    }
-                } else {
-#pragma unroll
-                    for (int c = 0; c < B; ++c) {
-                        T v = tk.Wh[(int64_t)c * tk.ld + r];
-                        if constexpr (sizeof(T) == 4) v += tk.Wl[(int64_t)c * tk.ld + r];
-                        sW[c * kTile + k] = v;
-                    }
+        for (int c = 0; c < B; ++c) {
+            if constexpr (sizeof(T) == 4) {
+                const F2 wv = f2_add(F2{act ? tk.Wh[(int64_t)c * ld + r] : 0.f, act ? tk.Wl[(int64_t)c * ld + r] : 0.f},
+                                     F2{-s[c], -l[c]});
+                if (act) {
+                    tk.Wh[(int64_t)c * ld + r] = wv.hi;
+                    tk.Wl[(int64_t)c * ld + r] = wv.lo;
                 }
-                if (MODE == 1) {
-#pragma unroll
-                    for (int i = 0; i < B; ++i)
-#pragma unroll
-                        for (int j = 0; j < B; ++j) gram[i][j].add(sW[i * kTile + k], sW[j * kTile + k]);
-                }
-            }
-            if (MODE == 0) {
-                __syncthreads();
-#pragma unroll
-                for (int g = 0; g < GMAX; ++g) {
-                    const int a = (g0 + g) * 8 + warp;
-                    if (g0 + g >= ng || a >= p) continue;
-                    for (int k = lane; k < nt; k += 32) {
-                        const T x = sV[(size_t)a * kTile + k];
-#pragma unroll
-                        for (int c = 0; c < B; ++c) acc[g][c].add(x, sW[c * kTile + k]);
-                    }
-                }
+                wr[c] = wv.hi + wv.lo;
+            } else {
+                const T wv = (act ? tk.Wh[(int64_t)c * ld + r] : T(0)) - s[c];
+                if (act) tk.Wh[(int64_t)c * ld + r] = wv;
+                wr[c] = wv;
             }
         }
-        if (MODE == 0) {
-#pragma unroll
-            for (int g = 0; g < GMAX; ++g) {
-                const int a = (g0 + g) * 8 + warp;
-                if (g0 + g >= ng || a >= p) continue;
-#pragma unroll
-                for (int c = 0; c < B; ++c) {
-                    const double v = wsum(acc[g][c].get());
-                    if (lane == 0) pout[a + c * p] = v;
-                    acc[g][c].zero();
-                }
-            }
-        }
-    }
-    if (MODE == 1) {
-        __shared__ double sg[kThreads / 32][B * B];
 #pragma unroll
         for (int i = 0; i < B; ++i)
 #pragma unroll
-            for (int j = 0; j < B; ++j) {
-                const double v = wsum(gram[i][j].get());
-                if (lane == 0) sg[warp][i + j * B] = v;
-            }
-        __syncthreads();
-        for (int e = threadIdx.x; e < B * B; e += kThreads) {
-            double s = 0.0;
-            for (int w2 = 0; w2 < kThreads / 32; ++w2) s += sg[w2][e];
-            pout[e] = s;
+            for (int j = 0; j < B; ++j) g[i][j] = fma(wr[i], wr[j], g[i][j]);
+    }
+#pragma unroll
+    for (int i = 0; i < B; ++i)
+#pragma unroll
+        for (int j = 0; j < B; ++j) warp_to_smem(g[i][j], sred, NE, i + j * B);
+    __syncthreads();
+    double* pout = partial + ((size_t)blockIdx.y * nchunks + blockIdx.x) * pstride;
+    for (int e = threadIdx.x; e < NE; e += kThreads) pout[e] = cta_entry(sred, NE, e);
+}
+
+// W <- W T for one row (T: B x B FP64 in shared memory); FP32 data in double-float.
+template <int B>
+__device__ __forceinline__ void scale_row(float (&xh)[B], float (&xl)[B], const double* sT, float (&res)[B]) {
+    F2 z[B];
+#pragma unroll
+    for (int c = 0; c < B; ++c) {
+        z[c] = F2{0.f, 0.f};
+#pragma unroll
+        for (int a = 0; a < B; ++a) z[c] = f2_add(z[c], f2_mul(F2{xh[a], xl[a]}, f2_from(sT[a + c * B])));
+    }
+#pragma unroll
+    for (int c = 0; c < B; ++c) {
+        xh[c] = z[c].hi;
+        xl[c] = z[c].lo;
+        res[c] = z[c].hi + z[c].lo;
+    }
+}
+template <int B>
+__device__ __forceinline__ void scale_row(double (&xh)[B], double (&)[B], const double* sT, double (&res)[B]) {
+    double z[B];
+#pragma unroll
+    for (int c = 0; c < B; ++c) {
+        z[c] = 0.0;
+#pragma unroll
+        for (int a = 0; a < B; ++a) z[c] = fma(xh[a], sT[a + c * B], z[c]);
+    }
+#pragma unroll
+    for (int c = 0; c < B; ++c) xh[c] = res[c] = z[c];
+}
+
+// =====================================================================================
+// k_scale_proj: W <- W T1 (normalisation of the block after the first Gram-Schmidt
+// pass) and partial h2 = V^T W of the normalised block, p <= kFuseP.  Computing the
+// second-pass coefficients from the normalised block keeps their error from being
+// magnified by the block's conditioning.
+// =====================================================================================
+template <typename T, int B>
+__global__ void __launch_bounds__(kThreads, 2) k_scale_proj(const UpdTask<T>* __restrict__ tasks, int64_t n,
+                                                            int64_t rows, int nchunks, int pstride,
+                                                            double* __restrict__ partial) {
+    constexpr int Q = kFuseP;
+    constexpr int NE = Q * B;
+    __shared__ double sT[B * B];
+    __shared__ double sred[kWarps * NE];
+    const UpdTask<T> tk = tasks[blockIdx.y];
+    const int p = tk.p;
+    for (int e = threadIdx.x; e < B * B; e += kThreads) sT[e] = tk.hm[(e % B) + (int64_t)(e / B) * tk.ldh];
+    __syncthreads();
+    const int64_t ld = tk.ld;
+    const int64_t r0 = (int64_t)blockIdx.x * rows;
+    const int64_t r1 = (r0 + rows < n) ? r0 + rows : n;
+    T acc[Q][B];
+#pragma unroll
+    for (int q = 0; q < Q; ++q)
+#pragma unroll
+        for (int c = 0; c < B; ++c) acc[q][c] = T(0);
+    for (int64_t base = r0; base < r1; base += kThreads) {
+        const int64_t r = base + threadIdx.x;
+        const bool act = r < r1;
+        T x[Q], xh[B], xl[B], res[B];
+#pragma unroll
+        for (int q = 0; q < Q; ++q) x[q] = (act && q < p) ? ldg(tk.V + (int64_t)q * ld + r) : T(0);
+#pragma unroll
+        for (int c = 0; c < B; ++c) {
+            xh[c] = act ? tk.Wh[(int64_t)c * ld + r] : T(0);
+            if constexpr (sizeof(T) == 4) xl[c] = act ? tk.Wl[(int64_t)c * ld + r] : 0.f;
         }
+        scale_row<B>(xh, xl, sT, res);
+        if (act) {
+#pragma unroll
+            for (int c = 0; c < B; ++c) {
+                tk.Wh[(int64_t)c * ld + r] = xh[c];
+                if constexpr (sizeof(T) == 4) tk.Wl[(int64_t)c * ld + r] = xl[c];
+            }
+        }
+#pragma unroll
+        for (int q = 0; q < Q; ++q)
+#pragma unroll
+            for (int c = 0; c < B; ++c) acc[q][c] = fma(x[q], res[c], acc[q][c]);
+    }
+#pragma unroll
+    for (int q = 0; q < Q; ++q)
+        if (q < p) {
+#pragma unroll
+            for (int c = 0; c < B; ++c) warp_to_smem(acc[q][c], sred, NE, q + c * Q);
+        }
+    __syncthreads();
+    double* pout = partial + ((size_t)blockIdx.y * nchunks + blockIdx.x) * pstride;
+    for (int e = threadIdx.x; e < NE; e += kThreads) {
+        const int q = e % Q, c = e / Q;
+        if (q < p) pout[q + c * p] = cta_entry(sred, NE, e);
     }
 }
 
 // =====================================================================================
-// Block scaling W <- W T (T: B x B), with the Gram matrix of the result (gram != 0)
-// or, for the final pass, the result rounded into the basis slot task.out.
+// k_vtw: partial h = V^T W over columns [z*PG, z*PG + PG) (grid z), W = hi + lo rounded.
 // =====================================================================================
 template <typename T, int B>
-__global__ void __launch_bounds__(kThreads) k_scale(const UpdTask<T>* __restrict__ tasks, int64_t n, int64_t rows,
-                                                    int nchunks, int gramflag, int pstride,
-                                                    double* __restrict__ partial) {
+__global__ void __launch_bounds__(kThreads, 2) k_vtw(const UpdTask<T>* __restrict__ tasks, int64_t n, int64_t rows,
+                                                  int nchunks, int pstride, double* __restrict__ partial) {
+    constexpr int PG = Group<T, B>::vtw;
+    constexpr int NE = PG * B;
+    __shared__ double sred[kWarps * NE];
     const UpdTask<T> tk = tasks[blockIdx.y];
-    const int ch = blockIdx.x;
-    const int64_t r0 = (int64_t)ch * rows;
+    const int p = tk.p;
+    const int a0 = blockIdx.z * PG;
+    if (a0 >= p) return;
+    const int na = min(PG, p - a0);
+    const int64_t ld = tk.ld;
+    const int64_t r0 = (int64_t)blockIdx.x * rows;
     const int64_t r1 = (r0 + rows < n) ? r0 + rows : n;
-    __shared__ double sh[B * B];
-    load_coeffs<T, B>(tk, B * B, sh);
+    T acc[PG][B];
+#pragma unroll
+    for (int q = 0; q < PG; ++q)
+#pragma unroll
+        for (int c = 0; c < B; ++c) acc[q][c] = T(0);
+    for (int64_t base = r0; base < r1; base += kThreads) {
+        const int64_t r = base + threadIdx.x;
+        const bool act = r < r1;
+        T x[PG], w[B];
+#pragma unroll
+        for (int q = 0; q < PG; ++q) x[q] = (act && q < na) ? ldg(tk.V + (int64_t)(a0 + q) * ld + r) : T(0);
+#pragma unroll
+        for (int c = 0; c < B; ++c) {
+            T v = act ? tk.Wh[(int64_t)c * ld + r] : T(0);
+            if constexpr (sizeof(T) == 4) v += act ? tk.Wl[(int64_t)c * ld + r] : 0.f;
+            w[c] = v;
+        }
+#pragma unroll
+        for (int q = 0; q < PG; ++q)
+#pragma unroll
+            for (int c = 0; c < B; ++c) acc[q][c] = fma(x[q], w[c], acc[q][c]);
+    }
+#pragma unroll
+    for (int q = 0; q < PG; ++q)
+        if (q < na) {
+#pragma unroll
+            for (int c = 0; c < B; ++c) warp_to_smem(acc[q][c], sred, NE, q + c * PG);
+        }
     __syncthreads();
-    Sum<T> gram[B][B];
+    double* pout = partial + ((size_t)blockIdx.y * nchunks + blockIdx.x) * pstride;
+    for (int e = threadIdx.x; e < NE; e += kThreads) {
+        const int q = e % PG, c = e / PG;
+        if (q < na) pout[(a0 + q) + c * p] = cta_entry(sred, NE, e);
+    }
+}
+
+// =====================================================================================
+// k_update1: W <- W - V h2 (second Gram-Schmidt pass) and partial G = W^T W.
+// h2 is at the orthogonality-error level, so V h2 is formed with FP32 products.
+// =====================================================================================
+template <typename T, int B>
+__global__ void __launch_bounds__(kThreads, 2) k_update1(const UpdTask<T>* __restrict__ tasks, int64_t n, int64_t rows,
+                                                      int nchunks, int pstride, double* __restrict__ partial) {
+    constexpr int Q = 16;
+    constexpr int NE = B * B;
+    extern __shared__ double sh_dyn[];
+    T* sh = reinterpret_cast<T*>(sh_dyn);
+    __shared__ double sred[kWarps * NE];
+    const UpdTask<T> tk = tasks[blockIdx.y];
+    const int p = tk.p;
+    for (int e = threadIdx.x; e < p * B; e += kThreads) sh[e] = (T)tk.hm[(e % p) + (int64_t)(e / p) * tk.ldh];
+    __syncthreads();
+    const int64_t ld = tk.ld;
+    const int64_t r0 = (int64_t)blockIdx.x * rows;
+    const int64_t r1 = (r0 + rows < n) ? r0 + rows : n;
+    T g[B][B];
 #pragma unroll
     for (int i = 0; i < B; ++i)
 #pragma unroll
-        for (int j = 0; j < B; ++j) gram[i][j].zero();
-    for (int64_t r = r0 + threadIdx.x; r < r1; r += kThreads) {
-        T res[B];
-        if constexpr (sizeof(T) == 4) {
-            F2 x[B], z[B];
+        for (int j = 0; j < B; ++j) g[i][j] = T(0);
+    for (int64_t base = r0; base < r1; base += kThreads) {
+        const int64_t r = base + threadIdx.x;
+        const bool act = r < r1;
+        T s[B];
 #pragma unroll
-            for (int c = 0; c < B; ++c) {
-                x[c] = F2{tk.Wh[(int64_t)c * tk.ld + r], tk.Wl[(int64_t)c * tk.ld + r]};
-                z[c] = F2{0.f, 0.f};
-            }
+        for (int c = 0; c < B; ++c) s[c] = T(0);
+        for (int q0 = 0; q0 < p; q0 += Q) {
+            T x[Q];
 #pragma unroll
-            for (int a = 0; a < B; ++a)
+            for (int q = 0; q < Q; ++q) x[q] = (act && q0 + q < p) ? ldg(tk.V + (int64_t)(q0 + q) * ld + r) : T(0);
 #pragma unroll
-                for (int c = 0; c < B; ++c) z[c] = f2_add(z[c], f2_mul(x[a], f2_from(sh[a + c * B])));
+            for (int c = 0; c < B; ++c)
 #pragma unroll
-            for (int c = 0; c < B; ++c) {
-                res[c] = z[c].hi + z[c].lo;
-                if (tk.out) {
-                    tk.out[(int64_t)c * tk.ld + r] = res[c];
-                } else {
-                    tk.Wh[(int64_t)c * tk.ld + r] = z[c].hi;
-                    tk.Wl[(int64_t)c * tk.ld + r] = z[c].lo;
+                for (int q = 0; q < Q; ++q)
+                    if (q0 + q < p) s[c] = fma(x[q], sh[(q0 + q) + c * p], s[c]);
+        }
+        T wr[B];
+#pragma unroll
+        for (int c = 0; c < B; ++c) {
+            if constexpr (sizeof(T) == 4) {
+                const F2 wv = f2_add(F2{act ? tk.Wh[(int64_t)c * ld + r] : 0.f, act ? tk.Wl[(int64_t)c * ld + r] : 0.f},
+                                     F2{-s[c], 0.f});
+                if (act) {
+                    tk.Wh[(int64_t)c * ld + r] = wv.hi;
+                    tk.Wl[(int64_t)c * ld + r] = wv.lo;
                 }
-            }
-        } else {
-            double x[B];
-#pragma unroll
-            for (int c = 0; c < B; ++c) x[c] = tk.Wh[(int64_t)c * tk.ld + r];
-#pragma unroll
-            for (int c = 0; c < B; ++c) {
-                double z = 0.0;
-#pragma unroll
-                for (int a = 0; a < B; ++a) z = fma(x[a], sh[a + c * B], z);
-                res[c] = z;
-                if (tk.out) tk.out[(int64_t)c * tk.ld + r] = z;
-                else tk.Wh[(int64_t)c * tk.ld + r] = z;
+                wr[c] = wv.hi + wv.lo;
+            } else {
+                const T wv = (act ? tk.Wh[(int64_t)c * ld + r] : T(0)) - s[c];
+                if (act) tk.Wh[(int64_t)c * ld + r] = wv;
+                wr[c] = wv;
             }
         }
-        if (gramflag) {
 #pragma unroll
-            for (int i = 0; i < B; ++i)
+        for (int i = 0; i < B; ++i)
 #pragma unroll
-                for (int j = 0; j < B; ++j) gram[i][j].add(res[i], res[j]);
+            for (int j = 0; j < B; ++j) g[i][j] = fma(wr[i], wr[j], g[i][j]);
+    }
+#pragma unroll
+    for (int i = 0; i < B; ++i)
+#pragma unroll
+        for (int j = 0; j < B; ++j) warp_to_smem(g[i][j], sred, NE, i + j * B);
+    __syncthreads();
+    double* pout = partial + ((size_t)blockIdx.y * nchunks + blockIdx.x) * pstride;
+    for (int e = threadIdx.x; e < NE; e += kThreads) pout[e] = cta_entry(sred, NE, e);
+}
+
+// =====================================================================================
+// k_scale: W <- W T (T: B x B, dense FP64), with the Gram matrix of the result
+// (gram != 0) or, for the final pass, the result rounded into the basis slot task.out.
+// Four rows per thread per iteration, loads first.
+// =====================================================================================
+template <typename T, int B>
+__global__ void __launch_bounds__(kThreads, 2) k_scale(const UpdTask<T>* __restrict__ tasks, int64_t n, int64_t rows,
+                                                       int nchunks, int gramflag, int pstride,
+                                                       double* __restrict__ partial) {
+    constexpr int U = 4;
+    constexpr int NE = B * B;
+    __shared__ double sT[B * B];
+    __shared__ double sred[kWarps * NE];
+    const UpdTask<T> tk = tasks[blockIdx.y];
+    for (int e = threadIdx.x; e < B * B; e += kThreads) sT[e] = tk.hm[(e % B) + (int64_t)(e / B) * tk.ldh];
+    __syncthreads();
+    const int64_t ld = tk.ld;
+    const int64_t r0 = (int64_t)blockIdx.x * rows;
+    const int64_t r1 = (r0 + rows < n) ? r0 + rows : n;
+    T g[B][B];
+#pragma unroll
+    for (int i = 0; i < B; ++i)
+#pragma unroll
+        for (int j = 0; j < B; ++j) g[i][j] = T(0);
+    for (int64_t base = r0; base < r1; base += (int64_t)kThreads * U) {
+        T xh[U][B], xl[U][B];
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            const int64_t r = base + (int64_t)u * kThreads + threadIdx.x;
+            const bool act = r < r1;
+#pragma unroll
+            for (int c = 0; c < B; ++c) {
+                xh[u][c] = act ? tk.Wh[(int64_t)c * ld + r] : T(0);
+                if constexpr (sizeof(T) == 4) xl[u][c] = act ? tk.Wl[(int64_t)c * ld + r] : 0.f;
+            }
+        }
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            const int64_t r = base + (int64_t)u * kThreads + threadIdx.x;
+            const bool act = r < r1;
+            T res[B];
+            scale_row<B>(xh[u], xl[u], sT, res);
+            if (act) {
+#pragma unroll
+                for (int c = 0; c < B; ++c) {
+                    if (tk.out) {
+                        tk.out[(int64_t)c * ld + r] = res[c];
+                        if constexpr (sizeof(T) == 4)
+                            if (tk.outlo) tk.outlo[(int64_t)c * ld + r] = (xh[u][c] - res[c]) + xl[u][c];
+                    } else {
+                        tk.Wh[(int64_t)c * ld + r] = xh[u][c];
+                        if constexpr (sizeof(T) == 4) tk.Wl[(int64_t)c * ld + r] = xl[u][c];
+                    }
+                }
+            }
+            if (gramflag) {
+#pragma unroll
+                for (int i = 0; i < B; ++i)
+#pragma unroll
+                    for (int j = 0; j < B; ++j) g[i][j] = fma(res[i], res[j], g[i][j]);
+            }
         }
     }
     if (gramflag) {
-        __shared__ double sg[kThreads / 32][B * B];
-        const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-        double* pout = partial + ((size_t)blockIdx.y * nchunks + ch) * pstride;
 #pragma unroll
         for (int i = 0; i < B; ++i)
 #pragma unroll
-            for (int j = 0; j < B; ++j) {
-                const double v = wsum(gram[i][j].get());
-                if (lane == 0) sg[warp][i + j * B] = v;
-            }
+            for (int j = 0; j < B; ++j) warp_to_smem(g[i][j], sred, NE, i + j * B);
         __syncthreads();
-        for (int e = threadIdx.x; e < B * B; e += kThreads) {
-            double s = 0.0;
-            for (int w2 = 0; w2 < kThreads / 32; ++w2) s += sg[w2][e];
-            pout[e] = s;
-        }
+        double* pout = partial + ((size_t)blockIdx.y * nchunks + blockIdx.x) * pstride;
+        for (int e = threadIdx.x; e < NE; e += kThreads) pout[e] = cta_entry(sred, NE, e);
+    }
+}
+
+// =====================================================================================
+// Sum of per-CTA partials into a dense FP64 block of each window's slab:
+// out(task) = wd + wins[task] * stride + off, entries [0, ne).
+// =====================================================================================
+__global__ void __launch_bounds__(kThreads) k_sum_parts(const double* __restrict__ part, int nchunks, int pstride, int ne,
+                                                        double* __restrict__ wd, int64_t stride, int64_t off,
+                                                        const int* __restrict__ wins) {
+    const Parts pp{part, nchunks, pstride};
+    double* out = wd + (int64_t)wins[blockIdx.x] * stride + off;
+    for (int e = threadIdx.x >> 5; e < ne; e += kWarps) {
+        const double v = parts_sum_warp(pp, blockIdx.x, e);
+        if ((threadIdx.x & 31) == 0) out[e] = v;
     }
 }
 
@@ -522,24 +797,22 @@ __global__ void __launch_bounds__(kThreads) k_source_gram(const T* const* __rest
 // launchers
 // =====================================================================================
 KGeom krylov_geom(int ntasks, int64_t n) {
+    // 2048 .. 8192 rows per CTA, and at least ~8 CTAs per SM in total where n allows
     KGeom g;
-    const int want = std::max(1, (4 * kNumSM + ntasks - 1) / ntasks);
-    const int64_t maxch = std::max<int64_t>(1, (n + kTile - 1) / kTile);
-    g.nchunks = (int)std::min<int64_t>(want, maxch);
-    g.rows = (n + g.nchunks - 1) / g.nchunks;
+    const int64_t lo = std::max<int64_t>(1, (n + 8191) / 8192);
+    const int64_t hi = std::max<int64_t>(1, (n + 2047) / 2048);
+    const int64_t want = (8 * kNumSM + ntasks - 1) / std::max(1, ntasks);
+    const int64_t ch = std::min(std::max(want, lo), hi);
+    g.rows = (n + ch - 1) / ch;
     g.rows = (g.rows + kTile - 1) / kTile * kTile;
     g.nchunks = (int)((n + g.rows - 1) / g.rows);
     return g;
 }
 
-size_t krylov_partial_doubles(int ntasks, int p_max, int b_max, int64_t n) {
-    const KGeom g = krylov_geom(ntasks, n);
-    const size_t stride = (size_t)3 * p_max * b_max + b_max;
-    return (size_t)ntasks * g.nchunks * std::max<size_t>(stride, (size_t)b_max * b_max) + 64;
-}
-
-size_t krylov_update_smem(int p_max, int b, size_t tsize) {
-    return sizeof(double) * (size_t)((p_max * b + 1) & ~1) + tsize * (size_t)(p_max + b) * kTile;
+size_t krylov_partial_slots(int ntasks_max, int64_t n) {
+    // ntasks * nchunks(ntasks) <= ntasks * ceil(n / 8192) + 8 * kNumSM + ntasks for every ntasks <= ntasks_max
+    const int64_t lo = std::max<int64_t>(1, (n + 8191) / 8192);
+    return (size_t)ntasks_max * (size_t)(lo + 1) + 8 * kNumSM + 64;
 }
 
 #define PEXP_B_DISPATCH(b, CALL)     \
@@ -552,28 +825,45 @@ size_t krylov_update_smem(int p_max, int b, size_t tsize) {
     }
 
 template <typename T>
-void launch_step_proj(const StepTask<T>* tasks, int ntasks, int b, int64_t n, int periodic, KGeom g,
+void launch_step_proj(const StepTask<T>* tasks, int ntasks, int b, int p, int64_t n, int periodic, KGeom g,
                       double* partial, int pstride, cudaStream_t s) {
     if (ntasks <= 0) return;
+    PEXP_B_DISPATCH(b, ({
+        constexpr int PG = Group<T, BB>::step;
+        dim3 grid(g.nchunks, ntasks, (p + PG - 1) / PG);
+        k_step_proj<T, BB><<<grid, kThreads, 0, s>>>(tasks, n, periodic, g.rows, g.nchunks, pstride, partial);
+    }));
+}
+
+bool proj_fused(int p, int b, size_t tsize) { return p <= kFuseP && (size_t)p * b * tsize <= 128; }
+
+template <typename T>
+void launch_update(const UpdTask<T>* tasks, int ntasks, int b, int p, int64_t n, int mode, KGeom g, double* partial,
+                   int pstride, cudaStream_t s) {
+    if (ntasks <= 0) return;
     dim3 grid(g.nchunks, ntasks);
-    PEXP_B_DISPATCH(b, (k_step_proj<T, BB><<<grid, kThreads, 0, s>>>(tasks, n, periodic, g.rows, g.nchunks, pstride, partial)));
+    if (mode == 0) {
+        const size_t sm = (size_t)p * b * (sizeof(T) == 4 ? sizeof(float2) : sizeof(double)) + 16;
+        PEXP_B_DISPATCH(b, (k_update0<T, BB><<<grid, kThreads, sm, s>>>(tasks, n, g.rows, g.nchunks, pstride, partial)));
+    } else {
+        const size_t sm = (size_t)p * b * sizeof(T) + 16;
+        PEXP_B_DISPATCH(b, (k_update1<T, BB><<<grid, kThreads, sm, s>>>(tasks, n, g.rows, g.nchunks, pstride, partial)));
+    }
 }
 
 template <typename T>
-void launch_update(const UpdTask<T>* tasks, int ntasks, int b, int p_max, int64_t n, int mode, KGeom g,
-                   double* partial, int pstride, cudaStream_t s) {
+void launch_scale_proj(const UpdTask<T>* tasks, int ntasks, int b, int p, int64_t n, KGeom g, double* partial,
+                       int pstride, cudaStream_t s) {
     if (ntasks <= 0) return;
     dim3 grid(g.nchunks, ntasks);
-    const size_t sm = krylov_update_smem(p_max, b, sizeof(T));
-    if (mode == 0) {
-        PEXP_B_DISPATCH(b, ({
-            if (sm > 48 * 1024) cudaFuncSetAttribute(k_update<T, BB, 0>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-            k_update<T, BB, 0><<<grid, kThreads, sm, s>>>(tasks, n, g.rows, g.nchunks, pstride, partial);
-        }));
+    if (proj_fused(p, b, sizeof(T))) {
+        PEXP_B_DISPATCH(b, (k_scale_proj<T, BB><<<grid, kThreads, 0, s>>>(tasks, n, g.rows, g.nchunks, pstride, partial)));
     } else {
         PEXP_B_DISPATCH(b, ({
-            if (sm > 48 * 1024) cudaFuncSetAttribute(k_update<T, BB, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-            k_update<T, BB, 1><<<grid, kThreads, sm, s>>>(tasks, n, g.rows, g.nchunks, pstride, partial);
+            k_scale<T, BB><<<grid, kThreads, 0, s>>>(tasks, n, g.rows, g.nchunks, 0, pstride, nullptr);
+            constexpr int PG = Group<T, BB>::vtw;
+            dim3 g3(g.nchunks, ntasks, (p + PG - 1) / PG);
+            k_vtw<T, BB><<<g3, kThreads, 0, s>>>(tasks, n, g.rows, g.nchunks, pstride, partial);
         }));
     }
 }
@@ -584,6 +874,12 @@ void launch_scale(const UpdTask<T>* tasks, int ntasks, int b, int64_t n, int gra
     if (ntasks <= 0) return;
     dim3 grid(g.nchunks, ntasks);
     PEXP_B_DISPATCH(b, (k_scale<T, BB><<<grid, kThreads, 0, s>>>(tasks, n, g.rows, g.nchunks, gram, pstride, partial)));
+}
+
+void launch_sum_parts(const double* part, int nchunks, int pstride, int ne, double* wd, int64_t stride, int64_t off,
+                      const int* wins, int ntasks, cudaStream_t s) {
+    if (ntasks <= 0 || ne <= 0) return;
+    k_sum_parts<<<ntasks, kThreads, 0, s>>>(part, nchunks, pstride, ne, wd, stride, off, wins);
 }
 
 template <typename T>
@@ -597,9 +893,10 @@ void launch_source_gram(const T* const* X, const int* sv, int ntasks, int s_max,
 }
 
 #define PEXP_KRY_INST(T)                                                                                           \
-    template void launch_step_proj<T>(const StepTask<T>*, int, int, int64_t, int, KGeom, double*, int, cudaStream_t); \
+    template void launch_step_proj<T>(const StepTask<T>*, int, int, int, int64_t, int, KGeom, double*, int, cudaStream_t); \
     template void launch_update<T>(const UpdTask<T>*, int, int, int, int64_t, int, KGeom, double*, int, cudaStream_t); \
     template void launch_scale<T>(const UpdTask<T>*, int, int, int64_t, int, KGeom, double*, int, cudaStream_t); \
+    template void launch_scale_proj<T>(const UpdTask<T>*, int, int, int, int64_t, KGeom, double*, int, cudaStream_t); \
     template void launch_source_gram<T>(const T* const*, const int*, int, int, int64_t, KGeom, double*, int, cudaStream_t);
 PEXP_KRY_INST(double)
 PEXP_KRY_INST(float)

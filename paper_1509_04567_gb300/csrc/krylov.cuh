@@ -15,21 +15,19 @@ struct StepTask {
     int p;
 };
 
-// W <- W - V h (mode 0/1) or W <- W T (scale).  h/T come either from a dense
-// FP64 matrix (hm, ld ldh) or, when hpart != NULL, from the sum over `hchunks`
-// partial results of the previous kernel (stride hstride, offset hoff per chunk).
+// W <- W - V h (mode 0/1) or W <- W T (scale), h/T a dense FP64 matrix (hm, ld ldh).
 template <typename T>
 struct UpdTask {
     const T* V;       // V_{1:i} (mode 0/1); unused by the scale kernel
     T* Wh;            // working block (hi)
     float* Wl;        // FP32 data: low parts; NULL for FP64
     T* out;           // scale kernel, final pass: destination of the rounded block (else NULL)
+    float* outlo;     // final pass, FP32 data: what the rounding into `out` left over (else NULL)
+    const float* Vlo; // mode 0, FP32 data: low parts of the last block of V_{1:i} (columns p-b..p-1), or NULL
     int64_t ld;
     int p;
     const double* hm;
     int ldh;
-    const double* hpart;
-    int hchunks, hstride;
 };
 
 struct KGeom {
@@ -37,24 +35,33 @@ struct KGeom {
     int64_t rows;
 };
 KGeom krylov_geom(int ntasks, int64_t n);
-size_t krylov_partial_doubles(int ntasks, int p_max, int b_max, int64_t n);
-size_t krylov_update_smem(int p_max, int b, size_t tsize);
+// upper bound of ntasks * krylov_geom(ntasks, n).nchunks over ntasks <= ntasks_max
+size_t krylov_partial_slots(int ntasks_max, int64_t n);
 
 // All launchers take the row-chunk geometry g (the same for every task of a step) and
 // write the partials of task k at partial + (k * g.nchunks + chunk) * pstride.
 // partial layout of k_step_proj per (task, chunk): E (p x b) | F (p x b) | h1 (p x b) | pre (b)
+// p = columns of V_{1:i} (the same for every task of the launch)
 template <typename T>
-void launch_step_proj(const StepTask<T>* tasks, int ntasks, int b, int64_t n, int periodic, KGeom g,
+void launch_step_proj(const StepTask<T>* tasks, int ntasks, int b, int p, int64_t n, int periodic, KGeom g,
                       double* partial, int pstride, cudaStream_t s);
-// mode 0: W -= V h, partial h2 = V^T W (p x b);  mode 1: W -= V h, partial G = W^T W (b x b)
+// mode 0 and 1: W -= V h (h = tk.hm, p x b), partial G = W^T W (b x b); mode 0 subtracts
+// in double-float (FP32 data), mode 1 with FP32 products (second-pass coefficients)
 template <typename T>
 void launch_update(const UpdTask<T>* tasks, int ntasks, int b, int p_max, int64_t n, int mode, KGeom g,
                    double* partial, int pstride, cudaStream_t s);
+// W <- W T (T = tk.hm, b x b) and partial h = V^T W (p x b) of the result
+template <typename T>
+void launch_scale_proj(const UpdTask<T>* tasks, int ntasks, int b, int p, int64_t n, KGeom g, double* partial,
+                       int pstride, cudaStream_t s);
 // W <- W T; gram != 0: partial G = W^T W; task.out != NULL: result rounded into task.out
 template <typename T>
 void launch_scale(const UpdTask<T>* tasks, int ntasks, int b, int64_t n, int gram, KGeom g, double* partial,
                   int pstride, cudaStream_t s);
 constexpr int kKrylovMaxB = 4;   // block widths handled by the fused kernels
+// Sums the per-CTA partials of each task into wd + wins[task] * stride + off (ne entries).
+void launch_sum_parts(const double* part, int nchunks, int pstride, int ne, double* wd, int64_t stride, int64_t off,
+                      const int* wins, int ntasks, cudaStream_t s);
 // Gram matrices of the source windows: X[k] points at the first of sv[k] (<= 31)
 // consecutive length-n vectors; partial (chunk) results s x s, both halves.
 template <typename T>

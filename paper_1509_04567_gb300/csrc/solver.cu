@@ -90,12 +90,16 @@ namespace {
 constexpr size_t kAlign = 256;
 
 // Relative thresholds below which a new Krylov direction counts as already in the
-// space (block deflation), per precision of the n-length data.
+// space (block deflation): its norm after Gram-Schmidt over its norm before.  FP32
+// data keep the working block in double-float, so directions far below FP32 rounding
+// are still resolved; dropping them (a threshold near sqrt of FP32 epsilon) left the
+// rounding noise of the stored basis, magnified by the shift-and-invert step,
+// unresolved in the projected problem.
 #ifndef PEXP_DEFL_FP64
 #define PEXP_DEFL_FP64 1e-10
 #endif
 #ifndef PEXP_DEFL_FP32
-#define PEXP_DEFL_FP32 1e-5
+#define PEXP_DEFL_FP32 1e-8
 #endif
 #ifndef PEXP_TN_EXACT_FP32
 #define PEXP_TN_EXACT_FP32 0
@@ -214,6 +218,14 @@ void d2h(pexp_ctx* c, void* dst, const void* src, size_t bytes) {
     sync(c);
 }
 
+// Partial-sum buffers of the fused Krylov kernels and the source Gram kernel: one slot
+// per (task, row chunk), each as wide as the largest partial (step projections at the
+// last step, or an s x s Gram matrix).
+size_t kpart_doubles(int P, int64_t n, int kmax, int b_cap, int smax) {
+    const size_t width = std::max<size_t>((size_t)(3 * kmax * b_cap * b_cap + b_cap + b_cap * b_cap), (size_t)smax * smax);
+    return krylov_partial_slots(P, n) * width + 64;
+}
+
 OpDesc make_opdesc(const pexp_operator& op) {
     OpDesc d;
     memset(&d, 0, sizeof(d));
@@ -272,6 +284,7 @@ struct Win {
     int b;        // block width
     float* Wlo;   // FP32 data: low parts of the working block (n x b); NULL for FP64
     float* V1lo;  // FP32 data: low parts of the start block V_1 (n x b); NULL for FP64
+    float* Vklo;  // FP32 data: low parts of the newest block V_k, k >= 2 (n x b); NULL for FP64
 };
 
 
@@ -331,7 +344,8 @@ struct Solver {
 
     // Fused block Krylov steps (1D operators, block widths <= kKrylovMaxB): per step one
     // projection pass (Galerkin sums by parts, first Gram-Schmidt coefficients, norms),
-    // the projected solve, and three passes for Gram-Schmidt and Cholesky QR.
+    // the projected solve, and four passes for block Gram-Schmidt with Cholesky QR,
+    // applied twice: update + Gram, scaling + second projection, update + Gram, scaling.
     int run_fused(std::vector<Win<T>> ws, int* max_steps) {
         int notconv = 0;
         *max_steps = 0;
@@ -346,7 +360,7 @@ struct Solver {
             const int ps1 = 3 * step * bmax * bmax + bmax;   // step_proj partial stride
             // ---- part A
             Stage sa(c, 0);
-            std::vector<const T*> xin;
+            std::vector<const T*> xin, xlo;
             std::vector<T*> yout, ylo;
             std::vector<StepTask<T>> st1(na);
             std::vector<int> wl(na);
@@ -354,8 +368,13 @@ struct Solver {
                 const Win<T>& W = act[a];
                 T* Vi = slot(W, step - 1);
                 T* Wn = slot(W, step);
+                // FP32 data: the newest block enters the solve with its low parts, so that its
+                // rounding (white noise, not in the Krylov space) is not turned by the solve and
+                // the normalisation of the next block into directions that never deflate
+                const float* vlo = (step == 1) ? W.V1lo : W.Vklo;
                 for (int cc = 0; cc < W.b; ++cc) {
                     xin.push_back(Vi + (int64_t)cc * n);
+                    xlo.push_back(vlo ? reinterpret_cast<const T*>(vlo) + (int64_t)cc * n : nullptr);
                     yout.push_back(Wn + (int64_t)cc * n);
                     ylo.push_back(W.Wlo ? reinterpret_cast<T*>(W.Wlo) + (int64_t)cc * n : nullptr);
                 }
@@ -364,6 +383,7 @@ struct Solver {
             }
             const int nv = (int)xin.size();
             const T* const* d_xin = sa.put(xin.data(), nv);
+            const T* const* d_xlo = std::is_same<T, float>::value ? sa.put(xlo.data(), nv) : nullptr;
             T* const* d_yout = sa.put(yout.data(), nv);
             T* const* d_ylo = std::is_same<T, float>::value ? sa.put(ylo.data(), nv) : nullptr;
             const StepTask<T>* d_st1 = sa.put(st1.data(), na);
@@ -373,7 +393,7 @@ struct Solver {
             const double wout = std::is_same<T, float>::value ? 8.0 : w;
             if (o->krylov == PEXP_KRYLOV_SAI) {
                 timed(c, PEXP_KC_SAI, (double)nv * n * (w + wout),
-                      [&] { launch_sai_solve<T>(od, sai, d_xin, d_yout, d_ylo, nv, sai_scr, st); });
+                      [&] { launch_sai_solve_lo<T>(od, sai, d_xin, d_xlo, d_yout, d_ylo, nv, sai_scr, st); });
             } else {
                 timed(c, PEXP_KC_STENCIL, (double)nv * n * (w + w), [&] { launch_stencil_ptrs<T>(od, d_xin, d_yout, nv, 0, st); });
                 for (const auto& W : act)
@@ -386,7 +406,7 @@ struct Solver {
                 for (int a0 = 0; a0 < na;) {
                     int a1 = a0;
                     while (a1 < na && act[a1].b == act[a0].b) ++a1;
-                    launch_step_proj<T>(d_st1 + a0, a1 - a0, act[a0].b, n, periodic, g,
+                    launch_step_proj<T>(d_st1 + a0, a1 - a0, act[a0].b, step * act[a0].b, n, periodic, g,
                                         kpart[0] + (size_t)a0 * g.nchunks * ps1, ps1, st);
                     check_launch(c);
                     a0 = a1;
@@ -410,7 +430,7 @@ struct Solver {
             }
             act.swap(next);
             if (act.empty()) break;
-            // ---- part B: two Gram-Schmidt passes and two Cholesky QR passes
+            // ---- part B: block classical Gram-Schmidt with Cholesky QR, twice (BCGS2)
             const int nb = (int)act.size();
             const KGeom gb = krylov_geom(nb, n);
             int bmb = 0;
@@ -428,14 +448,18 @@ struct Solver {
                 memset(&t, 0, sizeof(t));
                 t.V = W.V; t.Wh = Wn; t.Wl = W.Wlo; t.ld = n; t.p = p;
                 t.hm = D(W.w) + L.off_out1; t.ldh = p;                         // h1 from the projection pass
+                t.Vlo = (step == 1) ? W.V1lo : W.Vklo;                         // low parts of the newest block
                 u1[a] = t;
-                t.hm = nullptr; t.hpart = kpart[1] + (size_t)a * gb.nchunks * ps2; t.hchunks = gb.nchunks; t.hstride = ps2;
-                u2[a] = t;                                                     // h2 summed from partials
+                t.Vlo = nullptr;
+                t.hm = D(W.w) + L.off_T; t.ldh = W.b;                          // W <- W T1, h2 = V^T W
+                u3[a] = t;
+                t.hm = D(W.w) + L.off_h2; t.ldh = p;                           // h2 summed from the partials
+                u2[a] = t;
                 memset(&t, 0, sizeof(t));
                 t.Wh = Wn; t.Wl = W.Wlo; t.ld = n; t.p = W.b; t.hm = D(W.w) + L.off_T; t.ldh = W.b;
-                u3[a] = t;                                                     // W <- W T1 (Gram)
                 t.out = Wn;
-                u4[a] = t;                                                     // final: round into the slot
+                t.outlo = W.Vklo;
+                u4[a] = t;                                                     // final: W T2 rounded into the slot
                 wl2[a] = W.w;
             }
             const UpdTask<T>* d1 = sb.put(u1.data(), nb);
@@ -455,9 +479,28 @@ struct Solver {
                     a0 = a1;
                 }
             };
+            // pass 1: W <- W - V h1 (Gram of the result), Cholesky QR with deflation
             timed(c, PEXP_KC_UPDATE, (double)n * (pb * w + 2 * bb * wl_), [&] {
                 groups([&](int a0, int a1, int b) {
-                    launch_update<T>(d1 + a0, a1 - a0, b, step * b, n, 0, gb, kpart[1] + (size_t)a0 * gb.nchunks * ps2, ps2, st);
+                    launch_update<T>(d1 + a0, a1 - a0, b, step * b, n, 0, gb, kpart[0] + (size_t)a0 * gb.nchunks * psg, psg, st);
+                    check_launch(c);
+                });
+            });
+            timed(c, PEXP_KC_SMALL, 0.0, [&] {
+                launch_block_orth(L, wd, wi, d_wl2, nb, 1, step, defl, st, Parts{kpart[0], gb.nchunks, psg});
+            });
+            check_launch(c);
+            // pass 2: W <- W T1 and h2 = V^T W; W <- W - V h2 (Gram), Cholesky QR; round into the basis
+            timed(c, PEXP_KC_UPDATE, (double)n * (pb * w + 2 * bb * wl_), [&] {
+                groups([&](int a0, int a1, int b) {
+                    launch_scale_proj<T>(d3 + a0, a1 - a0, b, step * b, n, gb, kpart[1] + (size_t)a0 * gb.nchunks * ps2, ps2, st);
+                    check_launch(c);
+                });
+            });
+            timed(c, PEXP_KC_SMALL, 0.0, [&] {
+                groups([&](int a0, int a1, int b) {
+                    launch_sum_parts(kpart[1] + (size_t)a0 * gb.nchunks * ps2, gb.nchunks, ps2, step * b * b, wd, L.stride,
+                                     L.off_h2, d_wl2 + a0, a1 - a0, st);
                     check_launch(c);
                 });
             });
@@ -468,17 +511,7 @@ struct Solver {
                 });
             });
             timed(c, PEXP_KC_SMALL, 0.0, [&] {
-                launch_block_orth(L, wd, wi, d_wl2, nb, 1, step, defl, st, Parts{kpart[0], gb.nchunks, psg});
-            });
-            check_launch(c);
-            timed(c, PEXP_KC_UPDATE, (double)n * 2 * bb * wl_, [&] {
-                groups([&](int a0, int a1, int b) {
-                    launch_scale<T>(d3 + a0, a1 - a0, b, n, 1, gb, kpart[1] + (size_t)a0 * gb.nchunks * psg, psg, st);
-                    check_launch(c);
-                });
-            });
-            timed(c, PEXP_KC_SMALL, 0.0, [&] {
-                launch_block_orth(L, wd, wi, d_wl2, nb, 2, step, defl, st, Parts{kpart[1], gb.nchunks, psg});
+                launch_block_orth(L, wd, wi, d_wl2, nb, 2, step, defl, st, Parts{kpart[0], gb.nchunks, psg});
             });
             check_launch(c);
             timed(c, PEXP_KC_UPDATE, (double)n * bb * (wl_ + w), [&] {
@@ -769,8 +802,7 @@ size_t linear_workspace_bytes(int64_t n, const pexp_options* o, int g_conv, int 
     s += align_up(sizeof(int) * L.istride * 2 * P);
     s += align_up(sizeof(double) * (ts_tn_partial_doubles(P, std::max(std::max(pt.smax * pt.smax, 48 * (L.K_max + b_cap)), 48 * L.K_max), n) + 512));
     s += align_up(sizeof(double) * (size_t)L.K_max * 48);                   // orthogonality diagnostic
-    s += 2 * align_up(sizeof(double) * ((size_t)(8 * kNumSM + P + 8) *
-                                        std::max<size_t>((size_t)(3 * kmax * b_cap * b_cap + b_cap + b_cap * b_cap), (size_t)pt.smax * pt.smax) + 64));
+    s += 2 * align_up(sizeof(double) * kpart_doubles(P, n, kmax, b_cap, pt.smax));
     s += align_up(sizeof(double) * sai_scratch_doubles(n, P * b_cap) + 64);
     s += align_up(sizeof(double) * o->n_out);                               // (A u0) . g(t_i)
     s += (size_t)(4 * P + 32) * kAlign;   // alignment of the per-window allocations
@@ -820,8 +852,7 @@ int solve_linear_typed(pexp_ctx* c, const pexp_operator* op, const pexp_options*
     const size_t part_n = ts_tn_partial_doubles(P, std::max(std::max(pt.smax * pt.smax, 48 * (L.K_max + b_cap)), 48 * L.K_max), n) + 512;
     S.partial = as<double>(ws_alloc(c, sizeof(double) * part_n));
     S.diag = as<double>(ws_alloc(c, sizeof(double) * (size_t)L.K_max * 48));
-    const size_t kpart_n = (size_t)(8 * kNumSM + P + 8) *
-                           std::max<size_t>((size_t)(3 * S.kmax * b_cap * b_cap + b_cap + b_cap * b_cap), (size_t)pt.smax * pt.smax) + 64;
+    const size_t kpart_n = kpart_doubles(P, n, S.kmax, b_cap, pt.smax);
     for (int k = 0; k < 2; ++k) S.kpart[k] = as<double>(ws_alloc(c, sizeof(double) * kpart_n));
     S.sai_scr = as<double>(ws_alloc(c, sizeof(double) * (sai_scratch_doubles(n, P * b_cap) + 64)));
     // one pole for every window: gamma = sai_gamma * T / P (the nominal subinterval length)
@@ -915,17 +946,16 @@ int solve_linear_typed(pexp_ctx* c, const pexp_operator* op, const pexp_options*
         b_max = std::max(b_max, mj[j]);
         b_min = std::min(b_min, mj[j]);
     }
-    S.fused = (S.od.dim == 1) && (b_max <= kKrylovMaxB) &&
-              krylov_update_smem(S.kmax * b_max, b_max, sizeof(T)) <= 200u * 1024u;
+    S.fused = (S.od.dim == 1) && (b_max <= kKrylovMaxB);
     // bases laid out with the actual widths, in the basis pool
     {
         size_t need = 0;
         for (int j = 0; j < P; ++j)
             if (mj[j] > 0)
                 need += align_up(sizeof(T) * (size_t)n * mj[j] * (S.kmax + 1)) + align_up(sizeof(T) * (size_t)n * (L.ycols - 1) * mj[j]) +
-                        (std::is_same<T, float>::value ? 2 * align_up(sizeof(float) * (size_t)n * mj[j]) : 0);
+                        (std::is_same<T, float>::value ? 3 * align_up(sizeof(float) * (size_t)n * mj[j]) : 0);
         need += (size_t)P * align_up(sizeof(T) * (size_t)n * (S.kmax + 1));   // homogeneous bases
-        need += align_up(sizeof(T) * (size_t)n * (L.ycols - 1)) + 3 * align_up(sizeof(float) * (size_t)n) + (size_t)(6 * P + 8) * kAlign;
+        need += align_up(sizeof(T) * (size_t)n * (L.ycols - 1)) + 4 * align_up(sizeof(float) * (size_t)n) + (size_t)(7 * P + 8) * kAlign;
         const int r = bs_reserve(c, need);
         if (r) throw StatusError{r};
     }
@@ -941,6 +971,7 @@ int solve_linear_typed(pexp_ctx* c, const pexp_operator* op, const pexp_options*
         W.S = as<T>(bs_alloc(c, sizeof(T) * (size_t)n * (L.ycols - 1) * W.b));
         W.Wlo = std::is_same<T, float>::value ? as<float>(bs_alloc(c, sizeof(float) * (size_t)n * W.b)) : nullptr;
         W.V1lo = std::is_same<T, float>::value ? as<float>(bs_alloc(c, sizeof(float) * (size_t)n * W.b)) : nullptr;
+        W.Vklo = std::is_same<T, float>::value ? as<float>(bs_alloc(c, sizeof(float) * (size_t)n * W.b)) : nullptr;
         Vnh[j] = W.V;
         src_lo[j] = W.V1lo;
         src.push_back(W);
@@ -1036,6 +1067,7 @@ int solve_linear_typed(pexp_ctx* c, const pexp_operator* op, const pexp_options*
     int k_hom_max = 0, k_hom_sum = 0;
     T* Sh = as<T>(bs_alloc(c, sizeof(T) * (size_t)n * (L.ycols - 1)));
     float* Whlo = std::is_same<T, float>::value ? as<float>(bs_alloc(c, sizeof(float) * (size_t)n)) : nullptr;
+    float* Vhklo = std::is_same<T, float>::value ? as<float>(bs_alloc(c, sizeof(float) * (size_t)n)) : nullptr;
     // low parts of the homogeneous start vectors, two buffers used alternately along the chain
     float* Vh1lo_buf[2] = {nullptr, nullptr};
     if (std::is_same<T, float>::value)
@@ -1116,6 +1148,7 @@ int solve_linear_typed(pexp_ctx* c, const pexp_operator* op, const pexp_options*
         if (!(beta > 0.0)) { Kh[m] = 0; continue; }
         std::vector<Win<T>> one(1);
         one[0].w = P + m; one[0].V = Vh[m]; one[0].S = Sh; one[0].b = 1; one[0].Wlo = Whlo; one[0].V1lo = Vh1lo;
+        one[0].Vklo = Vhklo;
         int kh = 0;
         notconv += S.run(one, KIND_HOM, &kh);
         int kk = 0;

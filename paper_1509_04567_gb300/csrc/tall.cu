@@ -356,18 +356,21 @@ __device__ __forceinline__ R ipow(R x, int e) {
 template <typename T>
 __global__ void __launch_bounds__(kSaiThreads) k_sai_fwd_ends(int64_t n, int nch, double alpha,
                                                               const T* const* __restrict__ Xp,
+                                                              const T* const* __restrict__ Xlo,
                                                               double* __restrict__ ends,
                                                               double* __restrict__ decays) {
     using R = typename SaiR<T>::R;
     __shared__ R sa[kSaiThreads], sb[kSaiThreads];
     const int v = blockIdx.y, ch = blockIdx.x;
     const T* x = Xp[v];
+    const T* xl = Xlo ? Xlo[v] : nullptr;
     const int64_t start = (int64_t)ch * kSaiChunk + (int64_t)threadIdx.x * kSaiPer;
-    T vals[kSaiPer];
+    T vals[kSaiPer], lows[kSaiPer];
     const int cnt = sai_load(x, n, start, vals);
+    if (xl) sai_load(xl, n, start, lows);
     const R al = rfrom<R>(alpha);
     R b = rfrom<R>(0.0);
-    for (int j = 0; j < cnt; ++j) b = rfma(al, b, rfrom<R>((double)vals[j]));
+    for (int j = 0; j < cnt; ++j) b = rfma(al, b, load_r<T, R>(vals[j], xl ? lows[j] : T(0)));
     R a = ipow(al, cnt);
     R ea, eb, ta, tb;
     cta_affine_scan<R>(a, b, false, sa, sb, ea, eb, ta, tb);
@@ -419,6 +422,7 @@ __device__ __forceinline__ double sai_carry_warp(const double* ends, const doubl
 template <typename T>
 __global__ void __launch_bounds__(kSaiThreads) k_sai_fwd_apply(int64_t n, int nch, double alpha, double beta,
                                                                double alpha_n, const T* const* __restrict__ Xp,
+                                                               const T* const* __restrict__ Xlo,
                                                                T* const* __restrict__ Yp, T* const* __restrict__ Ylo,
                                                                const double* __restrict__ fends,
                                                                const double* __restrict__ fdecays,
@@ -435,19 +439,21 @@ __global__ void __launch_bounds__(kSaiThreads) k_sai_fwd_apply(int64_t n, int nc
         const double cv = sai_carry_warp(fends + (int64_t)v * nch, fdecays + (int64_t)v * nch, nch, ch, +1, alpha_n);
         if (threadIdx.x == 0) carry_in = cv;
     }
+    const T* xl = Xlo ? Xlo[v] : nullptr;
     const int64_t start = (int64_t)ch * kSaiChunk + (int64_t)threadIdx.x * kSaiPer;
-    T vals[kSaiPer];
+    T vals[kSaiPer], lows[kSaiPer];
     const int cnt = sai_load(x, n, start, vals);
+    if (xl) sai_load(xl, n, start, lows);
     const R al = rfrom<R>(alpha), be = rfrom<R>(beta);
     R b = rfrom<R>(0.0);
-    for (int j = 0; j < cnt; ++j) b = rfma(al, b, rfrom<R>((double)vals[j]));
+    for (int j = 0; j < cnt; ++j) b = rfma(al, b, load_r<T, R>(vals[j], xl ? lows[j] : T(0)));
     R a = ipow(al, cnt);
     R ea, eb, ta, tb;
     cta_affine_scan<R>(a, b, false, sa, sb, ea, eb, ta, tb);  // contains __syncthreads: carry_in visible
     R w = rfma(ea, rfrom<R>(carry_in), eb);
     R wv[kSaiPer];
     for (int j = 0; j < cnt; ++j) {
-        w = rfma(al, w, rfrom<R>((double)vals[j]));
+        w = rfma(al, w, load_r<T, R>(vals[j], xl ? lows[j] : T(0)));
         wv[j] = w;
         store_r<T>(y, ylo, start + j, w);
     }
@@ -504,6 +510,12 @@ __global__ void __launch_bounds__(kSaiThreads) k_sai_bwd_apply(int64_t n, int nc
 template <typename T>
 void launch_sai_solve(const OpDesc& op, const SaiCoef& cf, const T* const* X, T* const* Y, T* const* Ylo, int nvec,
                       double* scratch, cudaStream_t s) {
+    launch_sai_solve_lo<T>(op, cf, X, nullptr, Y, Ylo, nvec, scratch, s);
+}
+
+template <typename T>
+void launch_sai_solve_lo(const OpDesc& op, const SaiCoef& cf, const T* const* X, const T* const* Xlo, T* const* Y,
+                         T* const* Ylo, int nvec, double* scratch, cudaStream_t s) {
     if (nvec <= 0) return;
     const int64_t n = op.n;
     const int nch = (int)((n + kSaiChunk - 1) / kSaiChunk);
@@ -512,8 +524,8 @@ void launch_sai_solve(const OpDesc& op, const SaiCoef& cf, const T* const* X, T*
     double* bends = fdec + (size_t)nch * nvec;
     double* bdec = bends + (size_t)nch * nvec;
     dim3 g(nch, nvec);
-    k_sai_fwd_ends<T><<<g, kSaiThreads, 0, s>>>(n, nch, cf.alpha, X, fends, fdec);
-    k_sai_fwd_apply<T><<<g, kSaiThreads, 0, s>>>(n, nch, cf.alpha, cf.beta, cf.alpha_n, X, Y, Ylo, fends, fdec,
+    k_sai_fwd_ends<T><<<g, kSaiThreads, 0, s>>>(n, nch, cf.alpha, X, Xlo, fends, fdec);
+    k_sai_fwd_apply<T><<<g, kSaiThreads, 0, s>>>(n, nch, cf.alpha, cf.beta, cf.alpha_n, X, Xlo, Y, Ylo, fends, fdec,
                                                   bends, bdec);
     k_sai_bwd_apply<T><<<g, kSaiThreads, 0, s>>>(n, nch, cf.beta, cf.beta_n, cf.inv_c, Y, Ylo, bends, bdec);
 }
@@ -959,6 +971,8 @@ void launch_row_diff_norms(const T* A, const T* B, int64_t n, int nrows, double*
     template void launch_burgers_source<T>(const OpDesc&, const T*, T*, int, int, double, cudaStream_t);  \
     template void launch_sai_solve<T>(const OpDesc&, const SaiCoef&, const T* const*, T* const*, T* const*,  \
                                       int, double*, cudaStream_t);                                        \
+    template void launch_sai_solve_lo<T>(const OpDesc&, const SaiCoef&, const T* const*, const T* const*,       \
+                                         T* const*, T* const*, int, double*, cudaStream_t);                   \
     template void launch_ts_tn<T>(const TsTask<T>*, int, int, int, int64_t, double*, cudaStream_t, int);   \
     template void launch_ts_nn<T>(const TsTask<T>*, int, int, int64_t, cudaStream_t);                     \
     template void launch_recon<T, float>(const ReconTask<T>*, int, int, int64_t, const double*, float*,    \
