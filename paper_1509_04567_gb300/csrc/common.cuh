@@ -109,18 +109,20 @@ void launch_burgers_source(const OpDesc& op, const T* U, T* G, int nrows, int fo
 template <typename T>
 void launch_sai_solve(const OpDesc& op, const SaiCoef& cf, const T* const* X, T* const* Y, T* const* Ylo, int nvec,
                       double* scratch, cudaStream_t s);
-// Same with input low parts (FP32 data: X + Xlo is a double-float input; NULL = none).
+// Same with input low parts (FP32 data: X + Xlo is a double-float input; NULL = none) and
+// optional per-vector skip flags (vector v is left untouched while *skip[v] != 0).
 template <typename T>
 void launch_sai_solve_lo(const OpDesc& op, const SaiCoef& cf, const T* const* X, const T* const* Xlo, T* const* Y,
-                         T* const* Ylo, int nvec, double* scratch, cudaStream_t s);
+                         T* const* Ylo, int nvec, double* scratch, cudaStream_t s, const int* const* skip = nullptr);
 template <typename T>
 void launch_ts_tn(const TsTask<T>* tasks_dev, int ntasks, int max_pq, int max_q, int64_t n, double* partial,
                   cudaStream_t s, int exact = 0);
 template <typename T>
 void launch_ts_nn(const TsTask<T>* tasks_dev, int ntasks, int max_pq, int64_t n, cudaStream_t s);
+// max_ns: most samples of a task; max_k: most basis columns (K1 + K2) of a task
 template <typename T, typename TO>
 void launch_recon(const ReconTask<T>* tasks_dev, int ntasks, int max_ns, int64_t n, const double* u0,
-                  TO* out, int64_t ldo, int max_c_doubles, cudaStream_t s);
+                  TO* out, int64_t ldo, int max_k, cudaStream_t s);
 template <typename TI, typename TO>
 void launch_convert(const TI* x, TO* y, int64_t count, cudaStream_t s);
 // rows of A minus rows of B: partial[row] = ||A_row - B_row||^2, partial[nrows + row] = ||A_row||^2
@@ -131,7 +133,8 @@ template <typename T>
 void launch_add(T* y, const T* x, int64_t count, cudaStream_t s);
 void launch_ts_nn_df(const DfTask* tasks_dev, int ntasks, int max_pq, int64_t n, cudaStream_t s);
 template <typename T>
-void launch_row_dots(const double* u, const T* G, int64_t n, int nrows, double* out, cudaStream_t s);
+// split: 2n floats of scratch (FP32 data: u as a double-float pair)
+void launch_row_dots(const double* u, const T* G, int64_t n, int nrows, double* out, float* split, cudaStream_t s);
 
 int fail_cuda(cudaError_t e, const char* what, const char* file, int line);
 

@@ -183,6 +183,7 @@ __global__ void __launch_bounds__(kThreads, 2) k_step_proj(const StepTask<T>* __
     constexpr int NE = 3 * PG * B + B;
     __shared__ double sred[kWarps * NE];
     const StepTask<T> tk = tasks[blockIdx.y];
+    if (tk.conv && *tk.conv) return;
     const int p = tk.p;
     const int a0 = blockIdx.z * PG;
     if (a0 >= p) return;
@@ -366,6 +367,7 @@ __global__ void __launch_bounds__(kThreads, 2) k_update0(const UpdTask<T>* __res
     CT* sh = reinterpret_cast<CT*>(sh_dyn);
     __shared__ double sred[kWarps * NE];
     const UpdTask<T> tk = tasks[blockIdx.y];
+    if (tk.conv && *tk.conv) return;
     const int p = tk.p;
     stage_coeffs<T>(tk, p, B, sh);
     const int64_t ld = tk.ld;
@@ -472,6 +474,7 @@ __global__ void __launch_bounds__(kThreads, 2) k_scale_proj(const UpdTask<T>* __
     __shared__ double sT[B * B];
     __shared__ double sred[kWarps * NE];
     const UpdTask<T> tk = tasks[blockIdx.y];
+    if (tk.conv && *tk.conv) return;
     const int p = tk.p;
     for (int e = threadIdx.x; e < B * B; e += kThreads) sT[e] = tk.hm[(e % B) + (int64_t)(e / B) * tk.ldh];
     __syncthreads();
@@ -531,6 +534,7 @@ __global__ void __launch_bounds__(kThreads, 2) k_vtw(const UpdTask<T>* __restric
     constexpr int NE = PG * B;
     __shared__ double sred[kWarps * NE];
     const UpdTask<T> tk = tasks[blockIdx.y];
+    if (tk.conv && *tk.conv) return;
     const int p = tk.p;
     const int a0 = blockIdx.z * PG;
     if (a0 >= p) return;
@@ -587,6 +591,7 @@ __global__ void __launch_bounds__(kThreads, 2) k_update1(const UpdTask<T>* __res
     T* sh = reinterpret_cast<T*>(sh_dyn);
     __shared__ double sred[kWarps * NE];
     const UpdTask<T> tk = tasks[blockIdx.y];
+    if (tk.conv && *tk.conv) return;
     const int p = tk.p;
     for (int e = threadIdx.x; e < p * B; e += kThreads) sh[e] = (T)tk.hm[(e % p) + (int64_t)(e / p) * tk.ldh];
     __syncthreads();
@@ -659,6 +664,7 @@ __global__ void __launch_bounds__(kThreads, 2) k_scale(const UpdTask<T>* __restr
     __shared__ double sT[B * B];
     __shared__ double sred[kWarps * NE];
     const UpdTask<T> tk = tasks[blockIdx.y];
+    if (tk.conv && *tk.conv) return;
     for (int e = threadIdx.x; e < B * B; e += kThreads) sT[e] = tk.hm[(e % B) + (int64_t)(e / B) * tk.ldh];
     __syncthreads();
     const int64_t ld = tk.ld;
@@ -720,12 +726,71 @@ __global__ void __launch_bounds__(kThreads, 2) k_scale(const UpdTask<T>* __restr
 }
 
 // =====================================================================================
+// k_block_gram: partial G = X^T X of an n x b block (b <= 4, task.Wh, ld task.ld, b = task.p),
+// compensated FP32 sums for FP32 data.
+// =====================================================================================
+template <typename T>
+__global__ void __launch_bounds__(kThreads) k_block_gram(const UpdTask<T>* __restrict__ tasks, int64_t n, int64_t rows,
+                                                         int nchunks, int pstride, double* __restrict__ partial) {
+    constexpr int BM = 4;
+    constexpr int NE = BM * BM;
+    __shared__ double sred[kWarps * NE];
+    const UpdTask<T> tk = tasks[blockIdx.y];
+    const int b = tk.p;
+    const int64_t ld = tk.ld;
+    const int64_t r0 = (int64_t)blockIdx.x * rows;
+    const int64_t r1 = (r0 + rows < n) ? r0 + rows : n;
+    T gs[BM][BM], gc[BM][BM];
+#pragma unroll
+    for (int i = 0; i < BM; ++i)
+#pragma unroll
+        for (int j = 0; j < BM; ++j) gs[i][j] = gc[i][j] = T(0);
+    constexpr int U = 4;
+    for (int64_t base = r0; base < r1; base += (int64_t)kThreads * U) {
+        T x[U][BM];
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            const int64_t r = base + (int64_t)u * kThreads + threadIdx.x;
+#pragma unroll
+            for (int c = 0; c < BM; ++c) x[u][c] = (r < r1 && c < b) ? ldg(tk.Wh + (int64_t)c * ld + r) : T(0);
+        }
+#pragma unroll
+        for (int u = 0; u < U; ++u)
+#pragma unroll
+            for (int i = 0; i < BM; ++i)
+#pragma unroll
+                for (int j = i; j < BM; ++j) comp_add(gs[i][j], gc[i][j], x[u][i], x[u][j]);
+    }
+#pragma unroll
+    for (int i = 0; i < BM; ++i)
+#pragma unroll
+        for (int j = i; j < BM; ++j) warp_to_smem2(gs[i][j], gc[i][j], sred, NE, i + j * BM);
+    __syncthreads();
+    double* pout = partial + ((size_t)blockIdx.y * nchunks + blockIdx.x) * pstride;
+    for (int e = threadIdx.x; e < b * b; e += kThreads) {
+        const int i = e % b, j = e / b;
+        const int lo = i < j ? i : j, hi = i < j ? j : i;
+        pout[e] = cta_entry(sred, NE, lo + hi * BM);
+    }
+}
+
+template <typename T>
+void launch_block_gram(const UpdTask<T>* tasks, int ntasks, int64_t n, KGeom g, double* partial, int pstride,
+                       cudaStream_t s) {
+    if (ntasks <= 0) return;
+    dim3 grid(g.nchunks, ntasks);
+    k_block_gram<T><<<grid, kThreads, 0, s>>>(tasks, n, g.rows, g.nchunks, pstride, partial);
+}
+
+// =====================================================================================
 // Sum of per-CTA partials into a dense FP64 block of each window's slab:
 // out(task) = wd + wins[task] * stride + off, entries [0, ne).
 // =====================================================================================
 __global__ void __launch_bounds__(kThreads) k_sum_parts(const double* __restrict__ part, int nchunks, int pstride, int ne,
                                                         double* __restrict__ wd, int64_t stride, int64_t off,
-                                                        const int* __restrict__ wins) {
+                                                        const int* __restrict__ wins, const int* __restrict__ wi,
+                                                        int istride, int conv_field) {
+    if (wi && wi[(int64_t)wins[blockIdx.x] * istride + conv_field]) return;
     const Parts pp{part, nchunks, pstride};
     double* out = wd + (int64_t)wins[blockIdx.x] * stride + off;
     for (int e = threadIdx.x >> 5; e < ne; e += kWarps) {
@@ -877,9 +942,9 @@ void launch_scale(const UpdTask<T>* tasks, int ntasks, int b, int64_t n, int gra
 }
 
 void launch_sum_parts(const double* part, int nchunks, int pstride, int ne, double* wd, int64_t stride, int64_t off,
-                      const int* wins, int ntasks, cudaStream_t s) {
+                      const int* wins, int ntasks, const int* wi, int istride, int conv_field, cudaStream_t s) {
     if (ntasks <= 0 || ne <= 0) return;
-    k_sum_parts<<<ntasks, kThreads, 0, s>>>(part, nchunks, pstride, ne, wd, stride, off, wins);
+    k_sum_parts<<<ntasks, kThreads, 0, s>>>(part, nchunks, pstride, ne, wd, stride, off, wins, wi, istride, conv_field);
 }
 
 template <typename T>
@@ -897,6 +962,7 @@ void launch_source_gram(const T* const* X, const int* sv, int ntasks, int s_max,
     template void launch_update<T>(const UpdTask<T>*, int, int, int, int64_t, int, KGeom, double*, int, cudaStream_t); \
     template void launch_scale<T>(const UpdTask<T>*, int, int, int64_t, int, KGeom, double*, int, cudaStream_t); \
     template void launch_scale_proj<T>(const UpdTask<T>*, int, int, int, int64_t, KGeom, double*, int, cudaStream_t); \
+    template void launch_block_gram<T>(const UpdTask<T>*, int, int64_t, KGeom, double*, int, cudaStream_t); \
     template void launch_source_gram<T>(const T* const*, const int*, int, int, int64_t, KGeom, double*, int, cudaStream_t);
 PEXP_KRY_INST(double)
 PEXP_KRY_INST(float)

@@ -13,6 +13,7 @@ struct StepTask {
     const T* V;
     int64_t ld;
     int p;
+    const int* conv;  // the window's convergence flag: the kernels skip a converged window (NULL: never)
 };
 
 // W <- W - V h (mode 0/1) or W <- W T (scale), h/T a dense FP64 matrix (hm, ld ldh).
@@ -28,6 +29,7 @@ struct UpdTask {
     int p;
     const double* hm;
     int ldh;
+    const int* conv;  // the window's convergence flag: the kernels skip a converged window (NULL: never)
 };
 
 struct KGeom {
@@ -54,14 +56,19 @@ void launch_update(const UpdTask<T>* tasks, int ntasks, int b, int p_max, int64_
 template <typename T>
 void launch_scale_proj(const UpdTask<T>* tasks, int ntasks, int b, int p, int64_t n, KGeom g, double* partial,
                        int pstride, cudaStream_t s);
+// partial G = X^T X (b x b, b = task.p <= 4) of the block X = task.Wh
+template <typename T>
+void launch_block_gram(const UpdTask<T>* tasks, int ntasks, int64_t n, KGeom g, double* partial, int pstride,
+                       cudaStream_t s);
 // W <- W T; gram != 0: partial G = W^T W; task.out != NULL: result rounded into task.out
 template <typename T>
 void launch_scale(const UpdTask<T>* tasks, int ntasks, int b, int64_t n, int gram, KGeom g, double* partial,
                   int pstride, cudaStream_t s);
 constexpr int kKrylovMaxB = 4;   // block widths handled by the fused kernels
 // Sums the per-CTA partials of each task into wd + wins[task] * stride + off (ne entries).
+// Windows whose flag wi[w * istride + conv_field] is set are skipped.
 void launch_sum_parts(const double* part, int nchunks, int pstride, int ne, double* wd, int64_t stride, int64_t off,
-                      const int* wins, int ntasks, cudaStream_t s);
+                      const int* wins, int ntasks, const int* wi, int istride, int conv_field, cudaStream_t s);
 // Gram matrices of the source windows: X[k] points at the first of sv[k] (<= 31)
 // consecutive length-n vectors; partial (chunk) results s x s, both halves.
 template <typename T>

@@ -428,7 +428,15 @@ __global__ void k_start_orth(WinLayout L, double* __restrict__ wd, int* __restri
             }
         }
     } else {
-        D[L.off_scal + WS_BETA] = R[0];
+        D[L.off_scal + WS_BETA] = ok ? R[0] : 0.0;
+        if (!ok) {
+            // zero start vector: nothing to continue, the window is done with an empty basis
+            I[WI_CONV] = 1;
+            I[WI_K] = 0;
+            I[WI_STEPS] = 0;
+            for (int e = 0; e < b * b; ++e) T[e] = 0.0;
+            return;
+        }
     }
     if (!ok) I[WI_STATUS] = PEXP_ERR_BREAKDOWN;
 }
@@ -450,6 +458,7 @@ __global__ void k_block_orth(WinLayout L, double* __restrict__ wd, int* __restri
     const int w = wins[blockIdx.x];
     double* D = wd + (int64_t)w * L.stride;
     int* I = wi + (int64_t)w * L.istride;
+    if (I[WI_CONV]) return;  // converged (at this step's projection, or earlier)
     const int b = I[WI_B];
     __shared__ double sG[PEXP_MAX_RANK * PEXP_MAX_RANK];
     if (gp.part) {

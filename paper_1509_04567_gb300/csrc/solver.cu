@@ -73,9 +73,17 @@ struct pexp_ctx {
     char* bs = nullptr;   // device pool of the Krylov bases, sized once the block widths are known
     size_t bs_cap = 0;
     size_t bs_top = 0;
-    char* stage_h[2] = {nullptr, nullptr};   // pinned task staging
+    // task staging: a ring of slots (pinned host | device), each guarded by an event so a
+    // slot is rewritten only after its previous host-to-device copy has run
+    char* stage_h[2] = {nullptr, nullptr};
     char* stage_d[2] = {nullptr, nullptr};
-    size_t stage_cap = 0;
+    size_t stage_cap = 0;   // bytes per slot
+    cudaEvent_t slot_ev[16] = {};
+    bool slot_busy[16] = {};
+    int slot_next = 0;
+    int* flags_h = nullptr;  // pinned copy of the per-window int state (lookahead of the Krylov loop)
+    size_t flags_cap = 0;
+    cudaEvent_t flag_ev[2] = {nullptr, nullptr};
     cudaEvent_t ev0 = nullptr, ev1 = nullptr;
     cudaEvent_t evp[5] = {nullptr, nullptr, nullptr, nullptr, nullptr};   // phase boundaries
     int launches = 0;
@@ -104,7 +112,8 @@ constexpr size_t kAlign = 256;
 #ifndef PEXP_TN_EXACT_FP32
 #define PEXP_TN_EXACT_FP32 0
 #endif
-constexpr size_t kStageBytes = 8u << 20;
+constexpr size_t kStageBytes = 8u << 20;   // per half of the staging area
+constexpr int kSlots = 16;                   // ring slots over both halves
 
 struct OomError {};
 struct StatusError {
@@ -159,22 +168,40 @@ int bs_reserve(pexp_ctx* c, size_t need) {
 }
 
 // Task staging: host-side byte buffer copied to the device in one transfer.
+// Task arrays for one group of launches: filled on the host, copied to the device in one
+// stream-ordered copy.  Each Stage takes the next slot of the context's ring; the host may
+// run ahead of the device by up to kSlots - 1 stages.
 struct Stage {
     pexp_ctx* c;
-    int half;
+    int slot;
+    char* h;
+    char* d;
     size_t used = 0;
-    Stage(pexp_ctx* c_, int h) : c(c_), half(h) {}
+    Stage(pexp_ctx* c_, int) : c(c_) {
+        slot = c->slot_next;
+        c->slot_next = (slot + 1) % kSlots;
+        if (c->slot_busy[slot]) {
+            cudaEventSynchronize(c->slot_ev[slot]);
+            c->slot_busy[slot] = false;
+        }
+        const int per = kSlots / 2;
+        h = c->stage_h[slot / per] + (size_t)(slot % per) * c->stage_cap;
+        d = c->stage_d[slot / per] + (size_t)(slot % per) * c->stage_cap;
+    }
     template <typename X>
     X* put(const X* src, size_t count) {
         size_t off = (used + 15) / 16 * 16;
         size_t bytes = sizeof(X) * count;
         if (off + bytes > c->stage_cap) throw OomError();
-        memcpy(c->stage_h[half] + off, src, bytes);
+        memcpy(h + off, src, bytes);
         used = off + bytes;
-        return reinterpret_cast<X*>(c->stage_d[half] + off);
+        return reinterpret_cast<X*>(d + off);
     }
     void flush() {
-        if (used) cudaMemcpyAsync(c->stage_d[half], c->stage_h[half], used, cudaMemcpyHostToDevice, c->stream);
+        if (!used) return;
+        cudaMemcpyAsync(d, h, used, cudaMemcpyHostToDevice, c->stream);
+        cudaEventRecord(c->slot_ev[slot], c->stream);
+        c->slot_busy[slot] = true;
     }
 };
 
@@ -346,12 +373,30 @@ struct Solver {
     // projection pass (Galerkin sums by parts, first Gram-Schmidt coefficients, norms),
     // the projected solve, and four passes for block Gram-Schmidt with Cholesky QR,
     // applied twice: update + Gram, scaling + second projection, update + Gram, scaling.
+    //
+    // Every kernel of a step skips a window whose convergence flag is set, so the host does
+    // not wait for a step's flags before queueing the next step: the flags of step k come
+    // back by an asynchronous copy and are read (to drop converged windows) after step k+1
+    // has been queued.  A window converged at step k costs one step of empty launches.
     int run_fused(std::vector<Win<T>> ws, int* max_steps) {
         int notconv = 0;
         *max_steps = 0;
         std::stable_sort(ws.begin(), ws.end(), [](const Win<T>& a, const Win<T>& b) { return a.b < b.b; });
         std::vector<Win<T>> act = ws;
         const int periodic = od.x.periodic;
+        const size_t nint = wi_host.size();
+        if (c->flags_cap < 2 * nint) {
+            if (c->flags_h) cudaFreeHost(c->flags_h);
+            c->flags_h = nullptr;
+            c->flags_cap = 0;
+            if (cudaMallocHost(&c->flags_h, sizeof(int) * 2 * nint) != cudaSuccess) throw OomError();
+            c->flags_cap = 2 * nint;
+        }
+        if (!c->flag_ev[0]) {
+            cudaEventCreateWithFlags(&c->flag_ev[0], cudaEventDisableTiming);
+            cudaEventCreateWithFlags(&c->flag_ev[1], cudaEventDisableTiming);
+        }
+        auto conv_of = [&](const Win<T>& W) { return wi + (size_t)W.w * L.istride + WI_CONV; };
         for (int step = 1; step <= kmax && !act.empty(); ++step) {
             const int na = (int)act.size();
             int bmax = 0;
@@ -364,6 +409,7 @@ struct Solver {
             std::vector<T*> yout, ylo;
             std::vector<StepTask<T>> st1(na);
             std::vector<int> wl(na);
+            std::vector<const int*> skip;
             for (int a = 0; a < na; ++a) {
                 const Win<T>& W = act[a];
                 T* Vi = slot(W, step - 1);
@@ -377,8 +423,9 @@ struct Solver {
                     xlo.push_back(vlo ? reinterpret_cast<const T*>(vlo) + (int64_t)cc * n : nullptr);
                     yout.push_back(Wn + (int64_t)cc * n);
                     ylo.push_back(W.Wlo ? reinterpret_cast<T*>(W.Wlo) + (int64_t)cc * n : nullptr);
+                    skip.push_back(conv_of(W));
                 }
-                st1[a] = StepTask<T>{W.V, n, step * W.b};
+                st1[a] = StepTask<T>{W.V, n, step * W.b, conv_of(W)};
                 wl[a] = W.w;
             }
             const int nv = (int)xin.size();
@@ -387,13 +434,14 @@ struct Solver {
             T* const* d_yout = sa.put(yout.data(), nv);
             T* const* d_ylo = std::is_same<T, float>::value ? sa.put(ylo.data(), nv) : nullptr;
             const StepTask<T>* d_st1 = sa.put(st1.data(), na);
+            const int* const* d_skip = sa.put(skip.data(), nv);
             const int* d_wl = sa.put(wl.data(), na);
             sa.flush();
             const double w = sizeof(T);
             const double wout = std::is_same<T, float>::value ? 8.0 : w;
             if (o->krylov == PEXP_KRYLOV_SAI) {
                 timed(c, PEXP_KC_SAI, (double)nv * n * (w + wout),
-                      [&] { launch_sai_solve_lo<T>(od, sai, d_xin, d_xlo, d_yout, d_ylo, nv, sai_scr, st); });
+                      [&] { launch_sai_solve_lo<T>(od, sai, d_xin, d_xlo, d_yout, d_ylo, nv, sai_scr, st, d_skip); });
             } else {
                 timed(c, PEXP_KC_STENCIL, (double)nv * n * (w + w), [&] { launch_stencil_ptrs<T>(od, d_xin, d_yout, nv, 0, st); });
                 for (const auto& W : act)
@@ -417,20 +465,33 @@ struct Solver {
                                od.x.d, od.x.c);
             });
             check_launch(c);
-            d2h(c, wi_host.data(), wi, sizeof(int) * wi_host.size());
-            std::vector<Win<T>> next;
-            for (auto& W : act) {
-                const int* I = &wi_host[(size_t)W.w * L.istride];
-                *max_steps = std::max(*max_steps, I[WI_STEPS]);
-                if (!I[WI_CONV]) next.push_back(W);
+            if (step < kmax) part_b(act, step);
+            // flags of this step, read back without waiting; then the previous step's flags
+            int* fl = c->flags_h + (size_t)(step & 1) * nint;
+            cudaMemcpyAsync(fl, wi, sizeof(int) * nint, cudaMemcpyDeviceToHost, st);
+            cudaEventRecord(c->flag_ev[step & 1], st);
+            if (step >= 2) {
+                cudaEventSynchronize(c->flag_ev[(step - 1) & 1]);
+                const int* F = c->flags_h + (size_t)((step - 1) & 1) * nint;
+                std::vector<Win<T>> next;
+                for (auto& W : act)
+                    if (!F[(size_t)W.w * L.istride + WI_CONV]) next.push_back(W);
+                act.swap(next);
             }
-            if (step == kmax) {
-                notconv += (int)next.size();
-                break;
-            }
-            act.swap(next);
-            if (act.empty()) break;
-            // ---- part B: block classical Gram-Schmidt with Cholesky QR, twice (BCGS2)
+        }
+        d2h(c, wi_host.data(), wi, sizeof(int) * nint);
+        for (auto& W : ws) {
+            const int* I = &wi_host[(size_t)W.w * L.istride];
+            *max_steps = std::max(*max_steps, I[WI_STEPS]);
+            if (!I[WI_CONV]) ++notconv;
+        }
+        return notconv;
+    }
+
+    // Part B of a fused step: block classical Gram-Schmidt with Cholesky QR, twice (BCGS2).
+    void part_b(const std::vector<Win<T>>& act, int step) {
+        {
+            const double w = sizeof(T);
             const int nb = (int)act.size();
             const KGeom gb = krylov_geom(nb, n);
             int bmb = 0;
@@ -447,6 +508,7 @@ struct Solver {
                 UpdTask<T> t;
                 memset(&t, 0, sizeof(t));
                 t.V = W.V; t.Wh = Wn; t.Wl = W.Wlo; t.ld = n; t.p = p;
+                t.conv = wi + (size_t)W.w * L.istride + WI_CONV;
                 t.hm = D(W.w) + L.off_out1; t.ldh = p;                         // h1 from the projection pass
                 t.Vlo = (step == 1) ? W.V1lo : W.Vklo;                         // low parts of the newest block
                 u1[a] = t;
@@ -457,6 +519,7 @@ struct Solver {
                 u2[a] = t;
                 memset(&t, 0, sizeof(t));
                 t.Wh = Wn; t.Wl = W.Wlo; t.ld = n; t.p = W.b; t.hm = D(W.w) + L.off_T; t.ldh = W.b;
+                t.conv = wi + (size_t)W.w * L.istride + WI_CONV;
                 t.out = Wn;
                 t.outlo = W.Vklo;
                 u4[a] = t;                                                     // final: W T2 rounded into the slot
@@ -500,7 +563,7 @@ struct Solver {
             timed(c, PEXP_KC_SMALL, 0.0, [&] {
                 groups([&](int a0, int a1, int b) {
                     launch_sum_parts(kpart[1] + (size_t)a0 * gb.nchunks * ps2, gb.nchunks, ps2, step * b * b, wd, L.stride,
-                                     L.off_h2, d_wl2 + a0, a1 - a0, st);
+                                     L.off_h2, d_wl2 + a0, a1 - a0, wi, L.istride, WI_CONV, st);
                     check_launch(c);
                 });
             });
@@ -521,7 +584,6 @@ struct Solver {
                 });
             });
         }
-        return notconv;
     }
 
     // Runs block Krylov steps for the windows `ws` (each with its start block already
@@ -805,6 +867,7 @@ size_t linear_workspace_bytes(int64_t n, const pexp_options* o, int g_conv, int 
     s += 2 * align_up(sizeof(double) * kpart_doubles(P, n, kmax, b_cap, pt.smax));
     s += align_up(sizeof(double) * sai_scratch_doubles(n, P * b_cap) + 64);
     s += align_up(sizeof(double) * o->n_out);                               // (A u0) . g(t_i)
+    if (sizeof(T) == 4) s += align_up(sizeof(float) * n * 2);               // A u0 as a double-float pair
     s += (size_t)(4 * P + 32) * kAlign;   // alignment of the per-window allocations
     return s;
 }
@@ -879,6 +942,7 @@ int solve_linear_typed(pexp_ctx* c, const pexp_operator* op, const pexp_options*
     // ---- shift: A u0, ||u0||, ||A u0||^2, (A u0) . g(t_i)
     double* nrm = S.partial + part_n - 8;   // [0] = ||u0||^2, [1] = ||A u0||^2
     double* dots = G ? as<double>(ws_alloc(c, sizeof(double) * n_out)) : nullptr;
+    float* au0_split = (G && sizeof(T) == 4) ? as<float>(ws_alloc(c, sizeof(float) * n * 2)) : nullptr;
     launch_stencil<double>(S.od, u0d, Au0, 1, 0, st);
     check_launch(c);
     {
@@ -892,7 +956,7 @@ int solve_linear_typed(pexp_ctx* c, const pexp_operator* op, const pexp_options*
         launch_ts_tn<double>(dt, 2, 1, 1, n, S.partial, st, 0);
         check_launch(c);
         if (G) {
-            launch_row_dots<T>(Au0, G, n, n_out, dots, st);
+            launch_row_dots<T>(Au0, G, n, n_out, dots, au0_split, st);
             check_launch(c);
         }
         double nn = 0;
@@ -1037,7 +1101,26 @@ int solve_linear_typed(pexp_ctx* c, const pexp_operator* op, const pexp_options*
         if (ddu) launch_ts_nn_df(ddu, ns, mpq, n, st);
         else launch_ts_nn<T>(dtu, ns, mpq, n, st);
         check_launch(c);
-        launch_ts_tn<T>(dtg, ns, mpqg, mq, n, S.partial, st, 1); check_launch(c);
+        if (mq <= 4) {
+            // Gram of the start blocks: streamed partials, summed into each window's slab
+            std::vector<UpdTask<T>> gtk(ns);
+            for (int a = 0; a < ns; ++a) {
+                UpdTask<T> t;
+                memset(&t, 0, sizeof(t));
+                t.Wh = src[a].V; t.ld = n; t.p = src[a].b;
+                gtk[a] = t;
+            }
+            Stage sg(c, 0);
+            const UpdTask<T>* dgt = sg.put(gtk.data(), ns);
+            sg.flush();
+            const KGeom gq = krylov_geom(ns, n);
+            launch_block_gram<T>(dgt, ns, n, gq, S.kpart[1], mq * mq, st); check_launch(c);
+            launch_sum_parts(S.kpart[1], gq.nchunks, mq * mq, mq * mq, S.wd, L.stride, L.off_gw, dwl, ns, nullptr, 0, 0,
+                             st);
+            check_launch(c);
+        } else {
+            launch_ts_tn<T>(dtg, ns, mpqg, mq, n, S.partial, st, 1); check_launch(c);
+        }
         launch_start_orth(L, S.wd, S.wi, dwl, ns, st); check_launch(c);
         if (dds) launch_ts_nn_df(dds, ns, mpqg, n, st);
         else launch_ts_nn<T>(dts, ns, mpqg, n, st);
@@ -1143,16 +1226,13 @@ int solve_linear_typed(pexp_ctx* c, const pexp_operator* op, const pexp_options*
         if (dz) launch_ts_nn_df(dz + 2, 1, 1, n, st);
         else launch_ts_nn<T>(dts, 1, 1, n, st);
         check_launch(c);
-        double beta = 0;
-        d2h(c, &beta, S.D(P + m) + L.off_scal + WS_BETA, sizeof(double));
-        if (!(beta > 0.0)) { Kh[m] = 0; continue; }
+        // a zero z (nothing to continue) is marked converged with an empty basis on the device
         std::vector<Win<T>> one(1);
         one[0].w = P + m; one[0].V = Vh[m]; one[0].S = Sh; one[0].b = 1; one[0].Wlo = Whlo; one[0].V1lo = Vh1lo;
         one[0].Vklo = Vhklo;
         int kh = 0;
         notconv += S.run(one, KIND_HOM, &kh);
-        int kk = 0;
-        d2h(c, &kk, S.wi + (size_t)(P + m) * L.istride + WI_K, sizeof(int));
+        const int kk = S.wi_host[(size_t)(P + m) * L.istride + WI_K];   // state after the last step
         Kh[m] = kk;
         if (o->diagnostics & PEXP_DIAG_ORTH) orth_max = std::max(orth_max, S.orth_defect(Vh[m], kk));
         k_hom_max = std::max(k_hom_max, kh);
@@ -1174,7 +1254,7 @@ int solve_linear_typed(pexp_ctx* c, const pexp_operator* op, const pexp_options*
             rt.r0 = (m == 0) ? 0 : 1;
             rt.ns = s - rt.r0;
             rt.i0 = pt.idx[m] + rt.r0;
-            maxc = std::max(maxc, rt.ns * (rt.K1 + rt.K2));
+            maxc = std::max(maxc, rt.K1 + rt.K2);
             maxns = std::max(maxns, rt.ns);
             rts.push_back(rt);
         }
@@ -1322,7 +1402,7 @@ int pexp_create(pexp_ctx** out, int device, void* stream) {
     c->device = device;
     if (cudaSetDevice(device) != cudaSuccess) { delete c; return PEXP_ERR_CUDA; }
     c->stream = reinterpret_cast<cudaStream_t>(stream);
-    c->stage_cap = kStageBytes;
+    c->stage_cap = kStageBytes / (kSlots / 2);
     for (int h = 0; h < 2; ++h) {
         if (cudaMallocHost(&c->stage_h[h], kStageBytes) != cudaSuccess ||
             cudaMalloc(&c->stage_d[h], kStageBytes) != cudaSuccess) {
@@ -1330,6 +1410,7 @@ int pexp_create(pexp_ctx** out, int device, void* stream) {
             return PEXP_ERR_OOM;
         }
     }
+    for (int k = 0; k < kSlots; ++k) cudaEventCreateWithFlags(&c->slot_ev[k], cudaEventDisableTiming);
     cudaEventCreate(&c->ev0);
     cudaEventCreate(&c->ev1);
     for (int k = 0; k < 5; ++k) cudaEventCreate(&c->evp[k]);
@@ -1349,6 +1430,11 @@ int pexp_destroy(pexp_ctx* c) {
         if (c->stage_d[h]) cudaFree(c->stage_d[h]);
     }
     if (c->io_d) cudaFree(c->io_d);
+    for (int k = 0; k < kSlots; ++k)
+        if (c->slot_ev[k]) cudaEventDestroy(c->slot_ev[k]);
+    if (c->flags_h) cudaFreeHost(c->flags_h);
+    for (int k = 0; k < 2; ++k)
+        if (c->flag_ev[k]) cudaEventDestroy(c->flag_ev[k]);
     if (c->ev0) cudaEventDestroy(c->ev0);
     if (c->ev1) cudaEventDestroy(c->ev1);
     for (int k = 0; k < 5; ++k)

@@ -358,10 +358,12 @@ __global__ void __launch_bounds__(kSaiThreads) k_sai_fwd_ends(int64_t n, int nch
                                                               const T* const* __restrict__ Xp,
                                                               const T* const* __restrict__ Xlo,
                                                               double* __restrict__ ends,
-                                                              double* __restrict__ decays) {
+                                                              double* __restrict__ decays,
+                                                              const int* const* __restrict__ skip) {
     using R = typename SaiR<T>::R;
     __shared__ R sa[kSaiThreads], sb[kSaiThreads];
     const int v = blockIdx.y, ch = blockIdx.x;
+    if (skip && skip[v] && *skip[v]) return;
     const T* x = Xp[v];
     const T* xl = Xlo ? Xlo[v] : nullptr;
     const int64_t start = (int64_t)ch * kSaiChunk + (int64_t)threadIdx.x * kSaiPer;
@@ -427,11 +429,13 @@ __global__ void __launch_bounds__(kSaiThreads) k_sai_fwd_apply(int64_t n, int nc
                                                                const double* __restrict__ fends,
                                                                const double* __restrict__ fdecays,
                                                                double* __restrict__ bends,
-                                                               double* __restrict__ bdecays) {
+                                                               double* __restrict__ bdecays,
+                                                               const int* const* __restrict__ skip) {
     using R = typename SaiR<T>::R;
     __shared__ R sa[kSaiThreads], sb[kSaiThreads];
     __shared__ double carry_in;
     const int v = blockIdx.y, ch = blockIdx.x;
+    if (skip && skip[v] && *skip[v]) return;
     const T* x = Xp[v];
     T* y = Yp[v];
     T* ylo = Ylo ? Ylo[v] : nullptr;
@@ -476,11 +480,13 @@ __global__ void __launch_bounds__(kSaiThreads) k_sai_bwd_apply(int64_t n, int nc
                                                                double inv_c, T* const* __restrict__ Yp,
                                                                T* const* __restrict__ Ylo,
                                                                const double* __restrict__ bends,
-                                                               const double* __restrict__ bdecays) {
+                                                               const double* __restrict__ bdecays,
+                                                               const int* const* __restrict__ skip) {
     using R = typename SaiR<T>::R;
     __shared__ R sa[kSaiThreads], sb[kSaiThreads];
     __shared__ double carry_in;
     const int v = blockIdx.y, ch = blockIdx.x;
+    if (skip && skip[v] && *skip[v]) return;
     T* y = Yp[v];
     T* ylo = Ylo ? Ylo[v] : nullptr;
     if (threadIdx.x < 32) {
@@ -510,12 +516,12 @@ __global__ void __launch_bounds__(kSaiThreads) k_sai_bwd_apply(int64_t n, int nc
 template <typename T>
 void launch_sai_solve(const OpDesc& op, const SaiCoef& cf, const T* const* X, T* const* Y, T* const* Ylo, int nvec,
                       double* scratch, cudaStream_t s) {
-    launch_sai_solve_lo<T>(op, cf, X, nullptr, Y, Ylo, nvec, scratch, s);
+    launch_sai_solve_lo<T>(op, cf, X, nullptr, Y, Ylo, nvec, scratch, s, nullptr);
 }
 
 template <typename T>
 void launch_sai_solve_lo(const OpDesc& op, const SaiCoef& cf, const T* const* X, const T* const* Xlo, T* const* Y,
-                         T* const* Ylo, int nvec, double* scratch, cudaStream_t s) {
+                         T* const* Ylo, int nvec, double* scratch, cudaStream_t s, const int* const* skip) {
     if (nvec <= 0) return;
     const int64_t n = op.n;
     const int nch = (int)((n + kSaiChunk - 1) / kSaiChunk);
@@ -524,10 +530,10 @@ void launch_sai_solve_lo(const OpDesc& op, const SaiCoef& cf, const T* const* X,
     double* bends = fdec + (size_t)nch * nvec;
     double* bdec = bends + (size_t)nch * nvec;
     dim3 g(nch, nvec);
-    k_sai_fwd_ends<T><<<g, kSaiThreads, 0, s>>>(n, nch, cf.alpha, X, Xlo, fends, fdec);
+    k_sai_fwd_ends<T><<<g, kSaiThreads, 0, s>>>(n, nch, cf.alpha, X, Xlo, fends, fdec, skip);
     k_sai_fwd_apply<T><<<g, kSaiThreads, 0, s>>>(n, nch, cf.alpha, cf.beta, cf.alpha_n, X, Xlo, Y, Ylo, fends, fdec,
-                                                  bends, bdec);
-    k_sai_bwd_apply<T><<<g, kSaiThreads, 0, s>>>(n, nch, cf.beta, cf.beta_n, cf.inv_c, Y, Ylo, bends, bdec);
+                                                  bends, bdec, skip);
+    k_sai_bwd_apply<T><<<g, kSaiThreads, 0, s>>>(n, nch, cf.beta, cf.beta_n, cf.inv_c, Y, Ylo, bends, bdec, skip);
 }
 
 // =====================================================================================
@@ -751,87 +757,152 @@ void launch_ts_nn(const TsTask<T>* tasks_dev, int ntasks, int max_pq, int64_t n,
 // X and Z are (hi, lo) pairs of FP32 arrays (a missing lo array means 0, and for
 // Z means "round to FP32"); products and sums are error-free to ~2^-48, so the
 // cancellation of Gram-Schmidt leaves no FP32-sized noise in the new direction.
-__global__ void __launch_bounds__(256) k_ts_nn_df(const DfTask* __restrict__ tasks, int64_t n) {
+__global__ void __launch_bounds__(256, 2) k_ts_nn_df(const DfTask* __restrict__ tasks, int64_t n, int64_t rows) {
+    constexpr int QM = 16, PB = 16;   // block columns of Z, columns of X per batch of loads
     const DfTask tk = tasks[blockIdx.y];
     extern __shared__ float smem_df[];
     const int p = tk.p, q = tk.q;
-    float* Th = smem_df;
-    float* Tl = smem_df + p * q;
+    float2* Tc = reinterpret_cast<float2*>(smem_df);   // alpha T as (hi, lo), p x q
+    float2* cs = Tc + p * q;                            // column sums of alpha T (the xs term)
     for (int e = threadIdx.x; e < p * q; e += blockDim.x) {
         const int a = e % p, c = e / p;
         const double v = tk.alpha * tk.Tm[a + (int64_t)c * tk.ldt];
         const float h = (float)v;
-        Th[e] = h;
-        Tl[e] = (float)(v - (double)h);
+        Tc[e] = make_float2(h, (float)(v - (double)h));
+    }
+    if (tk.xs && threadIdx.x < q) {
+        double sum = 0.0;
+        for (int a = 0; a < p; ++a) sum += tk.alpha * tk.Tm[a + (int64_t)threadIdx.x * tk.ldt];
+        const float h = (float)sum;
+        cs[threadIdx.x] = make_float2(h, (float)(sum - (double)h));
     }
     __syncthreads();
-    const bool inplace = tk.Zh == tk.Xh;
     const int pl = (tk.Xl && tk.pl > 0) ? tk.pl : (tk.Xl ? p : 0);   // columns of X with a low part
-    for (int64_t r = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; r < n; r += (int64_t)gridDim.x * blockDim.x) {
-        DF xsh = DF{0.f, 0.f};
+    const int64_t r0 = (int64_t)blockIdx.x * rows;
+    const int64_t r1 = (r0 + rows < n) ? r0 + rows : n;
+    for (int64_t base = r0; base < r1; base += blockDim.x) {
+        const int64_t r = base + threadIdx.x;
+        const bool act = r < r1;
+        // Z[r, c] = sum_a (X[r, a] (+ xs[r])) T[a, c]: exact FP32 products x * t_hi (FMA), the
+        // small terms in a second sum, the running sums compensated (two-sum)
+        float sh[QM], sl[QM];
+#pragma unroll
+        for (int c = 0; c < QM; ++c) sh[c] = sl[c] = 0.f;
+        for (int a0 = 0; a0 < p; a0 += PB) {
+            float x[PB], xl[PB];
+#pragma unroll
+            for (int j = 0; j < PB; ++j) {
+                const int a = a0 + j;
+                x[j] = (act && a < p && tk.Xh) ? tk.Xh[(int64_t)a * tk.ldx + r] : 0.f;
+                xl[j] = (act && a < pl) ? tk.Xl[(int64_t)a * tk.ldx + r] : 0.f;
+            }
+#pragma unroll
+            for (int c = 0; c < QM; ++c) {
+                if (c >= q) break;
+                float s_ = sh[c], l_ = sl[c];
+#pragma unroll
+                for (int j = 0; j < PB; ++j) {
+                    if (a0 + j >= p) break;
+                    const float2 t = Tc[(a0 + j) + c * p];
+                    const float ph = x[j] * t.x;
+                    float pe = fmaf(x[j], t.x, -ph);
+                    pe = fmaf(x[j], t.y, pe);
+                    pe = fmaf(xl[j], t.x, pe);
+                    const float u = s_ + ph;
+                    const float bp = u - s_;
+                    l_ += ((s_ - (u - bp)) + (ph - bp)) + pe;
+                    s_ = u;
+                }
+                sh[c] = s_;
+                sl[c] = l_;
+            }
+        }
+        if (!act) continue;
+        DF xsd = DF{0.f, 0.f};
         if (tk.xs) {
             const double v = tk.xs[r];
             const float h = (float)v;
-            xsh = DF{h, (float)(v - (double)h)};
-        }
-        DF acc[16];
-#pragma unroll
-        for (int c = 0; c < 16; ++c) acc[c] = DF{0.f, 0.f};
-        if (inplace) {
-            DF xr[16];
-#pragma unroll
-            for (int a = 0; a < 16; ++a)
-                if (a < p) xr[a] = DF{tk.Xh[(int64_t)a * tk.ldx + r], a < pl ? tk.Xl[(int64_t)a * tk.ldx + r] : 0.f};
-#pragma unroll
-            for (int a = 0; a < 16; ++a)
-                if (a < p) {
-                    const DF x = tk.xs ? df_add(xr[a], xsh) : xr[a];
-#pragma unroll
-                    for (int c = 0; c < 16; ++c)
-                        if (c < q) acc[c] = df_add(acc[c], df_mul(x, DF{Th[a + c * p], Tl[a + c * p]}));
-                }
-        } else {
-            for (int a = 0; a < p; ++a) {
-                DF x = DF{tk.Xh ? tk.Xh[(int64_t)a * tk.ldx + r] : 0.f, a < pl ? tk.Xl[(int64_t)a * tk.ldx + r] : 0.f};
-                if (tk.xs) x = df_add(x, xsh);
-#pragma unroll
-                for (int c = 0; c < 16; ++c)
-                    if (c < q) acc[c] = df_add(acc[c], df_mul(x, DF{Th[a + c * p], Tl[a + c * p]}));
-            }
+            xsd = DF{h, (float)(v - (double)h)};
         }
 #pragma unroll
-        for (int c = 0; c < 16; ++c)
-            if (c < q) {
-                DF z = acc[c];
-                const int64_t o = (int64_t)c * tk.ldz + r;
-                if (tk.accumulate) z = df_add(z, DF{tk.Zh[o], tk.Zl ? tk.Zl[o] : 0.f});
-                if (tk.Zl) {
-                    tk.Zh[o] = z.hi;
-                    tk.Zl[o] = z.lo;
-                } else {
-                    tk.Zh[o] = z.hi + z.lo;
-                }
+        for (int c = 0; c < QM; ++c) {
+            if (c >= q) break;
+            DF z = df_fast2sum(sh[c], sl[c]);
+            if (tk.xs) z = df_add(z, df_mul(xsd, DF{cs[c].x, cs[c].y}));
+            const int64_t o = (int64_t)c * tk.ldz + r;
+            if (tk.accumulate) z = df_add(z, DF{tk.Zh[o], tk.Zl ? tk.Zl[o] : 0.f});
+            if (tk.Zl) {
+                tk.Zh[o] = z.hi;
+                tk.Zl[o] = z.lo;
+            } else {
+                tk.Zh[o] = z.hi + z.lo;
             }
+        }
     }
 }
 
 void launch_ts_nn_df(const DfTask* tasks_dev, int ntasks, int max_pq, int64_t n, cudaStream_t s) {
     if (ntasks <= 0) return;
-    int bx = std::max(1, std::min(grid_for(n, 256), (4 * kNumSM * 4 + ntasks - 1) / ntasks));
-    dim3 grid(bx, ntasks);
-    size_t sm = (size_t)max_pq * 2 * sizeof(float);
+    // row chunks of >= 256 rows, about 8 CTAs per SM in total
+    const int64_t maxch = std::max<int64_t>(1, (n + 255) / 256);
+    const int64_t want = std::max<int64_t>(1, (8 * kNumSM + ntasks - 1) / ntasks);
+    const int64_t ch = std::min(want, maxch);
+    int64_t rows = (n + ch - 1) / ch;
+    rows = (rows + 255) / 256 * 256;
+    dim3 grid((unsigned)((n + rows - 1) / rows), ntasks);
+    size_t sm = ((size_t)max_pq + 16) * sizeof(float2);
     if (sm > 48 * 1024) cudaFuncSetAttribute(k_ts_nn_df, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-    k_ts_nn_df<<<grid, 256, sm, s>>>(tasks_dev, n);
+    k_ts_nn_df<<<grid, 256, sm, s>>>(tasks_dev, n, rows);
 }
 
-// out[i] = sum_k u[k] * G[i*n + k] for the rows i < nrows (FP64 accumulation).
-template <typename T>
-__global__ void __launch_bounds__(256) k_row_dots(const double* __restrict__ u, const T* __restrict__ G, int64_t n,
-                                                 double* __restrict__ out) {
+// out[i] = sum_k u[k] * G[i*n + k] for the rows i < nrows.  FP64 data: FP64 FMAs.  FP32 data:
+// u enters as a double-float pair (uh, ul) prepared once; the products uh*g are exact (FMA),
+// the sums compensated, all in FP32 units (FP64 runs at 1/64 of the FP32 rate here).
+__device__ __forceinline__ void dot_acc(float& s, float& c, float uh, float ul, float g) {
+    const float p = uh * g;
+    float pe = fmaf(uh, g, -p);
+    pe = fmaf(ul, g, pe);
+    const float t = s + p;
+    const float bp = t - s;
+    c += ((s - (t - bp)) + (p - bp)) + pe;
+    s = t;
+}
+__global__ void __launch_bounds__(256) k_row_dots_f(const float* __restrict__ uh, const float* __restrict__ ul,
+                                                    const float* __restrict__ G, int64_t n, double* __restrict__ out) {
+    constexpr int U = 4;
     const int64_t row = blockIdx.x;
-    const T* g = G + row * n;
+    const float* g = G + row * n;
+    float s = 0.f, c = 0.f;
+    for (int64_t k0 = (int64_t)threadIdx.x; k0 < n; k0 += (int64_t)blockDim.x * U) {
+        float gv[U], hv[U], lv[U];
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            const int64_t k = k0 + (int64_t)u * blockDim.x;
+            const bool ok = k < n;
+            gv[u] = ok ? g[k] : 0.f;
+            hv[u] = ok ? __ldg(uh + k) : 0.f;
+            lv[u] = ok ? __ldg(ul + k) : 0.f;
+        }
+#pragma unroll
+        for (int u = 0; u < U; ++u) dot_acc(s, c, hv[u], lv[u], gv[u]);
+    }
+    double v = (double)s + (double)c;
+    __shared__ double red[8];
+    v = warp_sum(v);
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = v;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double t = 0;
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += red[w];
+        out[row] = t;
+    }
+}
+__global__ void __launch_bounds__(256) k_row_dots_d(const double* __restrict__ u, const double* __restrict__ G,
+                                                    int64_t n, double* __restrict__ out) {
+    const int64_t row = blockIdx.x;
+    const double* g = G + row * n;
     double s = 0.0;
-    for (int64_t k = threadIdx.x; k < n; k += blockDim.x) s = fma(u[k], (double)g[k], s);
+    for (int64_t k = threadIdx.x; k < n; k += blockDim.x) s = fma(u[k], g[k], s);
     __shared__ double red[8];
     s = warp_sum(s);
     if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = s;
@@ -842,10 +913,24 @@ __global__ void __launch_bounds__(256) k_row_dots(const double* __restrict__ u, 
         out[row] = t;
     }
 }
+__global__ void k_split_df(const double* __restrict__ u, float* __restrict__ uh, float* __restrict__ ul, int64_t n) {
+    for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < n; k += (int64_t)gridDim.x * blockDim.x) {
+        const double v = u[k];
+        const float h = (float)v;
+        uh[k] = h;
+        ul[k] = (float)(v - (double)h);
+    }
+}
 template <typename T>
-void launch_row_dots(const double* u, const T* G, int64_t n, int nrows, double* out, cudaStream_t s) {
+void launch_row_dots(const double* u, const T* G, int64_t n, int nrows, double* out, float* split, cudaStream_t s) {
     if (nrows <= 0) return;
-    k_row_dots<T><<<nrows, 256, 0, s>>>(u, G, n, out);
+    if constexpr (sizeof(T) == 4) {
+        k_split_df<<<std::min(grid_for(n, 256), 4 * kNumSM * 8), 256, 0, s>>>(u, split, split + n, n);
+        k_row_dots_f<<<nrows, 256, 0, s>>>(split, split + n, G, n, out);
+    } else {
+        (void)split;
+        k_row_dots_d<<<nrows, 256, 0, s>>>(u, G, n, out);
+    }
 }
 
 // =====================================================================================
@@ -853,54 +938,77 @@ void launch_row_dots(const double* u, const T* G, int64_t n, int nrows, double* 
 // =====================================================================================
 template <typename T, typename TO, int RM>
 __global__ void __launch_bounds__(256) k_recon(const ReconTask<T>* __restrict__ tasks, int64_t n,
-                                               const double* __restrict__ u0, TO* __restrict__ out, int64_t ldo) {
+                                               const double* __restrict__ u0, TO* __restrict__ out, int64_t ldo,
+                                               int64_t rows) {
+    constexpr int AB = 8;   // basis columns per batch of loads
     const ReconTask<T> tk = tasks[blockIdx.y];
     extern __shared__ double smem_rc[];
     const int K = tk.K1 + tk.K2;
-    // coefficients of rows r0..r0+ns-1 as T: sc[r*K + a]
+    const int ng = (tk.ns + RM - 1) / RM;   // groups of RM samples
+    // coefficients: sc[(g * K + a) * RM + r] = C(sample g*RM + r, column a) as T (0 past ns)
     T* sc = reinterpret_cast<T*>(smem_rc);
-    for (int e = threadIdx.x; e < tk.ns * K; e += blockDim.x) {
-        const int r = e / K, a = e % K;
-        sc[e] = (a < tk.K1) ? T(tk.C1[(int64_t)(tk.r0 + r) * tk.ldc1 + a])
-                            : T(tk.C2[(int64_t)(tk.r0 + r) * tk.ldc2 + (a - tk.K1)]);
+    for (int e = threadIdx.x; e < ng * K * RM; e += blockDim.x) {
+        const int r = e % RM, a = (e / RM) % K, g = e / (RM * K);
+        const int smp = g * RM + r;
+        T v = T(0);
+        if (smp < tk.ns)
+            v = (a < tk.K1) ? T(tk.C1[(int64_t)(tk.r0 + smp) * tk.ldc1 + a])
+                            : T(tk.C2[(int64_t)(tk.r0 + smp) * tk.ldc2 + (a - tk.K1)]);
+        sc[e] = v;
     }
     __syncthreads();
-    for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < n; k += (int64_t)gridDim.x * blockDim.x) {
-        const T base = u0 ? T(u0[k]) : T(0);
-        for (int rg = 0; rg < tk.ns; rg += RM) {
+    const int64_t k0 = (int64_t)blockIdx.x * rows;
+    const int64_t k1 = (k0 + rows < n) ? k0 + rows : n;
+    for (int64_t kb = k0; kb < k1; kb += blockDim.x) {
+        const int64_t k = kb + threadIdx.x;
+        const bool act = k < k1;
+        const T base = (act && u0) ? T(u0[k]) : T(0);
+        for (int g = 0; g < ng; ++g) {
             T acc[RM];
 #pragma unroll
             for (int r = 0; r < RM; ++r) acc[r] = base;
-            for (int a = 0; a < tk.K1; ++a) {
-                const T v = tk.V1[(int64_t)a * tk.ld1 + k];
+            for (int a0 = 0; a0 < K; a0 += AB) {
+                T v[AB];
+#pragma unroll
+                for (int j = 0; j < AB; ++j) {
+                    const int a = a0 + j;
+                    v[j] = T(0);
+                    if (act && a < K)
+                        v[j] = (a < tk.K1) ? tk.V1[(int64_t)a * tk.ld1 + k] : tk.V2[(int64_t)(a - tk.K1) * tk.ld2 + k];
+                }
+#pragma unroll
+                for (int j = 0; j < AB; ++j) {
+                    if (a0 + j >= K) break;
+                    const T* cj = sc + ((int64_t)g * K + a0 + j) * RM;
+#pragma unroll
+                    for (int r = 0; r < RM; ++r) acc[r] = fma(v[j], cj[r], acc[r]);
+                }
+            }
+            if (act) {
 #pragma unroll
                 for (int r = 0; r < RM; ++r)
-                    if (rg + r < tk.ns) acc[r] = fma(v, sc[(rg + r) * K + a], acc[r]);
+                    if (g * RM + r < tk.ns) out[(tk.i0 + g * RM + r) * ldo + k] = TO(acc[r]);
             }
-            for (int a = 0; a < tk.K2; ++a) {
-                const T v = tk.V2[(int64_t)a * tk.ld2 + k];
-#pragma unroll
-                for (int r = 0; r < RM; ++r)
-                    if (rg + r < tk.ns) acc[r] = fma(v, sc[(rg + r) * K + tk.K1 + a], acc[r]);
-            }
-#pragma unroll
-            for (int r = 0; r < RM; ++r)
-                if (rg + r < tk.ns) out[(tk.i0 + rg + r) * ldo + k] = TO(acc[r]);
         }
     }
 }
 
+// max_ns: most samples of a task; max_k: most basis columns (K1 + K2) of a task.
 template <typename T, typename TO>
 void launch_recon(const ReconTask<T>* tasks_dev, int ntasks, int max_ns, int64_t n, const double* u0, TO* out,
-                  int64_t ldo, int max_c_doubles, cudaStream_t s) {
-    (void)max_ns;
+                  int64_t ldo, int max_k, cudaStream_t s) {
     if (ntasks <= 0) return;
-    int bx = std::max(1, std::min(grid_for(n, 256), (4 * kNumSM * 4 + ntasks - 1) / ntasks));
-    dim3 grid(bx, ntasks);
-    size_t sm = (size_t)max_c_doubles * sizeof(T);
+    const int64_t maxch = std::max<int64_t>(1, (n + 255) / 256);
+    const int64_t want = std::max<int64_t>(1, (8 * kNumSM + ntasks - 1) / ntasks);
+    const int64_t ch = std::min(want, maxch);
+    int64_t rows = (n + ch - 1) / ch;
+    rows = (rows + 255) / 256 * 256;
+    dim3 grid((unsigned)((n + rows - 1) / rows), ntasks);
+    const size_t ng = (size_t)(std::max(max_ns, 1) + 16) / 17;
+    const size_t sm = ng * (size_t)std::max(max_k, 1) * 17 * sizeof(T);
     if (sm > 48 * 1024)
         cudaFuncSetAttribute(k_recon<T, TO, 17>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-    k_recon<T, TO, 17><<<grid, 256, sm, s>>>(tasks_dev, n, u0, out, ldo);
+    k_recon<T, TO, 17><<<grid, 256, sm, s>>>(tasks_dev, n, u0, out, ldo, rows);
 }
 
 // =====================================================================================
@@ -972,7 +1080,7 @@ void launch_row_diff_norms(const T* A, const T* B, int64_t n, int nrows, double*
     template void launch_sai_solve<T>(const OpDesc&, const SaiCoef&, const T* const*, T* const*, T* const*,  \
                                       int, double*, cudaStream_t);                                        \
     template void launch_sai_solve_lo<T>(const OpDesc&, const SaiCoef&, const T* const*, const T* const*,       \
-                                         T* const*, T* const*, int, double*, cudaStream_t);                   \
+                                         T* const*, T* const*, int, double*, cudaStream_t, const int* const*); \
     template void launch_ts_tn<T>(const TsTask<T>*, int, int, int, int64_t, double*, cudaStream_t, int);   \
     template void launch_ts_nn<T>(const TsTask<T>*, int, int, int64_t, cudaStream_t);                     \
     template void launch_recon<T, float>(const ReconTask<T>*, int, int, int64_t, const double*, float*,    \
@@ -981,7 +1089,7 @@ void launch_row_diff_norms(const T* A, const T* B, int64_t n, int nrows, double*
                                           int64_t, int, cudaStream_t);                                    \
     template void launch_row_diff_norms<T>(const T*, const T*, int64_t, int, double*, cudaStream_t); \
     template void launch_add<T>(T*, const T*, int64_t, cudaStream_t);                                   \
-    template void launch_row_dots<T>(const double*, const T*, int64_t, int, double*, cudaStream_t);
+    template void launch_row_dots<T>(const double*, const T*, int64_t, int, double*, float*, cudaStream_t);
 PEXP_INST_T(double)
 PEXP_INST_T(float)
 template void launch_convert<double, float>(const double*, float*, int64_t, cudaStream_t);
