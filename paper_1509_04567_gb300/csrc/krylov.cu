@@ -318,8 +318,8 @@ __device__ __forceinline__ void stage_coeffs(const UpdTask<T>& tk, int rows_h, i
 // W <- W - V h for one row: FP32 data in double-float with exact products x*h_hi
 // (FMA) and a compensated sum; FP64 data with FMAs.  Columns [q0, q0 + Q) of V.
 template <int Q, int B>
-__device__ __forceinline__ void sub_vh(const float (&x)[Q], const float (&xl)[Q], const float2* sh, int p, int q0,
-                                       float (&sh_)[B], float (&sl_)[B]) {
+__device__ __forceinline__ void sub_vh(const float (&x)[Q], const float2* sh, int p, int q0, float (&sh_)[B],
+                                       float (&sl_)[B]) {
 #pragma unroll
     for (int c = 0; c < B; ++c) {
         float s = sh_[c], l = sl_[c];
@@ -330,7 +330,6 @@ __device__ __forceinline__ void sub_vh(const float (&x)[Q], const float (&xl)[Q]
                 const float ph = x[q] * h.x;
                 float pe = fmaf(x[q], h.x, -ph);
                 pe = fmaf(x[q], h.y, pe);
-                pe = fmaf(xl[q], h.x, pe);
                 const float t = s + ph;
                 const float bp = t - s;
                 l += ((s - (t - bp)) + (ph - bp)) + pe;
@@ -342,8 +341,8 @@ __device__ __forceinline__ void sub_vh(const float (&x)[Q], const float (&xl)[Q]
     }
 }
 template <int Q, int B>
-__device__ __forceinline__ void sub_vh(const double (&x)[Q], const double (&)[Q], const double* sh, int p, int q0,
-                                       double (&sh_)[B], double (&)[B]) {
+__device__ __forceinline__ void sub_vh(const double (&x)[Q], const double* sh, int p, int q0, double (&sh_)[B],
+                                       double (&)[B]) {
 #pragma unroll
     for (int c = 0; c < B; ++c) {
         double s = sh_[c];
@@ -384,19 +383,31 @@ __global__ void __launch_bounds__(kThreads, 2) k_update0(const UpdTask<T>* __res
         T s[B], l[B];
 #pragma unroll
         for (int c = 0; c < B; ++c) s[c] = l[c] = T(0);
+        // low parts of the last block (the dominant direction of the step): loaded first
+        T vl[B];
+#pragma unroll
+        for (int j = 0; j < B; ++j) vl[j] = T(0);
+        if constexpr (sizeof(T) == 4) {
+            if (tk.Vlo) {
+#pragma unroll
+                for (int j = 0; j < B; ++j) vl[j] = act ? ldg(tk.Vlo + (int64_t)j * ld + r) : 0.f;
+            }
+        }
         for (int q0 = 0; q0 < p; q0 += Q) {
-            T x[Q], xl[Q];
+            T x[Q];
 #pragma unroll
             for (int q = 0; q < Q; ++q) {
                 const int a = q0 + q;
                 x[q] = (act && a < p) ? ldg(tk.V + (int64_t)a * ld + r) : T(0);
-                // low parts of the last block (the dominant direction of the step)
-                if constexpr (sizeof(T) == 4)
-                    xl[q] = (act && tk.Vlo && a < p && a >= p - B) ? ldg(tk.Vlo + (int64_t)(a - (p - B)) * ld + r) : 0.f;
-                else
-                    xl[q] = T(0);
             }
-            sub_vh<Q, B>(x, xl, sh, p, q0, s, l);
+            sub_vh<Q, B>(x, sh, p, q0, s, l);
+        }
+        if constexpr (sizeof(T) == 4) {
+            // the low parts' products vl * h_hi go into the small sums
+#pragma unroll
+            for (int c = 0; c < B; ++c)
+#pragma unroll
+                for (int j = 0; j < B; ++j) l[c] = fmaf(vl[j], sh[(p - B + j) + c * p].x, l[c]);
         }
         T wr[B];
 #pragma unroll
@@ -431,13 +442,16 @@ __global__ void __launch_bounds__(kThreads, 2) k_update0(const UpdTask<T>* __res
 
 // W <- W T for one row (T: B x B FP64 in shared memory); FP32 data in double-float.
 template <int B>
-__device__ __forceinline__ void scale_row(float (&xh)[B], float (&xl)[B], const double* sT, float (&res)[B]) {
+__device__ __forceinline__ void scale_row(float (&xh)[B], float (&xl)[B], const float2* sT, float (&res)[B]) {
     F2 z[B];
 #pragma unroll
     for (int c = 0; c < B; ++c) {
         z[c] = F2{0.f, 0.f};
 #pragma unroll
-        for (int a = 0; a < B; ++a) z[c] = f2_add(z[c], f2_mul(F2{xh[a], xl[a]}, f2_from(sT[a + c * B])));
+        for (int a = 0; a < B; ++a) {
+            const float2 t = sT[a + c * B];
+            z[c] = f2_add(z[c], f2_mul(F2{xh[a], xl[a]}, F2{t.x, t.y}));
+        }
     }
 #pragma unroll
     for (int c = 0; c < B; ++c) {
@@ -471,12 +485,13 @@ __global__ void __launch_bounds__(kThreads, 2) k_scale_proj(const UpdTask<T>* __
                                                             double* __restrict__ partial) {
     constexpr int Q = kFuseP;
     constexpr int NE = Q * B;
-    __shared__ double sT[B * B];
+    using CT = typename Coef<T>::type;
+    __shared__ CT sT[B * B];
     __shared__ double sred[kWarps * NE];
     const UpdTask<T> tk = tasks[blockIdx.y];
     if (tk.conv && *tk.conv) return;
     const int p = tk.p;
-    for (int e = threadIdx.x; e < B * B; e += kThreads) sT[e] = tk.hm[(e % B) + (int64_t)(e / B) * tk.ldh];
+    for (int e = threadIdx.x; e < B * B; e += kThreads) sT[e] = Coef<T>::make(tk.hm[(e % B) + (int64_t)(e / B) * tk.ldh]);
     __syncthreads();
     const int64_t ld = tk.ld;
     const int64_t r0 = (int64_t)blockIdx.x * rows;
@@ -661,11 +676,12 @@ __global__ void __launch_bounds__(kThreads, 2) k_scale(const UpdTask<T>* __restr
                                                        double* __restrict__ partial) {
     constexpr int U = 4;
     constexpr int NE = B * B;
-    __shared__ double sT[B * B];
+    using CT = typename Coef<T>::type;
+    __shared__ CT sT[B * B];
     __shared__ double sred[kWarps * NE];
     const UpdTask<T> tk = tasks[blockIdx.y];
     if (tk.conv && *tk.conv) return;
-    for (int e = threadIdx.x; e < B * B; e += kThreads) sT[e] = tk.hm[(e % B) + (int64_t)(e / B) * tk.ldh];
+    for (int e = threadIdx.x; e < B * B; e += kThreads) sT[e] = Coef<T>::make(tk.hm[(e % B) + (int64_t)(e / B) * tk.ldh]);
     __syncthreads();
     const int64_t ld = tk.ld;
     const int64_t r0 = (int64_t)blockIdx.x * rows;

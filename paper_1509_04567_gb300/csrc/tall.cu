@@ -291,42 +291,90 @@ template <typename T, typename R> __device__ __forceinline__ R load_r(T hi, T lo
 template <> __device__ __forceinline__ double load_r<double, double>(double hi, double lo) { return hi; }
 template <> __device__ __forceinline__ DF load_r<float, DF>(float hi, float lo) { return DF{hi, lo}; }
 
-// Hillis-Steele scan of affine maps f(z) = a z + b over the CTA in "virtual" order
-// v (v = t forward, v = NT-1-t backward); map v is applied after maps < v.
-// Returns the exclusive composition for this thread and the CTA total.
+// Shuffles of a recurrence value (FP64, or a double-float pair).
+__device__ __forceinline__ double rshfl_up(double v, int d) { return __shfl_up_sync(0xffffffffu, v, d); }
+__device__ __forceinline__ double rshfl_down(double v, int d) { return __shfl_down_sync(0xffffffffu, v, d); }
+__device__ __forceinline__ double rshfl_idx(double v, int l) { return __shfl_sync(0xffffffffu, v, l); }
+__device__ __forceinline__ DF rshfl_up(DF v, int d) {
+    return DF{__shfl_up_sync(0xffffffffu, v.hi, d), __shfl_up_sync(0xffffffffu, v.lo, d)};
+}
+__device__ __forceinline__ DF rshfl_down(DF v, int d) {
+    return DF{__shfl_down_sync(0xffffffffu, v.hi, d), __shfl_down_sync(0xffffffffu, v.lo, d)};
+}
+__device__ __forceinline__ DF rshfl_idx(DF v, int l) {
+    return DF{__shfl_sync(0xffffffffu, v.hi, l), __shfl_sync(0xffffffffu, v.lo, l)};
+}
+
+// Scan of affine maps f(z) = a z + b over the CTA in "virtual" order v (v = t forward,
+// v = NT-1-t backward); map v is applied after maps < v.  Returns the exclusive
+// composition for this thread and the CTA total.  Warps scan with shuffles (Kogge-Stone);
+// one warp then composes the warp totals: two barriers per scan.
 template <typename R>
 __device__ __forceinline__ void cta_affine_scan(R a, R b, bool reverse, R* sa, R* sb, R& ea, R& eb, R& ta,
                                                 R& tb) {
-    const int t = threadIdx.x;
-    const int v = reverse ? (kSaiThreads - 1 - t) : t;
-    sa[v] = a;
-    sb[v] = b;
-    __syncthreads();
-    for (int d = 1; d < kSaiThreads; d <<= 1) {
-        const R ca = sa[v], cb = sb[v];
-        R pa = rfrom<R>(1.0), pb = rfrom<R>(0.0);
-        const bool has = v >= d;
-        if (has) {
-            pa = sa[v - d];
-            pb = sb[v - d];
+    constexpr int NW = kSaiThreads / 32;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int lv = reverse ? 31 - lane : lane;        // virtual lane
+    const int wv = reverse ? NW - 1 - warp : warp;    // virtual warp
+    // inclusive scan within the warp in virtual order
+#pragma unroll
+    for (int d = 1; d < 32; d <<= 1) {
+        const R pa = reverse ? rshfl_down(a, d) : rshfl_up(a, d);
+        const R pb = reverse ? rshfl_down(b, d) : rshfl_up(b, d);
+        if (lv >= d) {
+            b = rfma(a, pb, b);
+            a = rmul(a, pa);
         }
-        __syncthreads();
-        if (has) {
-            sa[v] = rmul(ca, pa);
-            sb[v] = rfma(ca, pb, cb);
-        }
-        __syncthreads();
     }
-    if (v > 0) {
-        ea = sa[v - 1];
-        eb = sb[v - 1];
-    } else {
-        ea = rfrom<R>(1.0);
-        eb = rfrom<R>(0.0);
+    // exclusive within the warp: the inclusive value of the previous virtual lane
+    const int last = reverse ? 0 : 31;
+    R xa = reverse ? rshfl_down(a, 1) : rshfl_up(a, 1);
+    R xb = reverse ? rshfl_down(b, 1) : rshfl_up(b, 1);
+    if (lv == 0) {
+        xa = rfrom<R>(1.0);
+        xb = rfrom<R>(0.0);
     }
-    ta = sa[kSaiThreads - 1];
-    tb = sb[kSaiThreads - 1];
+    if (lane == last) {
+        sa[wv] = a;
+        sb[wv] = b;
+    }
     __syncthreads();
+    if (warp == 0) {
+        // exclusive scan of the warp totals (NW <= 32) in virtual warp order
+        R wa = lane < NW ? sa[lane] : rfrom<R>(1.0);
+        R wb = lane < NW ? sb[lane] : rfrom<R>(0.0);
+#pragma unroll
+        for (int d = 1; d < 32; d <<= 1) {
+            const R pa = rshfl_up(wa, d), pb = rshfl_up(wb, d);
+            if (lane >= d) {
+                wb = rfma(wa, pb, wb);
+                wa = rmul(wa, pa);
+            }
+        }
+        const R ta_ = rshfl_idx(wa, NW - 1), tb_ = rshfl_idx(wb, NW - 1);
+        R pa = rshfl_up(wa, 1), pb = rshfl_up(wb, 1);
+        if (lane == 0) {
+            pa = rfrom<R>(1.0);
+            pb = rfrom<R>(0.0);
+        }
+        __syncwarp();
+        if (lane < NW) {
+            sa[lane] = pa;   // exclusive prefix of virtual warp `lane`
+            sb[lane] = pb;
+        }
+        if (lane == 0) {
+            sa[NW] = ta_;
+            sb[NW] = tb_;
+        }
+    }
+    __syncthreads();
+    const R pa = sa[wv], pb = sb[wv];
+    // this thread's exclusive map = (within-warp exclusive) after (previous warps)
+    ea = rmul(xa, pa);
+    eb = rfma(xa, pb, xb);
+    ta = sa[NW];
+    tb = sb[NW];
+    __syncthreads();   // the shared arrays are reused by the next scan
 }
 
 template <typename T>
