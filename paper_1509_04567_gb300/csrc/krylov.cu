@@ -802,15 +802,15 @@ void launch_block_gram(const UpdTask<T>* tasks, int ntasks, int64_t n, KGeom g, 
 // Sum of per-CTA partials into a dense FP64 block of each window's slab:
 // out(task) = wd + wins[task] * stride + off, entries [0, ne).
 // =====================================================================================
-__global__ void __launch_bounds__(kThreads) k_sum_parts(const double* __restrict__ part, int nchunks, int pstride, int ne,
-                                                        double* __restrict__ wd, int64_t stride, int64_t off,
+__global__ void __launch_bounds__(kThreads) k_sum_parts(const double* __restrict__ part, int nchunks, int pstride, int e0,
+                                                        int ne, double* __restrict__ wd, int64_t stride, int64_t off,
                                                         const int* __restrict__ wins, const int* __restrict__ wi,
                                                         int istride, int conv_field) {
     if (wi && wi[(int64_t)wins[blockIdx.x] * istride + conv_field]) return;
     const Parts pp{part, nchunks, pstride};
     double* out = wd + (int64_t)wins[blockIdx.x] * stride + off;
     for (int e = threadIdx.x >> 5; e < ne; e += kWarps) {
-        const double v = parts_sum_warp(pp, blockIdx.x, e);
+        const double v = parts_sum_warp(pp, blockIdx.x, e0 + e);
         if ((threadIdx.x & 31) == 0) out[e] = v;
     }
 }
@@ -958,9 +958,10 @@ void launch_scale(const UpdTask<T>* tasks, int ntasks, int b, int64_t n, int gra
 }
 
 void launch_sum_parts(const double* part, int nchunks, int pstride, int ne, double* wd, int64_t stride, int64_t off,
-                      const int* wins, int ntasks, const int* wi, int istride, int conv_field, cudaStream_t s) {
+                      const int* wins, int ntasks, const int* wi, int istride, int conv_field, cudaStream_t s, int e0) {
     if (ntasks <= 0 || ne <= 0) return;
-    k_sum_parts<<<ntasks, kThreads, 0, s>>>(part, nchunks, pstride, ne, wd, stride, off, wins, wi, istride, conv_field);
+    k_sum_parts<<<ntasks, kThreads, 0, s>>>(part, nchunks, pstride, e0, ne, wd, stride, off, wins, wi, istride,
+                                            conv_field);
 }
 
 template <typename T>
@@ -969,7 +970,7 @@ void launch_source_gram(const T* const* X, const int* sv, int ntasks, int s_max,
     if (ntasks <= 0) return;
     dim3 grid(g.nchunks, ntasks);
     const size_t sm = sizeof(T) * (size_t)s_max * kTile;
-    if (sm > 48 * 1024) cudaFuncSetAttribute(k_source_gram<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    if (sm > 32 * 1024) cudaFuncSetAttribute(k_source_gram<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
     k_source_gram<T><<<grid, kThreads, sm, st>>>(X, sv, n, g.rows, g.nchunks, pstride, partial);
 }
 

@@ -66,9 +66,11 @@ void launch_scale(const UpdTask<T>* tasks, int ntasks, int b, int64_t n, int gra
                   int pstride, cudaStream_t s);
 constexpr int kKrylovMaxB = 4;   // block widths handled by the fused kernels
 // Sums the per-CTA partials of each task into wd + wins[task] * stride + off (ne entries).
+// Entries [e0, e0 + ne) of each partial go to entries [0, ne) of the output.
 // Windows whose flag wi[w * istride + conv_field] is set are skipped.
 void launch_sum_parts(const double* part, int nchunks, int pstride, int ne, double* wd, int64_t stride, int64_t off,
-                      const int* wins, int ntasks, const int* wi, int istride, int conv_field, cudaStream_t s);
+                      const int* wins, int ntasks, const int* wi, int istride, int conv_field, cudaStream_t s,
+                      int e0 = 0);
 // Gram matrices of the source windows: X[k] points at the first of sv[k] (<= 31)
 // consecutive length-n vectors; partial (chunk) results s x s, both halves.
 template <typename T>

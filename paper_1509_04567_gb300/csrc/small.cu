@@ -373,7 +373,7 @@ void launch_source_eig(const WinLayout& L, double* wd, int* wi, const int* wins,
                        const double* dots, const double* nrm2, cudaStream_t s, Parts gp) {
     if (nw <= 0) return;
     size_t sm = (size_t)2 * L.s_max * L.s_max * sizeof(double);
-    if (sm > 48 * 1024) cudaFuncSetAttribute(k_source_eig, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    if (sm > 32 * 1024) cudaFuncSetAttribute(k_source_eig, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
     k_source_eig<<<nw, 64, sm, s>>>(L, wd, wi, wins, thr, max_rank, dots, nrm2, gp);
 }
 
@@ -628,7 +628,9 @@ void launch_spline(const WinLayout& L, double* wd, int* wi, const int* wins, int
 // =====================================================================================
 __global__ void __launch_bounds__(256) k_project(WinLayout L, double* __restrict__ wd, int* __restrict__ wi,
                                                  const int* __restrict__ wins, int step, double h, double tol,
-                                                 double scale_ref, Parts fp, double dcoef, double ccoef) {
+                                                 double scale_ref, Parts fp, double dcoef, double ccoef, int nsm,
+                                                 int only_ef) {
+    extern __shared__ double sm_proj[];   // 9 nsm^2 doubles when nsm > 0
     const int w = wins[blockIdx.x];
     double* D = wd + (int64_t)w * L.stride;
     int* I = wi + (int64_t)w * L.istride;
@@ -646,7 +648,9 @@ __global__ void __launch_bounds__(256) k_project(WinLayout L, double* __restrict
     if (fp.part) {
         // fused partials: E (K x b) | F (K x b) | h1 (K x b) | pre (b) per chunk
         double* o1w = D + L.off_out1;
-        const int nfield = 3 * K * b + b;
+        // only_ef: h1 and pre are summed into out1 by another kernel (the Gram-Schmidt
+        // passes run concurrently with this one)
+        const int nfield = only_ef ? 2 * K * b : 3 * K * b + b;
         const int nwarps = blockDim.x >> 5;
         for (int e = threadIdx.x >> 5; e < nfield; e += nwarps) {
             const double sacc = parts_sum_warp(fp, blockIdx.x, e);
@@ -682,9 +686,12 @@ __global__ void __launch_bounds__(256) k_project(WinLayout L, double* __restrict
     }
     __syncthreads();
     const int N = (kind == KIND_SOURCE) ? K + 4 * b : K;
-    double* M = D + L.off_scr;
-    double* E = M + (int64_t)L.N_max * L.N_max;
-    double* work = E + (int64_t)L.N_max * L.N_max;
+    // the augmented matrix, its exponential and the Pade work space: in shared memory when
+    // they fit (each small product then costs shared-memory latency, not L2 latency)
+    const int64_t mstride = nsm > 0 ? (int64_t)nsm * nsm : (int64_t)L.N_max * L.N_max;
+    double* M = nsm > 0 ? sm_proj : D + L.off_scr;
+    double* E = M + mstride;
+    double* work = E + mstride;
     for (int e = threadIdx.x; e < N * N; e += blockDim.x) {
         const int i = e % N, j = e / N;
         double v = 0.0;
@@ -760,9 +767,17 @@ __global__ void __launch_bounds__(256) k_project(WinLayout L, double* __restrict
 }
 
 void launch_project(const WinLayout& L, double* wd, int* wi, const int* wins, int nw, int step, double h, double tol,
-                    double scale_ref, cudaStream_t s, Parts fp, double d, double cadv) {
+                    double scale_ref, cudaStream_t s, Parts fp, double d, double cadv, int b_launch, int only_ef) {
     if (nw <= 0) return;
-    k_project<<<nw, 256, 0, s>>>(L, wd, wi, wins, step, h, tol, scale_ref, fp, d, cadv);
+    // largest augmented matrix of this launch: step * b + 4 b (source windows)
+    const int nl = b_launch > 0 ? std::min(L.N_max, (step + 4) * b_launch) : L.N_max;
+    const size_t sm = (size_t)9 * nl * nl * sizeof(double);
+    if (sm <= 200u * 1024u) {
+        if (sm > 32 * 1024) cudaFuncSetAttribute(k_project, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+        k_project<<<nw, 256, sm, s>>>(L, wd, wi, wins, step, h, tol, scale_ref, fp, d, cadv, nl, only_ef);
+    } else {
+        k_project<<<nw, 256, 0, s>>>(L, wd, wi, wins, step, h, tol, scale_ref, fp, d, cadv, 0, only_ef);
+    }
 }
 
 // =====================================================================================

@@ -72,9 +72,12 @@ void launch_block_orth(const WinLayout& L, double* wd, int* wi, const int* wins,
 void launch_spline(const WinLayout& L, double* wd, int* wi, const int* wins, int nw, double h, cudaStream_t s);
 // With fused partials (E, F, h1, pre of the step) and the operator coefficients d, c:
 // H[a, i] = -d E - c F, H[i, a] = -d E + c F; h1 and pre are stored at out1.
+// b_launch: largest block width among the windows (0: unknown, the matrices stay in global memory
+// unless the layout's largest matrix fits in shared memory)
+// only_ef != 0 (fused partials): h1 and pre are left to another kernel.
 void launch_project(const WinLayout& L, double* wd, int* wi, const int* wins, int nw, int step, double h,
                     double tol, double scale_ref, cudaStream_t s, Parts fp = Parts{nullptr, 0, 0}, double d = 0.0,
-                    double cadv = 0.0);
+                    double cadv = 0.0, int b_launch = 0, int only_ef = 0);
 void launch_small_expm_batch(const double* M, double* E, int N, int batch, double* scratch, cudaStream_t s);
 size_t small_expm_scratch_doubles(int N);
 void init_pade_constants();

@@ -84,6 +84,9 @@ struct pexp_ctx {
     int* flags_h = nullptr;  // pinned copy of the per-window int state (lookahead of the Krylov loop)
     size_t flags_cap = 0;
     cudaEvent_t flag_ev[2] = {nullptr, nullptr};
+    // second stream: the projected solve of a Krylov step runs beside the Gram-Schmidt passes
+    cudaStream_t s2 = nullptr;
+    cudaEvent_t ev_sp = nullptr, ev_pj = nullptr;
     cudaEvent_t ev0 = nullptr, ev1 = nullptr;
     cudaEvent_t evp[5] = {nullptr, nullptr, nullptr, nullptr, nullptr};   // phase boundaries
     int launches = 0;
@@ -207,15 +210,16 @@ struct Stage {
 
 // Time a launch sequence as kernel class `cls` moving `bytes` algorithmic bytes.
 template <typename F>
-void timed(pexp_ctx* c, int cls, double bytes, F&& f) {
+void timed(pexp_ctx* c, int cls, double bytes, F&& f, cudaStream_t on = nullptr, bool on_set = false) {
     if (!c->kt.on) {
         f();
         return;
     }
+    cudaStream_t st = on_set ? on : c->stream;
     cudaEvent_t a = c->kt.next(), b = c->kt.next();
-    cudaEventRecord(a, c->stream);
+    cudaEventRecord(a, st);
     f();
-    cudaEventRecord(b, c->stream);
+    cudaEventRecord(b, st);
     c->kt.recs.push_back({cls, a, b, bytes});
 }
 
@@ -460,12 +464,32 @@ struct Solver {
                     a0 = a1;
                 }
             });
+            // h1 and the pre-Gram-Schmidt norms for the passes below; the projected solve (the
+            // Galerkin matrix, its exponential, the convergence test) runs on the second stream
+            // beside them: it is FP64-bound on one SM per window, the passes are HBM-bound
+            cudaEventRecord(c->ev_sp, st);
             timed(c, PEXP_KC_SMALL, 0.0, [&] {
-                launch_project(L, wd, wi, d_wl, na, step, h, o->tol, scale_ref, st, Parts{kpart[0], g.nchunks, ps1},
-                               od.x.d, od.x.c);
+                for (int a0 = 0; a0 < na;) {
+                    int a1 = a0;
+                    while (a1 < na && act[a1].b == act[a0].b) ++a1;
+                    const int bb = act[a0].b, pp = step * bb;
+                    launch_sum_parts(kpart[0] + (size_t)a0 * g.nchunks * ps1, g.nchunks, ps1, pp * bb + bb, wd, L.stride,
+                                     L.off_out1, d_wl + a0, a1 - a0, wi, L.istride, WI_CONV, st, 2 * pp * bb);
+                    check_launch(c);
+                    a0 = a1;
+                }
             });
+            cudaStreamWaitEvent(c->s2, c->ev_sp, 0);
+            timed(c, PEXP_KC_SMALL, 0.0, [&] {
+                launch_project(L, wd, wi, d_wl, na, step, h, o->tol, scale_ref, c->s2, Parts{kpart[0], g.nchunks, ps1},
+                               od.x.d, od.x.c, bmax, 1);
+            }, c->s2, true);
             check_launch(c);
+            cudaEventRecord(c->ev_pj, c->s2);
             if (step < kmax) part_b(act, step);
+            // the step's projected solve must be done before its flags are read and before the
+            // next step's projections overwrite the partial sums it reads
+            cudaStreamWaitEvent(st, c->ev_pj, 0);
             // flags of this step, read back without waiting; then the previous step's flags
             int* fl = c->flags_h + (size_t)(step & 1) * nint;
             cudaMemcpyAsync(fl, wi, sizeof(int) * nint, cudaMemcpyDeviceToHost, st);
@@ -489,6 +513,9 @@ struct Solver {
     }
 
     // Part B of a fused step: block classical Gram-Schmidt with Cholesky QR, twice (BCGS2).
+    // Part B of a fused step: block classical Gram-Schmidt with Cholesky QR, twice (BCGS2).
+    // All its partial sums go through kpart[1]: kpart[0] holds the step projections, which
+    // the projected solve on the second stream may still be reading.
     void part_b(const std::vector<Win<T>>& act, int step) {
         {
             const double w = sizeof(T);
@@ -545,12 +572,12 @@ struct Solver {
             // pass 1: W <- W - V h1 (Gram of the result), Cholesky QR with deflation
             timed(c, PEXP_KC_UPDATE, (double)n * (pb * w + 2 * bb * wl_), [&] {
                 groups([&](int a0, int a1, int b) {
-                    launch_update<T>(d1 + a0, a1 - a0, b, step * b, n, 0, gb, kpart[0] + (size_t)a0 * gb.nchunks * psg, psg, st);
+                    launch_update<T>(d1 + a0, a1 - a0, b, step * b, n, 0, gb, kpart[1] + (size_t)a0 * gb.nchunks * psg, psg, st);
                     check_launch(c);
                 });
             });
             timed(c, PEXP_KC_SMALL, 0.0, [&] {
-                launch_block_orth(L, wd, wi, d_wl2, nb, 1, step, defl, st, Parts{kpart[0], gb.nchunks, psg});
+                launch_block_orth(L, wd, wi, d_wl2, nb, 1, step, defl, st, Parts{kpart[1], gb.nchunks, psg});
             });
             check_launch(c);
             // pass 2: W <- W T1 and h2 = V^T W; W <- W - V h2 (Gram), Cholesky QR; round into the basis
@@ -569,12 +596,12 @@ struct Solver {
             });
             timed(c, PEXP_KC_UPDATE, (double)n * (pb * w + 2 * bb * wl_), [&] {
                 groups([&](int a0, int a1, int b) {
-                    launch_update<T>(d2 + a0, a1 - a0, b, step * b, n, 1, gb, kpart[0] + (size_t)a0 * gb.nchunks * psg, psg, st);
+                    launch_update<T>(d2 + a0, a1 - a0, b, step * b, n, 1, gb, kpart[1] + (size_t)a0 * gb.nchunks * psg, psg, st);
                     check_launch(c);
                 });
             });
             timed(c, PEXP_KC_SMALL, 0.0, [&] {
-                launch_block_orth(L, wd, wi, d_wl2, nb, 2, step, defl, st, Parts{kpart[0], gb.nchunks, psg});
+                launch_block_orth(L, wd, wi, d_wl2, nb, 2, step, defl, st, Parts{kpart[1], gb.nchunks, psg});
             });
             check_launch(c);
             timed(c, PEXP_KC_UPDATE, (double)n * bb * (wl_ + w), [&] {
@@ -1411,6 +1438,12 @@ int pexp_create(pexp_ctx** out, int device, void* stream) {
         }
     }
     for (int k = 0; k < kSlots; ++k) cudaEventCreateWithFlags(&c->slot_ev[k], cudaEventDisableTiming);
+    if (cudaStreamCreateWithFlags(&c->s2, cudaStreamNonBlocking) != cudaSuccess ||
+        cudaEventCreateWithFlags(&c->ev_sp, cudaEventDisableTiming) != cudaSuccess ||
+        cudaEventCreateWithFlags(&c->ev_pj, cudaEventDisableTiming) != cudaSuccess) {
+        pexp_destroy(c);
+        return PEXP_ERR_CUDA;
+    }
     cudaEventCreate(&c->ev0);
     cudaEventCreate(&c->ev1);
     for (int k = 0; k < 5; ++k) cudaEventCreate(&c->evp[k]);
@@ -1435,6 +1468,12 @@ int pexp_destroy(pexp_ctx* c) {
     if (c->flags_h) cudaFreeHost(c->flags_h);
     for (int k = 0; k < 2; ++k)
         if (c->flag_ev[k]) cudaEventDestroy(c->flag_ev[k]);
+    if (c->s2) {
+        cudaStreamSynchronize(c->s2);
+        cudaStreamDestroy(c->s2);
+    }
+    if (c->ev_sp) cudaEventDestroy(c->ev_sp);
+    if (c->ev_pj) cudaEventDestroy(c->ev_pj);
     if (c->ev0) cudaEventDestroy(c->ev0);
     if (c->ev1) cudaEventDestroy(c->ev1);
     for (int k = 0; k < 5; ++k)

@@ -796,7 +796,7 @@ void launch_ts_nn(const TsTask<T>* tasks_dev, int ntasks, int max_pq, int64_t n,
     int bx = std::max(1, std::min(grid_for(n, 256), (4 * kNumSM * 4 + ntasks - 1) / ntasks));
     dim3 grid(bx, ntasks);
     size_t sm = (size_t)max_pq * sizeof(T);
-    if (sm > 48 * 1024) cudaFuncSetAttribute(k_ts_nn<T, 16>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    if (sm > 32 * 1024) cudaFuncSetAttribute(k_ts_nn<T, 16>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
     k_ts_nn<T, 16><<<grid, 256, sm, s>>>(tasks_dev, n);
 }
 
@@ -899,7 +899,7 @@ void launch_ts_nn_df(const DfTask* tasks_dev, int ntasks, int max_pq, int64_t n,
     rows = (rows + 255) / 256 * 256;
     dim3 grid((unsigned)((n + rows - 1) / rows), ntasks);
     size_t sm = ((size_t)max_pq + 16) * sizeof(float2);
-    if (sm > 48 * 1024) cudaFuncSetAttribute(k_ts_nn_df, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    if (sm > 32 * 1024) cudaFuncSetAttribute(k_ts_nn_df, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
     k_ts_nn_df<<<grid, 256, sm, s>>>(tasks_dev, n, rows);
 }
 
@@ -1054,7 +1054,7 @@ void launch_recon(const ReconTask<T>* tasks_dev, int ntasks, int max_ns, int64_t
     dim3 grid((unsigned)((n + rows - 1) / rows), ntasks);
     const size_t ng = (size_t)(std::max(max_ns, 1) + 16) / 17;
     const size_t sm = ng * (size_t)std::max(max_k, 1) * 17 * sizeof(T);
-    if (sm > 48 * 1024)
+    if (sm > 32 * 1024)
         cudaFuncSetAttribute(k_recon<T, TO, 17>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
     k_recon<T, TO, 17><<<grid, 256, sm, s>>>(tasks_dev, n, u0, out, ldo, rows);
 }
