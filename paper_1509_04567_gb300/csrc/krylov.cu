@@ -383,16 +383,6 @@ __global__ void __launch_bounds__(kThreads, 2) k_update0(const UpdTask<T>* __res
         T s[B], l[B];
 #pragma unroll
         for (int c = 0; c < B; ++c) s[c] = l[c] = T(0);
-        // low parts of the last block (the dominant direction of the step): loaded first
-        T vl[B];
-#pragma unroll
-        for (int j = 0; j < B; ++j) vl[j] = T(0);
-        if constexpr (sizeof(T) == 4) {
-            if (tk.Vlo) {
-#pragma unroll
-                for (int j = 0; j < B; ++j) vl[j] = act ? ldg(tk.Vlo + (int64_t)j * ld + r) : 0.f;
-            }
-        }
         for (int q0 = 0; q0 < p; q0 += Q) {
             T x[Q];
 #pragma unroll
@@ -401,13 +391,6 @@ __global__ void __launch_bounds__(kThreads, 2) k_update0(const UpdTask<T>* __res
                 x[q] = (act && a < p) ? ldg(tk.V + (int64_t)a * ld + r) : T(0);
             }
             sub_vh<Q, B>(x, sh, p, q0, s, l);
-        }
-        if constexpr (sizeof(T) == 4) {
-            // the low parts' products vl * h_hi go into the small sums
-#pragma unroll
-            for (int c = 0; c < B; ++c)
-#pragma unroll
-                for (int j = 0; j < B; ++j) l[c] = fmaf(vl[j], sh[(p - B + j) + c * p].x, l[c]);
         }
         T wr[B];
 #pragma unroll
@@ -714,8 +697,6 @@ __global__ void __launch_bounds__(kThreads, 2) k_scale(const UpdTask<T>* __restr
                 for (int c = 0; c < B; ++c) {
                     if (tk.out) {
                         tk.out[(int64_t)c * ld + r] = res[c];
-                        if constexpr (sizeof(T) == 4)
-                            if (tk.outlo) tk.outlo[(int64_t)c * ld + r] = (xh[u][c] - res[c]) + xl[u][c];
                     } else {
                         tk.Wh[(int64_t)c * ld + r] = xh[u][c];
                         if constexpr (sizeof(T) == 4) tk.Wl[(int64_t)c * ld + r] = xl[u][c];

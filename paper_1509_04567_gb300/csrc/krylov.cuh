@@ -23,8 +23,6 @@ struct UpdTask {
     T* Wh;            // working block (hi)
     float* Wl;        // FP32 data: low parts; NULL for FP64
     T* out;           // scale kernel, final pass: destination of the rounded block (else NULL)
-    float* outlo;     // final pass, FP32 data: what the rounding into `out` left over (else NULL)
-    const float* Vlo; // mode 0, FP32 data: low parts of the last block of V_{1:i} (columns p-b..p-1), or NULL
     int64_t ld;
     int p;
     const double* hm;

@@ -314,8 +314,7 @@ struct Win {
     T* S;         // scratch n x (ycols-1) b: A V_i, A^T V_i (and their low parts for FP32 data)
     int b;        // block width
     float* Wlo;   // FP32 data: low parts of the working block (n x b); NULL for FP64
-    float* V1lo;  // FP32 data: low parts of the start block V_1 (n x b); NULL for FP64
-    float* Vklo;  // FP32 data: low parts of the newest block V_k, k >= 2 (n x b); NULL for FP64
+    float* V1lo;  // FP32 data: low parts of the start block while it is formed (n x b); NULL for FP64
 };
 
 
@@ -409,7 +408,7 @@ struct Solver {
             const int ps1 = 3 * step * bmax * bmax + bmax;   // step_proj partial stride
             // ---- part A
             Stage sa(c, 0);
-            std::vector<const T*> xin, xlo;
+            std::vector<const T*> xin;
             std::vector<T*> yout, ylo;
             std::vector<StepTask<T>> st1(na);
             std::vector<int> wl(na);
@@ -418,13 +417,11 @@ struct Solver {
                 const Win<T>& W = act[a];
                 T* Vi = slot(W, step - 1);
                 T* Wn = slot(W, step);
-                // FP32 data: the newest block enters the solve with its low parts, so that its
-                // rounding (white noise, not in the Krylov space) is not turned by the solve and
-                // the normalisation of the next block into directions that never deflate
-                const float* vlo = (step == 1) ? W.V1lo : W.Vklo;
+                // the solve takes the stored (rounded) block: the projected matrix is formed
+                // from the stored basis, and any part of the input outside it (e.g. a low part
+                // of the rounding) would follow the wrong projected dynamics
                 for (int cc = 0; cc < W.b; ++cc) {
                     xin.push_back(Vi + (int64_t)cc * n);
-                    xlo.push_back(vlo ? reinterpret_cast<const T*>(vlo) + (int64_t)cc * n : nullptr);
                     yout.push_back(Wn + (int64_t)cc * n);
                     ylo.push_back(W.Wlo ? reinterpret_cast<T*>(W.Wlo) + (int64_t)cc * n : nullptr);
                     skip.push_back(conv_of(W));
@@ -434,7 +431,6 @@ struct Solver {
             }
             const int nv = (int)xin.size();
             const T* const* d_xin = sa.put(xin.data(), nv);
-            const T* const* d_xlo = std::is_same<T, float>::value ? sa.put(xlo.data(), nv) : nullptr;
             T* const* d_yout = sa.put(yout.data(), nv);
             T* const* d_ylo = std::is_same<T, float>::value ? sa.put(ylo.data(), nv) : nullptr;
             const StepTask<T>* d_st1 = sa.put(st1.data(), na);
@@ -445,7 +441,7 @@ struct Solver {
             const double wout = std::is_same<T, float>::value ? 8.0 : w;
             if (o->krylov == PEXP_KRYLOV_SAI) {
                 timed(c, PEXP_KC_SAI, (double)nv * n * (w + wout),
-                      [&] { launch_sai_solve_lo<T>(od, sai, d_xin, d_xlo, d_yout, d_ylo, nv, sai_scr, st, d_skip); });
+                      [&] { launch_sai_solve_lo<T>(od, sai, d_xin, nullptr, d_yout, d_ylo, nv, sai_scr, st, d_skip); });
             } else {
                 timed(c, PEXP_KC_STENCIL, (double)nv * n * (w + w), [&] { launch_stencil_ptrs<T>(od, d_xin, d_yout, nv, 0, st); });
                 for (const auto& W : act)
@@ -537,9 +533,7 @@ struct Solver {
                 t.V = W.V; t.Wh = Wn; t.Wl = W.Wlo; t.ld = n; t.p = p;
                 t.conv = wi + (size_t)W.w * L.istride + WI_CONV;
                 t.hm = D(W.w) + L.off_out1; t.ldh = p;                         // h1 from the projection pass
-                t.Vlo = (step == 1) ? W.V1lo : W.Vklo;                         // low parts of the newest block
                 u1[a] = t;
-                t.Vlo = nullptr;
                 t.hm = D(W.w) + L.off_T; t.ldh = W.b;                          // W <- W T1, h2 = V^T W
                 u3[a] = t;
                 t.hm = D(W.w) + L.off_h2; t.ldh = p;                           // h2 summed from the partials
@@ -548,7 +542,6 @@ struct Solver {
                 t.Wh = Wn; t.Wl = W.Wlo; t.ld = n; t.p = W.b; t.hm = D(W.w) + L.off_T; t.ldh = W.b;
                 t.conv = wi + (size_t)W.w * L.istride + WI_CONV;
                 t.out = Wn;
-                t.outlo = W.Vklo;
                 u4[a] = t;                                                     // final: W T2 rounded into the slot
                 wl2[a] = W.w;
             }
@@ -1044,15 +1037,14 @@ int solve_linear_typed(pexp_ctx* c, const pexp_operator* op, const pexp_options*
         for (int j = 0; j < P; ++j)
             if (mj[j] > 0)
                 need += align_up(sizeof(T) * (size_t)n * mj[j] * (S.kmax + 1)) + align_up(sizeof(T) * (size_t)n * (L.ycols - 1) * mj[j]) +
-                        (std::is_same<T, float>::value ? 3 * align_up(sizeof(float) * (size_t)n * mj[j]) : 0);
+                        (std::is_same<T, float>::value ? 2 * align_up(sizeof(float) * (size_t)n * mj[j]) : 0);
         need += (size_t)P * align_up(sizeof(T) * (size_t)n * (S.kmax + 1));   // homogeneous bases
-        need += align_up(sizeof(T) * (size_t)n * (L.ycols - 1)) + 4 * align_up(sizeof(float) * (size_t)n) + (size_t)(7 * P + 8) * kAlign;
+        need += align_up(sizeof(T) * (size_t)n * (L.ycols - 1)) + 3 * align_up(sizeof(float) * (size_t)n) + (size_t)(6 * P + 8) * kAlign;
         const int r = bs_reserve(c, need);
         if (r) throw StatusError{r};
     }
     std::vector<Win<T>> src;
     std::vector<T*> Vnh(P, nullptr);
-    std::vector<float*> src_lo(P, nullptr);
     for (int j = 0; j < P; ++j) {
         if (mj[j] == 0) continue;
         Win<T> W;
@@ -1062,9 +1054,7 @@ int solve_linear_typed(pexp_ctx* c, const pexp_operator* op, const pexp_options*
         W.S = as<T>(bs_alloc(c, sizeof(T) * (size_t)n * (L.ycols - 1) * W.b));
         W.Wlo = std::is_same<T, float>::value ? as<float>(bs_alloc(c, sizeof(float) * (size_t)n * W.b)) : nullptr;
         W.V1lo = std::is_same<T, float>::value ? as<float>(bs_alloc(c, sizeof(float) * (size_t)n * W.b)) : nullptr;
-        W.Vklo = std::is_same<T, float>::value ? as<float>(bs_alloc(c, sizeof(float) * (size_t)n * W.b)) : nullptr;
         Vnh[j] = W.V;
-        src_lo[j] = W.V1lo;
         src.push_back(W);
     }
     {
@@ -1157,6 +1147,8 @@ int solve_linear_typed(pexp_ctx* c, const pexp_operator* op, const pexp_options*
     }
 
     cudaEventRecord(c->evp[1], st);
+    // the Krylov steps take the rounded start block (see the note on the solve's input)
+    for (auto& W : src) W.V1lo = nullptr;
     // ---- nonhomogeneous parts, all subintervals in one batch
     int k_nh = 0;
     int notconv = S.run(src, KIND_SOURCE, &k_nh);
@@ -1177,11 +1169,8 @@ int solve_linear_typed(pexp_ctx* c, const pexp_operator* op, const pexp_options*
     int k_hom_max = 0, k_hom_sum = 0;
     T* Sh = as<T>(bs_alloc(c, sizeof(T) * (size_t)n * (L.ycols - 1)));
     float* Whlo = std::is_same<T, float>::value ? as<float>(bs_alloc(c, sizeof(float) * (size_t)n)) : nullptr;
-    float* Vhklo = std::is_same<T, float>::value ? as<float>(bs_alloc(c, sizeof(float) * (size_t)n)) : nullptr;
-    // low parts of the homogeneous start vectors, two buffers used alternately along the chain
-    float* Vh1lo_buf[2] = {nullptr, nullptr};
-    if (std::is_same<T, float>::value)
-        for (int k = 0; k < 2; ++k) Vh1lo_buf[k] = as<float>(bs_alloc(c, sizeof(float) * (size_t)n));
+    // low part of z while it is formed and normalised
+    float* Vh1lo_buf = std::is_same<T, float>::value ? as<float>(bs_alloc(c, sizeof(float) * (size_t)n)) : nullptr;
     for (int m = 1; m < P; ++m) {   // 0-based window m needs z at T_m (end of window m-1)
         Vh[m] = as<T>(bs_alloc(c, sizeof(T) * (size_t)n * (S.kmax + 1)));
         const int wprev = m - 1;
@@ -1195,40 +1184,38 @@ int solve_linear_typed(pexp_ctx* c, const pexp_operator* op, const pexp_options*
         }
         rt.r0 = sprev - 1; rt.ns = 1; rt.i0 = 0;
         const ReconTask<T>* drt = s3.put(&rt, 1);
-        TsTask<T> tg, tsc;
-        memset(&tg, 0, sizeof(tg));
-        tg.X = Vh[m]; tg.ldx = n; tg.p = 1; tg.Y = Vh[m]; tg.ldy = n; tg.q = 1; tg.q1 = 1;
-        tg.out = S.D(P + m) + L.off_gw;
+        TsTask<T> tsc;
         memset(&tsc, 0, sizeof(tsc));
         tsc.X = Vh[m]; tsc.ldx = n; tsc.p = 1; tsc.q = 1; tsc.Z = Vh[m]; tsc.ldz = n;
         tsc.Tm = S.D(P + m) + L.off_T; tsc.ldt = 1; tsc.alpha = 1.0; tsc.beta = 0.0;
-        const TsTask<T>* dtg = s3.put(&tg, 1);
+        UpdTask<T> zg;
+        memset(&zg, 0, sizeof(zg));
+        zg.Wh = Vh[m]; zg.ld = n; zg.p = 1;
+        const UpdTask<T>* dzg = s3.put(&zg, 1);
         const TsTask<T>* dts = s3.put(&tsc, 1);
         int wsel = P + m;
         const int* dw = s3.put(&wsel, 1);
-        // FP32 data: z = u_hat(T_m) and its normalisation in double-float (z is the
-        // dominant direction of the window; see the note at step 1 of the Krylov loop)
+        // FP32 data: z = u_hat(T_m) and its normalisation in double-float, then rounded into
+        // the start vector: the window's Krylov space and its projected matrix both use that
+        // rounded vector, so the rounding (white noise) is resolved by the projected problem
+        // instead of following the dynamics of the start vector
         const DfTask* dz = nullptr;
         int nz = 0;
         DfTask zt[3];
         memset(zt, 0, sizeof(zt));
-        float* Vh1lo = Vh1lo_buf[m & 1];
-        float* Vh1lo_prev = Vh1lo_buf[(m - 1) & 1];
+        float* Vh1lo = Vh1lo_buf;
         if constexpr (std::is_same<T, float>::value) {
-            // z carries the state from window to window: its dominant columns (the source
-            // start block and the previous homogeneous start vector) enter with their low
-            // parts, so the FP32 rounding of those columns is not re-applied every window
             int acc = 0;
             if (rt.K1 > 0) {
                 DfTask& t = zt[nz++];
-                t.Xh = rt.V1; t.Xl = src_lo[wprev]; t.pl = mj[wprev]; t.ldx = n; t.Zh = Vh[m]; t.Zl = Vh1lo; t.ldz = n;
+                t.Xh = rt.V1; t.ldx = n; t.Zh = Vh[m]; t.Zl = Vh1lo; t.ldz = n;
                 t.Tm = rt.C1 + (int64_t)rt.r0 * rt.ldc1; t.ldt = rt.K1; t.p = rt.K1; t.q = 1; t.alpha = 1.0;
                 t.accumulate = acc;
                 acc = 1;
             }
             if (rt.K2 > 0) {
                 DfTask& t = zt[nz++];
-                t.Xh = rt.V2; t.Xl = Vh1lo_prev; t.pl = 1; t.ldx = n; t.Zh = Vh[m]; t.Zl = Vh1lo; t.ldz = n;
+                t.Xh = rt.V2; t.ldx = n; t.Zh = Vh[m]; t.Zl = Vh1lo; t.ldz = n;
                 t.Tm = rt.C2 + (int64_t)rt.r0 * rt.ldc2; t.ldt = rt.K2;
                 t.p = rt.K2; t.q = 1; t.alpha = 1.0; t.accumulate = acc;
             }
@@ -1248,15 +1235,20 @@ int solve_linear_typed(pexp_ctx* c, const pexp_operator* op, const pexp_options*
         } else {
             launch_recon<T, T>(drt, 1, 1, n, nullptr, Vh[m], n, maxc, st); check_launch(c);
         }
-        launch_ts_tn<T>(dtg, 1, 1, 1, n, S.partial, st, 1); check_launch(c);
+        {
+            // ||z||^2 for the normalisation: streamed partials summed into the window's slab
+            const KGeom gz = krylov_geom(1, n);
+            launch_block_gram<T>(dzg, 1, n, gz, S.kpart[1], 1, st); check_launch(c);
+            launch_sum_parts(S.kpart[1], gz.nchunks, 1, 1, S.wd, L.stride, L.off_gw, dw, 1, nullptr, 0, 0, st);
+            check_launch(c);
+        }
         launch_start_orth(L, S.wd, S.wi, dw, 1, st); check_launch(c);
         if (dz) launch_ts_nn_df(dz + 2, 1, 1, n, st);
         else launch_ts_nn<T>(dts, 1, 1, n, st);
         check_launch(c);
         // a zero z (nothing to continue) is marked converged with an empty basis on the device
         std::vector<Win<T>> one(1);
-        one[0].w = P + m; one[0].V = Vh[m]; one[0].S = Sh; one[0].b = 1; one[0].Wlo = Whlo; one[0].V1lo = Vh1lo;
-        one[0].Vklo = Vhklo;
+        one[0].w = P + m; one[0].V = Vh[m]; one[0].S = Sh; one[0].b = 1; one[0].Wlo = Whlo; one[0].V1lo = nullptr;
         int kh = 0;
         notconv += S.run(one, KIND_HOM, &kh);
         const int kk = S.wi_host[(size_t)(P + m) * L.istride + WI_K];   // state after the last step
