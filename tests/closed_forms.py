@@ -79,6 +79,46 @@ def exact_piecewise_cubic(lam: np.ndarray, u0: np.ndarray, t: np.ndarray, window
     return out
 
 
+def exact_at_samples(lam: np.ndarray, u0: np.ndarray, t: np.ndarray, windows, keep) -> dict:
+    """exact_piecewise_cubic at the output indices `keep` only, for large n.
+
+    The samples are uniform (spacing h) and `windows` may be a generator consumed in time
+    order.  The per-interval recurrence of exact_piecewise_cubic is summed in closed form:
+    s intervals after the window start t_{i0},
+        y(t_{i0+s}) = e^{lam s h} y(t_{i0})
+                      + sum_l l! h^{l+1} phi_{l+1}(lam h) sum_r Uh[:, r] sum_{q<s} e^{lam (s-1-q) h} coef[q, l, r],
+    so each window costs a few (n, s) products and only the kept outputs are transformed
+    back.  Returns {index: u(t_index)}."""
+    keep = sorted(set(int(k) for k in keep))
+    h = t[1] - t[0]
+    ph = phi_functions(lam * h)
+    a = [math.factorial(l) * h ** (l + 1) * ph[l + 1] for l in range(4)]
+    yh = np.zeros(u0.size, complex)
+    res = {0: u0.copy()} if 0 in keep else {}
+
+    def advance(y, Uh, coef, s):
+        out = np.exp(lam * (s * h)) * y
+        if Uh is None or s == 0:
+            return out
+        E = np.empty((s, lam.size), complex)  # E[q] = e^{lam (s-1-q) h}
+        E[s - 1] = 1.0
+        for q in range(s - 2, -1, -1):
+            np.multiply(E[q + 1], ph[0], out=E[q])
+        for l in range(4):
+            out += a[l] * np.einsum("ir,ir->i", Uh, E.T @ coef[:s, l, :])
+        return out
+
+    for (i0, i1, U, coef) in windows:
+        Uh = np.fft.fft(U, axis=0) if U.shape[1] else None
+        for k in keep:
+            if i0 < k < i1:
+                res[k] = u0 + np.real(np.fft.ifft(advance(yh, Uh, coef, k - i0)))
+        yh = advance(yh, Uh, coef, i1 - i0)
+        if i1 in keep:
+            res[i1] = u0 + np.real(np.fft.ifft(yh))
+    return res
+
+
 def dense_exact(A: np.ndarray, u0: np.ndarray, t: np.ndarray, windows) -> np.ndarray:
     """Same as exact_piecewise_cubic for any dense A (n small): the exponential of the
     augmented matrix [[hA, hU, 0..], [0, 0, I, ..], ...] of size n + 4m on each sample
@@ -138,6 +178,36 @@ def pulse_series(x: np.ndarray, t: float, a: float, nu: float) -> np.ndarray:
         ak = 2 * (-1) ** k * math.comb(2 * N, N - k) / 4 ** N
         u = u + ak * np.cos(2 * k * np.pi * (x - a * t)) * math.exp(-(2 * k * np.pi) ** 2 * nu * t)
     return u
+
+
+def iter_windows_from_oracle_model(op, opts, u0, G, compress, spline, partition, workers: int = 8):
+    """Generator form of fourier_windows_from_oracle_model: windows come in time order,
+    built `workers` at a time on threads (the SVDs release the GIL), so at most that many
+    windows are held at once."""
+    import collections
+    from concurrent.futures import ThreadPoolExecutor
+    import oracle.pebk as ob
+    n_out, P, T = opts["n_out"], opts["P"], opts["T"]
+    t = np.arange(n_out) * (T / (n_out - 1))
+    idx = partition(n_out, P)
+    Au0 = ob.operator_matrix(op) @ u0
+
+    def window(j):
+        i0, i1 = idx[j - 1], idx[j]
+        Ghat = np.tile(Au0[:, None], (1, i1 - i0 + 1))
+        if G is not None:
+            Ghat = Ghat + G[i0:i1 + 1].T
+        U, C, _ = compress(Ghat, opts["svd_tol"], opts["max_rank"])
+        return (i0, i1, U, spline(t[i0:i1 + 1] - t[i0], C))
+
+    with ThreadPoolExecutor(max(1, workers)) as ex:
+        pending = collections.deque()
+        for j in range(1, P + 1):
+            pending.append(ex.submit(window, j))
+            if len(pending) >= max(1, workers):
+                yield pending.popleft().result()
+        while pending:
+            yield pending.popleft().result()
 
 
 def fourier_windows_from_oracle_model(op, opts, u0, G, compress, spline, partition):

@@ -46,6 +46,16 @@ def test_small_case_mixed(c):
     assert relerr_rows(Y, Yref) < MIXED_TOL, rep
 
 
+@pytest.mark.parametrize("precision,gate", [(0, 1e-12), (1, 1e-6)], ids=["fp64", "mixed"])
+def test_krylov_bases_orthonormal(c, precision, gate):
+    """max over every block Krylov basis of max|V^T V - I|, measured on the device."""
+    pr = wl.adv_diff_1d(n=1024, P=8, n_out=101, tol=1e-12, restart_len=30)
+    opts = dict(pr.opts, precision=precision, tol=1e-7 if precision else 1e-12, diagnostics=1)
+    Y, rep = run_linear(c, pr, opts, dtype="f32" if precision else "f64")
+    assert rep["rc"] == 0, rep
+    assert 0.0 <= rep["orth_max"] <= gate, rep["orth_max"]
+
+
 @pytest.mark.parametrize("P,n_out", [(1, 17), (3, 40), (7, 50), (16, 33)])
 def test_partitions_fp64(c, P, n_out):
     pr = wl.adv_diff_1d(n=2000, nu=5e-3, P=P, n_out=n_out, T=0.5, tol=1e-12, restart_len=30)

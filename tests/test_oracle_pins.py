@@ -239,6 +239,23 @@ def test_oracle_matches_circulant_closed_form_small_case():
     assert err < 2e-11, err
 
 
+def test_sampled_closed_form_equals_the_recurrence():
+    """The windowed closed sum (used at 2^20 points, where the recurrence is too slow)
+    against the per-interval recurrence it sums, at interior points and window ends."""
+    pr = wl.adv_diff_1d(n=512, nu=2e-3, P=5, n_out=61, tol=1e-12)
+    t, wins = cf.fourier_windows_from_oracle_model(pr.op, pr.opts, pr.u0, pr.G, ob.compress_source,
+                                                   ob.spline_segments, ob.partition)
+    lam = cf.circulant_eigs(pr.n, 1.0, 2e-3)
+    Yx = cf.exact_piecewise_cubic(lam, pr.u0, t, wins)
+    keep = [0, 3, 12, 13, 30, 47, 59, 60]
+    gen = cf.iter_windows_from_oracle_model(pr.op, pr.opts, pr.u0, pr.G, ob.compress_source,
+                                            ob.spline_segments, ob.partition)
+    got = cf.exact_at_samples(lam, pr.u0, t, gen, keep)
+    assert sorted(got) == keep
+    for k in keep:
+        assert np.linalg.norm(got[k] - Yx[k]) <= 1e-13 * np.linalg.norm(Yx[k]), k
+
+
 @pytest.mark.parametrize("krylov", [0, 1])
 def test_oracle_matches_dense_bruteforce_dirichlet(krylov):
     """P2: n <= 64, homogeneous Dirichlet, both Krylov operators, vs the full augmented expm."""
