@@ -355,12 +355,19 @@ __device__ __forceinline__ void sub_vh(const double (&x)[Q], const double* sh, i
 
 // =====================================================================================
 // k_update0: W <- W - V h1 (first Gram-Schmidt pass) and partial G = W^T W.
+// Each thread takes R rows per iteration and issues all their loads (W first, then the
+// columns of V in groups of Q) before using any, so a row costs one memory round trip.
 // =====================================================================================
+constexpr int kUpdQ = 8;   // columns of V per load group of the update kernels
+constexpr int kUpdR = 2;   // rows per thread per iteration of the update kernels
+template <int B>
+constexpr int kUpdCtas = B <= 2 ? 3 : 2;   // resident CTAs per SM the update kernels are built for
+
 template <typename T, int B>
-__global__ void __launch_bounds__(kThreads, 2) k_update0(const UpdTask<T>* __restrict__ tasks, int64_t n, int64_t rows,
+__global__ void __launch_bounds__(kThreads, kUpdCtas<B>) k_update0(const UpdTask<T>* __restrict__ tasks, int64_t n, int64_t rows,
                                                          int nchunks, int pstride, double* __restrict__ partial) {
     using CT = typename Coef<T>::type;
-    constexpr int Q = 16;
+    constexpr int Q = kUpdQ, R = kUpdR;
     constexpr int NE = B * B;
     extern __shared__ double sh_dyn[];
     CT* sh = reinterpret_cast<CT*>(sh_dyn);
@@ -377,42 +384,54 @@ __global__ void __launch_bounds__(kThreads, 2) k_update0(const UpdTask<T>* __res
     for (int i = 0; i < B; ++i)
 #pragma unroll
         for (int j = 0; j < B; ++j) g[i][j] = T(0);
-    for (int64_t base = r0; base < r1; base += kThreads) {
-        const int64_t r = base + threadIdx.x;
-        const bool act = r < r1;
-        T s[B], l[B];
+    for (int64_t base = r0; base < r1; base += (int64_t)R * kThreads) {
+        int64_t r[R];
+        bool act[R];
+        T wh[R][B], wl[R][B], s[R][B], l[R][B];
 #pragma unroll
-        for (int c = 0; c < B; ++c) s[c] = l[c] = T(0);
+        for (int u = 0; u < R; ++u) {
+            r[u] = base + (int64_t)u * kThreads + threadIdx.x;
+            act[u] = r[u] < r1;
+#pragma unroll
+            for (int c = 0; c < B; ++c) {
+                wh[u][c] = act[u] ? tk.Wh[(int64_t)c * ld + r[u]] : T(0);
+                if constexpr (sizeof(T) == 4) wl[u][c] = act[u] ? tk.Wl[(int64_t)c * ld + r[u]] : 0.f;
+                s[u][c] = l[u][c] = T(0);
+            }
+        }
         for (int q0 = 0; q0 < p; q0 += Q) {
-            T x[Q];
+            T x[R][Q];
 #pragma unroll
-            for (int q = 0; q < Q; ++q) {
-                const int a = q0 + q;
-                x[q] = (act && a < p) ? ldg(tk.V + (int64_t)a * ld + r) : T(0);
-            }
-            sub_vh<Q, B>(x, sh, p, q0, s, l);
+            for (int u = 0; u < R; ++u)
+#pragma unroll
+                for (int q = 0; q < Q; ++q)
+                    x[u][q] = (act[u] && q0 + q < p) ? ldg(tk.V + (int64_t)(q0 + q) * ld + r[u]) : T(0);
+#pragma unroll
+            for (int u = 0; u < R; ++u) sub_vh<Q, B>(x[u], sh, p, q0, s[u], l[u]);
         }
-        T wr[B];
 #pragma unroll
-        for (int c = 0; c < B; ++c) {
-            if constexpr (sizeof(T) == 4) {
-                const F2 wv = f2_add(F2{act ? tk.Wh[(int64_t)c * ld + r] : 0.f, act ? tk.Wl[(int64_t)c * ld + r] : 0.f},
-                                     F2{-s[c], -l[c]});
-                if (act) {
-                    tk.Wh[(int64_t)c * ld + r] = wv.hi;
-                    tk.Wl[(int64_t)c * ld + r] = wv.lo;
+        for (int u = 0; u < R; ++u) {
+            T wr[B];
+#pragma unroll
+            for (int c = 0; c < B; ++c) {
+                if constexpr (sizeof(T) == 4) {
+                    const F2 wv = f2_add(F2{wh[u][c], wl[u][c]}, F2{-s[u][c], -l[u][c]});
+                    if (act[u]) {
+                        tk.Wh[(int64_t)c * ld + r[u]] = wv.hi;
+                        tk.Wl[(int64_t)c * ld + r[u]] = wv.lo;
+                    }
+                    wr[c] = wv.hi + wv.lo;
+                } else {
+                    const T wv = wh[u][c] - s[u][c];
+                    if (act[u]) tk.Wh[(int64_t)c * ld + r[u]] = wv;
+                    wr[c] = wv;
                 }
-                wr[c] = wv.hi + wv.lo;
-            } else {
-                const T wv = (act ? tk.Wh[(int64_t)c * ld + r] : T(0)) - s[c];
-                if (act) tk.Wh[(int64_t)c * ld + r] = wv;
-                wr[c] = wv;
             }
+#pragma unroll
+            for (int i = 0; i < B; ++i)
+#pragma unroll
+                for (int j = 0; j < B; ++j) g[i][j] = fma(wr[i], wr[j], g[i][j]);
         }
-#pragma unroll
-        for (int i = 0; i < B; ++i)
-#pragma unroll
-            for (int j = 0; j < B; ++j) g[i][j] = fma(wr[i], wr[j], g[i][j]);
     }
 #pragma unroll
     for (int i = 0; i < B; ++i)
@@ -579,11 +598,12 @@ __global__ void __launch_bounds__(kThreads, 2) k_vtw(const UpdTask<T>* __restric
 // =====================================================================================
 // k_update1: W <- W - V h2 (second Gram-Schmidt pass) and partial G = W^T W.
 // h2 is at the orthogonality-error level, so V h2 is formed with FP32 products.
+// Loads as in k_update0: R rows per thread, W first, V in groups of Q columns.
 // =====================================================================================
 template <typename T, int B>
-__global__ void __launch_bounds__(kThreads, 2) k_update1(const UpdTask<T>* __restrict__ tasks, int64_t n, int64_t rows,
+__global__ void __launch_bounds__(kThreads, kUpdCtas<B>) k_update1(const UpdTask<T>* __restrict__ tasks, int64_t n, int64_t rows,
                                                       int nchunks, int pstride, double* __restrict__ partial) {
-    constexpr int Q = 16;
+    constexpr int Q = kUpdQ, R = kUpdR;
     constexpr int NE = B * B;
     extern __shared__ double sh_dyn[];
     T* sh = reinterpret_cast<T*>(sh_dyn);
@@ -601,43 +621,59 @@ __global__ void __launch_bounds__(kThreads, 2) k_update1(const UpdTask<T>* __res
     for (int i = 0; i < B; ++i)
 #pragma unroll
         for (int j = 0; j < B; ++j) g[i][j] = T(0);
-    for (int64_t base = r0; base < r1; base += kThreads) {
-        const int64_t r = base + threadIdx.x;
-        const bool act = r < r1;
-        T s[B];
+    for (int64_t base = r0; base < r1; base += (int64_t)R * kThreads) {
+        int64_t r[R];
+        bool act[R];
+        T wh[R][B], wl[R][B], s[R][B];
 #pragma unroll
-        for (int c = 0; c < B; ++c) s[c] = T(0);
-        for (int q0 = 0; q0 < p; q0 += Q) {
-            T x[Q];
+        for (int u = 0; u < R; ++u) {
+            r[u] = base + (int64_t)u * kThreads + threadIdx.x;
+            act[u] = r[u] < r1;
 #pragma unroll
-            for (int q = 0; q < Q; ++q) x[q] = (act && q0 + q < p) ? ldg(tk.V + (int64_t)(q0 + q) * ld + r) : T(0);
-#pragma unroll
-            for (int c = 0; c < B; ++c)
-#pragma unroll
-                for (int q = 0; q < Q; ++q)
-                    if (q0 + q < p) s[c] = fma(x[q], sh[(q0 + q) + c * p], s[c]);
-        }
-        T wr[B];
-#pragma unroll
-        for (int c = 0; c < B; ++c) {
-            if constexpr (sizeof(T) == 4) {
-                const F2 wv = f2_add(F2{act ? tk.Wh[(int64_t)c * ld + r] : 0.f, act ? tk.Wl[(int64_t)c * ld + r] : 0.f},
-                                     F2{-s[c], 0.f});
-                if (act) {
-                    tk.Wh[(int64_t)c * ld + r] = wv.hi;
-                    tk.Wl[(int64_t)c * ld + r] = wv.lo;
-                }
-                wr[c] = wv.hi + wv.lo;
-            } else {
-                const T wv = (act ? tk.Wh[(int64_t)c * ld + r] : T(0)) - s[c];
-                if (act) tk.Wh[(int64_t)c * ld + r] = wv;
-                wr[c] = wv;
+            for (int c = 0; c < B; ++c) {
+                wh[u][c] = act[u] ? tk.Wh[(int64_t)c * ld + r[u]] : T(0);
+                if constexpr (sizeof(T) == 4) wl[u][c] = act[u] ? tk.Wl[(int64_t)c * ld + r[u]] : 0.f;
+                s[u][c] = T(0);
             }
         }
+        for (int q0 = 0; q0 < p; q0 += Q) {
+            T x[R][Q];
 #pragma unroll
-        for (int i = 0; i < B; ++i)
+            for (int u = 0; u < R; ++u)
 #pragma unroll
-            for (int j = 0; j < B; ++j) g[i][j] = fma(wr[i], wr[j], g[i][j]);
+                for (int q = 0; q < Q; ++q)
+                    x[u][q] = (act[u] && q0 + q < p) ? ldg(tk.V + (int64_t)(q0 + q) * ld + r[u]) : T(0);
+#pragma unroll
+            for (int u = 0; u < R; ++u)
+#pragma unroll
+                for (int c = 0; c < B; ++c)
+#pragma unroll
+                    for (int q = 0; q < Q; ++q)
+                        if (q0 + q < p) s[u][c] = fma(x[u][q], sh[(q0 + q) + c * p], s[u][c]);
+        }
+#pragma unroll
+        for (int u = 0; u < R; ++u) {
+            T wr[B];
+#pragma unroll
+            for (int c = 0; c < B; ++c) {
+                if constexpr (sizeof(T) == 4) {
+                    const F2 wv = f2_add(F2{wh[u][c], wl[u][c]}, F2{-s[u][c], 0.f});
+                    if (act[u]) {
+                        tk.Wh[(int64_t)c * ld + r[u]] = wv.hi;
+                        tk.Wl[(int64_t)c * ld + r[u]] = wv.lo;
+                    }
+                    wr[c] = wv.hi + wv.lo;
+                } else {
+                    const T wv = wh[u][c] - s[u][c];
+                    if (act[u]) tk.Wh[(int64_t)c * ld + r[u]] = wv;
+                    wr[c] = wv;
+                }
+            }
+#pragma unroll
+            for (int i = 0; i < B; ++i)
+#pragma unroll
+                for (int j = 0; j < B; ++j) g[i][j] = fma(wr[i], wr[j], g[i][j]);
+        }
     }
 #pragma unroll
     for (int i = 0; i < B; ++i)
