@@ -107,7 +107,11 @@ typedef struct {
 } pexp_options;
 
 #define PEXP_DIAG_ORTH  1   /* measure the orthogonality of every Krylov basis */
-#define PEXP_DIAG_KTIME 2   /* time every kernel class with CUDA events (report.k_*) */
+#define PEXP_DIAG_KTIME 2   /* time kernel classes with CUDA events (report.k_*) */
+/* With PEXP_DIAG_KTIME, bits 8..15 of `diagnostics` choose the classes that are timed:
+ * bit 8 + PEXP_KC_x times class x; no bit set times every class.  Each timed launch
+ * costs two event records on the host, so timing one class perturbs a solve least. */
+#define PEXP_DIAG_KTIME_CLASS(cls) (1 << (8 + (cls)))
 
 /* kernel classes of report.k_ms / k_launches / k_bytes */
 #define PEXP_KC_SAI     0   /* shift-and-invert recurrence solve */

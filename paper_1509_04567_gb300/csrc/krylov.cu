@@ -118,9 +118,11 @@ struct Budget<double> {
 template <typename T, int B>
 struct Group {
     // columns per CTA of k_step_proj: FP32 data keep E and F as compensated (s, c) pairs
-    // (5 registers per column and block column), FP64 data plain sums (3 doubles)
-    static constexpr int step = sizeof(T) == 4 ? 16 / B : Budget<T>::acc / (3 * B);
+    // (5 registers per column and block column), FP64 data plain sums (3 doubles); FP32
+    // single columns take 8, which fits 3 CTAs per SM (80 registers)
+    static constexpr int step = sizeof(T) == 4 ? (B == 1 ? 8 : 16 / B) : Budget<T>::acc / (3 * B);
     static constexpr int vtw = Budget<T>::acc / (B + 1);     // columns per CTA of k_vtw
+    static constexpr int ctas = (sizeof(T) == 4 && B == 1) ? 3 : 2;   // CTAs per SM k_step_proj is built for
 };
 constexpr int kFuseP = 16;   // k_scale_proj keeps V^T W accumulators for up to 16 columns
 
@@ -176,7 +178,7 @@ __device__ __forceinline__ double cta_entry(const double* sred, int ne, int e) {
 // [z*PG, z*PG + PG) of V_{1:p}; group 0 also sums diag(W^T W).
 // =====================================================================================
 template <typename T, int B>
-__global__ void __launch_bounds__(kThreads, 2) k_step_proj(const StepTask<T>* __restrict__ tasks, int64_t n, int periodic,
+__global__ void __launch_bounds__(kThreads, Group<T, B>::ctas) k_step_proj(const StepTask<T>* __restrict__ tasks, int64_t n, int periodic,
                                                         int64_t rows, int nchunks, int pstride,
                                                         double* __restrict__ partial) {
     constexpr int PG = Group<T, B>::step;
@@ -895,11 +897,13 @@ __global__ void __launch_bounds__(kThreads) k_source_gram(const T* const* __rest
 // launchers
 // =====================================================================================
 KGeom krylov_geom(int ntasks, int64_t n) {
-    // 2048 .. 8192 rows per CTA, and at least ~8 CTAs per SM in total where n allows
+    // 1024 .. 8192 rows per CTA; batches of many tasks take the 8192-row floor, and a
+    // single task (one window of the homogeneous chain) is cut into 3 chunks per SM, so
+    // that its launches run in one wave at the 3 CTAs per SM its kernels are built for
     KGeom g;
     const int64_t lo = std::max<int64_t>(1, (n + 8191) / 8192);
-    const int64_t hi = std::max<int64_t>(1, (n + 2047) / 2048);
-    const int64_t want = (8 * kNumSM + ntasks - 1) / std::max(1, ntasks);
+    const int64_t hi = std::max<int64_t>(1, (n + 1023) / 1024);
+    const int64_t want = (3 * kNumSM + ntasks - 1) / std::max(1, ntasks);
     const int64_t ch = std::min(std::max(want, lo), hi);
     g.rows = (n + ch - 1) / ch;
     g.rows = (g.rows + kTile - 1) / kTile * kTile;
@@ -908,7 +912,7 @@ KGeom krylov_geom(int ntasks, int64_t n) {
 }
 
 size_t krylov_partial_slots(int ntasks_max, int64_t n) {
-    // ntasks * nchunks(ntasks) <= ntasks * ceil(n / 8192) + 8 * kNumSM + ntasks for every ntasks <= ntasks_max
+    // ntasks * nchunks(ntasks) <= ntasks * ceil(n / 8192) + 3 * kNumSM + ntasks for every ntasks <= ntasks_max
     const int64_t lo = std::max<int64_t>(1, (n + 8191) / 8192);
     return (size_t)ntasks_max * (size_t)(lo + 1) + 8 * kNumSM + 64;
 }

@@ -37,6 +37,7 @@ using namespace pexp;
 // solve's stream, read back once the solve has completed.
 struct KTimer {
     bool on = false;
+    unsigned mask = 0xffu;   // timed classes (bit = PEXP_KC_*)
     std::vector<cudaEvent_t> pool;
     size_t used = 0;
     struct Rec {
@@ -53,8 +54,9 @@ struct KTimer {
         }
         return pool[used++];
     }
-    void reset(bool enable) {
+    void reset(bool enable, unsigned classes) {
         on = enable;
+        mask = classes ? classes : 0xffu;
         used = 0;
         recs.clear();
     }
@@ -211,7 +213,7 @@ struct Stage {
 // Time a launch sequence as kernel class `cls` moving `bytes` algorithmic bytes.
 template <typename F>
 void timed(pexp_ctx* c, int cls, double bytes, F&& f, cudaStream_t on = nullptr, bool on_set = false) {
-    if (!c->kt.on) {
+    if (!c->kt.on || !((c->kt.mask >> cls) & 1u)) {
         f();
         return;
     }
@@ -1490,7 +1492,7 @@ int pexp_solve_linear(pexp_ctx* c, const pexp_operator* op, const pexp_options* 
     if (rep) memset(rep, 0, sizeof(*rep));
     cudaSetDevice(c->device);
     c->launches = 0;
-    c->kt.reset((o->diagnostics & PEXP_DIAG_KTIME) != 0);
+    c->kt.reset((o->diagnostics & PEXP_DIAG_KTIME) != 0, ((unsigned)o->diagnostics >> 8) & 0xffu);
     cudaEventRecord(c->ev0, c->stream);
     int r = guarded([&] { return solve_linear_dispatch(c, op, o, y0_dev, G_dev, g_dtype, Y_dev, y_dtype, rep, 0); });
     cudaEventRecord(c->ev1, c->stream);

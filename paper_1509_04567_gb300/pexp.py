@@ -34,6 +34,13 @@ KRYLOV_POLY = 0
 KRYLOV_SAI = 1
 DIAG_ORTH = 1
 DIAG_KTIME = 2
+
+
+def DIAG_KTIME_CLASS(cls: int) -> int:
+    """diagnostics bit that restricts PEXP_DIAG_KTIME to kernel class `cls` (index into KC_NAMES)."""
+    return 1 << (8 + cls)
+
+
 KC_NAMES = ["sai", "stencil", "proj", "update", "small", "source", "recon", "other"]
 FP64 = 0
 MIXED = 1
