@@ -213,6 +213,9 @@ void launch_burgers_source(const OpDesc& op, const T* U, T* G, int nrows, int fo
 // Each recurrence is a scan of affine maps f(z) = a z + b: chunks of 2048
 // elements per CTA (8 per thread), a CTA-wide scan, and a circular sum over
 // chunk summaries for the carry into each chunk (terms decay like alpha^2048).
+// Three passes, each reading the input: forward chunk summaries; forward values
+// in registers -> backward chunk summaries (w is not stored); forward values
+// again (the same arithmetic, so the same w) -> backward values -> output.
 // =====================================================================================
 constexpr int kSaiThreads = 256;
 constexpr int kSaiPer = 8;
@@ -281,12 +284,6 @@ template <> struct SaiR<float> { using R = DF; };
 template <typename T, typename R> __device__ __forceinline__ T rto(R x);
 template <> __device__ __forceinline__ double rto<double, double>(double x) { return x; }
 template <> __device__ __forceinline__ float rto<float, DF>(DF x) { return x.hi + x.lo; }
-// Store a recurrence value: FP64 as is; FP32 as a (hi, lo) pair when a low-part
-// array is given (the working block keeps double-float precision), else rounded.
-template <typename T> __device__ __forceinline__ void store_r(T* y, T* ylo, int64_t k, double v) { y[k] = v; }
-template <typename T> __device__ __forceinline__ void store_r(T* y, T* ylo, int64_t k, DF v) {
-    if (ylo) { y[k] = v.hi; ylo[k] = v.lo; } else { y[k] = v.hi + v.lo; }
-}
 template <typename T, typename R> __device__ __forceinline__ R load_r(T hi, T lo);
 template <> __device__ __forceinline__ double load_r<double, double>(double hi, double lo) { return hi; }
 template <> __device__ __forceinline__ DF load_r<float, DF>(float hi, float lo) { return DF{hi, lo}; }
@@ -377,8 +374,45 @@ __device__ __forceinline__ void cta_affine_scan(R a, R b, bool reverse, R* sa, R
     __syncthreads();   // the shared arrays are reused by the next scan
 }
 
+// Loads and stores of a thread's kSaiPer consecutive elements: 16-byte vector
+// accesses when the run is whole and aligned, else element by element.
 template <typename T>
-__device__ __forceinline__ int sai_load(const T* __restrict__ x, int64_t n, int64_t start, T* vals) {
+__device__ __forceinline__ bool sai_vec_ok(const T* p, int64_t n, int64_t start) {
+    return start + kSaiPer <= n && ((reinterpret_cast<uintptr_t>(p + start) & 15u) == 0);
+}
+__device__ __forceinline__ void sai_vload(const float* p, float* v) {
+#pragma unroll
+    for (int j = 0; j < kSaiPer / 4; ++j) {
+        const float4 a = reinterpret_cast<const float4*>(p)[j];
+        v[4 * j] = a.x;
+        v[4 * j + 1] = a.y;
+        v[4 * j + 2] = a.z;
+        v[4 * j + 3] = a.w;
+    }
+}
+__device__ __forceinline__ void sai_vload(const double* p, double* v) {
+#pragma unroll
+    for (int j = 0; j < kSaiPer / 2; ++j) {
+        const double2 a = reinterpret_cast<const double2*>(p)[j];
+        v[2 * j] = a.x;
+        v[2 * j + 1] = a.y;
+    }
+}
+__device__ __forceinline__ void sai_vstore(float* p, const float* v) {
+#pragma unroll
+    for (int j = 0; j < kSaiPer / 4; ++j)
+        reinterpret_cast<float4*>(p)[j] = make_float4(v[4 * j], v[4 * j + 1], v[4 * j + 2], v[4 * j + 3]);
+}
+__device__ __forceinline__ void sai_vstore(double* p, const double* v) {
+#pragma unroll
+    for (int j = 0; j < kSaiPer / 2; ++j) reinterpret_cast<double2*>(p)[j] = make_double2(v[2 * j], v[2 * j + 1]);
+}
+template <typename T>
+__device__ __forceinline__ int sai_load(const T* x, int64_t n, int64_t start, T* vals) {
+    if (sai_vec_ok(x, n, start)) {
+        sai_vload(x + start, vals);
+        return kSaiPer;
+    }
     int cnt = 0;
 #pragma unroll
     for (int j = 0; j < kSaiPer; ++j) {
@@ -391,6 +425,32 @@ __device__ __forceinline__ int sai_load(const T* __restrict__ x, int64_t n, int6
         }
     }
     return cnt;
+}
+template <typename T>
+__device__ __forceinline__ void sai_store(T* y, int64_t n, int64_t start, int cnt, const T* vals) {
+    if (cnt == kSaiPer && sai_vec_ok(y, n, start)) {
+        sai_vstore(y + start, vals);
+        return;
+    }
+#pragma unroll
+    for (int j = 0; j < kSaiPer; ++j)
+        if (j < cnt) y[start + j] = vals[j];
+}
+// Split of a recurrence value into the stored pair: FP64 as is; FP32 as (hi, lo)
+// when a low-part array is given (the working block keeps double-float
+// precision), else rounded.
+__device__ __forceinline__ void split_r(double v, bool pair, double& h, double& l) {
+    h = v;
+    l = 0.0;
+}
+__device__ __forceinline__ void split_r(DF v, bool pair, float& h, float& l) {
+    if (pair) {
+        h = v.hi;
+        l = v.lo;
+    } else {
+        h = v.hi + v.lo;
+        l = 0.f;
+    }
 }
 
 template <typename R>
@@ -420,7 +480,9 @@ __global__ void __launch_bounds__(kSaiThreads) k_sai_fwd_ends(int64_t n, int nch
     if (xl) sai_load(xl, n, start, lows);
     const R al = rfrom<R>(alpha);
     R b = rfrom<R>(0.0);
-    for (int j = 0; j < cnt; ++j) b = rfma(al, b, load_r<T, R>(vals[j], xl ? lows[j] : T(0)));
+#pragma unroll
+    for (int j = 0; j < kSaiPer; ++j)
+        if (j < cnt) b = rfma(al, b, load_r<T, R>(vals[j], xl ? lows[j] : T(0)));
     R a = ipow(al, cnt);
     R ea, eb, ta, tb;
     cta_affine_scan<R>(a, b, false, sa, sb, ea, eb, ta, tb);
@@ -467,13 +529,32 @@ __device__ __forceinline__ double sai_carry_warp(const double* ends, const doubl
     return sum / (1.0 - rho_n);
 }
 
-// Pass 2: forward recurrence with carries -> w (written to Y); summaries of the
+// Forward values w of this thread's elements (cnt of them, registers): the local maps
+// composed over the CTA and the circular carry into the chunk.  Contains barriers.
+template <typename T, typename R>
+__device__ __forceinline__ void sai_forward_values(const T* vals, const T* lows, bool has_lo, int cnt, R al,
+                                                   double carry, R* sa, R* sb, R* wv) {
+    R b = rfrom<R>(0.0);
+#pragma unroll
+    for (int j = 0; j < kSaiPer; ++j)
+        if (j < cnt) b = rfma(al, b, load_r<T, R>(vals[j], has_lo ? lows[j] : T(0)));
+    R a = ipow(al, cnt);
+    R ea, eb, ta, tb;
+    cta_affine_scan<R>(a, b, false, sa, sb, ea, eb, ta, tb);
+    R w = rfma(ea, rfrom<R>(carry), eb);
+#pragma unroll
+    for (int j = 0; j < kSaiPer; ++j) {
+        if (j < cnt) w = rfma(al, w, load_r<T, R>(vals[j], has_lo ? lows[j] : T(0)));
+        wv[j] = w;
+    }
+}
+
+// Pass 2: forward values with carries (kept in registers) -> summaries of the
 // backward recurrence of w with zero carry from the right.
 template <typename T>
 __global__ void __launch_bounds__(kSaiThreads) k_sai_fwd_apply(int64_t n, int nch, double alpha, double beta,
                                                                double alpha_n, const T* const* __restrict__ Xp,
                                                                const T* const* __restrict__ Xlo,
-                                                               T* const* __restrict__ Yp, T* const* __restrict__ Ylo,
                                                                const double* __restrict__ fends,
                                                                const double* __restrict__ fdecays,
                                                                double* __restrict__ bends,
@@ -484,35 +565,26 @@ __global__ void __launch_bounds__(kSaiThreads) k_sai_fwd_apply(int64_t n, int nc
     __shared__ double carry_in;
     const int v = blockIdx.y, ch = blockIdx.x;
     if (skip && skip[v] && *skip[v]) return;
-    const T* x = Xp[v];
-    T* y = Yp[v];
-    T* ylo = Ylo ? Ylo[v] : nullptr;
     if (threadIdx.x < 32) {
         const double cv = sai_carry_warp(fends + (int64_t)v * nch, fdecays + (int64_t)v * nch, nch, ch, +1, alpha_n);
         if (threadIdx.x == 0) carry_in = cv;
     }
+    const T* x = Xp[v];
     const T* xl = Xlo ? Xlo[v] : nullptr;
     const int64_t start = (int64_t)ch * kSaiChunk + (int64_t)threadIdx.x * kSaiPer;
     T vals[kSaiPer], lows[kSaiPer];
     const int cnt = sai_load(x, n, start, vals);
     if (xl) sai_load(xl, n, start, lows);
-    const R al = rfrom<R>(alpha), be = rfrom<R>(beta);
-    R b = rfrom<R>(0.0);
-    for (int j = 0; j < cnt; ++j) b = rfma(al, b, load_r<T, R>(vals[j], xl ? lows[j] : T(0)));
-    R a = ipow(al, cnt);
-    R ea, eb, ta, tb;
-    cta_affine_scan<R>(a, b, false, sa, sb, ea, eb, ta, tb);  // contains __syncthreads: carry_in visible
-    R w = rfma(ea, rfrom<R>(carry_in), eb);
+    __syncthreads();   // carry_in
     R wv[kSaiPer];
-    for (int j = 0; j < cnt; ++j) {
-        w = rfma(al, w, load_r<T, R>(vals[j], xl ? lows[j] : T(0)));
-        wv[j] = w;
-        store_r<T>(y, ylo, start + j, w);
-    }
-    // backward summaries over this thread's w values (kept at full precision)
+    sai_forward_values<T, R>(vals, lows, xl != nullptr, cnt, rfrom<R>(alpha), carry_in, sa, sb, wv);
+    const R be = rfrom<R>(beta);
     R gb = rfrom<R>(0.0);
-    for (int j = cnt - 1; j >= 0; --j) gb = rfma(be, gb, wv[j]);
+#pragma unroll
+    for (int j = kSaiPer - 1; j >= 0; --j)
+        if (j < cnt) gb = rfma(be, gb, wv[j]);
     R ga = ipow(be, cnt);
+    R ea, eb, ta, tb;
     cta_affine_scan<R>(ga, gb, true, sa, sb, ea, eb, ta, tb);
     if (threadIdx.x == 0) {
         bends[(int64_t)v * nch + ch] = rdbl(tb);
@@ -520,45 +592,65 @@ __global__ void __launch_bounds__(kSaiThreads) k_sai_fwd_apply(int64_t n, int nc
     }
 }
 
-// Pass 3: backward recurrence with carries, scaled by 1/c, in place on Y.  The
-// intermediate w is re-read from Y in the data type; for FP32 data its rounding
-// (relative 6e-8, uncorrelated) is the only FP32 error left in the solve.
+// Pass 3: the forward values again (same inputs and arithmetic as pass 2, so the
+// same w), then the backward recurrence with carries, scaled by 1/c, into Y.
 template <typename T>
-__global__ void __launch_bounds__(kSaiThreads) k_sai_bwd_apply(int64_t n, int nch, double beta, double beta_n,
-                                                               double inv_c, T* const* __restrict__ Yp,
-                                                               T* const* __restrict__ Ylo,
+__global__ void __launch_bounds__(kSaiThreads) k_sai_bwd_apply(int64_t n, int nch, double alpha, double alpha_n,
+                                                               double beta, double beta_n, double inv_c,
+                                                               const T* const* __restrict__ Xp,
+                                                               const T* const* __restrict__ Xlo,
+                                                               T* const* __restrict__ Yp, T* const* __restrict__ Ylo,
+                                                               const double* __restrict__ fends,
+                                                               const double* __restrict__ fdecays,
                                                                const double* __restrict__ bends,
                                                                const double* __restrict__ bdecays,
                                                                const int* const* __restrict__ skip) {
     using R = typename SaiR<T>::R;
     __shared__ R sa[kSaiThreads], sb[kSaiThreads];
-    __shared__ double carry_in;
+    __shared__ double carry_f, carry_b;
     const int v = blockIdx.y, ch = blockIdx.x;
     if (skip && skip[v] && *skip[v]) return;
+    if (threadIdx.x < 32) {
+        const double cf = sai_carry_warp(fends + (int64_t)v * nch, fdecays + (int64_t)v * nch, nch, ch, +1, alpha_n);
+        const double cb = sai_carry_warp(bends + (int64_t)v * nch, bdecays + (int64_t)v * nch, nch, ch, -1, beta_n);
+        if (threadIdx.x == 0) {
+            carry_f = cf;
+            carry_b = cb;
+        }
+    }
+    const T* x = Xp[v];
+    const T* xl = Xlo ? Xlo[v] : nullptr;
     T* y = Yp[v];
     T* ylo = Ylo ? Ylo[v] : nullptr;
-    if (threadIdx.x < 32) {
-        const double cv = sai_carry_warp(bends + (int64_t)v * nch, bdecays + (int64_t)v * nch, nch, ch, -1, beta_n);
-        if (threadIdx.x == 0) carry_in = cv;
-    }
     const int64_t start = (int64_t)ch * kSaiChunk + (int64_t)threadIdx.x * kSaiPer;
     T vals[kSaiPer], lows[kSaiPer];
-    const int cnt = sai_load<T>(y, n, start, vals);
-    if (ylo) sai_load<T>(ylo, n, start, lows);
+    const int cnt = sai_load(x, n, start, vals);
+    if (xl) sai_load(xl, n, start, lows);
+    __syncthreads();   // carry_f, carry_b
     R wv[kSaiPer];
-    for (int j = 0; j < cnt; ++j) wv[j] = load_r<T, R>(vals[j], ylo ? lows[j] : T(0));
+    sai_forward_values<T, R>(vals, lows, xl != nullptr, cnt, rfrom<R>(alpha), carry_f, sa, sb, wv);
     const R be = rfrom<R>(beta);
     R gb = rfrom<R>(0.0);
-    for (int j = cnt - 1; j >= 0; --j) gb = rfma(be, gb, wv[j]);
+#pragma unroll
+    for (int j = kSaiPer - 1; j >= 0; --j)
+        if (j < cnt) gb = rfma(be, gb, wv[j]);
     R ga = ipow(be, cnt);
     R ea, eb, ta, tb;
     cta_affine_scan<R>(ga, gb, true, sa, sb, ea, eb, ta, tb);
-    R xv = rfma(ea, rfrom<R>(carry_in), eb);
+    R xv = rfma(ea, rfrom<R>(carry_b), eb);
     const R ic = rfrom<R>(inv_c);
-    for (int j = cnt - 1; j >= 0; --j) {
-        xv = rfma(be, xv, wv[j]);
-        store_r<T>(y, ylo, start + j, rmul(xv, ic));
+    T oh[kSaiPer], ol[kSaiPer];
+#pragma unroll
+    for (int j = kSaiPer - 1; j >= 0; --j) {
+        if (j < cnt) {
+            xv = rfma(be, xv, wv[j]);
+            split_r(rmul(xv, ic), ylo != nullptr, oh[j], ol[j]);
+        } else {
+            oh[j] = ol[j] = T(0);
+        }
     }
+    sai_store(y, n, start, cnt, oh);
+    if (ylo) sai_store(ylo, n, start, cnt, ol);
 }
 
 template <typename T>
@@ -579,9 +671,10 @@ void launch_sai_solve_lo(const OpDesc& op, const SaiCoef& cf, const T* const* X,
     double* bdec = bends + (size_t)nch * nvec;
     dim3 g(nch, nvec);
     k_sai_fwd_ends<T><<<g, kSaiThreads, 0, s>>>(n, nch, cf.alpha, X, Xlo, fends, fdec, skip);
-    k_sai_fwd_apply<T><<<g, kSaiThreads, 0, s>>>(n, nch, cf.alpha, cf.beta, cf.alpha_n, X, Xlo, Y, Ylo, fends, fdec,
-                                                  bends, bdec, skip);
-    k_sai_bwd_apply<T><<<g, kSaiThreads, 0, s>>>(n, nch, cf.beta, cf.beta_n, cf.inv_c, Y, Ylo, bends, bdec, skip);
+    k_sai_fwd_apply<T><<<g, kSaiThreads, 0, s>>>(n, nch, cf.alpha, cf.beta, cf.alpha_n, X, Xlo, fends, fdec, bends,
+                                                  bdec, skip);
+    k_sai_bwd_apply<T><<<g, kSaiThreads, 0, s>>>(n, nch, cf.alpha, cf.alpha_n, cf.beta, cf.beta_n, cf.inv_c, X, Xlo, Y,
+                                                  Ylo, fends, fdec, bends, bdec, skip);
 }
 
 // =====================================================================================
