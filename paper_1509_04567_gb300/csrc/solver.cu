@@ -83,9 +83,9 @@ struct pexp_ctx {
     cudaEvent_t slot_ev[16] = {};
     bool slot_busy[16] = {};
     int slot_next = 0;
-    int* flags_h = nullptr;  // pinned copy of the per-window int state (lookahead of the Krylov loop)
+    int* flags_h = nullptr;  // pinned copies of the per-window int state (lookahead of the Krylov loop)
     size_t flags_cap = 0;
-    cudaEvent_t flag_ev[2] = {nullptr, nullptr};
+    cudaEvent_t flag_ev[4] = {};   // one per pinned copy (kFlagBufs)
     // second stream: the projected solve of a Krylov step runs beside the Gram-Schmidt passes
     cudaStream_t s2 = nullptr;
     cudaEvent_t ev_sp = nullptr, ev_pj = nullptr;
@@ -119,6 +119,10 @@ constexpr size_t kAlign = 256;
 #endif
 constexpr size_t kStageBytes = 8u << 20;   // per half of the staging area
 constexpr int kSlots = 16;                   // ring slots over both halves
+constexpr int kFlagBufs = 4;                 // pinned copies of the window flags in flight
+constexpr int kLookahead = 1;                // steps between queueing a step and reading its flags
+static_assert(kLookahead + 1 <= kFlagBufs, "a flag copy is read before its buffer is reused");
+static_assert(std::extent<decltype(pexp_ctx::flag_ev)>::value == kFlagBufs, "one event per flag copy");
 
 struct OomError {};
 struct StatusError {
@@ -390,17 +394,15 @@ struct Solver {
         std::vector<Win<T>> act = ws;
         const int periodic = od.x.periodic;
         const size_t nint = wi_host.size();
-        if (c->flags_cap < 2 * nint) {
+        if (c->flags_cap < kFlagBufs * nint) {
             if (c->flags_h) cudaFreeHost(c->flags_h);
             c->flags_h = nullptr;
             c->flags_cap = 0;
-            if (cudaMallocHost(&c->flags_h, sizeof(int) * 2 * nint) != cudaSuccess) throw OomError();
-            c->flags_cap = 2 * nint;
+            if (cudaMallocHost(&c->flags_h, sizeof(int) * kFlagBufs * nint) != cudaSuccess) throw OomError();
+            c->flags_cap = kFlagBufs * nint;
         }
-        if (!c->flag_ev[0]) {
-            cudaEventCreateWithFlags(&c->flag_ev[0], cudaEventDisableTiming);
-            cudaEventCreateWithFlags(&c->flag_ev[1], cudaEventDisableTiming);
-        }
+        for (int k = 0; k < kFlagBufs; ++k)
+            if (!c->flag_ev[k]) cudaEventCreateWithFlags(&c->flag_ev[k], cudaEventDisableTiming);
         auto conv_of = [&](const Win<T>& W) { return wi + (size_t)W.w * L.istride + WI_CONV; };
         for (int step = 1; step <= kmax && !act.empty(); ++step) {
             const int na = (int)act.size();
@@ -488,13 +490,15 @@ struct Solver {
             // the step's projected solve must be done before its flags are read and before the
             // next step's projections overwrite the partial sums it reads
             cudaStreamWaitEvent(st, c->ev_pj, 0);
-            // flags of this step, read back without waiting; then the previous step's flags
-            int* fl = c->flags_h + (size_t)(step & 1) * nint;
+            // flags of this step, read back without waiting; then those of the step kLookahead
+            // before, so that the host prepares the next launches while the device runs this step
+            int* fl = c->flags_h + (size_t)(step % kFlagBufs) * nint;
             cudaMemcpyAsync(fl, wi, sizeof(int) * nint, cudaMemcpyDeviceToHost, st);
-            cudaEventRecord(c->flag_ev[step & 1], st);
-            if (step >= 2) {
-                cudaEventSynchronize(c->flag_ev[(step - 1) & 1]);
-                const int* F = c->flags_h + (size_t)((step - 1) & 1) * nint;
+            cudaEventRecord(c->flag_ev[step % kFlagBufs], st);
+            if (step > kLookahead) {
+                const int old = (step - kLookahead) % kFlagBufs;
+                cudaEventSynchronize(c->flag_ev[old]);
+                const int* F = c->flags_h + (size_t)old * nint;
                 std::vector<Win<T>> next;
                 for (auto& W : act)
                     if (!F[(size_t)W.w * L.istride + WI_CONV]) next.push_back(W);
@@ -1460,7 +1464,7 @@ int pexp_destroy(pexp_ctx* c) {
     for (int k = 0; k < kSlots; ++k)
         if (c->slot_ev[k]) cudaEventDestroy(c->slot_ev[k]);
     if (c->flags_h) cudaFreeHost(c->flags_h);
-    for (int k = 0; k < 2; ++k)
+    for (int k = 0; k < kFlagBufs; ++k)
         if (c->flag_ev[k]) cudaEventDestroy(c->flag_ev[k]);
     if (c->s2) {
         cudaStreamSynchronize(c->s2);
