@@ -112,6 +112,12 @@ typedef struct {
  * bit 8 + PEXP_KC_x times class x; no bit set times every class.  Each timed launch
  * costs two event records on the host, so timing one class perturbs a solve least. */
 #define PEXP_DIAG_KTIME_CLASS(cls) (1 << (8 + (cls)))
+/* With PEXP_DIAG_KTIME, bits 16..19 = k > 0 time a sample of about 1 in 2^k of the launches
+ * of the chosen classes, picked by a fixed pseudo-random sequence (so that no kernel of a
+ * repeating launch pattern is favoured); report.k_* then cover the sampled launches only.
+ * Events between the kernels of a Krylov step stop their launches from overlapping, so
+ * sampling keeps the timing from slowing the solve it measures. */
+#define PEXP_DIAG_KTIME_SAMPLE(k) ((k) << 16)
 
 /* kernel classes of report.k_ms / k_launches / k_bytes */
 #define PEXP_KC_SAI     0   /* shift-and-invert recurrence solve */

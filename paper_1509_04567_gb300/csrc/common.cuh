@@ -138,6 +138,33 @@ void launch_row_dots(const double* u, const T* G, int64_t n, int nrows, double* 
 
 int fail_cuda(cudaError_t e, const char* what, const char* file, int line);
 
+// Programmatic dependent launch for the kernels of a Krylov step, which run back to back
+// on one stream.  Such a kernel is launched with programmatic stream serialization, so
+// its launch may overlap the kernel before it; it calls pdl_entry() before its first
+// memory access: griddepcontrol.wait returns once the grids it depends on have completed
+// and their writes are visible (at once when it was launched without the attribute), then
+// griddepcontrol.launch_dependents lets the next kernel of the stream be launched.
+__device__ __forceinline__ void pdl_entry() {
+    asm volatile("griddepcontrol.wait;" ::: "memory");
+    asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+}
+
+template <typename... KArgs, typename... Args>
+inline void launch_pdl(void (*kernel)(KArgs...), dim3 grid, dim3 block, size_t smem, cudaStream_t s,
+                       Args&&... args) {
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = grid;
+    cfg.blockDim = block;
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = s;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    cudaLaunchKernelEx(&cfg, kernel, static_cast<Args&&>(args)...);
+}
+
 }  // namespace pexp
 
 #define PEXP_CUDA_TRY(expr)                                                                \

@@ -181,6 +181,7 @@ template <typename T, int B>
 __global__ void __launch_bounds__(kThreads, Group<T, B>::ctas) k_step_proj(const StepTask<T>* __restrict__ tasks, int64_t n, int periodic,
                                                         int64_t rows, int nchunks, int pstride,
                                                         double* __restrict__ partial) {
+    pdl_entry();
     constexpr int PG = Group<T, B>::step;
     constexpr int NE = 3 * PG * B + B;
     __shared__ double sred[kWarps * NE];
@@ -368,6 +369,7 @@ constexpr int kUpdCtas = B <= 2 ? 3 : 2;   // resident CTAs per SM the update ke
 template <typename T, int B>
 __global__ void __launch_bounds__(kThreads, kUpdCtas<B>) k_update0(const UpdTask<T>* __restrict__ tasks, int64_t n, int64_t rows,
                                                          int nchunks, int pstride, double* __restrict__ partial) {
+    pdl_entry();
     using CT = typename Coef<T>::type;
     constexpr int Q = kUpdQ, R = kUpdR;
     constexpr int NE = B * B;
@@ -487,6 +489,7 @@ template <typename T, int B>
 __global__ void __launch_bounds__(kThreads, 2) k_scale_proj(const UpdTask<T>* __restrict__ tasks, int64_t n,
                                                             int64_t rows, int nchunks, int pstride,
                                                             double* __restrict__ partial) {
+    pdl_entry();
     constexpr int Q = kFuseP;
     constexpr int NE = Q * B;
     using CT = typename Coef<T>::type;
@@ -605,6 +608,7 @@ __global__ void __launch_bounds__(kThreads, 2) k_vtw(const UpdTask<T>* __restric
 template <typename T, int B>
 __global__ void __launch_bounds__(kThreads, kUpdCtas<B>) k_update1(const UpdTask<T>* __restrict__ tasks, int64_t n, int64_t rows,
                                                       int nchunks, int pstride, double* __restrict__ partial) {
+    pdl_entry();
     constexpr int Q = kUpdQ, R = kUpdR;
     constexpr int NE = B * B;
     extern __shared__ double sh_dyn[];
@@ -695,6 +699,7 @@ template <typename T, int B>
 __global__ void __launch_bounds__(kThreads, 2) k_scale(const UpdTask<T>* __restrict__ tasks, int64_t n, int64_t rows,
                                                        int nchunks, int gramflag, int pstride,
                                                        double* __restrict__ partial) {
+    pdl_entry();
     constexpr int U = 4;
     constexpr int NE = B * B;
     using CT = typename Coef<T>::type;
@@ -825,6 +830,7 @@ __global__ void __launch_bounds__(kThreads) k_sum_parts(const double* __restrict
                                                         int ne, double* __restrict__ wd, int64_t stride, int64_t off,
                                                         const int* __restrict__ wins, const int* __restrict__ wi,
                                                         int istride, int conv_field) {
+    pdl_entry();
     if (wi && wi[(int64_t)wins[blockIdx.x] * istride + conv_field]) return;
     const Parts pp{part, nchunks, pstride};
     double* out = wd + (int64_t)wins[blockIdx.x] * stride + off;
@@ -933,7 +939,7 @@ void launch_step_proj(const StepTask<T>* tasks, int ntasks, int b, int p, int64_
     PEXP_B_DISPATCH(b, ({
         constexpr int PG = Group<T, BB>::step;
         dim3 grid(g.nchunks, ntasks, (p + PG - 1) / PG);
-        k_step_proj<T, BB><<<grid, kThreads, 0, s>>>(tasks, n, periodic, g.rows, g.nchunks, pstride, partial);
+        launch_pdl(k_step_proj<T, BB>, grid, dim3(kThreads), 0, s, tasks, n, periodic, g.rows, g.nchunks, pstride, partial);
     }));
 }
 
@@ -946,10 +952,10 @@ void launch_update(const UpdTask<T>* tasks, int ntasks, int b, int p, int64_t n,
     dim3 grid(g.nchunks, ntasks);
     if (mode == 0) {
         const size_t sm = (size_t)p * b * (sizeof(T) == 4 ? sizeof(float2) : sizeof(double)) + 16;
-        PEXP_B_DISPATCH(b, (k_update0<T, BB><<<grid, kThreads, sm, s>>>(tasks, n, g.rows, g.nchunks, pstride, partial)));
+        PEXP_B_DISPATCH(b, (launch_pdl(k_update0<T, BB>, grid, dim3(kThreads), sm, s, tasks, n, g.rows, g.nchunks, pstride, partial)));
     } else {
         const size_t sm = (size_t)p * b * sizeof(T) + 16;
-        PEXP_B_DISPATCH(b, (k_update1<T, BB><<<grid, kThreads, sm, s>>>(tasks, n, g.rows, g.nchunks, pstride, partial)));
+        PEXP_B_DISPATCH(b, (launch_pdl(k_update1<T, BB>, grid, dim3(kThreads), sm, s, tasks, n, g.rows, g.nchunks, pstride, partial)));
     }
 }
 
@@ -959,10 +965,10 @@ void launch_scale_proj(const UpdTask<T>* tasks, int ntasks, int b, int p, int64_
     if (ntasks <= 0) return;
     dim3 grid(g.nchunks, ntasks);
     if (proj_fused(p, b, sizeof(T))) {
-        PEXP_B_DISPATCH(b, (k_scale_proj<T, BB><<<grid, kThreads, 0, s>>>(tasks, n, g.rows, g.nchunks, pstride, partial)));
+        PEXP_B_DISPATCH(b, (launch_pdl(k_scale_proj<T, BB>, grid, dim3(kThreads), 0, s, tasks, n, g.rows, g.nchunks, pstride, partial)));
     } else {
         PEXP_B_DISPATCH(b, ({
-            k_scale<T, BB><<<grid, kThreads, 0, s>>>(tasks, n, g.rows, g.nchunks, 0, pstride, nullptr);
+            launch_pdl(k_scale<T, BB>, grid, dim3(kThreads), 0, s, tasks, n, g.rows, g.nchunks, 0, pstride, (double*)nullptr);
             constexpr int PG = Group<T, BB>::vtw;
             dim3 g3(g.nchunks, ntasks, (p + PG - 1) / PG);
             k_vtw<T, BB><<<g3, kThreads, 0, s>>>(tasks, n, g.rows, g.nchunks, pstride, partial);
@@ -975,13 +981,13 @@ void launch_scale(const UpdTask<T>* tasks, int ntasks, int b, int64_t n, int gra
                   int pstride, cudaStream_t s) {
     if (ntasks <= 0) return;
     dim3 grid(g.nchunks, ntasks);
-    PEXP_B_DISPATCH(b, (k_scale<T, BB><<<grid, kThreads, 0, s>>>(tasks, n, g.rows, g.nchunks, gram, pstride, partial)));
+    PEXP_B_DISPATCH(b, (launch_pdl(k_scale<T, BB>, grid, dim3(kThreads), 0, s, tasks, n, g.rows, g.nchunks, gram, pstride, partial)));
 }
 
 void launch_sum_parts(const double* part, int nchunks, int pstride, int ne, double* wd, int64_t stride, int64_t off,
                       const int* wins, int ntasks, const int* wi, int istride, int conv_field, cudaStream_t s, int e0) {
     if (ntasks <= 0 || ne <= 0) return;
-    k_sum_parts<<<ntasks, kThreads, 0, s>>>(part, nchunks, pstride, e0, ne, wd, stride, off, wins, wi, istride,
+    launch_pdl(k_sum_parts, dim3(ntasks), dim3(kThreads), 0, s, part, nchunks, pstride, e0, ne, wd, stride, off, wins, wi, istride,
                                             conv_field);
 }
 

@@ -455,6 +455,7 @@ void launch_start_orth(const WinLayout& L, double* wd, int* wi, const int* wins,
 // =====================================================================================
 __global__ void k_block_orth(WinLayout L, double* __restrict__ wd, int* __restrict__ wi, const int* __restrict__ wins,
                              int pass, int step, double defl, Parts gp) {
+    pdl_entry();
     const int w = wins[blockIdx.x];
     double* D = wd + (int64_t)w * L.stride;
     int* I = wi + (int64_t)w * L.istride;
@@ -539,7 +540,7 @@ __global__ void k_block_orth(WinLayout L, double* __restrict__ wd, int* __restri
 void launch_block_orth(const WinLayout& L, double* wd, int* wi, const int* wins, int nw, int pass, int step,
                        double defl, cudaStream_t s, Parts gp) {
     if (nw <= 0) return;
-    k_block_orth<<<nw, 32, 0, s>>>(L, wd, wi, wins, pass, step, defl, gp);
+    launch_pdl(k_block_orth, dim3(nw), dim3(32), 0, s, L, wd, wi, wins, pass, step, defl, gp);
 }
 
 // =====================================================================================

@@ -38,6 +38,15 @@ using namespace pexp;
 struct KTimer {
     bool on = false;
     unsigned mask = 0xffu;   // timed classes (bit = PEXP_KC_*)
+    unsigned sample = 0;     // time about 1 in 2^sample of the launches of those classes
+    uint32_t rng = 0;        // xorshift32 state of the sample choice (fixed seed per call)
+    bool pick() {
+        if (!sample) return true;
+        rng ^= rng << 13;
+        rng ^= rng >> 17;
+        rng ^= rng << 5;
+        return (rng & ((1u << sample) - 1u)) == 0;
+    }
     std::vector<cudaEvent_t> pool;
     size_t used = 0;
     struct Rec {
@@ -54,9 +63,11 @@ struct KTimer {
         }
         return pool[used++];
     }
-    void reset(bool enable, unsigned classes) {
+    void reset(bool enable, unsigned classes, unsigned sample_log2) {
         on = enable;
         mask = classes ? classes : 0xffu;
+        sample = sample_log2 < 16 ? sample_log2 : 15;
+        rng = 0x9e3779b9u;
         used = 0;
         recs.clear();
     }
@@ -217,7 +228,7 @@ struct Stage {
 // Time a launch sequence as kernel class `cls` moving `bytes` algorithmic bytes.
 template <typename F>
 void timed(pexp_ctx* c, int cls, double bytes, F&& f, cudaStream_t on = nullptr, bool on_set = false) {
-    if (!c->kt.on || !((c->kt.mask >> cls) & 1u)) {
+    if (!c->kt.on || !((c->kt.mask >> cls) & 1u) || !c->kt.pick()) {
         f();
         return;
     }
@@ -1496,7 +1507,8 @@ int pexp_solve_linear(pexp_ctx* c, const pexp_operator* op, const pexp_options* 
     if (rep) memset(rep, 0, sizeof(*rep));
     cudaSetDevice(c->device);
     c->launches = 0;
-    c->kt.reset((o->diagnostics & PEXP_DIAG_KTIME) != 0, ((unsigned)o->diagnostics >> 8) & 0xffu);
+    c->kt.reset((o->diagnostics & PEXP_DIAG_KTIME) != 0, ((unsigned)o->diagnostics >> 8) & 0xffu,
+                ((unsigned)o->diagnostics >> 16) & 0xfu);
     cudaEventRecord(c->ev0, c->stream);
     int r = guarded([&] { return solve_linear_dispatch(c, op, o, y0_dev, G_dev, g_dtype, Y_dev, y_dtype, rep, 0); });
     cudaEventRecord(c->ev1, c->stream);

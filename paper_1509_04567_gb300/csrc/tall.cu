@@ -468,6 +468,7 @@ __global__ void __launch_bounds__(kSaiThreads) k_sai_fwd_ends(int64_t n, int nch
                                                               double* __restrict__ ends,
                                                               double* __restrict__ decays,
                                                               const int* const* __restrict__ skip) {
+    pdl_entry();
     using R = typename SaiR<T>::R;
     __shared__ R sa[kSaiThreads], sb[kSaiThreads];
     const int v = blockIdx.y, ch = blockIdx.x;
@@ -560,6 +561,7 @@ __global__ void __launch_bounds__(kSaiThreads) k_sai_fwd_apply(int64_t n, int nc
                                                                double* __restrict__ bends,
                                                                double* __restrict__ bdecays,
                                                                const int* const* __restrict__ skip) {
+    pdl_entry();
     using R = typename SaiR<T>::R;
     __shared__ R sa[kSaiThreads], sb[kSaiThreads];
     __shared__ double carry_in;
@@ -605,6 +607,7 @@ __global__ void __launch_bounds__(kSaiThreads) k_sai_bwd_apply(int64_t n, int nc
                                                                const double* __restrict__ bends,
                                                                const double* __restrict__ bdecays,
                                                                const int* const* __restrict__ skip) {
+    pdl_entry();
     using R = typename SaiR<T>::R;
     __shared__ R sa[kSaiThreads], sb[kSaiThreads];
     __shared__ double carry_f, carry_b;
@@ -670,11 +673,12 @@ void launch_sai_solve_lo(const OpDesc& op, const SaiCoef& cf, const T* const* X,
     double* bends = fdec + (size_t)nch * nvec;
     double* bdec = bends + (size_t)nch * nvec;
     dim3 g(nch, nvec);
-    k_sai_fwd_ends<T><<<g, kSaiThreads, 0, s>>>(n, nch, cf.alpha, X, Xlo, fends, fdec, skip);
-    k_sai_fwd_apply<T><<<g, kSaiThreads, 0, s>>>(n, nch, cf.alpha, cf.beta, cf.alpha_n, X, Xlo, fends, fdec, bends,
-                                                  bdec, skip);
-    k_sai_bwd_apply<T><<<g, kSaiThreads, 0, s>>>(n, nch, cf.alpha, cf.alpha_n, cf.beta, cf.beta_n, cf.inv_c, X, Xlo, Y,
-                                                  Ylo, fends, fdec, bends, bdec, skip);
+    launch_pdl(k_sai_fwd_ends<T>, g, dim3(kSaiThreads), 0, s, n, nch, cf.alpha, X, Xlo, fends, fdec, skip);
+    launch_pdl(k_sai_fwd_apply<T>, g, dim3(kSaiThreads), 0, s, n, nch, cf.alpha, cf.beta, cf.alpha_n, X, Xlo, fends,
+               (const double*)fdec, bends, bdec, skip);
+    launch_pdl(k_sai_bwd_apply<T>, g, dim3(kSaiThreads), 0, s, n, nch, cf.alpha, cf.alpha_n, cf.beta, cf.beta_n,
+               cf.inv_c, X, Xlo, Y, Ylo, (const double*)fends, (const double*)fdec, (const double*)bends,
+               (const double*)bdec, skip);
 }
 
 // =====================================================================================

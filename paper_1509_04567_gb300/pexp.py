@@ -41,6 +41,11 @@ def DIAG_KTIME_CLASS(cls: int) -> int:
     return 1 << (8 + cls)
 
 
+def DIAG_KTIME_SAMPLE(k: int) -> int:
+    """diagnostics bits that make PEXP_DIAG_KTIME time about 1 in 2**k of the chosen launches."""
+    return k << 16
+
+
 KC_NAMES = ["sai", "stencil", "proj", "update", "small", "source", "recon", "other"]
 FP64 = 0
 MIXED = 1
