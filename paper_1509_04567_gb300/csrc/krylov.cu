@@ -607,7 +607,8 @@ __global__ void __launch_bounds__(kThreads, 2) k_vtw(const UpdTask<T>* __restric
 // =====================================================================================
 template <typename T, int B>
 __global__ void __launch_bounds__(kThreads, kUpdCtas<B>) k_update1(const UpdTask<T>* __restrict__ tasks, int64_t n, int64_t rows,
-                                                      int nchunks, int pstride, double* __restrict__ partial) {
+                                                      int nchunks, int pstride, double* __restrict__ partial,
+                                                      const double* __restrict__ hpart, int hstride) {
     pdl_entry();
     constexpr int Q = kUpdQ, R = kUpdR;
     constexpr int NE = B * B;
@@ -617,7 +618,18 @@ __global__ void __launch_bounds__(kThreads, kUpdCtas<B>) k_update1(const UpdTask
     const UpdTask<T> tk = tasks[blockIdx.y];
     if (tk.conv && *tk.conv) return;
     const int p = tk.p;
-    for (int e = threadIdx.x; e < p * B; e += kThreads) sh[e] = (T)tk.hm[(e % p) + (int64_t)(e / p) * tk.ldh];
+    if (hpart) {
+        // h2 straight from the chunk partials of k_scale_proj (p x B, column-major), summed
+        // in the fixed order of parts_sum_warp: every CTA gets the same coefficients, and
+        // the same ones that a separate summing kernel would have stored
+        const Parts hp{hpart, nchunks, hstride};
+        for (int e = threadIdx.x >> 5; e < p * B; e += kWarps) {
+            const double v = parts_sum_warp(hp, blockIdx.y, e);
+            if ((threadIdx.x & 31) == 0) sh[e] = (T)v;
+        }
+    } else {
+        for (int e = threadIdx.x; e < p * B; e += kThreads) sh[e] = (T)tk.hm[(e % p) + (int64_t)(e / p) * tk.ldh];
+    }
     __syncthreads();
     const int64_t ld = tk.ld;
     const int64_t r0 = (int64_t)blockIdx.x * rows;
@@ -947,7 +959,7 @@ bool proj_fused(int p, int b, size_t tsize) { return p <= kFuseP && (size_t)p * 
 
 template <typename T>
 void launch_update(const UpdTask<T>* tasks, int ntasks, int b, int p, int64_t n, int mode, KGeom g, double* partial,
-                   int pstride, cudaStream_t s) {
+                   int pstride, cudaStream_t s, const double* hpart, int hstride) {
     if (ntasks <= 0) return;
     dim3 grid(g.nchunks, ntasks);
     if (mode == 0) {
@@ -955,7 +967,8 @@ void launch_update(const UpdTask<T>* tasks, int ntasks, int b, int p, int64_t n,
         PEXP_B_DISPATCH(b, (launch_pdl(k_update0<T, BB>, grid, dim3(kThreads), sm, s, tasks, n, g.rows, g.nchunks, pstride, partial)));
     } else {
         const size_t sm = (size_t)p * b * sizeof(T) + 16;
-        PEXP_B_DISPATCH(b, (launch_pdl(k_update1<T, BB>, grid, dim3(kThreads), sm, s, tasks, n, g.rows, g.nchunks, pstride, partial)));
+        PEXP_B_DISPATCH(b, (launch_pdl(k_update1<T, BB>, grid, dim3(kThreads), sm, s, tasks, n, g.rows, g.nchunks, pstride,
+                                       partial, hpart, hstride)));
     }
 }
 
@@ -1003,7 +1016,8 @@ void launch_source_gram(const T* const* X, const int* sv, int ntasks, int s_max,
 
 #define PEXP_KRY_INST(T)                                                                                           \
     template void launch_step_proj<T>(const StepTask<T>*, int, int, int, int64_t, int, KGeom, double*, int, cudaStream_t); \
-    template void launch_update<T>(const UpdTask<T>*, int, int, int, int64_t, int, KGeom, double*, int, cudaStream_t); \
+    template void launch_update<T>(const UpdTask<T>*, int, int, int, int64_t, int, KGeom, double*, int, cudaStream_t, \
+                                   const double*, int);                                                             \
     template void launch_scale<T>(const UpdTask<T>*, int, int, int64_t, int, KGeom, double*, int, cudaStream_t); \
     template void launch_scale_proj<T>(const UpdTask<T>*, int, int, int, int64_t, KGeom, double*, int, cudaStream_t); \
     template void launch_block_gram<T>(const UpdTask<T>*, int, int64_t, KGeom, double*, int, cudaStream_t); \

@@ -46,10 +46,12 @@ template <typename T>
 void launch_step_proj(const StepTask<T>* tasks, int ntasks, int b, int p, int64_t n, int periodic, KGeom g,
                       double* partial, int pstride, cudaStream_t s);
 // mode 0 and 1: W -= V h (h = tk.hm, p x b), partial G = W^T W (b x b); mode 0 subtracts
-// in double-float (FP32 data), mode 1 with FP32 products (second-pass coefficients)
+// in double-float (FP32 data), mode 1 with FP32 products (second-pass coefficients).
+// Mode 1 with hpart: h is summed by each CTA from the chunk partials at hpart (task-major,
+// stride hstride, g.nchunks chunks) instead of read from tk.hm; `partial` must not overlap them.
 template <typename T>
 void launch_update(const UpdTask<T>* tasks, int ntasks, int b, int p_max, int64_t n, int mode, KGeom g,
-                   double* partial, int pstride, cudaStream_t s);
+                   double* partial, int pstride, cudaStream_t s, const double* hpart = nullptr, int hstride = 0);
 // W <- W T (T = tk.hm, b x b) and partial h = V^T W (p x b) of the result
 template <typename T>
 void launch_scale_proj(const UpdTask<T>* tasks, int ntasks, int b, int p, int64_t n, KGeom g, double* partial,

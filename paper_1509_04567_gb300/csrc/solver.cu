@@ -553,7 +553,7 @@ struct Solver {
                 u1[a] = t;
                 t.hm = D(W.w) + L.off_T; t.ldh = W.b;                          // W <- W T1, h2 = V^T W
                 u3[a] = t;
-                t.hm = D(W.w) + L.off_h2; t.ldh = p;                           // h2 summed from the partials
+                t.hm = D(W.w) + L.off_h2; t.ldh = p;                           // unused: the pass sums h2 itself
                 u2[a] = t;
                 memset(&t, 0, sizeof(t));
                 t.Wh = Wn; t.Wl = W.Wlo; t.ld = n; t.p = W.b; t.hm = D(W.w) + L.off_T; t.ldh = W.b;
@@ -597,21 +597,18 @@ struct Solver {
                     check_launch(c);
                 });
             });
-            timed(c, PEXP_KC_SMALL, 0.0, [&] {
-                groups([&](int a0, int a1, int b) {
-                    launch_sum_parts(kpart[1] + (size_t)a0 * gb.nchunks * ps2, gb.nchunks, ps2, step * b * b, wd, L.stride,
-                                     L.off_h2, d_wl2 + a0, a1 - a0, wi, L.istride, WI_CONV, st);
-                    check_launch(c);
-                });
-            });
+            // the second pass sums h2 from the partials above itself; its Gram partials go after
+            // them in the same buffer (ps2 + psg <= the buffer's width per chunk slot)
+            const size_t off2 = (size_t)nb * gb.nchunks * ps2;
             timed(c, PEXP_KC_UPDATE, (double)n * (pb * w + 2 * bb * wl_), [&] {
                 groups([&](int a0, int a1, int b) {
-                    launch_update<T>(d2 + a0, a1 - a0, b, step * b, n, 1, gb, kpart[1] + (size_t)a0 * gb.nchunks * psg, psg, st);
+                    launch_update<T>(d2 + a0, a1 - a0, b, step * b, n, 1, gb, kpart[1] + off2 + (size_t)a0 * gb.nchunks * psg,
+                                     psg, st, kpart[1] + (size_t)a0 * gb.nchunks * ps2, ps2);
                     check_launch(c);
                 });
             });
             timed(c, PEXP_KC_SMALL, 0.0, [&] {
-                launch_block_orth(L, wd, wi, d_wl2, nb, 2, step, defl, st, Parts{kpart[1], gb.nchunks, psg});
+                launch_block_orth(L, wd, wi, d_wl2, nb, 2, step, defl, st, Parts{kpart[1] + off2, gb.nchunks, psg});
             });
             check_launch(c);
             timed(c, PEXP_KC_UPDATE, (double)n * bb * (wl_ + w), [&] {
