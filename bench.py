@@ -144,6 +144,24 @@ def cpu_sample(seconds_hint: float = 20.0) -> dict:
             "sample_seconds": t_nh + t_hom}
 
 
+def max_over_ranks(ms: float, dist, device) -> float:
+    """The slowest rank's time per step: every rank calls this after its timed region
+    (one process: the time itself)."""
+    if dist is None:
+        return ms
+    import torch
+    t = torch.tensor([ms], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    dist.barrier()
+    return float(t.item())
+
+
+def job_value(world: int, ms: float) -> float:
+    """Whole-job solves/s: each of the `world` ranks runs one full solve per step on its own
+    GPU (replicas, no data-path collective), and the slowest rank sets the pace."""
+    return world * 1e3 / ms
+
+
 def run_reference(args) -> None:
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
@@ -234,13 +252,8 @@ def main() -> None:
     ev1.record(stream)
     torch.cuda.synchronize(dev)
     ck = clocks.stop()
-    ms = ev0.elapsed_time(ev1) / args.steps
-    if dist is not None:
-        t = torch.tensor([ms], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
-        dist.barrier()
-    value = world * 1e3 / ms
+    ms = max_over_ranks(ev0.elapsed_time(ev1) / args.steps, dist, dev)
+    value = job_value(world, ms)
 
     # the dominant kernel class, timed live over the timed region, sets the roofline line
     k_ms = np.sum([r["k_ms"] for r in reps], axis=0)
