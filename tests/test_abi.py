@@ -67,3 +67,37 @@ def test_create_without_gpu_fails_cleanly(lib):
     h = ctypes.c_void_p()
     rc = lib.pexp_create(ctypes.byref(h), 0, None)
     assert rc != 0 and not h.value
+
+
+def _header_defines():
+    txt = open(os.path.join(ROOT, "include", "pexp.h")).read()
+    txt = re.sub(r"/\*.*?\*/", "", txt, flags=re.S)
+    consts = {m.group(1): int(m.group(2)) for m in re.finditer(r"#define\s+(PEXP_\w+)\s+(-?\d+)\s*$", txt, re.M)}
+    macros = {m.group(1): (m.group(2), m.group(3).strip())
+              for m in re.finditer(r"#define\s+(PEXP_\w+)\((\w+)\)\s+(.+)$", txt, re.M)}
+    return consts, macros
+
+
+def test_binding_constants_match_header():
+    from paper_1509_04567_gb300 import pexp
+    consts, macros = _header_defines()
+    for name, value in consts.items():
+        short = name[len("PEXP_"):]
+        if hasattr(pexp, short):
+            assert getattr(pexp, short) == value, name
+    for name in ("OK", "ERR_INVALID_ARG", "ERR_NOT_CONVERGED", "ERR_SCRATCH_LIMIT", "DIAG_ORTH", "DIAG_KTIME",
+                 "KRYLOV_SAI", "BC_DIRICHLET0", "MIXED", "F32"):
+        assert "PEXP_" + name in consts, name
+    # kernel-class indices name the entries of KC_NAMES
+    for name, value in consts.items():
+        if name.startswith("PEXP_KC_") and name != "PEXP_KC_COUNT":
+            assert pexp.KC_NAMES[value] == name[len("PEXP_KC_"):].lower(), name
+    assert len(pexp.KC_NAMES) == consts["PEXP_KC_COUNT"]
+    # the function-like diagnostics macros, evaluated for a few arguments
+    for mname, fn in (("PEXP_DIAG_KTIME_CLASS", pexp.DIAG_KTIME_CLASS), ("PEXP_DIAG_KTIME_SAMPLE", pexp.DIAG_KTIME_SAMPLE)):
+        arg, body = macros[mname]
+        for x in range(8):
+            assert eval(re.sub(r"\b%s\b" % arg, str(x), body)) == fn(x), (mname, x)
+    # the class and sample fields do not overlap each other or the flag bits
+    assert pexp.DIAG_KTIME_CLASS(7) < pexp.DIAG_KTIME_SAMPLE(1)
+    assert pexp.DIAG_KTIME_CLASS(0) > (pexp.DIAG_ORTH | pexp.DIAG_KTIME)
