@@ -9,17 +9,18 @@
 // cancellation, so FP32 products are accurate to FP32 relative to H, whereas
 // v_a^T (A v_i) would multiply the rounding of A v_i by ||A||.
 //
-// Kernels (CTA = 256 threads on a chunk of 2048-8192 rows of one window):
+// Kernels (CTA = 256 threads on a chunk of 1024-8192 rows of one window):
 //   k_step_proj  E = dV^T dV_i, F = V^T (S V_i - S^-1 V_i), h1 = V^T W, pre = diag(W^T W)
 //   k_update0    W <- W - V h1, then G = W^T W           (first Gram-Schmidt pass)
 //   k_scale_proj W <- W T1 (Cholesky QR), then h2 = V^T W
-//   k_update1    W <- W - V h2, then G = W^T W           (second pass)
+//   k_update1    W <- W - V h2, then G = W^T W           (second pass; each CTA sums
+//                h2 from the k_scale_proj partials itself)
 //   k_scale      W <- W T2; the final pass rounds W into the basis
 // i.e. block classical Gram-Schmidt with Cholesky QR, applied twice (BCGS2).
 //
 // Memory-level parallelism: every thread owns rows and issues the loads of all the
-// columns it needs for a row before using any of them, so a CTA keeps tens of KB in
-// flight; the +-1 neighbours of the stencil sums come from adjacent lanes (warps
+// columns it needs for a row before using any of them (the update passes take two rows
+// at a time, W first), so a CTA keeps tens of KB in flight; the +-1 neighbours of the stencil sums come from adjacent lanes (warps
 // overlap by one row on each side).  Sums: each thread accumulates FP32 (FP64 data:
 // FP64) products of its rows; warps reduce in the data type; the 8 warps and the
 // CTAs are combined in FP64 (one partial per CTA, summed in a fixed order by the
@@ -106,7 +107,8 @@ constexpr int kTile = 256;    // rows per shared-memory tile of k_source_gram
 constexpr int kHalo = 30;     // active rows per warp in k_step_proj (lanes 1..30)
 
 // per-thread accumulator budget (registers) of the projection kernels
-// (two CTAs of 256 threads per SM: at most 128 registers per thread)
+// (two CTAs of 256 threads per SM: at most 128 registers per thread; the kernels built
+// for three, at 80 registers, keep fewer columns per CTA)
 template <typename T>
 struct Budget {
     static constexpr int acc = 72;
