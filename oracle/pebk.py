@@ -30,7 +30,13 @@ Readings of points the paper leaves open (each is listed in the design doc):
     max_i ||u_{k+1}(t_i) - u_k(t_i)|| / max_i ||u_{k+1}(t_i)|| <= wr_tol.
   * restarting after restart_len block steps is not carried out: the Krylov
     space grows up to restart_len * (max_restarts + 1) block steps and a
-    subproblem that has not converged by then is reported as such.
+    subproblem that has not converged by then is reported as such;
+  * the averaged-Jacobian waveform relaxation (eq. ivp4 with the per-subinterval
+    average of eq. piecewiseJac) averages over each subinterval by the trapezoidal
+    rule on its samples; the Jacobian is linear in the state for the quadratic
+    Burgers term, so this is the Jacobian of the averaged iterate.  Its shifted
+    source (eq. sourceParallel) is read as A u0 + g_k - J_k u_hat_k: the printed
+    +J_k u0 would move the fixed point.
 
 Parity pins: see tests/test_oracle_pins.py (closed forms, dense brute force,
 invariants).  No function here is "parity unpinned".
@@ -400,6 +406,53 @@ def solve_linear(op: dict, opts: dict, u0: np.ndarray, G: np.ndarray | None,
     return Y, rep
 
 
+def solve_linear_piecewise(A_list: list, opts: dict, u0: np.ndarray, G_list: list, op: dict | None = None):
+    """Paraexp-EBK with one operator per subinterval (Sec. 2.4, eq. ivpSubproblem, whose
+    matrix A + J_k(t) is piecewise constant by eq. piecewiseJac).
+
+    A_list[j-1]: the sparse operator on subinterval j.  G_list[j-1]: the source at the
+    s_j samples of subinterval j, shape (s_j, n), both end samples included (a sample
+    shared by two subintervals has one value in each).  On subinterval j the shift
+    u = u0 + u_hat gives u_hat' = A_j u_hat + (A_j u0 + g_j) (eq. linivp_shift taken piece by
+    piece); subproblem j's nonhomogeneous part is solved with A_j and its homogeneous part
+    is carried through each later subinterval m with A_m; the parts add up (eq.
+    superposition, eq. updateSolution).  Returns (Y, report) with Y (n_out, n)."""
+    n = u0.size
+    T, P, n_out = opts["T"], opts["P"], opts["n_out"]
+    t = np.arange(n_out) * (T / (n_out - 1))
+    idx = partition(n_out, P)
+    kmax = opts["restart_len"] * (opts.get("max_restarts", 0) + 1)
+    tol = opts["tol"]
+    scale_ref = float(np.linalg.norm(u0))
+    gamma = opts.get("sai_gamma", 0.1) * T / P
+    kops = [KrylovOperator(op, sp.csr_matrix(A_list[j]), opts["krylov"], gamma) for j in range(P)]
+    Y = np.tile(u0, (n_out, 1))
+    rep = dict(m=[], k_nh=[], conv_nh=[], k_hom=[], conv_hom=[], boundaries=idx)
+    for j in range(1, P + 1):
+        i0, i1 = idx[j - 1], idx[j]
+        tau = t[i0:i1 + 1] - t[i0]
+        Ghat = (kops[j - 1].A @ u0)[:, None] + np.asarray(G_list[j - 1]).T
+        U, C, _ = compress_source(Ghat, opts["svd_tol"], opts["max_rank"])
+        rep["m"].append(U.shape[1])
+        if U.shape[1] == 0:
+            rep["k_nh"].append(0); rep["conv_nh"].append(True); rep["k_hom"].append([]); rep["conv_hom"].append([])
+            continue
+        V, Yp, info = ebk_nonhomogeneous(kops[j - 1], U, tau, spline_segments(tau, C), tol, scale_ref, kmax)
+        rep["k_nh"].append(info["steps"]); rep["conv_nh"].append(info["converged"])
+        Y[i0:i1 + 1] += Yp @ V.T
+        w = V @ Yp[-1]
+        khs, chs = [], []
+        for mm in range(j + 1, P + 1):
+            a0, a1 = idx[mm - 1], idx[mm]
+            Vh, Yh, ih = ebk_homogeneous(kops[mm - 1], w, t[a0:a1 + 1] - t[a0], tol, scale_ref, kmax)
+            khs.append(ih["steps"]); chs.append(ih["converged"])
+            seg = Yh @ Vh.T
+            Y[a0 + 1:a1 + 1] += seg[1:]
+            w = seg[-1].copy()
+        rep["k_hom"].append(khs); rep["conv_hom"].append(chs)
+    return Y, rep
+
+
 # --------------------------------------------------------------------------------------
 # Nonlinear problems: waveform relaxation (Sec. 2.3 eqs. source, ivp3; Sec. 2.4; Fig. 5)
 # --------------------------------------------------------------------------------------
@@ -425,6 +478,93 @@ def burgers_source(op: dict, Usamp: np.ndarray, form: int = 0) -> np.ndarray:
         else:
             out[r] = -u * (up - um) / (2.0 * dx)
     return out if Usamp.ndim == 2 else out[0]
+
+
+def burgers_jacobian(op: dict, ubar: np.ndarray, form: int = 0) -> sp.csr_matrix:
+    """The Jacobian d g / d u of burgers_source at the state ubar (the matrix inside the
+    integral of eq. jacobian / eq. piecewiseJac), as a sparse n x n matrix.
+
+    form 0, g_i = -(u_{i+1}^2 - u_{i-1}^2)/(4 dx): dg_i/du_{i+1} = -u_{i+1}/(2 dx),
+    dg_i/du_{i-1} = u_{i-1}/(2 dx).  form 1, g_i = -u_i (u_{i+1} - u_{i-1})/(2 dx):
+    dg_i/du_i = -(u_{i+1} - u_{i-1})/(2 dx), dg_i/du_{i+1} = -u_i/(2 dx),
+    dg_i/du_{i-1} = u_i/(2 dx).  Periodic indices wrap; homogeneous Dirichlet has zero
+    ghost values and no entries outside the mesh.  g is quadratic in u, so the Jacobian
+    is linear in ubar and its time average is the Jacobian of the time-averaged state."""
+    n = op["nx"]
+    dx = _mesh_width(n, op["Lx"], op["bc"])
+    periodic = op["bc"] == BC_PERIODIC
+    i = np.arange(n)
+    if periodic:
+        im, ip = (i - 1) % n, (i + 1) % n
+        has_m = has_p = np.ones(n, bool)
+    else:
+        im, ip = i - 1, i + 1
+        has_m, has_p = i >= 1, i <= n - 2
+    ub = np.asarray(ubar, dtype=float)
+    u_m = np.where(has_m, ub[np.clip(im, 0, n - 1)], 0.0)
+    u_p = np.where(has_p, ub[np.clip(ip, 0, n - 1)], 0.0)
+    rows, cols, vals = [], [], []
+    if form == 0:
+        rows += [i[has_p], i[has_m]]
+        cols += [ip[has_p], im[has_m]]
+        vals += [-u_p[has_p] / (2 * dx), u_m[has_m] / (2 * dx)]
+    else:
+        rows += [i, i[has_p], i[has_m]]
+        cols += [i, ip[has_p], im[has_m]]
+        vals += [-(u_p - u_m) / (2 * dx), -ub[has_p] / (2 * dx), ub[has_m] / (2 * dx)]
+    return sp.csr_matrix((np.concatenate(vals), (np.concatenate(rows), np.concatenate(cols))), shape=(n, n))
+
+
+def window_average(Uw: np.ndarray, tau: np.ndarray) -> np.ndarray:
+    """Time average over one subinterval of the sampled iterate Uw (s, n) at the offsets tau
+    (tau[0] = 0): the integral of eq. piecewiseJac by the trapezoidal rule on the samples."""
+    w = np.zeros(tau.size)
+    dt = np.diff(tau)
+    w[:-1] += 0.5 * dt
+    w[1:] += 0.5 * dt
+    return (w @ Uw) / tau[-1]
+
+
+def solve_burgers_jacobian(op: dict, opts: dict, u0: np.ndarray, forcing: np.ndarray | None = None,
+                           init: np.ndarray | None = None, callback=None):
+    """Waveform relaxation with the averaged-Jacobian correction (Sec. 2.3 eq. ivp4,
+    Sec. 2.4 eqs. piecewiseJac and ivpSubproblem).
+
+    Iterate k: g_k(t_i) = -u_k u_k,x (t_i) + f(t_i) (eq. source); on each subinterval j,
+    J_{k,j} = the Jacobian of g at the subinterval's time-averaged iterate (window_average);
+    then u_{k+1}' = (A + J_{k,j}) u_{k+1} + g_k - J_{k,j} u_k on subinterval j, u_{k+1}(0) = u0,
+    solved by solve_linear_piecewise.  At a fixed point the J terms cancel, so the limit is
+    the same as Picard's (solve_burgers); only the convergence speed changes.  The shifted
+    source of eq. sourceParallel is read as A u0 + g_k - J_{k,j} u_hat_k (its printed
+    +J_k u0 would move the fixed point).  Stops as solve_burgers does.  Returns (U, report)."""
+    n_out, P, T = opts["n_out"], opts["P"], opts["T"]
+    form = opts.get("burgers_form", 0)
+    t = np.arange(n_out) * (T / (n_out - 1))
+    idx = partition(n_out, P)
+    A = operator_matrix(op)
+    Uk = np.tile(u0, (n_out, 1)) if init is None else init.copy()
+    rep = dict(iters=0, deltas=[], converged=False)
+    for k in range(opts["wr_max_iter"]):
+        Gk = burgers_source(op, Uk, form)
+        if forcing is not None:
+            Gk = Gk + forcing
+        A_list, G_list = [], []
+        for j in range(1, P + 1):
+            i0, i1 = idx[j - 1], idx[j]
+            J = burgers_jacobian(op, window_average(Uk[i0:i1 + 1], t[i0:i1 + 1] - t[i0]), form)
+            A_list.append((A + J).tocsr())
+            G_list.append(Gk[i0:i1 + 1] - (J @ Uk[i0:i1 + 1].T).T)
+        Unew, _ = solve_linear_piecewise(A_list, opts, u0, G_list, op)
+        delta = float(np.max(np.linalg.norm(Unew - Uk, axis=1)) / np.max(np.linalg.norm(Unew, axis=1)))
+        rep["deltas"].append(delta)
+        rep["iters"] = k + 1
+        Uk = Unew
+        if callback is not None:
+            callback(k, Uk, delta)
+        if delta <= opts["wr_tol"]:
+            rep["converged"] = True
+            break
+    return Uk, rep
 
 
 def solve_burgers(op: dict, opts: dict, u0: np.ndarray, forcing: np.ndarray | None = None,

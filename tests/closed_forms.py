@@ -119,6 +119,29 @@ def exact_at_samples(lam: np.ndarray, u0: np.ndarray, t: np.ndarray, windows, ke
     return res
 
 
+def exact_piecewise_operators(lams: list, u0: np.ndarray, t: np.ndarray, windows) -> np.ndarray:
+    """Exact u(t_i) = u0 + u_hat(t_i) when subinterval j has its own circulant operator
+    (eigenvalues lams[j-1], FFT order) and source model (U_j, coef_j): u_hat is carried
+    across the subinterval ends and advanced in each subinterval, mode by mode, with that
+    subinterval's eigenvalues and phi-functions (the recurrence of exact_piecewise_cubic)."""
+    n_out = t.size
+    yh = np.zeros(u0.size, complex)
+    out = np.zeros((n_out, u0.size))
+    out[0] = u0
+    for lam, (i0, i1, U, coef) in zip(lams, windows):
+        Uh = np.fft.fft(U, axis=0) if U.shape[1] else None
+        for i in range(i0, i1):
+            h = t[i + 1] - t[i]
+            ph = phi_functions(lam * h)
+            yn = ph[0] * yh
+            if Uh is not None:
+                for l in range(4):
+                    yn = yn + math.factorial(l) * h ** (l + 1) * ph[l + 1] * (Uh @ coef[i - i0][l])
+            yh = yn
+            out[i + 1] = u0 + np.real(np.fft.ifft(yh))
+    return out
+
+
 def dense_exact(A: np.ndarray, u0: np.ndarray, t: np.ndarray, windows) -> np.ndarray:
     """Same as exact_piecewise_cubic for any dense A (n small): the exponential of the
     augmented matrix [[hA, hU, 0..], [0, 0, I, ..], ...] of size n + 4m on each sample

@@ -391,3 +391,104 @@ def test_burgers_wr_converges_to_fine_implicit_reference_and_conserves_mean():
     err = np.max(np.abs(U - sol.y.T))
     assert err < 2e-6, err
     np.testing.assert_allclose(U.mean(axis=1), u0.mean(), atol=1e-10)
+
+
+# ---------------------------------------------------------------- averaged-Jacobian WR (Sec. 2.3-2.4)
+@pytest.mark.parametrize("bc", [wl.BC_PERIODIC, wl.BC_DIRICHLET0])
+@pytest.mark.parametrize("form", [0, 1])
+def test_burgers_jacobian_matches_central_differences(bc, form):
+    """The Jacobian of eq. jacobian against central differences of the source itself
+    (exact up to rounding: the discrete nonlinearity is quadratic)."""
+    n = 12
+    op = wl.make_op(n, 1e-2, 0.0, bc=bc)
+    u = np.random.default_rng(7).standard_normal(n)
+    J = ob.burgers_jacobian(op, u, form).toarray()
+    eps = 1e-3
+    for c in range(n):
+        e = np.zeros(n)
+        e[c] = eps
+        col = (ob.burgers_source(op, u + e, form) - ob.burgers_source(op, u - e, form)) / (2 * eps)
+        np.testing.assert_allclose(J[:, c], col, rtol=0, atol=1e-9 * np.max(np.abs(J)))
+
+
+def test_window_average_is_the_trapezoidal_time_mean():
+    tau = np.array([0.0, 0.1, 0.3, 0.6])
+    Uw = np.stack([np.full(3, 1.0 + 2.0 * s) for s in tau])   # linear in time: trapezoid is exact
+    np.testing.assert_allclose(ob.window_average(Uw, tau), 1.0 + 2.0 * 0.3, rtol=1e-15)
+
+
+def test_piecewise_solver_with_one_operator_is_solve_linear():
+    pr = wl.adv_diff_1d(n=256, nu=5e-3, P=5, n_out=41, T=0.5, tol=1e-12, restart_len=30)
+    Y, _ = ob.solve_linear(pr.op, pr.opts, pr.u0, pr.G)
+    idx = ob.partition(41, 5)
+    A = ob.operator_matrix(pr.op)
+    Yp, _ = ob.solve_linear_piecewise([A] * 5, pr.opts, pr.u0, [pr.G[idx[j]:idx[j + 1] + 1] for j in range(5)], pr.op)
+    assert np.max(np.linalg.norm(Yp - Y, axis=1) / np.linalg.norm(Y, axis=1)) < 1e-12
+
+
+@pytest.mark.parametrize("krylov", [0, 1])
+def test_piecewise_solver_matches_per_window_circulant_closed_form(krylov):
+    """Subintervals with different advection speeds and viscosities (a piecewise-constant
+    A + J_k(t), eq. ivpSubproblem) against the exact per-mode solution with each
+    subinterval's own eigenvalues and the oracle's source model."""
+    n, P, n_out, T = 128, 4, 33, 0.4
+    x = wl.grid_1d(n)
+    t = wl.out_times(T, n_out)
+    u0 = np.sin(2 * np.pi * x) + 0.5 * np.cos(6 * np.pi * x)
+    G = np.cos(3 * t)[:, None] * np.sin(4 * np.pi * x)[None, :]
+    coeffs = [(1.0, 1e-2), (-0.5, 2e-2), (1.5, 5e-3), (0.25, 1e-2)]   # (a_j, nu_j)
+    ops = [wl.make_op(n, nu, a) for a, nu in coeffs]
+    A_list = [ob.operator_matrix(o) for o in ops]
+    idx = ob.partition(n_out, P)
+    G_list = [G[idx[j]:idx[j + 1] + 1] for j in range(P)]
+    opts = wl.default_opts(T=T, P=P, n_out=n_out, tol=1e-13, svd_tol=1e-13, max_rank=16, restart_len=40,
+                           krylov=krylov)
+    Y, rep = ob.solve_linear_piecewise(A_list, opts, u0, G_list, ops[0])
+    assert all(rep["conv_nh"]) and all(all(c) for c in rep["conv_hom"])
+    wins = []
+    for j in range(P):
+        i0, i1 = idx[j], idx[j + 1]
+        Ghat = (A_list[j] @ u0)[:, None] + G_list[j].T
+        U, C, _ = ob.compress_source(Ghat, opts["svd_tol"], opts["max_rank"])
+        wins.append((i0, i1, U, ob.spline_segments(t[i0:i1 + 1] - t[i0], C)))
+    lams = [cf.circulant_eigs(n, a, nu) for a, nu in coeffs]
+    Yx = cf.exact_piecewise_operators(lams, u0, t, wins)
+    err = np.max(np.linalg.norm(Y - Yx, axis=1) / np.linalg.norm(Yx, axis=1))
+    assert err < 1e-10, err
+
+
+def _burgers_case(T, nu, max_iter):
+    n = 64
+    op = wl.make_op(n, nu, 0.0)
+    u0 = 0.5 + np.sin(2 * np.pi * wl.grid_1d(n))
+    opts = wl.default_opts(T=T, P=4, n_out=41, tol=1e-13, svd_tol=1e-13, max_rank=16, wr_tol=1e-10,
+                           wr_max_iter=max_iter, restart_len=40)
+    A = ob.operator_matrix(op)
+    ref = sint.solve_ivp(lambda tt, u: A @ u + ob.burgers_source(op, u, 0), (0, T), u0,
+                         t_eval=wl.out_times(T, 41), method="Radau", rtol=1e-12, atol=1e-13).y.T
+    return op, opts, u0, ref
+
+
+def test_averaged_jacobian_wr_has_picards_limit_in_fewer_iterations():
+    """eq. ivp4: the J terms cancel at the fixed point, so the limit is Picard's (eq. ivp3),
+    and the averaged Jacobian (eq. piecewiseJac) takes fewer iterations to reach it."""
+    op, opts, u0, ref = _burgers_case(0.1, 5e-2, 60)
+    Up, rp = ob.solve_burgers(op, opts, u0)
+    Uj, rj = ob.solve_burgers_jacobian(op, opts, u0)
+    assert rp["converged"] and rj["converged"]
+    assert rj["iters"] * 2 <= rp["iters"], (rj["iters"], rp["iters"])
+    assert np.max(np.abs(Uj - Up)) < 1e-8
+    assert np.max(np.abs(Uj - ref)) < 2e-6
+    np.testing.assert_allclose(Uj.mean(axis=1), u0.mean(), atol=1e-10)
+
+
+def test_averaged_jacobian_wr_converges_where_picard_diverges():
+    """Longer interval, smaller viscosity: the Picard updates grow, the averaged-Jacobian
+    iteration converges to the semi-discrete solution (to the source model's accuracy)."""
+    op, opts, u0, ref = _burgers_case(0.3, 1e-2, 4)
+    _, rp = ob.solve_burgers(op, opts, u0)
+    assert rp["deltas"][3] > rp["deltas"][0], rp["deltas"]
+    opts = dict(opts, wr_max_iter=30)
+    Uj, rj = ob.solve_burgers_jacobian(op, opts, u0)
+    assert rj["converged"] and rj["iters"] <= 20, rj["deltas"]
+    assert np.max(np.abs(Uj - ref)) < 5e-5
