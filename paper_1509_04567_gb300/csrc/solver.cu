@@ -457,6 +457,7 @@ struct Solver {
             if (o->krylov == PEXP_KRYLOV_SAI) {
                 timed(c, PEXP_KC_SAI, (double)nv * n * (w + wout),
                       [&] { launch_sai_solve_lo<T>(od, sai, d_xin, nullptr, d_yout, d_ylo, nv, sai_scr, st, d_skip); });
+                c->launches += 2;   // the solve is three kernels; check_launch below counts one
             } else {
                 timed(c, PEXP_KC_STENCIL, (double)nv * n * (w + w), [&] { launch_stencil_ptrs<T>(od, d_xin, d_yout, nv, 0, st); });
                 for (const auto& W : act)
@@ -706,6 +707,7 @@ struct Solver {
             if (o->krylov == PEXP_KRYLOV_SAI) {
                 timed(c, PEXP_KC_SAI, (double)nv * n * (w + wout),
                       [&] { launch_sai_solve<T>(od, sai, d_xin, d_yout, d_ylo, nv, sai_scr, st); });
+                c->launches += 2;   // the solve is three kernels; check_launch below counts one
             } else {
                 launch_stencil_ptrs<T>(od, d_xin, d_yout, nv, 0, st);
                 for (const auto& W : act)
