@@ -101,3 +101,48 @@ def test_binding_constants_match_header():
     # the class and sample fields do not overlap each other or the flag bits
     assert pexp.DIAG_KTIME_CLASS(7) < pexp.DIAG_KTIME_SAMPLE(1)
     assert pexp.DIAG_KTIME_CLASS(0) > (pexp.DIAG_ORTH | pexp.DIAG_KTIME)
+
+
+C_PROGRAM = r"""
+#include <stdio.h>
+#include <string.h>
+#include "pexp.h"
+
+int main(void) {
+    pexp_options o;
+    pexp_report r;
+    pexp_operator op;
+    pexp_ctx* ctx = NULL;
+    memset(&r, 0, sizeof(r));
+    memset(&op, 0, sizeof(op));
+    pexp_default_options(&o);
+    if (o.restart_len != 20 || o.krylov != PEXP_KRYLOV_SAI) return 2;
+    if (strcmp(pexp_status_string(PEXP_OK), "ok") != 0) return 3;
+    if (pexp_solve_linear(ctx, &op, &o, NULL, NULL, PEXP_F64, NULL, PEXP_F64, &r) != PEXP_ERR_INVALID_ARG) return 4;
+    printf("%d %d\n", o.P, PEXP_DIAG_KTIME | PEXP_DIAG_KTIME_CLASS(PEXP_KC_UPDATE) | PEXP_DIAG_KTIME_SAMPLE(2));
+    return 0;
+}
+"""
+
+
+def test_header_is_c99_and_links_from_plain_c(lib, tmp_path):
+    """The boundary is a C ABI: a C99 program including only include/pexp.h compiles
+    without warnings, links against libpexp.so and calls it (no CUDA call is made:
+    the null context is rejected before any)."""
+    import shutil
+    import subprocess
+    cc = shutil.which("gcc") or shutil.which("cc")
+    if cc is None:
+        pytest.skip("no C compiler")
+    from paper_1509_04567_gb300 import pexp
+    src = tmp_path / "abi.c"
+    src.write_text(C_PROGRAM)
+    exe = tmp_path / "abi"
+    libdir = os.path.dirname(pexp.LIB_PATH)
+    r = subprocess.run([cc, "-std=c99", "-Wall", "-Wextra", "-Werror", "-pedantic", "-I", os.path.join(ROOT, "include"),
+                        str(src), "-o", str(exe), "-L", libdir, "-lpexp", "-Wl,-rpath," + libdir],
+                       capture_output=True, text=True)
+    assert r.returncode == 0, r.stderr
+    run = subprocess.run([str(exe)], capture_output=True, text=True, timeout=60)
+    assert run.returncode == 0, (run.returncode, run.stderr)
+    assert run.stdout.split() == ["1", str(2 | (1 << 11) | (2 << 16))]
