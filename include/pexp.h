@@ -217,8 +217,10 @@ int pexp_sai_solve(pexp_ctx* ctx, const pexp_operator* op, double gamma, const v
  * consecutive in memory (Pade-13 scaling and squaring, Higham 2005). N <= 128. */
 int pexp_small_expm(pexp_ctx* ctx, const double* M_dev, double* E_dev, int N, int batch);
 
-/* g(t_i) = -u u_x at every row of U (n_out rows of n), conservative (form 0) or
- * advective (form 1) central differences (Sec. 4; reading in the design doc). */
+/* g(t_i) = -u u_x at every row of U (n_out rows of n), conservative (form 0,
+ * -(u_{i+1}^2 - u_{i-1}^2)/(4 dx), which conserves the discrete mean) or advective
+ * (form 1, -u_i (u_{i+1} - u_{i-1})/(2 dx)) central differences (Sec. 4: the paper
+ * does not fix the discretisation of the nonlinear term). */
 int pexp_burgers_source(pexp_ctx* ctx, const pexp_operator* op, const void* U_dev, void* G_dev,
                         int n_rows, int dtype, int form);
 

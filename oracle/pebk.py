@@ -4,7 +4,7 @@ Paper: G.L. Kooij, M.A. Botchev, B.J. Geurts, "A block Krylov subspace
 implementation of the time-parallel Paraexp method and its extension for
 nonlinear partial differential equations", arXiv:1509.04567.
 
-Readings of points the paper leaves open (each is listed in the design doc):
+Readings of points the paper leaves open:
   * the projected IVP (the paper used MATLAB ode15s, Sec. 3) is solved exactly
     through the exponential of an augmented block matrix, which is exact for the
     piecewise-cubic source model;

@@ -1330,7 +1330,11 @@ int solve_linear_typed(pexp_ctx* c, const pexp_operator* op, const pexp_options*
         rep->orth_max = orth_max;
         const double w = (double)sizeof(T);
         double bytes = 0;
-        // algorithmic bytes: source reads, Krylov steps, reconstruction
+        // algorithmic bytes, each array counted once per pass the method needs: two passes
+        // over the source samples and the write of U per window; per Krylov step of a
+        // window, the basis reads of the projection and Gram-Schmidt passes (2k(k+1) columns
+        // over k steps) and ~14 column passes of the working block; the homogeneous chain
+        // likewise; the reconstruction below
         for (int j = 0; j < P; ++j) {
             const int s = pt.idx[j + 1] - pt.idx[j] + 1;
             bytes += 2.0 * n * s * w + (double)n * mj[j] * w;
