@@ -117,6 +117,40 @@ def travelling_pulses(n=1000, nu=1e-2, a=1.0, T=1.0, P=2, n_out=201, tol=1e-4,
                    u0=u0, G=G, meta=dict(exact=lambda tt: 0.5 - 0.5 * np.cos(10 * np.pi * (x - tt))))
 
 
+def smoothed_sawtooth(xi: np.ndarray, kmax: int = 100, eps: float = 0.1):
+    """The smoothed sawtooth of Sec. 4 (eq. modifiedSawtooth): u(xi) = 1/2 - sum_k
+    sin(2 pi k xi) Phi_k / (pi k), Phi_k = (pi k eps/2) / sinh(pi k eps/2), k = 1..kmax.
+    Returns (u, u', u'') at the points xi."""
+    k = np.arange(1, kmax + 1, dtype=np.float64)[:, None]
+    phi = (np.pi * k * eps / 2) / np.sinh(np.pi * k * eps / 2)
+    arg = 2 * np.pi * k * np.asarray(xi, dtype=np.float64)[None, :]
+    s, c = np.sin(arg), np.cos(arg)
+    u = 0.5 - np.sum(s * phi / (np.pi * k), axis=0)
+    du = -np.sum(2 * c * phi, axis=0)
+    d2u = np.sum(4 * np.pi * k * s * phi, axis=0)
+    return u, du, d2u
+
+
+def burgers_sawtooth(n=400, nu=1e-2, T=1.0, P=10, s=50, tol=1e-4, max_rank=12, kmax=100, eps=0.1,
+                     **kw) -> Problem:
+    """Burgers travelling wave of Sec. 4: the smoothed sawtooth moving right at speed 1/2,
+    u(x, t) = u_saw(x - t/2 + 1/2), kept alive by the forcing f = u_t + u u_x - nu u_xx
+    (evaluated analytically, so f = (u - 1/2) u' - nu u'').  s samples per subinterval
+    (shared ends): n_out = P (s - 1) + 1.  `meta["exact"]` gives u at the output times."""
+    x = grid_1d(n)
+    n_out = P * (s - 1) + 1
+    t = out_times(T, n_out)
+    U = np.zeros((n_out, n))
+    F = np.zeros((n_out, n))
+    for i, tt in enumerate(t):
+        u, du, d2u = smoothed_sawtooth(x - tt / 2 + 0.5, kmax, eps)
+        U[i] = u
+        F[i] = (u - 0.5) * du - nu * d2u
+    return Problem(name=f"burgers_sawtooth_n{n}", op=make_op(n, nu, 0.0),
+                   opts=default_opts(T=T, P=P, n_out=n_out, tol=tol, max_rank=max_rank, **kw),
+                   u0=U[0].copy(), G=F, meta=dict(exact=U))
+
+
 def burgers_1d(n=65536, nu=5e-3, T=0.5, P=32, n_out=513, tol=1e-8, svd_tol=1e-8,
                max_rank=16, wr_tol=1e-6, wr_max_iter=200, **kw) -> Problem:
     """Viscous Burgers u_t + u u_x = nu u_xx (Sec. 4), periodic, u0 = 0.5 + sin(2 pi x), no forcing."""

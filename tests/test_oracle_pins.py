@@ -492,3 +492,38 @@ def test_averaged_jacobian_wr_converges_where_picard_diverges():
     Uj, rj = ob.solve_burgers_jacobian(op, opts, u0)
     assert rj["converged"] and rj["iters"] <= 20, rj["deltas"]
     assert np.max(np.abs(Uj - ref)) < 5e-5
+
+
+def test_smoothed_sawtooth_is_the_sawtooth_series():
+    """eq. modifiedSawtooth: with no smoothing, sum_k sin(2 pi k xi)/(pi k) = 1/2 - xi on
+    (0, 1) (the sawtooth's Fourier series), so u = xi there; the returned derivatives match
+    central differences."""
+    xi = np.linspace(0.05, 0.95, 19)
+    u, _, _ = wl.smoothed_sawtooth(xi, kmax=20000, eps=1e-9)
+    np.testing.assert_allclose(u, xi, atol=2e-4)
+    xi = np.linspace(0.0, 1.0, 7)
+    h = 1e-5
+    u, du, d2u = wl.smoothed_sawtooth(xi)
+    up, dup, _ = wl.smoothed_sawtooth(xi + h)
+    um, dum, _ = wl.smoothed_sawtooth(xi - h)
+    np.testing.assert_allclose(du, (up - um) / (2 * h), rtol=1e-6, atol=1e-6)
+    np.testing.assert_allclose(d2u, (dup - dum) / (2 * h), rtol=1e-6, atol=1e-4)
+
+
+def test_burgers_travelling_sawtooth_error_is_second_order_in_dx():
+    """Sec. 4 travelling wave (Fig. error_differentdx): with the averaged-Jacobian WR the
+    error against the manufactured solution settles at a value set by the mesh, and halving
+    dx divides it by about 4 (second-order central differences).  Here T = 0.5 with the
+    paper's subinterval length 0.1, s = 50 samples, m = 12, tol 1e-4."""
+    floors = []
+    for n in (64, 128):
+        pr = wl.burgers_sawtooth(n=n, T=0.5, P=5, s=50, svd_tol=1e-6, wr_tol=1e-12, wr_max_iter=8, restart_len=40)
+        errs = []
+        ob.solve_burgers_jacobian(pr.op, pr.opts, pr.u0, forcing=pr.G,
+                                  callback=lambda k, Uk, d: errs.append(
+                                      np.max(np.linalg.norm(Uk - pr.meta["exact"], axis=1)
+                                             / np.linalg.norm(pr.meta["exact"], axis=1))))
+        assert errs[-1] < 0.05 * errs[0]
+        assert abs(errs[-1] - errs[-2]) < 0.05 * errs[-1]   # settled at the mesh's error
+        floors.append(errs[-1])
+    assert 3.2 < floors[0] / floors[1] < 5.0, floors
