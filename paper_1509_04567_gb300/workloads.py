@@ -151,6 +151,15 @@ def burgers_sawtooth(n=400, nu=1e-2, T=1.0, P=10, s=50, tol=1e-4, max_rank=12, k
                    u0=U[0].copy(), G=F, meta=dict(exact=U))
 
 
+def multiscale_solution(x: np.ndarray, t: float, k0: int):
+    """The multiscale Burgers solution of Sec. 4 (eq. multiscale_solution),
+    u = sin(2 pi x) sin(2 pi t) + sin(2 k0 pi x) sin(2 k0 pi t) / k0, and its time derivative."""
+    u = np.sin(2 * np.pi * x) * np.sin(2 * np.pi * t) + np.sin(2 * k0 * np.pi * x) * np.sin(2 * k0 * np.pi * t) / k0
+    ut = (2 * np.pi * np.sin(2 * np.pi * x) * np.cos(2 * np.pi * t)
+          + 2 * np.pi * np.sin(2 * k0 * np.pi * x) * np.cos(2 * k0 * np.pi * t))
+    return u, ut
+
+
 def burgers_1d(n=65536, nu=5e-3, T=0.5, P=32, n_out=513, tol=1e-8, svd_tol=1e-8,
                max_rank=16, wr_tol=1e-6, wr_max_iter=200, **kw) -> Problem:
     """Viscous Burgers u_t + u u_x = nu u_xx (Sec. 4), periodic, u0 = 0.5 + sin(2 pi x), no forcing."""

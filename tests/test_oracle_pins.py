@@ -527,3 +527,36 @@ def test_burgers_travelling_sawtooth_error_is_second_order_in_dx():
         assert abs(errs[-1] - errs[-2]) < 0.05 * errs[-1]   # settled at the mesh's error
         floors.append(errs[-1])
     assert 3.2 < floors[0] / floors[1] < 5.0, floors
+
+
+@pytest.mark.parametrize("k0", [4, 16])
+def test_burgers_multiscale_with_discrete_forcing_has_no_spatial_error(k0):
+    """Sec. 4 multiscale example, with the forcing of the Burgers efficiency runs: it is
+    built from the discrete operators (f = u_t - A u - g(u) at the grid points), so the
+    semi-discrete solution is the exact one and the WR error is time integration alone.
+    Its floor therefore does not change with dx, and widening the spectrum (k0 = 16) does
+    not slow the iterations down."""
+    floors, reach = [], []
+    for n in (64, 128):
+        P, s, T = 2, 33, 0.2
+        n_out = P * (s - 1) + 1
+        t = wl.out_times(T, n_out)
+        x = wl.grid_1d(n)
+        op = wl.make_op(n, 1e-2, 0.0)
+        A = ob.operator_matrix(op)
+        U = np.zeros((n_out, n))
+        F = np.zeros((n_out, n))
+        for i, tt in enumerate(t):
+            u, ut = wl.multiscale_solution(x, tt, k0)
+            U[i] = u
+            F[i] = ut - A @ u - ob.burgers_source(op, u, 0)
+        opts = wl.default_opts(T=T, P=P, n_out=n_out, tol=1e-8, svd_tol=1e-10, max_rank=12, wr_tol=1e-12,
+                               wr_max_iter=9, restart_len=40)
+        errs = []
+        ob.solve_burgers_jacobian(op, opts, U[0], forcing=F, callback=lambda k, Uk, d: errs.append(
+            np.max(np.linalg.norm(Uk - U, axis=1)) / np.max(np.linalg.norm(U, axis=1))))
+        floors.append(errs[-1])
+        reach.append(next(k for k, e in enumerate(errs) if e < 2 * errs[-1]) + 1)
+    assert max(floors) < 1e-5, floors
+    assert 1 / 1.3 < floors[0] / floors[1] < 1.3, floors
+    assert max(reach) <= 8, reach
