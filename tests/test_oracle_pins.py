@@ -560,3 +560,37 @@ def test_burgers_multiscale_with_discrete_forcing_has_no_spatial_error(k0):
     assert max(floors) < 1e-5, floors
     assert 1 / 1.3 < floors[0] / floors[1] < 1.3, floors
     assert max(reach) <= 8, reach
+
+
+def _sawtooth_discrete_errors(P, T, s, iters, n=64):
+    """WR error history on the travelling sawtooth with the discretely manufactured forcing
+    (semi-discrete solution exact), max over output times, relative to max ||u||."""
+    x = wl.grid_1d(n)
+    op = wl.make_op(n, 1e-2, 0.0)
+    A = ob.operator_matrix(op)
+    n_out = P * (s - 1) + 1
+    t = wl.out_times(T, n_out)
+    U = np.zeros((n_out, n))
+    F = np.zeros((n_out, n))
+    for i, tt in enumerate(t):
+        u, du, _ = wl.smoothed_sawtooth(x - tt / 2 + 0.5)
+        U[i] = u
+        F[i] = -0.5 * du - A @ u - ob.burgers_source(op, u, 0)   # u_t = -u'/2 for xi = x - t/2 + 1/2
+    opts = wl.default_opts(T=T, P=P, n_out=n_out, tol=1e-8, svd_tol=1e-10, max_rank=12, wr_tol=1e-14,
+                           wr_max_iter=iters, restart_len=40)
+    errs = []
+    ob.solve_burgers_jacobian(op, opts, U[0], forcing=F, callback=lambda k, Uk, d: errs.append(
+        np.max(np.linalg.norm(Uk - U, axis=1)) / np.max(np.linalg.norm(U, axis=1))))
+    return errs
+
+
+def test_burgers_iterations_grow_with_the_interval_and_shrink_with_the_subinterval():
+    """Sec. 4 (Fig. be1_history): with a fixed subinterval length (T = P dT) the WR error
+    after a fixed number of iterations grows with P, because the interval grows; with a
+    fixed T (dT = T/P, the samples kept) it falls with P, because the averaged Jacobian is a
+    better model on shorter subintervals (Sec. 4, parallel efficiency)."""
+    k = 4
+    fixed_dt = [_sawtooth_discrete_errors(P, 0.1 * P, 33, k)[-1] for P in (1, 2, 4)]
+    fixed_t = [_sawtooth_discrete_errors(P, 0.2, 64 // P + 1, k)[-1] for P in (1, 2, 4)]
+    assert fixed_dt[0] < fixed_dt[1] < fixed_dt[2], fixed_dt
+    assert fixed_t[0] > fixed_t[1] > fixed_t[2], fixed_t
