@@ -594,3 +594,27 @@ def test_burgers_iterations_grow_with_the_interval_and_shrink_with_the_subinterv
     fixed_t = [_sawtooth_discrete_errors(P, 0.2, 64 // P + 1, k)[-1] for P in (1, 2, 4)]
     assert fixed_dt[0] < fixed_dt[1] < fixed_dt[2], fixed_dt
     assert fixed_t[0] > fixed_t[1] > fixed_t[2], fixed_t
+
+
+@pytest.mark.parametrize("krylov", [0, 1])
+@pytest.mark.parametrize("bc", [wl.BC_PERIODIC, wl.BC_DIRICHLET0])
+def test_oracle_matches_dense_bruteforce_2d(krylov, bc):
+    """The 2D five-point operator (the large configuration's operator) in both Krylov
+    spaces, nx * ny = 48 <= 64 unknowns, against the exponential of the full augmented
+    matrix with the same source model."""
+    nx, ny = 8, 6
+    op = wl.make_op(nx, 2e-2, 0.7, dim=2, ny=ny, ay=-0.4, bc=bc)
+    xs = wl.grid_1d(nx, bc=bc)
+    ys = wl.grid_1d(ny, bc=bc)
+    X, Yg = np.meshgrid(xs, ys)                   # unknown (ix, iy) at index iy * nx + ix
+    u0 = (np.sin(np.pi * X) * np.cos(np.pi * Yg) + 0.3 * X * Yg).ravel()
+    t = wl.out_times(0.4, 17)
+    G = np.cos(4 * t)[:, None] * (X * (1 - Yg)).ravel()[None, :] + t[:, None] * np.sin(2 * np.pi * Yg).ravel()[None, :]
+    opts = wl.default_opts(T=0.4, P=4, n_out=17, tol=1e-13, svd_tol=1e-14, krylov=krylov, restart_len=40)
+    Y, rep = ob.solve_linear(op, opts, u0, G)
+    assert all(rep["conv_nh"]) and all(all(c) for c in rep["conv_hom"])
+    tt, wins = cf.fourier_windows_from_oracle_model(op, opts, u0, G, ob.compress_source,
+                                                    ob.spline_segments, ob.partition)
+    Yx = cf.dense_exact(ob.operator_matrix(op).toarray(), u0, tt, wins)
+    err = np.max(np.linalg.norm(Y - Yx, axis=1) / np.linalg.norm(Yx, axis=1))
+    assert err < 1e-10, err
