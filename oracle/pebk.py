@@ -27,7 +27,9 @@ Readings of points the paper leaves open:
     -(u_{i+1}^2 - u_{i-1}^2)/(4 dx) (burgers_form=0) or advective central form
     -u_i (u_{i+1} - u_{i-1})/(2 dx) (burgers_form=1); waveform relaxation is plain
     Picard iteration (eq. ivp3) stopped on the relative update
-    max_i ||u_{k+1}(t_i) - u_k(t_i)|| / max_i ||u_{k+1}(t_i)|| <= wr_tol.
+    max_i ||u_{k+1}(t_i) - u_k(t_i)|| / max_i ||u_{k+1}(t_i)|| <= wr_tol, or once that
+    update has grown in wr_diverge (default 3) successive iterations (divergence; the
+    paper states no rule for it).
   * restarting after restart_len block steps is not carried out: the Krylov
     space grows up to restart_len * (max_restarts + 1) block steps and a
     subproblem that has not converged by then is reported as such;
@@ -361,11 +363,7 @@ def solve_linear(op: dict, opts: dict, u0: np.ndarray, G: np.ndarray | None,
     rep = dict(m=[], sigma_ratio=[], k_nh=[], est_nh=[], conv_nh=[], k_hom=[], conv_hom=[], boundaries=idx)
     parts = {}
     # one shift-and-invert pole for all windows: gamma = sai_gamma * T / P
-    kop_all = KrylovOperator(op, A, opts["krylov"], opts.get("sai_gamma", 0.1) * T / P)
-
-    def kop_for(width):
-        return kop_all
-
+    kop = KrylovOperator(op, A, opts["krylov"], opts.get("sai_gamma", 0.1) * T / P)
     for j in js:
         i0, i1 = idx[j - 1], idx[j]
         tau = t[i0:i1 + 1] - t[i0]
@@ -383,7 +381,6 @@ def solve_linear(op: dict, opts: dict, u0: np.ndarray, G: np.ndarray | None,
             parts[j] = vj
             continue
         coef = spline_segments(tau, C)
-        kop = kop_for(t[i1] - t[i0])
         V, Yp, info = ebk_nonhomogeneous(kop, U, tau, coef, tol, scale_ref, kmax)
         rep["k_nh"].append(info["steps"]); rep["est_nh"].append(info["est"]); rep["conv_nh"].append(info["converged"])
         vj[i0:i1 + 1] = Yp @ V.T
@@ -392,8 +389,7 @@ def solve_linear(op: dict, opts: dict, u0: np.ndarray, G: np.ndarray | None,
         for mm in range(j + 1, P + 1):
             a0, a1 = idx[mm - 1], idx[mm]
             tau_h = t[a0:a1 + 1] - t[a0]
-            kh = kop_for(t[a1] - t[a0])
-            Vh, Yh, ih = ebk_homogeneous(kh, w, tau_h, tol, scale_ref, kmax)
+            Vh, Yh, ih = ebk_homogeneous(kop, w, tau_h, tol, scale_ref, kmax)
             khs.append(ih["steps"]); chs.append(ih["converged"])
             seg = Yh @ Vh.T
             vj[a0 + 1:a1 + 1] = seg[1:]
@@ -525,6 +521,18 @@ def window_average(Uw: np.ndarray, tau: np.ndarray) -> np.ndarray:
     return (w @ Uw) / tau[-1]
 
 
+def _wr_stop(deltas: list, opts: dict):
+    """Stopping rule of the waveform relaxation loop on the relative updates so far:
+    "converged" once the last one is <= wr_tol; "diverged" once the update has grown in
+    wr_diverge successive iterations (default 3; 0 never stops on growth); else None."""
+    if deltas[-1] <= opts["wr_tol"]:
+        return "converged"
+    q = opts.get("wr_diverge", 3)
+    if q > 0 and len(deltas) > q and all(deltas[-i] > deltas[-i - 1] for i in range(1, q + 1)):
+        return "diverged"
+    return None
+
+
 def solve_burgers_jacobian(op: dict, opts: dict, u0: np.ndarray, forcing: np.ndarray | None = None,
                            init: np.ndarray | None = None, callback=None):
     """Waveform relaxation with the averaged-Jacobian correction (Sec. 2.3 eq. ivp4,
@@ -543,7 +551,7 @@ def solve_burgers_jacobian(op: dict, opts: dict, u0: np.ndarray, forcing: np.nda
     idx = partition(n_out, P)
     A = operator_matrix(op)
     Uk = np.tile(u0, (n_out, 1)) if init is None else init.copy()
-    rep = dict(iters=0, deltas=[], converged=False)
+    rep = dict(iters=0, deltas=[], converged=False, diverged=False)
     for k in range(opts["wr_max_iter"]):
         Gk = burgers_source(op, Uk, form)
         if forcing is not None:
@@ -561,8 +569,9 @@ def solve_burgers_jacobian(op: dict, opts: dict, u0: np.ndarray, forcing: np.nda
         Uk = Unew
         if callback is not None:
             callback(k, Uk, delta)
-        if delta <= opts["wr_tol"]:
-            rep["converged"] = True
+        stop = _wr_stop(rep["deltas"], opts)
+        if stop is not None:
+            rep[stop] = True
             break
     return Uk, rep
 
@@ -577,7 +586,7 @@ def solve_burgers(op: dict, opts: dict, u0: np.ndarray, forcing: np.ndarray | No
     wr_max_iter iterations have been made.  Returns (U, report) with U (n_out, n)."""
     n_out = opts["n_out"]
     Uk = np.tile(u0, (n_out, 1)) if init is None else init.copy()
-    rep = dict(iters=0, deltas=[], converged=False)
+    rep = dict(iters=0, deltas=[], converged=False, diverged=False)
     for k in range(opts["wr_max_iter"]):
         Gk = burgers_source(op, Uk, opts.get("burgers_form", 0))
         if forcing is not None:
@@ -589,7 +598,8 @@ def solve_burgers(op: dict, opts: dict, u0: np.ndarray, forcing: np.ndarray | No
         Uk = Unew
         if callback is not None:
             callback(k, Uk, delta)
-        if delta <= opts["wr_tol"]:
-            rep["converged"] = True
+        stop = _wr_stop(rep["deltas"], opts)
+        if stop is not None:
+            rep[stop] = True
             break
     return Uk, rep

@@ -618,3 +618,24 @@ def test_oracle_matches_dense_bruteforce_2d(krylov, bc):
     Yx = cf.dense_exact(ob.operator_matrix(op).toarray(), u0, tt, wins)
     err = np.max(np.linalg.norm(Y - Yx, axis=1) / np.linalg.norm(Yx, axis=1))
     assert err < 1e-10, err
+
+
+def test_wr_stopping_rule():
+    """Waveform relaxation stops on a small update, or on an update that grew wr_diverge
+    times in a row (the paper gives no divergence rule); 0 disables the latter."""
+    o = dict(wr_tol=1e-6, wr_diverge=3)
+    assert ob._wr_stop([1e-2, 1e-7], o) == "converged"
+    assert ob._wr_stop([1.0, 2.0, 3.0], o) is None          # two growths
+    assert ob._wr_stop([1.0, 2.0, 3.0, 4.0], o) == "diverged"
+    assert ob._wr_stop([1.0, 2.0, 1.5, 3.0, 4.0], o) is None  # the run of growths restarted
+    assert ob._wr_stop([1.0, 2.0, 3.0, 4.0], dict(o, wr_diverge=0)) is None
+
+
+def test_picard_divergence_is_detected():
+    """The Picard updates grow on this case (the averaged-Jacobian pin below converges on
+    it): the oracle stops at the third growth in a row and says so."""
+    op, opts, u0, _ = _burgers_case(0.3, 1e-2, 30)
+    _, rp = ob.solve_burgers(op, dict(opts, wr_diverge=3), u0)
+    d = rp["deltas"]
+    assert rp["diverged"] and not rp["converged"] and len(d) < 30, d
+    assert d[-1] > d[-2] > d[-3] > d[-4]
