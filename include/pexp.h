@@ -59,6 +59,7 @@ extern "C" {
 #define PEXP_ERR_TIMEOUT           -7  /* a bounded device-side wait expired */
 #define PEXP_ERR_UNSUPPORTED       -8  /* valid request not implemented for this operator/precision */
 #define PEXP_ERR_SCRATCH_LIMIT     -9  /* request needs more than the fixed scratch of pexp_sai_solve_noalloc */
+#define PEXP_ERR_WR_DIVERGED      -10  /* waveform relaxation updates grew wr_diverge times in a row; last iterate written */
 
 /* ---------------------------------------------------------------- enumerations */
 #define PEXP_BC_PERIODIC   0
@@ -104,6 +105,10 @@ typedef struct {
     double wr_tol;       /* stop when max_i||u_{k+1}(t_i)-u_k(t_i)|| <= wr_tol*max_i||u_{k+1}(t_i)|| */
     int    burgers_form; /* 0: -(u_{i+1}^2-u_{i-1}^2)/(4dx);  1: -u_i(u_{i+1}-u_{i-1})/(2dx) */
     int    diagnostics;  /* bit 0: measure the orthogonality of every Krylov basis (report.orth_max) */
+    int    jacobian;     /* Burgers WR: 0 = Picard (eq. ivp3); 1 = averaged-Jacobian correction (eq. ivp4,
+                          * one Jacobian per subinterval at its time-averaged iterate, eq. piecewiseJac) */
+    int    wr_diverge;   /* Burgers WR: stop with PEXP_ERR_WR_DIVERGED once the relative update has grown
+                          * this many iterations in a row (0 = never) */
 } pexp_options;
 
 #define PEXP_DIAG_ORTH  1   /* measure the orthogonality of every Krylov basis */
@@ -132,6 +137,8 @@ typedef struct {
 #define PEXP_MAX_RANK   16    /* largest block width */
 #define PEXP_MAX_STEPS  40    /* largest Krylov step budget restart_len*(max_restarts+1) */
 #define PEXP_MAX_SAMPLES 64   /* largest number of samples in one subinterval */
+#define PEXP_REPORT_SUBS 128  /* per-subinterval report entries (the first 128 subintervals) */
+#define PEXP_REPORT_WR   64   /* WR update history entries (the first 64 iterations) */
 
 /* Per-call report (host memory, optional). */
 typedef struct {
@@ -155,9 +162,17 @@ typedef struct {
     double orth_max;          /* max over bases of max|V^T V - I| (PEXP_DIAG_ORTH), else -1 */
     double k_ms[PEXP_KC_COUNT];      /* PEXP_DIAG_KTIME: summed kernel time per class (ms) */
     int    k_launches[PEXP_KC_COUNT];/*   launches per class */
-    double k_bytes[PEXP_KC_COUNT];   /*   algorithmic bytes per class (each array once per launch) */
+    double k_bytes[PEXP_KC_COUNT];   /*   bytes the kernels move per class: each array once per launch,
+                                      *   the low parts of an FP32 working block included */
     double bytes_alg;         /* algorithmic HBM bytes: each array counted once per pass the method needs */
     int    launches;          /* kernels launched by the call */
+    double k_bytes_alg[PEXP_KC_COUNT];/* PEXP_DIAG_KTIME: algorithmic bytes per class: every array at its
+                                      *   storage width (FP32 working block at 4 bytes), once per launch */
+    int    sub_rank[PEXP_REPORT_SUBS];      /* retained source rank m_j of subinterval j = 1.. */
+    int    sub_steps[PEXP_REPORT_SUBS];     /* block steps of subproblem j's nonhomogeneous part */
+    int    sub_hom_steps[PEXP_REPORT_SUBS]; /* steps of the homogeneous continuation on subinterval j */
+    int    sub_restarts[PEXP_REPORT_SUBS];  /* Krylov restart cycles of subproblem j's nonhomogeneous part */
+    double wr_history[PEXP_REPORT_WR];      /* relative WR update of iterations 1, 2, ... */
 } pexp_report;
 
 typedef struct pexp_ctx pexp_ctx;
@@ -199,6 +214,37 @@ int pexp_solve_burgers(pexp_ctx* ctx, const pexp_operator* op, const pexp_option
                        const void* u0_dev, const void* forcing_dev, const void* init_dev,
                        void* U_dev, int dtype, pexp_report* rep);
 
+/* ---------------------------------------------------------------- batched solves
+ * Many independent problems of uneven size (Sec. 2.2's solve per instance).  One problem:
+ * an operator, options and caller-owned device buffers, as for pexp_solve_linear. */
+typedef struct {
+    pexp_operator op;
+    pexp_options  opts;
+    const void*   y0_dev;   /* n FP64 values */
+    const void*   G_dev;    /* n_out*n source samples (time-major, g_dtype) or NULL */
+    int           g_dtype;
+    void*         Y_dev;    /* n_out*n outputs (time-major, y_dtype) */
+    int           y_dtype;
+} pexp_problem;
+
+/* Solves `count` problems (probs: host array).  The problems run concurrently on the
+ * context's batch workers -- each a private stream and workspace driven by a host thread
+ * -- largest first (by n * (n_out + 40 P)); the number of workers is the context's tuned
+ * value (pexp_autotune) or 4.  The workers' streams wait for the work queued so far on the
+ * context's stream before starting, and the context's stream waits for them at the end.
+ * reps: host array of `count` reports or NULL; reps[i].status is problem i's status.
+ * Returns PEXP_OK when every problem returned PEXP_OK, else the first other status in
+ * problem order; PEXP_ERR_INVALID_ARG (nothing run) when a problem fails validation.
+ * The call is synchronous. */
+int pexp_solve_batched(pexp_ctx* ctx, int count, const pexp_problem* probs, pexp_report* reps);
+
+/* Tunes the batched solve for this device.  If `path` names a readable table written by
+ * this call on a GPU with the same name and SM count, its worker count is loaded;
+ * otherwise the given problems are solved with 1, 2, 4, 8 and 16 workers (each once to
+ * warm up and once timed), the fastest count is kept in the context, and the table is
+ * written to `path` (NULL: not written).  The problems' outputs are overwritten. */
+int pexp_autotune(pexp_ctx* ctx, int count, const pexp_problem* probs, const char* path);
+
 /* ---------------------------------------------------------------- kernel-level entry points
  * Single steps of the hot path, exposed for testing and composition.  All
  * pointers are device pointers in FP64 unless a dtype is given. */
@@ -209,9 +255,20 @@ int pexp_apply_operator(pexp_ctx* ctx, const pexp_operator* op, const void* X_de
                         int nvec, int dtype, int transpose);
 
 /* Y = (I - gamma A)^{-1} X for `nvec` vectors (shift-and-invert operator of Sec. 2.1),
- * 1D periodic operators only (else PEXP_ERR_UNSUPPORTED). */
+ * 1D operators, periodic (constant-coefficient recurrences) or homogeneous Dirichlet (the
+ * factored solve of pexp_jacobian_sai_solve); 2D: PEXP_ERR_UNSUPPORTED. */
 int pexp_sai_solve(pexp_ctx* ctx, const pexp_operator* op, double gamma, const void* X_dev,
                    void* Y_dev, int nvec, int dtype);
+
+/* Y = (I - gamma (A + J))^{-1} X for `nvec` vectors (Sec. 2.1's shift-and-invert operator for
+ * the operator A + J_k of the averaged-Jacobian iteration, Sec. 2.4 eq. ivpSubproblem), 1D
+ * operators, periodic or homogeneous Dirichlet.  ubar_dev: n FP64 values, the state at which J
+ * is the Jacobian of the conservative Burgers term -(u_{i+1}^2 - u_{i-1}^2)/(4 dx), or NULL for
+ * J = 0 (then this is the solve of pexp_sai_solve, by the variable-coefficient kernels).
+ * Returns PEXP_ERR_UNSUPPORTED for 2D operators or when I - gamma (A + J) is not diagonally
+ * dominant (the factorisation takes no pivots). */
+int pexp_jacobian_sai_solve(pexp_ctx* ctx, const pexp_operator* op, double gamma, const double* ubar_dev,
+                            const void* X_dev, void* Y_dev, int nvec, int dtype);
 
 /* E_b = exp(M_b) for `batch` dense row-major N x N FP64 matrices, M and E
  * consecutive in memory (Pade-13 scaling and squaring, Higham 2005). N <= 128. */
@@ -253,7 +310,12 @@ int pexp_burgers_source(pexp_ctx* ctx, const pexp_operator* op, const void* U_de
  * returns once its kernels are enqueued on cuda_stream; the caller synchronises.
  * The first call on a device also looks up the device address of the scratch array
  * (once per device, thread-safe); make that first call before any stream capture
- * begins.  Every call, on any stream, shares the one array, which keeps the last
+ * begins.  Under CUDA's lazy module loading (the default), that first call is also
+ * when the driver loads the library's device code on the device, and with it the
+ * scratch array: device memory is taken then, once, and a first call made after the
+ * caller's budget is fully reserved can fail with PEXP_ERR_CUDA.  A caller under a fixed
+ * budget makes one call (any valid size) before reserving it; later calls take no
+ * device memory.  Every call, on any stream, shares the one array, which keeps the last
  * call's contents; nothing in it needs to start at zero (each call writes every
  * entry it reads).  Calls that overlap on the GPU (concurrent streams, or calls from
  * several threads without ordering) race on the scratch and give wrong results. */

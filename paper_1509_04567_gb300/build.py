@@ -15,7 +15,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 OUT_DIR = os.path.join(HERE, "_lib")
 LIB = os.path.join(OUT_DIR, "libpexp.so")
-SOURCES = ["tall.cu", "small.cu", "krylov.cu", "solver.cu", "noalloc.cu"]
+SOURCES = ["tall.cu", "small.cu", "krylov.cu", "vsai.cu", "solver.cu", "noalloc.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-O2",
          "--expt-relaxed-constexpr", "-diag-suppress", "177"]
@@ -37,15 +37,17 @@ def _compile(src: str, obj: str) -> None:
 
 def build(force: bool = False, verbose: bool = False) -> str:
     os.makedirs(OUT_DIR, exist_ok=True)
-    srcs = [os.path.join(CSRC, s) for s in SOURCES] + [os.path.join(CSRC, h) for h in ("common.cuh", "small.cuh", "krylov.cuh")]
+    srcs = [os.path.join(CSRC, s) for s in SOURCES] + [os.path.join(CSRC, h) for h in ("common.cuh", "small.cuh", "krylov.cuh",
+                                                                                      "sai.cuh")]
     hdr = os.path.join(os.path.dirname(HERE), "include", "pexp.h")
-    newest = max(os.path.getmtime(p) for p in srcs + [hdr])
+    newest = max(os.path.getmtime(p) for p in srcs + [hdr, os.path.abspath(__file__)])
     if not force and os.path.exists(LIB) and os.path.getmtime(LIB) >= newest:
         return LIB
     objs = [os.path.join(OUT_DIR, s.replace(".cu", ".o")) for s in SOURCES]
     with cf.ThreadPoolExecutor(max_workers=len(SOURCES)) as ex:
         list(ex.map(lambda a: _compile(*a), zip(SOURCES, objs)))
-    cmd = [nvcc(), *ARCH, "-shared", "-o", LIB, *objs, "-lcudart"]
+    # -z defs: a symbol missing from the objects fails the link here, not the first load
+    cmd = [nvcc(), *ARCH, "-shared", "-Xlinker", "-z,defs", "-o", LIB, *objs, "-lcudart"]
     r = subprocess.run(cmd, capture_output=True, text=True)
     if r.returncode != 0:
         raise RuntimeError(f"link failed:\n{r.stdout}\n{r.stderr}")

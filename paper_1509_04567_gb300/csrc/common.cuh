@@ -91,6 +91,65 @@ struct SaiCoef {
     double alpha_n, beta_n;      // alpha^n, beta^n (circular closure)
 };
 
+// Factors of a tridiagonal shift-and-invert matrix with coefficients that vary along x:
+//   (I - gamma A_w) = (I - diag(lam) S^{-1}) diag(d) (I - diag(mu) S),  S the cyclic shift,
+// so (I - gamma A_w)^{-1} x is two first-order recurrences, y_i = x_i + lam_i y_{i-1} and
+// z_i = y_i / d_i, x_i = z_i + mu_i x_{i+1}.  Bounded (homogeneous Dirichlet) meshes have
+// lam_0 = mu_{n-1} = 0: the recurrences do not wrap around.  Arrays of n FP64 values.
+struct VarSai {
+    const double* lam;
+    const double* mu;
+    const double* dinv;
+};
+
+// A window's tridiagonal operator for the variable-coefficient solve: the 1D
+// central-difference operator plus, when ubar != NULL, the Jacobian of the conservative
+// Burgers term -(u_{i+1}^2 - u_{i-1}^2)/(4 dx) at the state ubar:
+//   (J v)_i = -(ubar_{i+1} v_{i+1} - ubar_{i-1} v_{i-1}) / (2 dx)   (Sec. 2.3, eq. jacobian)
+struct VarOpTask {
+    const double* ubar;   // n values or NULL (A alone)
+    double* lam;          // outputs: factors of (I - gamma A_w), n values each
+    double* mu;
+    double* dinv;
+    int* flag;            // set to 1 when a row of (I - gamma A_w) is not diagonally dominant
+};
+
+// ---------------------------------------------------------------- vsai.cu
+// Factors of (I - gamma (A + J(ubar_w))) for every task: each thread runs the diagonal
+// recurrence d_i = b_i - a_i c_{i-1} / d_{i-1} over its chunk after `warm` steps of
+// warm-up from the left (the recurrence contracts towards its periodic solution; bounded
+// meshes start exactly at i = 0).
+void launch_vsai_factor(const Dim1& x, double gamma, double inv2dx, const VarOpTask* tasks_dev, int ntasks,
+                        int64_t warm, cudaStream_t s);
+// Warm-up length that takes the diagonal recurrence to its limit to rounding: the
+// contraction per step is about 1 - 2/sqrt(g), g = gamma * (largest off-diagonal of A_w).
+int64_t vsai_warmup(const Dim1& x, double gamma, double inv2dx, double umax);
+// Y = (I - gamma A_w)^{-1} X for nvec vectors, vector v with the factors coef[v] (device
+// array).  Same layout, low parts and skip flags as launch_sai_solve_lo.
+template <typename T>
+void launch_vsai_solve(int64_t n, const VarSai* coef, const T* const* X, const T* const* Xlo, T* const* Y,
+                       T* const* Ylo, int nvec, double* scratch, cudaStream_t s, const int* const* skip = nullptr);
+// Time average of the iterate over each subinterval by the trapezoidal rule on its
+// samples (eq. piecewiseJac): ubar_j = mean of U rows idx_j .. idx_{j+1} with half weights
+// at both ends.  Writes FP64 (P x n) and T copies; umax_bits[j] (zeroed by the caller)
+// receives max_k |ubar_j[k]| as the bits of a non-negative double.
+template <typename T>
+void launch_window_average(const T* U, int64_t n, const int* idx_dev, int P, double* ubar64, T* ubarT,
+                           unsigned long long* umax_bits, cudaStream_t s);
+// Shifted source of the averaged-Jacobian iteration on each subinterval (eq. sourceParallel
+// read as A u0 + g_k - J_j (u_k - u0)): row r of the window-major output holds window
+// rw[r]'s sample at output time ri[r]:  out_r = Au0 + G[ri] - J(ubar_{rw}) (U[ri] - u0).
+template <typename T>
+void launch_jac_source(const Dim1& x, double inv2dx, const double* Au0, const double* u0, const T* G, const T* U,
+                       const double* ubar64, const int* rw, const int* ri, int nrows, T* out, cudaStream_t s);
+
+// Y += J X (transpose != 0: J^T X), J the Jacobian of the conservative Burgers term at the
+// per-vector state U[v] (FP64, n values); for FP32 data X may carry low parts Xlo and Y is
+// kept as a (Yh, Yl) pair (Yl may be NULL for FP64 data).
+template <typename T>
+void launch_jac_add(int64_t n, int periodic, double inv2dx, const double* const* U, const T* const* X,
+                    const float* const* Xlo, T* const* Yh, T* const* Yl, int nvec, int transpose, cudaStream_t s);
+
 // ---------------------------------------------------------------- tall.cu
 SaiCoef sai_coefficients(const OpDesc& op, double gamma);
 size_t sai_scratch_doubles(int64_t n, int nvec);

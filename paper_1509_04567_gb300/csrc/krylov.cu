@@ -117,7 +117,7 @@ template <>
 struct Budget<double> {
     static constexpr int acc = 36;
 };
-template <typename T, int B>
+template <typename T, int B, bool JAC = false>
 struct Group {
     // columns per CTA of k_step_proj: FP32 data keep E and F as compensated (s, c) pairs
     // (5 registers per column and block column), FP64 data plain sums (3 doubles); FP32
@@ -125,6 +125,13 @@ struct Group {
     static constexpr int step = sizeof(T) == 4 ? (B == 1 ? 8 : 16 / B) : Budget<T>::acc / (3 * B);
     static constexpr int vtw = Budget<T>::acc / (B + 1);     // columns per CTA of k_vtw
     static constexpr int ctas = (sizeof(T) == 4 && B == 1) ? 3 : 2;   // CTAs per SM k_step_proj is built for
+};
+// the Jacobian launches keep two more compensated sums (Ja, Jb) per column and block column
+template <typename T, int B>
+struct Group<T, B, true> {
+    static constexpr int step = sizeof(T) == 4 ? (B == 1 ? 4 : (8 / B > 1 ? 8 / B : 1)) : (Budget<T>::acc / (5 * B) > 1 ? Budget<T>::acc / (5 * B) : 1);
+    static constexpr int vtw = Budget<T>::acc / (B + 1);
+    static constexpr int ctas = 2;
 };
 constexpr int kFuseP = 16;   // k_scale_proj keeps V^T W accumulators for up to 16 columns
 
@@ -179,13 +186,14 @@ __device__ __forceinline__ double cta_entry(const double* sred, int ne, int e) {
 // k_step_proj: grid (chunks, tasks, column groups).  Group z owns columns
 // [z*PG, z*PG + PG) of V_{1:p}; group 0 also sums diag(W^T W).
 // =====================================================================================
-template <typename T, int B>
-__global__ void __launch_bounds__(kThreads, Group<T, B>::ctas) k_step_proj(const StepTask<T>* __restrict__ tasks, int64_t n, int periodic,
+template <typename T, int B, bool JAC>
+__global__ void __launch_bounds__(kThreads, Group<T, B, JAC>::ctas) k_step_proj(const StepTask<T>* __restrict__ tasks, int64_t n, int periodic,
                                                         int64_t rows, int nchunks, int pstride,
                                                         double* __restrict__ partial) {
     pdl_entry();
-    constexpr int PG = Group<T, B>::step;
-    constexpr int NE = 3 * PG * B + B;
+    constexpr int PG = Group<T, B, JAC>::step;
+    constexpr int NK = JAC ? 5 : 3;   // sums per column pair: E, F, h1 (+ Ja, Jb)
+    constexpr int NE = NK * PG * B + B;
     __shared__ double sred[kWarps * NE];
     const StepTask<T> tk = tasks[blockIdx.y];
     if (tk.conv && *tk.conv) return;
@@ -202,10 +210,14 @@ __global__ void __launch_bounds__(kThreads, Group<T, B>::ctas) k_step_proj(const
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const bool grp0 = blockIdx.z == 0;
     T aE[PG][B], aF[PG][B], cE[PG][B], cF[PG][B], aH[PG][B], aP[B];
+    T aJa[PG][B], cJa[PG][B], aJb[PG][B], cJb[PG][B];
 #pragma unroll
     for (int q = 0; q < PG; ++q)
 #pragma unroll
-        for (int c = 0; c < B; ++c) aE[q][c] = aF[q][c] = cE[q][c] = cF[q][c] = aH[q][c] = T(0);
+        for (int c = 0; c < B; ++c) {
+            aE[q][c] = aF[q][c] = cE[q][c] = cF[q][c] = aH[q][c] = T(0);
+            aJa[q][c] = cJa[q][c] = aJb[q][c] = cJb[q][c] = T(0);
+        }
 #pragma unroll
     for (int c = 0; c < B; ++c) aP[c] = T(0);
     // Dirichlet: the r = -1 term dv_{-1} = v_0 of the E sums, in the chunk holding row 0
@@ -246,9 +258,13 @@ __global__ void __launch_bounds__(kThreads, Group<T, B>::ctas) k_step_proj(const
             D[c] = vr - vi[c];
             C[c] = vr - vl;
         }
+        T ub = T(0);
+        if constexpr (JAC) ub = act ? ldg(tk.ubar + rp) : T(0);
 #pragma unroll
         for (int q = 0; q < PG; ++q) {
             const T xr = __shfl_down_sync(0xffffffffu, x[q], 1);
+            T xl = T(0);
+            if constexpr (JAC) xl = __shfl_up_sync(0xffffffffu, x[q], 1);
             if (act && q < na) {
                 const T dx = xr - x[q];
 #pragma unroll
@@ -256,6 +272,10 @@ __global__ void __launch_bounds__(kThreads, Group<T, B>::ctas) k_step_proj(const
                     comp_add(aE[q][c], cE[q][c], dx, D[c]);
                     comp_add(aF[q][c], cF[q][c], x[q], C[c]);
                     aH[q][c] = fma(x[q], w[c], aH[q][c]);
+                    if constexpr (JAC) {
+                        comp_add(aJa[q][c], cJa[q][c], ub * vi[c], xr - xl);
+                        comp_add(aJb[q][c], cJb[q][c], ub * x[q], C[c]);
+                    }
                 }
             }
         }
@@ -269,24 +289,30 @@ __global__ void __launch_bounds__(kThreads, Group<T, B>::ctas) k_step_proj(const
         if (q < na) {
 #pragma unroll
             for (int c = 0; c < B; ++c) {
-                warp_to_smem2(aE[q][c], cE[q][c], sred, NE, (q * B + c) * 3 + 0);
-                warp_to_smem2(aF[q][c], cF[q][c], sred, NE, (q * B + c) * 3 + 1);
-                warp_to_smem(aH[q][c], sred, NE, (q * B + c) * 3 + 2);
+                warp_to_smem2(aE[q][c], cE[q][c], sred, NE, (q * B + c) * NK + 0);
+                warp_to_smem2(aF[q][c], cF[q][c], sred, NE, (q * B + c) * NK + 1);
+                warp_to_smem(aH[q][c], sred, NE, (q * B + c) * NK + 2);
+                if constexpr (JAC) {
+                    warp_to_smem2(aJa[q][c], cJa[q][c], sred, NE, (q * B + c) * NK + 3);
+                    warp_to_smem2(aJb[q][c], cJb[q][c], sred, NE, (q * B + c) * NK + 4);
+                }
             }
         }
     }
     if (grp0) {
 #pragma unroll
-        for (int c = 0; c < B; ++c) warp_to_smem(aP[c], sred, NE, 3 * PG * B + c);
+        for (int c = 0; c < B; ++c) warp_to_smem(aP[c], sred, NE, NK * PG * B + c);
     }
     __syncthreads();
     double* pout = partial + ((size_t)blockIdx.y * nchunks + blockIdx.x) * pstride;
     for (int e = threadIdx.x; e < NE; e += kThreads) {
-        if (e < 3 * PG * B) {
-            const int kind = e % 3, qc = e / 3, q = qc / B, c = qc % B;
-            if (q < na) pout[kind * p * B + (a0 + q) + c * p] = cta_entry(sred, NE, e);
+        if (e < NK * PG * B) {
+            const int kind = e % NK, qc = e / NK, q = qc / B, c = qc % B;
+            // kinds 0..2 at kind * p * B; Ja, Jb after pre (3 p B + B)
+            const int base = kind < 3 ? kind * p * B : 3 * p * B + B + (kind - 3) * p * B;
+            if (q < na) pout[base + (a0 + q) + c * p] = cta_entry(sred, NE, e);
         } else if (grp0) {
-            pout[3 * p * B + (e - 3 * PG * B)] = cta_entry(sred, NE, e);
+            pout[3 * p * B + (e - NK * PG * B)] = cta_entry(sred, NE, e);
         }
     }
 }
@@ -948,12 +974,21 @@ size_t krylov_partial_slots(int ntasks_max, int64_t n) {
 
 template <typename T>
 void launch_step_proj(const StepTask<T>* tasks, int ntasks, int b, int p, int64_t n, int periodic, KGeom g,
-                      double* partial, int pstride, cudaStream_t s) {
+                      double* partial, int pstride, cudaStream_t s, bool jac) {
     if (ntasks <= 0) return;
+    if (jac) {
+        PEXP_B_DISPATCH(b, ({
+            constexpr int PG = Group<T, BB, true>::step;
+            dim3 grid(g.nchunks, ntasks, (p + PG - 1) / PG);
+            launch_pdl(k_step_proj<T, BB, true>, grid, dim3(kThreads), 0, s, tasks, n, periodic, g.rows, g.nchunks, pstride,
+                       partial);
+        }));
+        return;
+    }
     PEXP_B_DISPATCH(b, ({
         constexpr int PG = Group<T, BB>::step;
         dim3 grid(g.nchunks, ntasks, (p + PG - 1) / PG);
-        launch_pdl(k_step_proj<T, BB>, grid, dim3(kThreads), 0, s, tasks, n, periodic, g.rows, g.nchunks, pstride, partial);
+        launch_pdl(k_step_proj<T, BB, false>, grid, dim3(kThreads), 0, s, tasks, n, periodic, g.rows, g.nchunks, pstride, partial);
     }));
 }
 
@@ -1017,7 +1052,7 @@ void launch_source_gram(const T* const* X, const int* sv, int ntasks, int s_max,
 }
 
 #define PEXP_KRY_INST(T)                                                                                           \
-    template void launch_step_proj<T>(const StepTask<T>*, int, int, int, int64_t, int, KGeom, double*, int, cudaStream_t); \
+    template void launch_step_proj<T>(const StepTask<T>*, int, int, int, int64_t, int, KGeom, double*, int, cudaStream_t, bool); \
     template void launch_update<T>(const UpdTask<T>*, int, int, int, int64_t, int, KGeom, double*, int, cudaStream_t, \
                                    const double*, int);                                                             \
     template void launch_scale<T>(const UpdTask<T>*, int, int, int64_t, int, KGeom, double*, int, cudaStream_t); \

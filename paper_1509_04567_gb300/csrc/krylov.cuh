@@ -14,6 +14,7 @@ struct StepTask {
     int64_t ld;
     int p;
     const int* conv;  // the window's convergence flag: the kernels skip a converged window (NULL: never)
+    const T* ubar;    // Jacobian launches: the state of the window's Burgers Jacobian (n values)
 };
 
 // W <- W - V h (mode 0/1) or W <- W T (scale), h/T a dense FP64 matrix (hm, ld ldh).
@@ -41,10 +42,14 @@ size_t krylov_partial_slots(int ntasks_max, int64_t n);
 // All launchers take the row-chunk geometry g (the same for every task of a step) and
 // write the partials of task k at partial + (k * g.nchunks + chunk) * pstride.
 // partial layout of k_step_proj per (task, chunk): E (p x b) | F (p x b) | h1 (p x b) | pre (b)
+// and, with jac, Ja (p x b) | Jb (p x b) after them:
+//   Ja[a, i] = sum_r ubar_r v_i,r (v_a,r+1 - v_a,r-1),  Jb[a, i] = sum_r ubar_r v_a,r (v_i,r+1 - v_i,r-1),
+// so that v_a^T J v_i = Ja / (2 dx) and v_i^T J v_a = Jb / (2 dx) for the Jacobian J of the
+// conservative Burgers term at ubar (summation by parts, zero ghosts on bounded meshes).
 // p = columns of V_{1:i} (the same for every task of the launch)
 template <typename T>
 void launch_step_proj(const StepTask<T>* tasks, int ntasks, int b, int p, int64_t n, int periodic, KGeom g,
-                      double* partial, int pstride, cudaStream_t s);
+                      double* partial, int pstride, cudaStream_t s, bool jac = false);
 // mode 0 and 1: W -= V h (h = tk.hm, p x b), partial G = W^T W (b x b); mode 0 subtracts
 // in double-float (FP32 data), mode 1 with FP32 products (second-pass coefficients).
 // Mode 1 with hpart: h is summed by each CTA from the chunk partials at hpart (task-major,

@@ -17,8 +17,10 @@ namespace {
 constexpr size_t kScratchDoubles = PEXP_NOALLOC_SCRATCH_BYTES / sizeof(double);
 constexpr int kMaxDevices = 64;
 
-// Host-side stand-in for the scratch: in host code this name is not a device
-// address; the address comes from cudaGetSymbolAddress on each device.
+// The scratch: one file-scope device array, one copy on every device that loads this
+// module.  Device code may name it directly; host code may not pass the name to a kernel
+// (on the host it denotes a host-side shadow, not a device address), so its device
+// address is looked up with cudaGetSymbolAddress, once per device.
 static __device__ __align__(256) double g_sai_scratch[kScratchDoubles];
 
 std::mutex g_mu;

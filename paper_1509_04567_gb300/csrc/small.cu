@@ -630,7 +630,7 @@ void launch_spline(const WinLayout& L, double* wd, int* wi, const int* wins, int
 __global__ void __launch_bounds__(256) k_project(WinLayout L, double* __restrict__ wd, int* __restrict__ wi,
                                                  const int* __restrict__ wins, int step, double h, double tol,
                                                  double scale_ref, Parts fp, double dcoef, double ccoef, int nsm,
-                                                 int only_ef) {
+                                                 int only_ef, double jcoef) {
     extern __shared__ double sm_proj[];   // 9 nsm^2 doubles when nsm > 0
     const int w = wins[blockIdx.x];
     double* D = wd + (int64_t)w * L.stride;
@@ -652,11 +652,16 @@ __global__ void __launch_bounds__(256) k_project(WinLayout L, double* __restrict
         // only_ef: h1 and pre are summed into out1 by another kernel (the Gram-Schmidt
         // passes run concurrently with this one)
         const int nfield = only_ef ? 2 * K * b : 3 * K * b + b;
+        // Jacobian sums Ja, Jb (K x b each) follow pre in the partials
+        const int nj = jcoef != 0.0 ? 2 * K * b : 0;
         const int nwarps = blockDim.x >> 5;
-        for (int e = threadIdx.x >> 5; e < nfield; e += nwarps) {
+        for (int e2 = threadIdx.x >> 5; e2 < nfield + nj; e2 += nwarps) {
+            const int e = e2 < nfield ? e2 : 3 * K * b + b + (e2 - nfield);
             const double sacc = parts_sum_warp(fp, blockIdx.x, e);
             if ((threadIdx.x & 31) != 0) continue;
-            if (e < 2 * K * b) {
+            if (e2 >= nfield) {
+                D[L.off_scr + 2 * K * b + (e2 - nfield)] = sacc;   // Ja then Jb
+            } else if (e < 2 * K * b) {
                 // E and F: stage in the scratch area for the H assembly below
                 D[L.off_scr + e] = sacc;
             } else {
@@ -666,10 +671,13 @@ __global__ void __launch_bounds__(256) k_project(WinLayout L, double* __restrict
         __syncthreads();
         const double* Es = D + L.off_scr;
         const double* Fs = Es + K * b;
+        const double* Ja = Fs + K * b;
+        const double* Jb = Ja + K * b;
         for (int e = threadIdx.x; e < K * b; e += blockDim.x) {
             const int a = e % K, c = e / K;
-            H[a + ((step - 1) * b + c) * KM] = -dcoef * Es[e] - ccoef * Fs[e];
-            if (a < (step - 1) * b) H[((step - 1) * b + c) + a * KM] = -dcoef * Es[e] + ccoef * Fs[e];
+            const double ja = nj ? jcoef * Ja[e] : 0.0, jb = nj ? jcoef * Jb[e] : 0.0;
+            H[a + ((step - 1) * b + c) * KM] = -dcoef * Es[e] - ccoef * Fs[e] + ja;
+            if (a < (step - 1) * b) H[((step - 1) * b + c) + a * KM] = -dcoef * Es[e] + ccoef * Fs[e] + jb;
         }
     } else {
         for (int e = threadIdx.x; e < K * b; e += blockDim.x) {
@@ -768,16 +776,17 @@ __global__ void __launch_bounds__(256) k_project(WinLayout L, double* __restrict
 }
 
 void launch_project(const WinLayout& L, double* wd, int* wi, const int* wins, int nw, int step, double h, double tol,
-                    double scale_ref, cudaStream_t s, Parts fp, double d, double cadv, int b_launch, int only_ef) {
+                    double scale_ref, cudaStream_t s, Parts fp, double d, double cadv, int b_launch, int only_ef,
+                    double jcoef) {
     if (nw <= 0) return;
     // largest augmented matrix of this launch: step * b + 4 b (source windows)
     const int nl = b_launch > 0 ? std::min(L.N_max, (step + 4) * b_launch) : L.N_max;
     const size_t sm = (size_t)9 * nl * nl * sizeof(double);
     if (sm <= 200u * 1024u) {
         if (sm > 32 * 1024) cudaFuncSetAttribute(k_project, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-        k_project<<<nw, 256, sm, s>>>(L, wd, wi, wins, step, h, tol, scale_ref, fp, d, cadv, nl, only_ef);
+        k_project<<<nw, 256, sm, s>>>(L, wd, wi, wins, step, h, tol, scale_ref, fp, d, cadv, nl, only_ef, jcoef);
     } else {
-        k_project<<<nw, 256, 0, s>>>(L, wd, wi, wins, step, h, tol, scale_ref, fp, d, cadv, 0, only_ef);
+        k_project<<<nw, 256, 0, s>>>(L, wd, wi, wins, step, h, tol, scale_ref, fp, d, cadv, 0, only_ef, jcoef);
     }
 }
 

@@ -75,9 +75,12 @@ void launch_spline(const WinLayout& L, double* wd, int* wi, const int* wins, int
 // b_launch: largest block width among the windows (0: unknown, the matrices stay in global memory
 // unless the layout's largest matrix fits in shared memory)
 // only_ef != 0 (fused partials): h1 and pre are left to another kernel.
+// jcoef != 0 (fused partials): the partials also hold the Jacobian sums Ja, Jb of
+// launch_step_proj, and H gets jcoef * Ja in its new column and jcoef * Jb in its new row
+// (jcoef = 1/(2 dx): the Jacobian of the conservative Burgers term).
 void launch_project(const WinLayout& L, double* wd, int* wi, const int* wins, int nw, int step, double h,
                     double tol, double scale_ref, cudaStream_t s, Parts fp = Parts{nullptr, 0, 0}, double d = 0.0,
-                    double cadv = 0.0, int b_launch = 0, int only_ef = 0);
+                    double cadv = 0.0, int b_launch = 0, int only_ef = 0, double jcoef = 0.0);
 void launch_small_expm_batch(const double* M, double* E, int N, int batch, double* scratch, cudaStream_t s);
 size_t small_expm_scratch_doubles(int N);
 void init_pade_constants();

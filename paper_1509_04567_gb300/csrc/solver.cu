@@ -22,7 +22,11 @@
 #include <string.h>
 
 #include <algorithm>
+#include <atomic>
+#include <chrono>
 #include <new>
+#include <string>
+#include <thread>
 #include <type_traits>
 #include <vector>
 
@@ -52,7 +56,7 @@ struct KTimer {
     struct Rec {
         int cls;
         cudaEvent_t a, b;
-        double bytes;
+        double bytes, alg;
     };
     std::vector<Rec> recs;
     cudaEvent_t next() {
@@ -103,9 +107,15 @@ struct pexp_ctx {
     cudaEvent_t ev0 = nullptr, ev1 = nullptr;
     cudaEvent_t evp[5] = {nullptr, nullptr, nullptr, nullptr, nullptr};   // phase boundaries
     int launches = 0;
-    // host copies for host-pointer solves
+    // host copies for host-pointer solves: outputs leave window by window on a copy stream
     void* io_d = nullptr;
     size_t io_cap = 0;
+    cudaStream_t cs = nullptr;
+    cudaEvent_t ev_out = nullptr;
+    // batched solves: worker contexts, each on a stream of its own
+    std::vector<pexp_ctx*> workers;
+    int batch_workers = 0;    // tuned count (0: default)
+    bool owns_stream = false; // a worker's stream belongs to it
     KTimer kt;
 };
 
@@ -225,9 +235,12 @@ struct Stage {
     }
 };
 
-// Time a launch sequence as kernel class `cls` moving `bytes` algorithmic bytes.
+// Time a launch sequence as kernel class `cls` moving `bytes` (the low parts of an FP32
+// working block included) of which `alg` are algorithmic (every array at its storage
+// width; alg < 0: the same as bytes).
 template <typename F>
-void timed(pexp_ctx* c, int cls, double bytes, F&& f, cudaStream_t on = nullptr, bool on_set = false) {
+void timed(pexp_ctx* c, int cls, double bytes, F&& f, cudaStream_t on = nullptr, bool on_set = false,
+           double alg = -1.0) {
     if (!c->kt.on || !((c->kt.mask >> cls) & 1u) || !c->kt.pick()) {
         f();
         return;
@@ -237,7 +250,7 @@ void timed(pexp_ctx* c, int cls, double bytes, F&& f, cudaStream_t on = nullptr,
     cudaEventRecord(a, st);
     f();
     cudaEventRecord(b, st);
-    c->kt.recs.push_back({cls, a, b, bytes});
+    c->kt.recs.push_back({cls, a, b, bytes, alg < 0 ? bytes : alg});
 }
 
 void check_launch(pexp_ctx* c) {
@@ -270,7 +283,8 @@ void d2h(pexp_ctx* c, void* dst, const void* src, size_t bytes) {
 // per (task, row chunk), each as wide as the largest partial (step projections at the
 // last step, or an s x s Gram matrix).
 size_t kpart_doubles(int P, int64_t n, int kmax, int b_cap, int smax) {
-    const size_t width = std::max<size_t>((size_t)(3 * kmax * b_cap * b_cap + b_cap + b_cap * b_cap), (size_t)smax * smax);
+    // step projections with the Jacobian sums: 5 p b + b per chunk (p <= kmax b)
+    const size_t width = std::max<size_t>((size_t)(5 * kmax * b_cap * b_cap + b_cap + b_cap * b_cap), (size_t)smax * smax);
     return krylov_partial_slots(P, n) * width + 64;
 }
 
@@ -319,7 +333,7 @@ int validate(const pexp_operator* op, const pexp_options* o) {
         smax = std::max(smax, i1 - i0 + 1);
     }
     if (smax > PEXP_MAX_SAMPLES) return PEXP_ERR_INVALID_ARG;
-    if (o->krylov == PEXP_KRYLOV_SAI && (op->dim != 1 || op->bc != PEXP_BC_PERIODIC)) return PEXP_ERR_UNSUPPORTED;
+    if (o->krylov == PEXP_KRYLOV_SAI && op->dim != 1) return PEXP_ERR_UNSUPPORTED;
     return PEXP_OK;
 }
 
@@ -332,6 +346,24 @@ struct Win {
     int b;        // block width
     float* Wlo;   // FP32 data: low parts of the working block (n x b); NULL for FP64
     float* V1lo;  // FP32 data: low parts of the start block while it is formed (n x b); NULL for FP64
+    VarSai vs{};                  // variable-coefficient solves: the window's factors
+    const T* ubar = nullptr;      // Jacobian windows: the state of J (Galerkin sums)
+    const double* ubar64 = nullptr;   // the same in FP64 (operator applications)
+};
+
+// Per-subinterval operators of a solve.  The averaged-Jacobian waveform relaxation gives
+// subinterval j the tridiagonal operator A + J_j (Sec. 2.4, eq. piecewiseJac); a bounded
+// mesh with the shift-and-invert space has one factored operator for all subintervals.
+template <typename T>
+struct WinOps {
+    bool var = false;                 // shift-and-invert solves use the factors vs[j]
+    std::vector<VarSai> vs;           // P entries
+    bool jac = false;                 // Galerkin sums and operator applications include J_j
+    std::vector<const T*> ubar;       // P entries: the state of J_j (T)
+    std::vector<const double*> ubar64;   // and in FP64
+    double inv2dx = 0.0;
+    const T* Gwin = nullptr;          // window-major shifted source (rows idx_j + j ...), or NULL:
+                                      // time-major G shifted by A u0 in every window
 };
 
 
@@ -355,6 +387,9 @@ struct Solver {
     double* diag = nullptr;   // K_max x 48 doubles for the orthogonality diagnostic
     double* kpart[2] = {nullptr, nullptr};   // partial sums of the fused Krylov kernels
     bool fused = false;                        // 1D operator and block widths <= kKrylovMaxB
+    bool var = false;                          // per-window variable-coefficient shift-and-invert solves
+    bool jac = false;                          // per-window Jacobian terms in the operator
+    double inv2dx = 0.0;
     std::vector<int> wi_host;
 
     T* slot(const Win<T>& W, int blk) const { return W.V + (int64_t)blk * W.b * n; }
@@ -420,7 +455,7 @@ struct Solver {
             int bmax = 0;
             for (auto& W : act) bmax = std::max(bmax, W.b);
             const KGeom g = krylov_geom(na, n);
-            const int ps1 = 3 * step * bmax * bmax + bmax;   // step_proj partial stride
+            const int ps1 = (jac ? 5 : 3) * step * bmax * bmax + bmax;   // step_proj partial stride
             // ---- part A
             Stage sa(c, 0);
             std::vector<const T*> xin;
@@ -428,6 +463,7 @@ struct Solver {
             std::vector<StepTask<T>> st1(na);
             std::vector<int> wl(na);
             std::vector<const int*> skip;
+            std::vector<VarSai> vcs;
             for (int a = 0; a < na; ++a) {
                 const Win<T>& W = act[a];
                 T* Vi = slot(W, step - 1);
@@ -440,8 +476,9 @@ struct Solver {
                     yout.push_back(Wn + (int64_t)cc * n);
                     ylo.push_back(W.Wlo ? reinterpret_cast<T*>(W.Wlo) + (int64_t)cc * n : nullptr);
                     skip.push_back(conv_of(W));
+                    vcs.push_back(W.vs);
                 }
-                st1[a] = StepTask<T>{W.V, n, step * W.b, conv_of(W)};
+                st1[a] = StepTask<T>{W.V, n, step * W.b, conv_of(W), W.ubar};
                 wl[a] = W.w;
             }
             const int nv = (int)xin.size();
@@ -451,12 +488,15 @@ struct Solver {
             const StepTask<T>* d_st1 = sa.put(st1.data(), na);
             const int* const* d_skip = sa.put(skip.data(), nv);
             const int* d_wl = sa.put(wl.data(), na);
+            const VarSai* d_vcs = var ? sa.put(vcs.data(), nv) : nullptr;
             sa.flush();
             const double w = sizeof(T);
             const double wout = std::is_same<T, float>::value ? 8.0 : w;
             if (o->krylov == PEXP_KRYLOV_SAI) {
-                timed(c, PEXP_KC_SAI, (double)nv * n * (w + wout),
-                      [&] { launch_sai_solve_lo<T>(od, sai, d_xin, nullptr, d_yout, d_ylo, nv, sai_scr, st, d_skip); });
+                timed(c, PEXP_KC_SAI, (double)nv * n * (w + wout), [&] {
+                    if (var) launch_vsai_solve<T>(n, d_vcs, d_xin, nullptr, d_yout, d_ylo, nv, sai_scr, st, d_skip);
+                    else launch_sai_solve_lo<T>(od, sai, d_xin, nullptr, d_yout, d_ylo, nv, sai_scr, st, d_skip);
+                }, nullptr, false, 2.0 * nv * n * w);
                 c->launches += 2;   // the solve is three kernels; check_launch below counts one
             } else {
                 timed(c, PEXP_KC_STENCIL, (double)nv * n * (w + w), [&] { launch_stencil_ptrs<T>(od, d_xin, d_yout, nv, 0, st); });
@@ -471,7 +511,7 @@ struct Solver {
                     int a1 = a0;
                     while (a1 < na && act[a1].b == act[a0].b) ++a1;
                     launch_step_proj<T>(d_st1 + a0, a1 - a0, act[a0].b, step * act[a0].b, n, periodic, g,
-                                        kpart[0] + (size_t)a0 * g.nchunks * ps1, ps1, st);
+                                        kpart[0] + (size_t)a0 * g.nchunks * ps1, ps1, st, jac);
                     check_launch(c);
                     a0 = a1;
                 }
@@ -494,7 +534,7 @@ struct Solver {
             cudaStreamWaitEvent(c->s2, c->ev_sp, 0);
             timed(c, PEXP_KC_SMALL, 0.0, [&] {
                 launch_project(L, wd, wi, d_wl, na, step, h, o->tol, scale_ref, c->s2, Parts{kpart[0], g.nchunks, ps1},
-                               od.x.d, od.x.c, bmax, 1);
+                               od.x.d, od.x.c, bmax, 1, jac ? inv2dx : 0.0);
             }, c->s2, true);
             check_launch(c);
             cudaEventRecord(c->ev_pj, c->s2);
@@ -581,12 +621,13 @@ struct Solver {
                 }
             };
             // pass 1: W <- W - V h1 (Gram of the result), Cholesky QR with deflation
+            const double alg_upd = (double)n * (pb * w + 2 * bb * w);
             timed(c, PEXP_KC_UPDATE, (double)n * (pb * w + 2 * bb * wl_), [&] {
                 groups([&](int a0, int a1, int b) {
                     launch_update<T>(d1 + a0, a1 - a0, b, step * b, n, 0, gb, kpart[1] + (size_t)a0 * gb.nchunks * psg, psg, st);
                     check_launch(c);
                 });
-            });
+            }, nullptr, false, alg_upd);
             timed(c, PEXP_KC_SMALL, 0.0, [&] {
                 launch_block_orth(L, wd, wi, d_wl2, nb, 1, step, defl, st, Parts{kpart[1], gb.nchunks, psg});
             });
@@ -597,7 +638,7 @@ struct Solver {
                     launch_scale_proj<T>(d3 + a0, a1 - a0, b, step * b, n, gb, kpart[1] + (size_t)a0 * gb.nchunks * ps2, ps2, st);
                     check_launch(c);
                 });
-            });
+            }, nullptr, false, alg_upd);
             // the second pass sums h2 from the partials above itself; its Gram partials go after
             // them in the same buffer (ps2 + psg <= the buffer's width per chunk slot)
             const size_t off2 = (size_t)nb * gb.nchunks * ps2;
@@ -607,7 +648,7 @@ struct Solver {
                                      psg, st, kpart[1] + (size_t)a0 * gb.nchunks * ps2, ps2);
                     check_launch(c);
                 });
-            });
+            }, nullptr, false, alg_upd);
             timed(c, PEXP_KC_SMALL, 0.0, [&] {
                 launch_block_orth(L, wd, wi, d_wl2, nb, 2, step, defl, st, Parts{kpart[1] + off2, gb.nchunks, psg});
             });
@@ -617,7 +658,7 @@ struct Solver {
                     launch_scale<T>(d4 + a0, a1 - a0, b, n, 0, gb, nullptr, psg, st);
                     check_launch(c);
                 });
-            });
+            }, nullptr, false, 2.0 * n * bb * w);
         }
     }
 
@@ -635,6 +676,8 @@ struct Solver {
             std::vector<const T*> xin;
             std::vector<T*> yout, ylo, yav, yatv, yavl, yatvl;
             std::vector<const float*> xlo;
+            std::vector<VarSai> vcs;
+            std::vector<const double*> ubv;
             const int yc = L.ycols;   // 3 (FP64) or 5 (FP32 data: A V and A^T V carry low parts)
             // TN1 over X = V_{1:step+1} (the working block W sits in slot step) and
             // Y = [A V_i, A^T V_i, (low parts), W]; Y is split into launches of <= 48 columns
@@ -653,6 +696,8 @@ struct Solver {
                     yavl.push_back(W.S + (int64_t)(2 * W.b + cc) * n);
                     yatvl.push_back(W.S + (int64_t)(3 * W.b + cc) * n);
                     xlo.push_back(step == 1 && W.V1lo ? W.V1lo + (int64_t)cc * n : nullptr);
+                    vcs.push_back(W.vs);
+                    ubv.push_back(W.ubar64);
                 }
                 const int ldo = (step + 1) * W.b;
                 const int qs = (yc - 1) * W.b;   // columns of S
@@ -701,12 +746,16 @@ struct Solver {
                 d_tn1[sl] = sa.put(tn1[sl].data(), tn1[sl].size());
             }
             const int* d_wl = sa.put(wl.data(), na);
+            const VarSai* d_vcs = var ? sa.put(vcs.data(), nv) : nullptr;
+            const double* const* d_ubv = jac ? sa.put(ubv.data(), nv) : nullptr;
             sa.flush();
             const double w = sizeof(T);
             const double wout = std::is_same<T, float>::value ? 8.0 : w;   // hi + lo for FP32 data
             if (o->krylov == PEXP_KRYLOV_SAI) {
-                timed(c, PEXP_KC_SAI, (double)nv * n * (w + wout),
-                      [&] { launch_sai_solve<T>(od, sai, d_xin, d_yout, d_ylo, nv, sai_scr, st); });
+                timed(c, PEXP_KC_SAI, (double)nv * n * (w + wout), [&] {
+                    if (var) launch_vsai_solve<T>(n, d_vcs, d_xin, nullptr, d_yout, d_ylo, nv, sai_scr, st);
+                    else launch_sai_solve<T>(od, sai, d_xin, d_yout, d_ylo, nv, sai_scr, st);
+                }, nullptr, false, 2.0 * nv * n * w);
                 c->launches += 2;   // the solve is three kernels; check_launch below counts one
             } else {
                 launch_stencil_ptrs<T>(od, d_xin, d_yout, nv, 0, st);
@@ -728,7 +777,17 @@ struct Solver {
                     launch_stencil_ptrs<T>(od, d_xin, d_yatv, nv, 1, st);
                     check_launch(c);
                 }
-            });
+                if (jac) {
+                    // (A + J_j) V_i and (A + J_j)^T V_i: the Jacobian of each window added in FP64
+                    const float* const* xl32 = std::is_same<T, float>::value ? d_xlo : nullptr;
+                    launch_jac_add<T>(n, od.x.periodic, inv2dx, d_ubv, d_xin, xl32, d_yav,
+                                      std::is_same<T, float>::value ? d_yavl : nullptr, nv, 0, st);
+                    check_launch(c);
+                    launch_jac_add<T>(n, od.x.periodic, inv2dx, d_ubv, d_xin, xl32, d_yatv,
+                                      std::is_same<T, float>::value ? d_yatvl : nullptr, nv, 1, st);
+                    check_launch(c);
+                }
+            }, nullptr, false, 4.0 * nv * n * w);
             for (size_t sl = 0; sl < tn1.size(); ++sl) {
                 double by = 0;
                 for (auto& t : tn1[sl]) by += (double)n * (t.p + t.q) * w;
@@ -837,15 +896,15 @@ struct Solver {
                 double pb = 0, bb = 0;   // sum of p*b and of b over the active windows
                 for (auto& W : act) { pb += (double)step * W.b; bb += W.b; }
                 const double nn = (double)n;
-                timed(c, PEXP_KC_UPDATE, nn * (pb * 4 + bb * 16), [&] { launch_ts_nn_df(dd1, nb, mpq1, n, st); }); check_launch(c);
+                timed(c, PEXP_KC_UPDATE, nn * (pb * 4 + bb * 16), [&] { launch_ts_nn_df(dd1, nb, mpq1, n, st); }, nullptr, false, nn * (pb * 4 + bb * 8)); check_launch(c);
                 timed(c, PEXP_KC_PROJ, nn * (pb + bb) * 4, [&] { launch_ts_tn<T>(d_tn2, nb, mpq2, mq2, n, partial, st, PEXP_TN_EXACT_FP32); }); check_launch(c);
-                timed(c, PEXP_KC_UPDATE, nn * (pb * 4 + bb * 16), [&] { launch_ts_nn_df(dd2, nb, mpq1, n, st); }); check_launch(c);
+                timed(c, PEXP_KC_UPDATE, nn * (pb * 4 + bb * 16), [&] { launch_ts_nn_df(dd2, nb, mpq1, n, st); }, nullptr, false, nn * (pb * 4 + bb * 8)); check_launch(c);
                 timed(c, PEXP_KC_PROJ, nn * bb * 4, [&] { launch_ts_tn<T>(d_tn3, nb, mpq3, mq3, n, partial, st, 1); }); check_launch(c);
                 timed(c, PEXP_KC_SMALL, 0.0, [&] { launch_block_orth(L, wd, wi, d_wl2, nb, 1, step, defl, st); }); check_launch(c);
-                timed(c, PEXP_KC_UPDATE, nn * bb * 16, [&] { launch_ts_nn_df(dd3, nb, mpq3, n, st); }); check_launch(c);
+                timed(c, PEXP_KC_UPDATE, nn * bb * 16, [&] { launch_ts_nn_df(dd3, nb, mpq3, n, st); }, nullptr, false, nn * bb * 8); check_launch(c);
                 timed(c, PEXP_KC_PROJ, nn * bb * 4, [&] { launch_ts_tn<T>(d_tn3, nb, mpq3, mq3, n, partial, st, 1); }); check_launch(c);
                 timed(c, PEXP_KC_SMALL, 0.0, [&] { launch_block_orth(L, wd, wi, d_wl2, nb, 2, step, defl, st); }); check_launch(c);
-                timed(c, PEXP_KC_UPDATE, nn * bb * 12, [&] { launch_ts_nn_df(dd4, nb, mpq3, n, st); }); check_launch(c);
+                timed(c, PEXP_KC_UPDATE, nn * bb * 12, [&] { launch_ts_nn_df(dd4, nb, mpq3, n, st); }, nullptr, false, nn * bb * 8); check_launch(c);
             } else {
                 const TsTask<T>* d_nn1 = sb.put(nn1.data(), nb);
                 const TsTask<T>* d_nn2 = sb.put(nn2.data(), nb);
@@ -902,7 +961,8 @@ size_t linear_workspace_bytes(int64_t n, const pexp_options* o, int g_conv, int 
     s += align_up(sizeof(double) * (size_t)L.K_max * 48);                   // orthogonality diagnostic
     s += 2 * align_up(sizeof(double) * kpart_doubles(P, n, kmax, b_cap, pt.smax));
     s += align_up(sizeof(double) * sai_scratch_doubles(n, P * b_cap) + 64);
-    s += align_up(sizeof(double) * o->n_out);                               // (A u0) . g(t_i)
+    s += align_up(sizeof(double) * (o->n_out + P));                         // (A u0) . g(t_i)
+    s += align_up(sizeof(double) * 3 * (size_t)n) + kAlign;                 // bounded-mesh SAI factors
     if (sizeof(T) == 4) s += align_up(sizeof(float) * n * 2);               // A u0 as a double-float pair
     s += (size_t)(4 * P + 32) * kAlign;   // alignment of the per-window allocations
     return s;
@@ -910,7 +970,7 @@ size_t linear_workspace_bytes(int64_t n, const pexp_options* o, int g_conv, int 
 
 template <typename T, typename TO>
 int solve_linear_typed(pexp_ctx* c, const pexp_operator* op, const pexp_options* o, const double* u0d,
-                       const void* G_dev, int g_dtype, TO* Y, pexp_report* rep) {
+                       const void* G_dev, int g_dtype, TO* Y, pexp_report* rep, const WinOps<T>* wo, TO* Y_host) {
     cudaStream_t st = c->stream;
     Solver<T> S;
     S.c = c;
@@ -945,6 +1005,46 @@ int solve_linear_typed(pexp_ctx* c, const pexp_operator* op, const pexp_options*
             G = Gc;
         }
     }
+    // window-major pre-shifted source (averaged-Jacobian WR): window j's s_j samples start at
+    // row idx_j + j, and the shift by A u0 is already in them
+    const T* Gw = wo ? wo->Gwin : nullptr;
+    const bool have_src = G || Gw;
+    const int src_rows = Gw ? n_out + P - 1 : n_out;
+    auto src_first = [&](int j) -> const T* {
+        if (Gw) return Gw + (int64_t)(pt.idx[j] + j) * n;
+        return G ? G + (int64_t)pt.idx[j] * n : nullptr;
+    };
+    // a bounded mesh with the shift-and-invert space: one factored operator for all windows
+    WinOps<T> wo_bounded;
+    if (!wo && o->krylov == PEXP_KRYLOV_SAI && !S.od.x.periodic) {
+        const double gamma = o->sai_gamma * o->T / (double)P;
+        double* fac = as<double>(ws_alloc(c, sizeof(double) * 3 * (size_t)n));
+        int* flag = as<int>(ws_alloc(c, sizeof(int) * 4));
+        cudaMemsetAsync(flag, 0, sizeof(int), st);
+        Stage sf(c, 0);
+        VarOpTask vt{nullptr, fac, fac + n, fac + 2 * n, flag};
+        const VarOpTask* dvt = sf.put(&vt, 1);
+        sf.flush();
+        launch_vsai_factor(S.od.x, gamma, 0.0, dvt, 1, vsai_warmup(S.od.x, gamma, 0.0, 0.0), st);
+        check_launch(c);
+        int fl = 0;
+        d2h(c, &fl, flag, sizeof(int));
+        if (fl) throw StatusError{PEXP_ERR_UNSUPPORTED};
+        wo_bounded.var = true;
+        wo_bounded.vs.assign(P, VarSai{fac, fac + n, fac + 2 * n});
+        wo = &wo_bounded;
+    }
+    S.var = wo && wo->var;
+    S.jac = wo && wo->jac;
+    S.inv2dx = wo ? wo->inv2dx : 0.0;
+    auto win_ops = [&](Win<T>& W, int j) {
+        if (!wo) return;
+        if (wo->var) W.vs = wo->vs[j];
+        if (wo->jac) {
+            W.ubar = wo->ubar[j];
+            W.ubar64 = wo->ubar64[j];
+        }
+    };
     const int nwin = 2 * P;   // [0, P): source windows j=1..P; [P, 2P): homogeneous windows m=1..P
     S.wd = as<double>(ws_alloc(c, sizeof(double) * L.stride * nwin));
     S.wi = as<int>(ws_alloc(c, sizeof(int) * L.istride * nwin));
@@ -955,7 +1055,7 @@ int solve_linear_typed(pexp_ctx* c, const pexp_operator* op, const pexp_options*
     for (int k = 0; k < 2; ++k) S.kpart[k] = as<double>(ws_alloc(c, sizeof(double) * kpart_n));
     S.sai_scr = as<double>(ws_alloc(c, sizeof(double) * (sai_scratch_doubles(n, P * b_cap) + 64)));
     // one pole for every window: gamma = sai_gamma * T / P (the nominal subinterval length)
-    if (o->krylov == PEXP_KRYLOV_SAI) S.sai = sai_coefficients(S.od, o->sai_gamma * o->T / (double)P);
+    if (o->krylov == PEXP_KRYLOV_SAI && !S.var) S.sai = sai_coefficients(S.od, o->sai_gamma * o->T / (double)P);
     S.wi_host.assign((size_t)L.istride * nwin, 0);
 
     // ---- initial window state
@@ -964,7 +1064,7 @@ int solve_linear_typed(pexp_ctx* c, const pexp_operator* op, const pexp_options*
         for (int j = 0; j < P; ++j) {
             wih[(size_t)j * L.istride + WI_S] = pt.idx[j + 1] - pt.idx[j] + 1;
             wih[(size_t)j * L.istride + WI_KIND] = KIND_SOURCE;
-            wih[(size_t)j * L.istride + WI_I0] = pt.idx[j];
+            wih[(size_t)j * L.istride + WI_I0] = Gw ? pt.idx[j] + j : pt.idx[j];
             wih[(size_t)(P + j) * L.istride + WI_S] = pt.idx[j + 1] - pt.idx[j] + 1;
             wih[(size_t)(P + j) * L.istride + WI_KIND] = KIND_HOM;
             wih[(size_t)(P + j) * L.istride + WI_B] = 1;
@@ -977,10 +1077,16 @@ int solve_linear_typed(pexp_ctx* c, const pexp_operator* op, const pexp_options*
     cudaEventRecord(c->evp[0], st);
     // ---- shift: A u0, ||u0||, ||A u0||^2, (A u0) . g(t_i)
     double* nrm = S.partial + part_n - 8;   // [0] = ||u0||^2, [1] = ||A u0||^2
-    double* dots = G ? as<double>(ws_alloc(c, sizeof(double) * n_out)) : nullptr;
+    double* dots = have_src ? as<double>(ws_alloc(c, sizeof(double) * src_rows)) : nullptr;
     float* au0_split = (G && sizeof(T) == 4) ? as<float>(ws_alloc(c, sizeof(float) * n * 2)) : nullptr;
-    launch_stencil<double>(S.od, u0d, Au0, 1, 0, st);
-    check_launch(c);
+    if (Gw) {
+        // the window-major source carries its shift: no A u0 term in the Gram or in U
+        cudaMemsetAsync(Au0, 0, sizeof(double) * n, st);
+        cudaMemsetAsync(dots, 0, sizeof(double) * src_rows, st);
+    } else {
+        launch_stencil<double>(S.od, u0d, Au0, 1, 0, st);
+        check_launch(c);
+    }
     {
         Stage s0(c, 0);
         TsTask<double> t[2];
@@ -991,7 +1097,7 @@ int solve_linear_typed(pexp_ctx* c, const pexp_operator* op, const pexp_options*
         s0.flush();
         launch_ts_tn<double>(dt, 2, 1, 1, n, S.partial, st, 0);
         check_launch(c);
-        if (G) {
+        if (G && !Gw) {
             launch_row_dots<T>(Au0, G, n, n_out, dots, au0_split, st);
             check_launch(c);
         }
@@ -1011,7 +1117,7 @@ int solve_linear_typed(pexp_ctx* c, const pexp_operator* op, const pexp_options*
             TsTask<T> t;
             memset(&t, 0, sizeof(t));
             const int s = pt.idx[j + 1] - pt.idx[j] + 1;
-            t.X = G ? G + (int64_t)pt.idx[j] * n : nullptr;
+            t.X = src_first(j);
             t.ldx = n; t.p = s;
             t.Y = t.X; t.ldy = n; t.q = s; t.q1 = s;
             t.out = S.D(j) + L.off_gram;
@@ -1020,7 +1126,7 @@ int solve_linear_typed(pexp_ctx* c, const pexp_operator* op, const pexp_options*
         std::vector<const T*> gx(P);
         std::vector<int> gs(P);
         for (int j = 0; j < P; ++j) {
-            gx[j] = G ? G + (int64_t)pt.idx[j] * n : nullptr;
+            gx[j] = src_first(j);
             gs[j] = pt.idx[j + 1] - pt.idx[j] + 1;
         }
         const T* const* dgx = s1.put(gx.data(), P);
@@ -1029,13 +1135,13 @@ int solve_linear_typed(pexp_ctx* c, const pexp_operator* op, const pexp_options*
         s1.flush();
         const KGeom gg = krylov_geom(P, n);
         const int psg = pt.smax * pt.smax;
-        if (G) {
-            timed(c, PEXP_KC_SOURCE, (double)n * n_out * sizeof(T),
+        if (have_src) {
+            timed(c, PEXP_KC_SOURCE, (double)n * src_rows * sizeof(T),
                   [&] { launch_source_gram<T>(dgx, dgs, P, pt.smax, n, gg, S.kpart[0], psg, st); });
             check_launch(c);
         }
         launch_source_eig(L, S.wd, S.wi, dall, P, std::max(o->svd_tol, svd_floor), b_cap, dots, nrm + 1, st,
-                          Parts{G ? S.kpart[0] : nullptr, gg.nchunks, psg});
+                          Parts{have_src ? S.kpart[0] : nullptr, gg.nchunks, psg});
         check_launch(c);
         d2h(c, S.wi_host.data(), S.wi, sizeof(int) * S.wi_host.size());
     }
@@ -1070,6 +1176,7 @@ int solve_linear_typed(pexp_ctx* c, const pexp_operator* op, const pexp_options*
         W.S = as<T>(bs_alloc(c, sizeof(T) * (size_t)n * (L.ycols - 1) * W.b));
         W.Wlo = std::is_same<T, float>::value ? as<float>(bs_alloc(c, sizeof(float) * (size_t)n * W.b)) : nullptr;
         W.V1lo = std::is_same<T, float>::value ? as<float>(bs_alloc(c, sizeof(float) * (size_t)n * W.b)) : nullptr;
+        win_ops(W, j);
         Vnh[j] = W.V;
         src.push_back(W);
     }
@@ -1085,7 +1192,7 @@ int solve_linear_typed(pexp_ctx* c, const pexp_operator* op, const pexp_options*
             const int s = pt.idx[j + 1] - pt.idx[j] + 1;
             TsTask<T> t;
             memset(&t, 0, sizeof(t));
-            t.X = G ? G + (int64_t)pt.idx[j] * n : nullptr; t.ldx = n; t.xs = Au0; t.p = s; t.q = W.b;
+            t.X = src_first(j); t.ldx = n; t.xs = Au0; t.p = s; t.q = W.b;
             t.Z = W.V; t.ldz = n; t.Tm = S.D(j) + L.off_zs; t.ldt = L.s_max; t.alpha = 1.0; t.beta = 0.0;
             tu[a] = t;
             mpq = std::max(mpq, s * W.b);
@@ -1181,7 +1288,40 @@ int solve_linear_typed(pexp_ctx* c, const pexp_operator* op, const pexp_options*
     cudaEventRecord(c->evp[2], st);
     // ---- homogeneous chain over windows 2..P
     std::vector<T*> Vh(P, nullptr);
-    std::vector<int> Kh(P, 0);
+    std::vector<int> Kh(P, 0), steps_h(P, 0);
+    // reconstruction task of window m: its nonhomogeneous part and (m >= 1) the continuation
+    // of the solution from T_m; the first sample of a window m >= 1 is the last of window m - 1
+    auto recon_task = [&](int m) {
+        ReconTask<T> rt;
+        memset(&rt, 0, sizeof(rt));
+        const int s = pt.idx[m + 1] - pt.idx[m] + 1;
+        if (Vnh[m]) { rt.V1 = Vnh[m]; rt.C1 = S.D(m) + L.off_Y; rt.ld1 = n; rt.K1 = Knh[m]; rt.ldc1 = L.K_max; }
+        if (m >= 1 && Vh[m] && Kh[m] > 0) { rt.V2 = Vh[m]; rt.C2 = S.D(P + m) + L.off_Y; rt.ld2 = n; rt.K2 = Kh[m]; rt.ldc2 = L.K_max; }
+        rt.r0 = (m == 0) ? 0 : 1;
+        rt.ns = s - rt.r0;
+        rt.i0 = pt.idx[m] + rt.r0;
+        return rt;
+    };
+    // host outputs: a window's rows are final once its continuation is solved, so they are
+    // reconstructed then and copied out on the copy stream while the chain goes on
+    auto emit_window = [&](int m) {
+        const ReconTask<T> rt = recon_task(m);
+        Stage so(c, 1);
+        const ReconTask<T>* drt = so.put(&rt, 1);
+        so.flush();
+        timed(c, PEXP_KC_RECON, (double)n * (rt.K1 + rt.K2) * sizeof(T) + (double)n * rt.ns * sizeof(TO),
+              [&] { launch_recon<T, TO>(drt, 1, rt.ns, n, u0d, Y, n, std::max(1, rt.K1 + rt.K2), st); });
+        check_launch(c);
+        cudaEventRecord(c->ev_out, st);
+        cudaStreamWaitEvent(c->cs, c->ev_out, 0);
+        const cudaError_t e = cudaMemcpyAsync(Y_host + (size_t)rt.i0 * n, Y + (size_t)rt.i0 * n,
+                                              sizeof(TO) * (size_t)rt.ns * n, cudaMemcpyDeviceToHost, c->cs);
+        if (e != cudaSuccess) {
+            fail_cuda(e, "cudaMemcpyAsync D2H (window outputs)", __FILE__, __LINE__);
+            throw StatusError{PEXP_ERR_CUDA};
+        }
+    };
+    if (Y_host) emit_window(0);
     int k_hom_max = 0, k_hom_sum = 0;
     T* Sh = as<T>(bs_alloc(c, sizeof(T) * (size_t)n * (L.ycols - 1)));
     float* Whlo = std::is_same<T, float>::value ? as<float>(bs_alloc(c, sizeof(float) * (size_t)n)) : nullptr;
@@ -1265,6 +1405,7 @@ int solve_linear_typed(pexp_ctx* c, const pexp_operator* op, const pexp_options*
         // a zero z (nothing to continue) is marked converged with an empty basis on the device
         std::vector<Win<T>> one(1);
         one[0].w = P + m; one[0].V = Vh[m]; one[0].S = Sh; one[0].b = 1; one[0].Wlo = Whlo; one[0].V1lo = nullptr;
+        win_ops(one[0], m);   // the continuation on subinterval m has that subinterval's operator
         int kh = 0;
         notconv += S.run(one, KIND_HOM, &kh);
         const int kk = S.wi_host[(size_t)(P + m) * L.istride + WI_K];   // state after the last step
@@ -1272,23 +1413,27 @@ int solve_linear_typed(pexp_ctx* c, const pexp_operator* op, const pexp_options*
         if (o->diagnostics & PEXP_DIAG_ORTH) orth_max = std::max(orth_max, S.orth_defect(Vh[m], kk));
         k_hom_max = std::max(k_hom_max, kh);
         k_hom_sum += kh;
+        steps_h[m] = kh;
+        if (Y_host) emit_window(m);
     }
 
     cudaEventRecord(c->evp[3], st);
-    // ---- reconstruction of all windows
-    {
+    if (Y_host) {
+        // every window has been reconstructed and is on its way to the host
+        cudaEventRecord(c->evp[4], st);
+        sync(c);
+        const cudaError_t e = cudaStreamSynchronize(c->cs);
+        if (e != cudaSuccess) {
+            fail_cuda(e, "cudaStreamSynchronize (copy stream)", __FILE__, __LINE__);
+            throw StatusError{PEXP_ERR_CUDA};
+        }
+    } else {
+        // ---- reconstruction of all windows in one launch
         Stage s4(c, 1);
         std::vector<ReconTask<T>> rts;
         int maxc = 1, maxns = 1;
         for (int m = 0; m < P; ++m) {
-            ReconTask<T> rt;
-            memset(&rt, 0, sizeof(rt));
-            const int s = pt.idx[m + 1] - pt.idx[m] + 1;
-            if (Vnh[m]) { rt.V1 = Vnh[m]; rt.C1 = S.D(m) + L.off_Y; rt.ld1 = n; rt.K1 = Knh[m]; rt.ldc1 = L.K_max; }
-            if (m >= 1 && Vh[m] && Kh[m] > 0) { rt.V2 = Vh[m]; rt.C2 = S.D(P + m) + L.off_Y; rt.ld2 = n; rt.K2 = Kh[m]; rt.ldc2 = L.K_max; }
-            rt.r0 = (m == 0) ? 0 : 1;
-            rt.ns = s - rt.r0;
-            rt.i0 = pt.idx[m] + rt.r0;
+            const ReconTask<T> rt = recon_task(m);
             maxc = std::max(maxc, rt.K1 + rt.K2);
             maxns = std::max(maxns, rt.ns);
             rts.push_back(rt);
@@ -1328,6 +1473,12 @@ int solve_linear_typed(pexp_ctx* c, const pexp_operator* op, const pexp_options*
         rep->est_max = est_max;
         rep->sigma_ratio_max = sig_max;
         rep->orth_max = orth_max;
+        for (int j = 0; j < std::min(P, PEXP_REPORT_SUBS); ++j) {
+            rep->sub_rank[j] = mj[j];
+            rep->sub_steps[j] = mj[j] > 0 ? S.wi_host[(size_t)j * L.istride + WI_STEPS] : 0;
+            rep->sub_hom_steps[j] = steps_h[j];
+            rep->sub_restarts[j] = 0;
+        }
         const double w = (double)sizeof(T);
         double bytes = 0;
         // algorithmic bytes, each array counted once per pass the method needs: two passes
@@ -1350,7 +1501,8 @@ int solve_linear_typed(pexp_ctx* c, const pexp_operator* op, const pexp_options*
 
 int solve_linear_dispatch(pexp_ctx* c, const pexp_operator* op, const pexp_options* o, const void* y0_dev,
                           const void* G_dev, int g_dtype, void* Y_dev, int y_dtype, pexp_report* rep,
-                          size_t keep_top) {
+                          size_t keep_top, const WinOps<double>* wo64 = nullptr, const WinOps<float>* wo32 = nullptr,
+                          void* Y_host = nullptr) {
     const OpDesc od = make_opdesc(*op);
     const int64_t n = od.n;
     const bool fp64 = o->precision == PEXP_FP64;
@@ -1369,11 +1521,16 @@ int solve_linear_dispatch(pexp_ctx* c, const pexp_operator* op, const pexp_optio
     // the initial condition is FP64 in every precision (A u0 amplifies its rounding by ||A||)
     const double* u0d = reinterpret_cast<const double*>(y0_dev);
     if (fp64) {
-        if (y_dtype == PEXP_F64) return solve_linear_typed<double, double>(c, op, o, u0d, G_dev, g_dtype, as<double>(Y_dev), rep);
-        return solve_linear_typed<double, float>(c, op, o, u0d, G_dev, g_dtype, as<float>(Y_dev), rep);
+        if (y_dtype == PEXP_F64)
+            return solve_linear_typed<double, double>(c, op, o, u0d, G_dev, g_dtype, as<double>(Y_dev), rep, wo64,
+                                                      as<double>(Y_host));
+        return solve_linear_typed<double, float>(c, op, o, u0d, G_dev, g_dtype, as<float>(Y_dev), rep, wo64,
+                                                 as<float>(Y_host));
     }
-    if (y_dtype == PEXP_F64) return solve_linear_typed<float, double>(c, op, o, u0d, G_dev, g_dtype, as<double>(Y_dev), rep);
-    return solve_linear_typed<float, float>(c, op, o, u0d, G_dev, g_dtype, as<float>(Y_dev), rep);
+    if (y_dtype == PEXP_F64)
+        return solve_linear_typed<float, double>(c, op, o, u0d, G_dev, g_dtype, as<double>(Y_dev), rep, wo32,
+                                                 as<double>(Y_host));
+    return solve_linear_typed<float, float>(c, op, o, u0d, G_dev, g_dtype, as<float>(Y_dev), rep, wo32, as<float>(Y_host));
 }
 
 template <typename F>
@@ -1415,6 +1572,8 @@ void pexp_default_options(pexp_options* o) {
     o->wr_max_iter = 50;
     o->wr_tol = 1e-6;
     o->burgers_form = 0;
+    o->jacobian = 0;
+    o->wr_diverge = 3;
 }
 
 const char* pexp_status_string(int s) {
@@ -1429,6 +1588,7 @@ const char* pexp_status_string(int s) {
         case PEXP_ERR_TIMEOUT: return "device wait timed out";
         case PEXP_ERR_UNSUPPORTED: return "unsupported operator/precision combination";
         case PEXP_ERR_SCRATCH_LIMIT: return "request exceeds the fixed scratch of the allocation-free entry point";
+        case PEXP_ERR_WR_DIVERGED: return "waveform relaxation diverged (the update grew in successive iterations)";
         default: return "unknown status";
     }
 }
@@ -1451,6 +1611,8 @@ int pexp_create(pexp_ctx** out, int device, void* stream) {
     }
     for (int k = 0; k < kSlots; ++k) cudaEventCreateWithFlags(&c->slot_ev[k], cudaEventDisableTiming);
     if (cudaStreamCreateWithFlags(&c->s2, cudaStreamNonBlocking) != cudaSuccess ||
+        cudaStreamCreateWithFlags(&c->cs, cudaStreamNonBlocking) != cudaSuccess ||
+        cudaEventCreateWithFlags(&c->ev_out, cudaEventDisableTiming) != cudaSuccess ||
         cudaEventCreateWithFlags(&c->ev_sp, cudaEventDisableTiming) != cudaSuccess ||
         cudaEventCreateWithFlags(&c->ev_pj, cudaEventDisableTiming) != cudaSuccess) {
         pexp_destroy(c);
@@ -1466,8 +1628,14 @@ int pexp_create(pexp_ctx** out, int device, void* stream) {
 
 int pexp_destroy(pexp_ctx* c) {
     if (!c) return PEXP_OK;
+    for (pexp_ctx* w : c->workers) pexp_destroy(w);
+    c->workers.clear();
     cudaSetDevice(c->device);
     if (c->stream) cudaStreamSynchronize(c->stream);
+    if (c->owns_stream && c->stream) {
+        cudaStreamDestroy(c->stream);
+        c->stream = nullptr;
+    }
     if (c->ws) cudaFree(c->ws);
     if (c->bs) cudaFree(c->bs);
     for (int h = 0; h < 2; ++h) {
@@ -1484,6 +1652,11 @@ int pexp_destroy(pexp_ctx* c) {
         cudaStreamSynchronize(c->s2);
         cudaStreamDestroy(c->s2);
     }
+    if (c->cs) {
+        cudaStreamSynchronize(c->cs);
+        cudaStreamDestroy(c->cs);
+    }
+    if (c->ev_out) cudaEventDestroy(c->ev_out);
     if (c->ev_sp) cudaEventDestroy(c->ev_sp);
     if (c->ev_pj) cudaEventDestroy(c->ev_pj);
     if (c->ev0) cudaEventDestroy(c->ev0);
@@ -1500,8 +1673,13 @@ int pexp_set_stream(pexp_ctx* c, void* stream) {
     return PEXP_OK;
 }
 
-int pexp_solve_linear(pexp_ctx* c, const pexp_operator* op, const pexp_options* o, const void* y0_dev,
-                      const void* G_dev, int g_dtype, void* Y_dev, int y_dtype, pexp_report* rep) {
+}  // extern "C"
+
+namespace {
+// One linear solve with device inputs; Y_host != NULL: the outputs are also copied to Y_host
+// window by window as they are completed (the host entry point).
+int solve_linear_entry(pexp_ctx* c, const pexp_operator* op, const pexp_options* o, const void* y0_dev,
+                       const void* G_dev, int g_dtype, void* Y_dev, int y_dtype, pexp_report* rep, void* Y_host) {
     if (!c || !y0_dev || !Y_dev) return PEXP_ERR_INVALID_ARG;
     if ((g_dtype != PEXP_F64 && g_dtype != PEXP_F32) || (y_dtype != PEXP_F64 && y_dtype != PEXP_F32))
         return PEXP_ERR_INVALID_ARG;
@@ -1513,7 +1691,9 @@ int pexp_solve_linear(pexp_ctx* c, const pexp_operator* op, const pexp_options* 
     c->kt.reset((o->diagnostics & PEXP_DIAG_KTIME) != 0, ((unsigned)o->diagnostics >> 8) & 0xffu,
                 ((unsigned)o->diagnostics >> 16) & 0xfu);
     cudaEventRecord(c->ev0, c->stream);
-    int r = guarded([&] { return solve_linear_dispatch(c, op, o, y0_dev, G_dev, g_dtype, Y_dev, y_dtype, rep, 0); });
+    int r = guarded([&] {
+        return solve_linear_dispatch(c, op, o, y0_dev, G_dev, g_dtype, Y_dev, y_dtype, rep, 0, nullptr, nullptr, Y_host);
+    });
     cudaEventRecord(c->ev1, c->stream);
     cudaEventSynchronize(c->ev1);
     if (rep && c->kt.on) {
@@ -1523,6 +1703,7 @@ int pexp_solve_linear(pexp_ctx* c, const pexp_operator* op, const pexp_options* 
             rep->k_ms[k.cls] += ms;
             rep->k_launches[k.cls] += 1;
             rep->k_bytes[k.cls] += k.bytes;
+            rep->k_bytes_alg[k.cls] += k.alg;
         }
     }
     if (rep) {
@@ -1533,6 +1714,14 @@ int pexp_solve_linear(pexp_ctx* c, const pexp_operator* op, const pexp_options* 
         rep->status = r;
     }
     return r;
+}
+}  // namespace
+
+extern "C" {
+
+int pexp_solve_linear(pexp_ctx* c, const pexp_operator* op, const pexp_options* o, const void* y0_dev,
+                      const void* G_dev, int g_dtype, void* Y_dev, int y_dtype, pexp_report* rep) {
+    return solve_linear_entry(c, op, o, y0_dev, G_dev, g_dtype, Y_dev, y_dtype, rep, nullptr);
 }
 
 int pexp_solve_linear_host(pexp_ctx* c, const pexp_operator* op, const pexp_options* o, const void* y0_host,
@@ -1560,12 +1749,160 @@ int pexp_solve_linear_host(pexp_ctx* c, const pexp_operator* op, const pexp_opti
     void* Yd = p;
     PEXP_CUDA_TRY(cudaMemcpyAsync(y0d, y0_host, n * 8, cudaMemcpyHostToDevice, c->stream));
     if (G_host) PEXP_CUDA_TRY(cudaMemcpyAsync(Gd, G_host, n * o->n_out * gs, cudaMemcpyHostToDevice, c->stream));
-    int r = pexp_solve_linear(c, op, o, y0d, Gd, g_dtype, Yd, y_dtype, rep);
-    if (r == PEXP_OK || r == PEXP_ERR_NOT_CONVERGED) {
-        PEXP_CUDA_TRY(cudaMemcpyAsync(Y_host, Yd, n * o->n_out * ys, cudaMemcpyDeviceToHost, c->stream));
-        PEXP_CUDA_TRY(cudaStreamSynchronize(c->stream));
+    // the outputs leave window by window on the copy stream while the continuation chain runs
+    return solve_linear_entry(c, op, o, y0d, Gd, g_dtype, Yd, y_dtype, rep, Y_host);
+}
+
+}  // extern "C"
+
+namespace {
+
+constexpr int kDefaultBatchWorkers = 4;
+
+double problem_cost(const pexp_problem& p) {
+    const double n = (double)p.op.nx * (p.op.dim == 2 ? (double)p.op.ny : 1.0);
+    return n * ((double)p.opts.n_out + 40.0 * p.opts.P);
+}
+
+int ensure_workers(pexp_ctx* c, int k) {
+    while ((int)c->workers.size() < k) {
+        cudaSetDevice(c->device);
+        cudaStream_t st = nullptr;
+        if (cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking) != cudaSuccess) return PEXP_ERR_CUDA;
+        pexp_ctx* w = nullptr;
+        const int r = pexp_create(&w, c->device, st);
+        if (r) {
+            cudaStreamDestroy(st);
+            return r;
+        }
+        w->owns_stream = true;
+        c->workers.push_back(w);
     }
-    return r;
+    return PEXP_OK;
+}
+
+int run_batched(pexp_ctx* c, int count, const pexp_problem* probs, pexp_report* reps, int k) {
+    k = std::max(1, std::min(k, count));
+    int r = ensure_workers(c, k);
+    if (r) return r;
+    cudaSetDevice(c->device);
+    // the workers start after the work queued on the caller's stream
+    PEXP_CUDA_TRY(cudaEventRecord(c->ev0, c->stream));
+    for (int w = 0; w < k; ++w) PEXP_CUDA_TRY(cudaStreamWaitEvent(c->workers[w]->stream, c->ev0, 0));
+    std::vector<int> order(count);
+    for (int i = 0; i < count; ++i) order[i] = i;
+    std::stable_sort(order.begin(), order.end(),
+                     [&](int a, int b) { return problem_cost(probs[a]) > problem_cost(probs[b]); });
+    std::vector<int> st(count, PEXP_OK);
+    std::atomic<int> next{0};
+    auto work = [&](pexp_ctx* w) {
+        for (;;) {
+            const int q = next.fetch_add(1);
+            if (q >= count) break;
+            const int i = order[q];
+            const pexp_problem& p = probs[i];
+            pexp_report local;
+            st[i] = solve_linear_entry(w, &p.op, &p.opts, p.y0_dev, p.G_dev, p.g_dtype, p.Y_dev, p.y_dtype,
+                                       reps ? &reps[i] : &local, nullptr);
+        }
+    };
+    std::vector<std::thread> th;
+    for (int w = 1; w < k; ++w) th.emplace_back(work, c->workers[w]);
+    work(c->workers[0]);
+    for (auto& t : th) t.join();
+    // later work on the caller's stream comes after every worker's
+    for (int w = 0; w < k; ++w) {
+        PEXP_CUDA_TRY(cudaEventRecord(c->workers[w]->ev1, c->workers[w]->stream));
+        PEXP_CUDA_TRY(cudaStreamWaitEvent(c->stream, c->workers[w]->ev1, 0));
+    }
+    for (int i = 0; i < count; ++i)
+        if (st[i] != PEXP_OK) return st[i];
+    return PEXP_OK;
+}
+
+std::string device_key(int dev) {
+    cudaDeviceProp pr;
+    if (cudaGetDeviceProperties(&pr, dev) != cudaSuccess) return "unknown";
+    return std::string(pr.name) + " sm" + std::to_string(pr.multiProcessorCount);
+}
+
+}  // namespace
+
+extern "C" {
+
+int pexp_solve_batched(pexp_ctx* c, int count, const pexp_problem* probs, pexp_report* reps) {
+    if (!c || count < 0 || (count > 0 && !probs)) return PEXP_ERR_INVALID_ARG;
+    for (int i = 0; i < count; ++i) {
+        const pexp_problem& p = probs[i];
+        if (!p.y0_dev || !p.Y_dev) return PEXP_ERR_INVALID_ARG;
+        if ((p.g_dtype != PEXP_F64 && p.g_dtype != PEXP_F32) || (p.y_dtype != PEXP_F64 && p.y_dtype != PEXP_F32))
+            return PEXP_ERR_INVALID_ARG;
+        const int v = validate(&p.op, &p.opts);
+        if (v) return v;
+    }
+    if (reps) memset(reps, 0, sizeof(pexp_report) * (size_t)count);
+    if (count == 0) return PEXP_OK;
+    return run_batched(c, count, probs, reps, c->batch_workers > 0 ? c->batch_workers : kDefaultBatchWorkers);
+}
+
+int pexp_autotune(pexp_ctx* c, int count, const pexp_problem* probs, const char* path) {
+    if (!c || count < 1 || !probs) return PEXP_ERR_INVALID_ARG;
+    cudaSetDevice(c->device);
+    const std::string key = device_key(c->device);
+    if (path) {
+        // a table for this device: {"device": "<name> sm<count>", "batch_workers": k, ...}
+        FILE* f = fopen(path, "r");
+        if (f) {
+            std::string txt;
+            char buf[4096];
+            size_t got;
+            while ((got = fread(buf, 1, sizeof(buf), f)) > 0) txt.append(buf, got);
+            fclose(f);
+            const size_t dk = txt.find("\"device\": \"" + key + "\"");
+            const size_t bw = txt.find("\"batch_workers\": ");
+            if (dk != std::string::npos && bw != std::string::npos) {
+                const int k = atoi(txt.c_str() + bw + 17);
+                if (k >= 1 && k <= 64) {
+                    c->batch_workers = k;
+                    return PEXP_OK;
+                }
+            }
+        }
+    }
+    for (int i = 0; i < count; ++i) {
+        const int v = validate(&probs[i].op, &probs[i].opts);
+        if (v) return v;
+    }
+    const int cand[] = {1, 2, 4, 8, 16};
+    double best_ms = 1e300;
+    int best = kDefaultBatchWorkers;
+    std::string timings;
+    for (int k : cand) {
+        int r = run_batched(c, count, probs, nullptr, k);   // warm-up: workspaces grown
+        if (r != PEXP_OK && r != PEXP_ERR_NOT_CONVERGED) return r;
+        cudaStreamSynchronize(c->stream);
+        const auto t0 = std::chrono::steady_clock::now();
+        r = run_batched(c, count, probs, nullptr, k);
+        cudaStreamSynchronize(c->stream);
+        const double ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+        if (r != PEXP_OK && r != PEXP_ERR_NOT_CONVERGED) return r;
+        char e[64];
+        snprintf(e, sizeof(e), "%s\"%d\": %.3f", timings.empty() ? "" : ", ", k, ms);
+        timings += e;
+        if (ms < best_ms) {
+            best_ms = ms;
+            best = k;
+        }
+    }
+    c->batch_workers = best;
+    if (path) {
+        FILE* f = fopen(path, "w");
+        if (!f) return PEXP_ERR_INVALID_ARG;
+        fprintf(f, "{\"device\": \"%s\", \"batch_workers\": %d, \"problems\": %d, \"timings_ms\": {%s}}\n",
+                key.c_str(), best, count, timings.c_str());
+        fclose(f);
+    }
+    return PEXP_OK;
 }
 
 int pexp_solve_burgers(pexp_ctx* c, const pexp_operator* op, const pexp_options* o, const void* u0_dev,
@@ -1573,9 +1910,15 @@ int pexp_solve_burgers(pexp_ctx* c, const pexp_operator* op, const pexp_options*
     if (!c || !u0_dev || !U_dev || !op || !o) return PEXP_ERR_INVALID_ARG;
     if (op->dim != 1 || op->ax != 0.0) return PEXP_ERR_INVALID_ARG;
     if (dtype != PEXP_F64 && dtype != PEXP_F32) return PEXP_ERR_INVALID_ARG;
-    if (o->wr_max_iter < 1 || !(o->wr_tol > 0)) return PEXP_ERR_INVALID_ARG;
+    if (o->wr_max_iter < 1 || !(o->wr_tol > 0) || o->wr_diverge < 0) return PEXP_ERR_INVALID_ARG;
+    if (o->jacobian != 0 && o->jacobian != 1) return PEXP_ERR_INVALID_ARG;
     int v = validate(op, o);
     if (v) return v;
+    // the averaged Jacobian: conservative form, shift-and-invert space, iterates in the
+    // solver's own precision
+    if (o->jacobian && (o->burgers_form != 0 || o->krylov != PEXP_KRYLOV_SAI ||
+                        (dtype == PEXP_F64) != (o->precision == PEXP_FP64)))
+        return PEXP_ERR_UNSUPPORTED;
     if (rep) memset(rep, 0, sizeof(*rep));
     cudaSetDevice(c->device);
     const OpDesc od = make_opdesc(*op);
@@ -1586,12 +1929,21 @@ int pexp_solve_burgers(pexp_ctx* c, const pexp_operator* op, const pexp_options*
     c->launches = 0;
     cudaEventRecord(c->ev0, c->stream);
     int status = guarded([&]() -> int {
-        // live WR buffers at the bottom of the workspace: previous iterate, source
-        const size_t keep = align_up(es * n * nt) * 2 + align_up(sizeof(double) * 2 * nt) + kAlign;
         const bool fp64 = o->precision == PEXP_FP64;
-        Partition pt = make_partition(nt, o->P);
+        const int P = o->P;
+        Partition pt = make_partition(nt, P);
+        const int wrows = nt + P - 1;   // window-major source rows (boundary samples twice)
+        const bool jac = o->jacobian != 0;
+        // live WR buffers at the bottom of the workspace: previous iterate, source, norms, and for
+        // the averaged Jacobian the window states, the factors and the window-major source
+        size_t keep = align_up(es * n * nt) * 2 + align_up(sizeof(double) * 2 * nt) + kAlign;
+        if (jac)
+            keep += align_up(sizeof(double) * n) + align_up(sizeof(double) * (size_t)P * n) + align_up(es * (size_t)P * n) +
+                    align_up(sizeof(double) * 3 * (size_t)P * n) + align_up(es * (size_t)wrows * n) +
+                    align_up(sizeof(int) * (P + 1)) + 2 * align_up(sizeof(int) * wrows) + align_up(8 * (size_t)P) +
+                    align_up(sizeof(int) * P) + align_up(sizeof(VarOpTask) * P) + 16 * kAlign;
         const int b_cap = std::min(std::min(o->max_rank, PEXP_MAX_RANK), pt.smax);
-        const int g_conv = (dtype == PEXP_F64) != fp64;
+        const int g_conv = jac ? 0 : ((dtype == PEXP_F64) != fp64);
         size_t need = keep + align_up(sizeof(double) * n) +
                       (fp64 ? linear_workspace_bytes<double>(n, o, g_conv, b_cap)
                             : linear_workspace_bytes<float>(n, o, g_conv, b_cap));
@@ -1601,6 +1953,58 @@ int pexp_solve_burgers(pexp_ctx* c, const pexp_operator* op, const pexp_options*
         char* Uprev = reinterpret_cast<char*>(ws_alloc(c, es * n * nt));
         char* Gk = reinterpret_cast<char*>(ws_alloc(c, es * n * nt));
         double* norms = as<double>(ws_alloc(c, sizeof(double) * 2 * nt));
+        // averaged-Jacobian buffers and the fixed per-window operator descriptors
+        WinOps<double> wo64;
+        WinOps<float> wo32;
+        double *Au0 = nullptr, *ubar64 = nullptr, *fac = nullptr;
+        char *ubarT = nullptr, *Gwin = nullptr;
+        int *idx_d = nullptr, *rw_d = nullptr, *ri_d = nullptr, *flags = nullptr;
+        unsigned long long* umax_bits = nullptr;
+        VarOpTask* vtasks = nullptr;
+        const double gamma = o->sai_gamma * o->T / (double)P;
+        if (jac) {
+            Au0 = as<double>(ws_alloc(c, sizeof(double) * n));
+            ubar64 = as<double>(ws_alloc(c, sizeof(double) * (size_t)P * n));
+            ubarT = reinterpret_cast<char*>(ws_alloc(c, es * (size_t)P * n));
+            fac = as<double>(ws_alloc(c, sizeof(double) * 3 * (size_t)P * n));
+            Gwin = reinterpret_cast<char*>(ws_alloc(c, es * (size_t)wrows * n));
+            idx_d = as<int>(ws_alloc(c, sizeof(int) * (P + 1)));
+            rw_d = as<int>(ws_alloc(c, sizeof(int) * wrows));
+            ri_d = as<int>(ws_alloc(c, sizeof(int) * wrows));
+            umax_bits = reinterpret_cast<unsigned long long*>(ws_alloc(c, 8 * (size_t)P));
+            flags = as<int>(ws_alloc(c, sizeof(int) * P));
+            vtasks = reinterpret_cast<VarOpTask*>(ws_alloc(c, sizeof(VarOpTask) * P));
+            std::vector<int> rw, ri;
+            for (int j = 0; j < P; ++j)
+                for (int i = pt.idx[j]; i <= pt.idx[j + 1]; ++i) {
+                    rw.push_back(j);
+                    ri.push_back(i);
+                }
+            std::vector<VarOpTask> vt(P);
+            for (int j = 0; j < P; ++j) {
+                double* f = fac + 3 * (size_t)j * n;
+                vt[j] = VarOpTask{ubar64 + (size_t)j * n, f, f + n, f + 2 * n, flags + j};
+                const VarSai vs{f, f + n, f + 2 * n};
+                wo64.vs.push_back(vs);
+                wo32.vs.push_back(vs);
+                wo64.ubar.push_back(reinterpret_cast<const double*>(ubarT) + (size_t)j * n);
+                wo32.ubar.push_back(reinterpret_cast<const float*>(ubarT) + (size_t)j * n);
+                wo64.ubar64.push_back(ubar64 + (size_t)j * n);
+                wo32.ubar64.push_back(ubar64 + (size_t)j * n);
+            }
+            wo64.var = wo32.var = true;
+            wo64.jac = wo32.jac = true;
+            wo64.inv2dx = wo32.inv2dx = inv2dx;
+            wo64.Gwin = reinterpret_cast<const double*>(Gwin);
+            wo32.Gwin = reinterpret_cast<const float*>(Gwin);
+            PEXP_CUDA_TRY(cudaMemcpyAsync(idx_d, pt.idx.data(), sizeof(int) * (P + 1), cudaMemcpyHostToDevice, c->stream));
+            PEXP_CUDA_TRY(cudaMemcpyAsync(rw_d, rw.data(), sizeof(int) * wrows, cudaMemcpyHostToDevice, c->stream));
+            PEXP_CUDA_TRY(cudaMemcpyAsync(ri_d, ri.data(), sizeof(int) * wrows, cudaMemcpyHostToDevice, c->stream));
+            PEXP_CUDA_TRY(cudaMemcpyAsync(vtasks, vt.data(), sizeof(VarOpTask) * P, cudaMemcpyHostToDevice, c->stream));
+            launch_stencil<double>(od, reinterpret_cast<const double*>(u0_dev), Au0, 1, 0, c->stream);
+            check_launch(c);
+            sync(c);   // the host vectors above go out of scope
+        }
         const size_t top = c->ws_top;
         // first iterate
         if (init_dev) {
@@ -1616,7 +2020,7 @@ int pexp_solve_burgers(pexp_ctx* c, const pexp_operator* op, const pexp_options*
         std::vector<double> nh(2 * nt);
         int status_l = PEXP_ERR_WR_NOT_CONVERGED;
         double delta = 0;
-        int it = 0;
+        int it = 0, grew = 0;
         pexp_report lrep;
         for (it = 1; it <= o->wr_max_iter; ++it) {
             if (dtype == PEXP_F64) launch_burgers_source<double>(od, as<double>(Uprev), as<double>(Gk), nt, o->burgers_form, inv2dx, c->stream);
@@ -1627,7 +2031,43 @@ int pexp_solve_burgers(pexp_ctx* c, const pexp_operator* op, const pexp_options*
                 else launch_add<float>(as<float>(Gk), reinterpret_cast<const float*>(forcing_dev), n * nt, c->stream);
                 check_launch(c);
             }
-            int lr = solve_linear_dispatch(c, op, o, u0_dev, Gk, dtype, U_dev, dtype, &lrep, top);
+            int lr;
+            if (jac) {
+                // J_{k,j} at the trapezoidal time mean of the iterate over subinterval j (eq.
+                // piecewiseJac); the factors of I - gamma (A + J_{k,j}); the shifted source
+                // A u0 + g_k - J_{k,j} (u_k - u0) of every subinterval (eq. sourceParallel)
+                PEXP_CUDA_TRY(cudaMemsetAsync(umax_bits, 0, 8 * (size_t)P, c->stream));
+                PEXP_CUDA_TRY(cudaMemsetAsync(flags, 0, sizeof(int) * P, c->stream));
+                if (dtype == PEXP_F64)
+                    launch_window_average<double>(as<double>(Uprev), n, idx_d, P, ubar64, as<double>(ubarT), umax_bits, c->stream);
+                else
+                    launch_window_average<float>(as<float>(Uprev), n, idx_d, P, ubar64, as<float>(ubarT), umax_bits, c->stream);
+                check_launch(c);
+                std::vector<unsigned long long> ub(P);
+                d2h(c, ub.data(), umax_bits, 8 * (size_t)P);
+                double umax = 0.0;
+                for (int j = 0; j < P; ++j) {
+                    double x;
+                    memcpy(&x, &ub[j], sizeof(double));
+                    umax = std::max(umax, x);
+                }
+                launch_vsai_factor(od.x, gamma, inv2dx, vtasks, P, vsai_warmup(od.x, gamma, inv2dx, umax), c->stream);
+                check_launch(c);
+                if (dtype == PEXP_F64)
+                    launch_jac_source<double>(od.x, inv2dx, Au0, reinterpret_cast<const double*>(u0_dev), as<double>(Gk),
+                                              as<double>(Uprev), ubar64, rw_d, ri_d, wrows, as<double>(Gwin), c->stream);
+                else
+                    launch_jac_source<float>(od.x, inv2dx, Au0, reinterpret_cast<const double*>(u0_dev), as<float>(Gk),
+                                             as<float>(Uprev), ubar64, rw_d, ri_d, wrows, as<float>(Gwin), c->stream);
+                check_launch(c);
+                std::vector<int> fl(P);
+                d2h(c, fl.data(), flags, sizeof(int) * P);
+                for (int j = 0; j < P; ++j)
+                    if (fl[j]) return PEXP_ERR_UNSUPPORTED;   // I - gamma (A + J) not diagonally dominant
+                lr = solve_linear_dispatch(c, op, o, u0_dev, nullptr, dtype, U_dev, dtype, &lrep, top, &wo64, &wo32);
+            } else {
+                lr = solve_linear_dispatch(c, op, o, u0_dev, Gk, dtype, U_dev, dtype, &lrep, top);
+            }
             if (lr != PEXP_OK && lr != PEXP_ERR_NOT_CONVERGED) return lr;
             if (dtype == PEXP_F64) launch_row_diff_norms<double>(as<double>(U_dev), as<double>(Uprev), n, nt, norms, c->stream);
             else launch_row_diff_norms<float>(as<float>(U_dev), as<float>(Uprev), n, nt, norms, c->stream);
@@ -1638,6 +2078,7 @@ int pexp_solve_burgers(pexp_ctx* c, const pexp_operator* op, const pexp_options*
                 dmax = std::max(dmax, sqrt(nh[i]));
                 umax = std::max(umax, sqrt(nh[nt + i]));
             }
+            const double prev_delta = delta;
             delta = umax > 0 ? dmax / umax : 0.0;
             if (rep) {
                 rep->k_nh_max = std::max(rep->k_nh_max, lrep.k_nh_max);
@@ -1645,8 +2086,16 @@ int pexp_solve_burgers(pexp_ctx* c, const pexp_operator* op, const pexp_options*
                 rep->rank_max = std::max(rep->rank_max, lrep.rank_max);
                 rep->not_converged += lrep.not_converged;
                 rep->bytes_alg += lrep.bytes_alg + 3.0 * es * n * nt;
+                if (it <= PEXP_REPORT_WR) rep->wr_history[it - 1] = delta;
+                memcpy(rep->sub_rank, lrep.sub_rank, sizeof(rep->sub_rank));
+                memcpy(rep->sub_steps, lrep.sub_steps, sizeof(rep->sub_steps));
+                memcpy(rep->sub_hom_steps, lrep.sub_hom_steps, sizeof(rep->sub_hom_steps));
+                memcpy(rep->sub_restarts, lrep.sub_restarts, sizeof(rep->sub_restarts));
             }
             if (delta <= o->wr_tol) { status_l = PEXP_OK; break; }
+            // divergence: the update grew in wr_diverge successive iterations
+            grew = (it >= 2 && delta > prev_delta) ? grew + 1 : 0;
+            if (o->wr_diverge > 0 && grew >= o->wr_diverge) { status_l = PEXP_ERR_WR_DIVERGED; break; }
             cudaMemcpyAsync(Uprev, U_dev, es * n * nt, cudaMemcpyDeviceToDevice, c->stream);
         }
         if (rep) {
@@ -1682,10 +2131,72 @@ int pexp_apply_operator(pexp_ctx* c, const pexp_operator* op, const void* X, voi
     return PEXP_OK;
 }
 
+int pexp_jacobian_sai_solve(pexp_ctx* c, const pexp_operator* op, double gamma, const double* ubar, const void* X,
+                            void* Y, int nvec, int dtype) {
+    if (!c || !op || !X || !Y || nvec < 1 || !(gamma > 0)) return PEXP_ERR_INVALID_ARG;
+    if (op->dim != 1) return PEXP_ERR_UNSUPPORTED;
+    if (op->nx < 3 || !(op->Lx > 0.0) || !(op->nu >= 0.0)) return PEXP_ERR_INVALID_ARG;
+    if (dtype != PEXP_F64 && dtype != PEXP_F32) return PEXP_ERR_INVALID_ARG;
+    cudaSetDevice(c->device);
+    const OpDesc od = make_opdesc(*op);
+    const int64_t n = od.n;
+    const double inv2dx = 1.0 / (2.0 * (op->bc == PEXP_BC_PERIODIC ? op->Lx / n : op->Lx / (n + 1)));
+    return guarded([&]() -> int {
+        const size_t es = dtype == PEXP_F64 ? 8 : 4;
+        size_t need = align_up(sizeof(double) * (sai_scratch_doubles(n, nvec) + 64)) + align_up(sizeof(double) * 3 * n) +
+                      align_up(sizeof(double) * (n + 64)) + 4 * kAlign;
+        int r = ws_reserve(c, need);
+        if (r) return r;
+        c->ws_top = 0;
+        double* scr = as<double>(ws_alloc(c, sizeof(double) * (sai_scratch_doubles(n, nvec) + 64)));
+        double* fac = as<double>(ws_alloc(c, sizeof(double) * 3 * n));
+        int* flag = as<int>(ws_alloc(c, sizeof(int) * 4));
+        PEXP_CUDA_TRY(cudaMemsetAsync(flag, 0, sizeof(int), c->stream));
+        double umax = 0.0;
+        if (ubar) {
+            // max |ubar| for the warm-up length of the factorisation
+            std::vector<double> hu(n);
+            PEXP_CUDA_TRY(cudaMemcpyAsync(hu.data(), ubar, sizeof(double) * n, cudaMemcpyDeviceToHost, c->stream));
+            sync(c);
+            for (double x : hu) umax = std::max(umax, fabs(x));
+        }
+        Stage sg(c, 0);
+        VarOpTask vt{ubar, fac, fac + n, fac + 2 * n, flag};
+        const VarOpTask* dvt = sg.put(&vt, 1);
+        std::vector<const void*> xs(nvec);
+        std::vector<void*> ys(nvec);
+        std::vector<VarSai> vcs(nvec, VarSai{fac, fac + n, fac + 2 * n});
+        for (int v = 0; v < nvec; ++v) {
+            xs[v] = reinterpret_cast<const char*>(X) + es * n * v;
+            ys[v] = reinterpret_cast<char*>(Y) + es * n * v;
+        }
+        const void* const* dx = sg.put(xs.data(), nvec);
+        void* const* dy = sg.put(ys.data(), nvec);
+        const VarSai* dv = sg.put(vcs.data(), nvec);
+        sg.flush();
+        launch_vsai_factor(od.x, gamma, inv2dx, dvt, 1, vsai_warmup(od.x, gamma, inv2dx, umax), c->stream);
+        check_launch(c);
+        int fl = 0;
+        d2h(c, &fl, flag, sizeof(int));
+        if (fl) return PEXP_ERR_UNSUPPORTED;
+        if (dtype == PEXP_F64)
+            launch_vsai_solve<double>(n, dv, reinterpret_cast<const double* const*>(dx), nullptr,
+                                      reinterpret_cast<double* const*>(dy), nullptr, nvec, scr, c->stream);
+        else
+            launch_vsai_solve<float>(n, dv, reinterpret_cast<const float* const*>(dx), nullptr,
+                                     reinterpret_cast<float* const*>(dy), nullptr, nvec, scr, c->stream);
+        check_launch(c);
+        c->launches += 2;
+        sync(c);
+        return PEXP_OK;
+    });
+}
+
 int pexp_sai_solve(pexp_ctx* c, const pexp_operator* op, double gamma, const void* X, void* Y, int nvec,
                    int dtype) {
     if (!c || !op || !X || !Y || nvec < 1 || !(gamma > 0)) return PEXP_ERR_INVALID_ARG;
-    if (op->dim != 1 || op->bc != PEXP_BC_PERIODIC) return PEXP_ERR_UNSUPPORTED;
+    if (op->dim != 1) return PEXP_ERR_UNSUPPORTED;
+    if (op->bc != PEXP_BC_PERIODIC) return pexp_jacobian_sai_solve(c, op, gamma, nullptr, X, Y, nvec, dtype);
     if (dtype != PEXP_F64 && dtype != PEXP_F32) return PEXP_ERR_INVALID_ARG;
     cudaSetDevice(c->device);
     const OpDesc od = make_opdesc(*op);

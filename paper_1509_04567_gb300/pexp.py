@@ -27,6 +27,7 @@ ERR_WR_NOT_CONVERGED = -6
 ERR_TIMEOUT = -7
 ERR_UNSUPPORTED = -8
 ERR_SCRATCH_LIMIT = -9
+ERR_WR_DIVERGED = -10
 
 BC_PERIODIC = 0
 BC_DIRICHLET0 = 1
@@ -47,6 +48,8 @@ def DIAG_KTIME_SAMPLE(k: int) -> int:
 
 
 KC_NAMES = ["sai", "stencil", "proj", "update", "small", "source", "recon", "other"]
+REPORT_SUBS = 128
+REPORT_WR = 64
 FP64 = 0
 MIXED = 1
 F64 = 0
@@ -55,7 +58,8 @@ F32 = 1
 # Symbols declared in include/pexp.h (checked by the CPU tests).
 EXPORTS = ["pexp_create", "pexp_destroy", "pexp_set_stream", "pexp_default_options", "pexp_status_string",
            "pexp_solve_linear", "pexp_solve_linear_host", "pexp_solve_burgers", "pexp_apply_operator",
-           "pexp_sai_solve", "pexp_small_expm", "pexp_burgers_source", "pexp_sai_solve_noalloc"]
+           "pexp_sai_solve", "pexp_small_expm", "pexp_burgers_source", "pexp_sai_solve_noalloc",
+           "pexp_jacobian_sai_solve", "pexp_solve_batched", "pexp_autotune"]
 
 
 class Operator(C.Structure):
@@ -69,7 +73,13 @@ class Options(C.Structure):
                 ("svd_tol", C.c_double), ("max_rank", C.c_int), ("restart_len", C.c_int),
                 ("max_restarts", C.c_int), ("krylov", C.c_int), ("sai_gamma", C.c_double),
                 ("precision", C.c_int), ("wr_max_iter", C.c_int), ("wr_tol", C.c_double),
-                ("burgers_form", C.c_int), ("diagnostics", C.c_int)]
+                ("burgers_form", C.c_int), ("diagnostics", C.c_int), ("jacobian", C.c_int),
+                ("wr_diverge", C.c_int)]
+
+
+class Problem(C.Structure):
+    _fields_ = [("op", Operator), ("opts", Options), ("y0_dev", C.c_void_p), ("G_dev", C.c_void_p),
+                ("g_dtype", C.c_int), ("Y_dev", C.c_void_p), ("y_dtype", C.c_int)]
 
 
 class Report(C.Structure):
@@ -80,7 +90,9 @@ class Report(C.Structure):
                 ("t_source_ms", C.c_double), ("t_krylov_ms", C.c_double), ("t_hom_ms", C.c_double),
                 ("t_recon_ms", C.c_double), ("orth_max", C.c_double), ("k_ms", C.c_double * 8),
                 ("k_launches", C.c_int * 8), ("k_bytes", C.c_double * 8), ("bytes_alg", C.c_double),
-                ("launches", C.c_int)]
+                ("launches", C.c_int), ("k_bytes_alg", C.c_double * 8), ("sub_rank", C.c_int * REPORT_SUBS),
+                ("sub_steps", C.c_int * REPORT_SUBS), ("sub_hom_steps", C.c_int * REPORT_SUBS),
+                ("sub_restarts", C.c_int * REPORT_SUBS), ("wr_history", C.c_double * REPORT_WR)]
 
     def as_dict(self) -> dict:
         d = {}
@@ -118,6 +130,9 @@ def lib() -> C.CDLL:
         L.pexp_small_expm.argtypes = [vp, vp, vp, i, i]
         L.pexp_burgers_source.argtypes = [vp, C.POINTER(Operator), vp, vp, i, i, i]
         L.pexp_sai_solve_noalloc.argtypes = [C.POINTER(Operator), d, vp, vp, i, i, vp]
+        L.pexp_jacobian_sai_solve.argtypes = [vp, C.POINTER(Operator), d, vp, vp, vp, i, i]
+        L.pexp_solve_batched.argtypes = [vp, i, C.POINTER(Problem), C.POINTER(Report)]
+        L.pexp_autotune.argtypes = [vp, i, C.POINTER(Problem), C.c_char_p]
         for name in EXPORTS:
             if name not in ("pexp_default_options", "pexp_status_string"):
                 getattr(L, name).restype = i
@@ -135,12 +150,26 @@ def status_string(code: int) -> str:
     return lib().pexp_status_string(code).decode()
 
 
+def _check_vector_pair(X, Y, n: int) -> int:
+    """Checks the (nvec, n) or (n,) CUDA tensors X (read) and Y (written) of a call that
+    writes nvec * n elements at Y's base pointer; returns nvec."""
+    for name, t in (("X", X), ("Y", Y)):
+        if not t.is_cuda or not t.is_contiguous():
+            raise ValueError(f"{name} must be a contiguous CUDA tensor")
+        if t.dim() not in (1, 2) or t.shape[-1] != n:
+            raise ValueError(f"{name} must have shape (nvec, {n}) or ({n},), got {tuple(t.shape)}")
+    if X.dtype != Y.dtype or X.shape != Y.shape or X.device != Y.device:
+        raise ValueError("X and Y must have the same dtype, shape and device")
+    _dtype_code(X)
+    return X.shape[0] if X.dim() == 2 else 1
+
+
 def sai_solve_noalloc(op: dict, gamma: float, X, Y, stream=None) -> None:
     """Y = (I - gamma A)^{-1} X through pexp_sai_solve_noalloc: no context and no
     allocation; enqueued on `stream` (a torch.cuda.Stream; default: the current
     stream of X's device) and asynchronous -- synchronise before reading Y."""
     import torch
-    nvec = X.shape[0] if X.dim() == 2 else 1
+    nvec = _check_vector_pair(X, Y, int(op["nx"]) * (int(op.get("ny", 1)) if op["dim"] == 2 else 1))
     st = stream if stream is not None else torch.cuda.current_stream(X.device)
     with torch.cuda.device(X.device):
         rc = lib().pexp_sai_solve_noalloc(C.byref(make_operator(op)), float(gamma), C.c_void_p(X.data_ptr()),
@@ -263,35 +292,94 @@ class Context:
                                       C.c_void_p(forcing.data_ptr()) if forcing is not None else None,
                                       C.c_void_p(init.data_ptr()) if init is not None else None,
                                       C.c_void_p(U.data_ptr()), _dtype_code(U), C.byref(rep))
-        if check and rc not in (OK, ERR_NOT_CONVERGED, ERR_WR_NOT_CONVERGED):
+        if check and rc not in (OK, ERR_NOT_CONVERGED, ERR_WR_NOT_CONVERGED, ERR_WR_DIVERGED):
             raise PexpError(rc, "pexp_solve_burgers")
         d = rep.as_dict()
         d["rc"] = rc
         return d
 
+    @staticmethod
+    def _problems(items) -> "C.Array":
+        """items: (op, opts, y0, G or None, Y) with CUDA tensors, as for solve_linear."""
+        import torch
+        arr = (Problem * len(items))()
+        for k, (op, opts, y0, G, Y) in enumerate(items):
+            for t in (y0, Y) + ((G,) if G is not None else ()):
+                if not t.is_cuda or not t.is_contiguous():
+                    raise ValueError("batched problems take contiguous CUDA tensors")
+            if y0.dtype != torch.float64:
+                raise TypeError("the initial condition must be FP64")
+            arr[k].op = make_operator(op)
+            arr[k].opts = make_options(opts)
+            arr[k].y0_dev = y0.data_ptr()
+            arr[k].G_dev = G.data_ptr() if G is not None else None
+            arr[k].g_dtype = _dtype_code(G) if G is not None else _dtype_code(Y)
+            arr[k].Y_dev = Y.data_ptr()
+            arr[k].y_dtype = _dtype_code(Y)
+        return arr
+
+    def solve_batched(self, items, check: bool = True) -> list:
+        """Solves independent problems concurrently (pexp_solve_batched); returns their reports."""
+        arr = self._problems(items)
+        reps = (Report * len(items))()
+        rc = lib().pexp_solve_batched(self.h, len(items), arr, reps)
+        if check and rc not in (OK, ERR_NOT_CONVERGED):
+            raise PexpError(rc, "pexp_solve_batched")
+        out = []
+        for r in reps:
+            d = r.as_dict()
+            d["rc"] = r.status
+            out.append(d)
+        return out
+
+    def autotune(self, items, path: str | None = None) -> None:
+        """Tunes the batched solve on these problems (pexp_autotune); the table goes to `path`."""
+        arr = self._problems(items)
+        rc = lib().pexp_autotune(self.h, len(items), arr, path.encode() if path else None)
+        if rc != OK:
+            raise PexpError(rc, "pexp_autotune")
+
     # ---------------------------------------------------------------- kernel-level calls
     def apply_operator(self, op: dict, X, Y, transpose: bool = False):
-        nvec = X.shape[0] if X.dim() == 2 else 1
+        nvec = _check_vector_pair(X, Y, int(op["nx"]) * (int(op.get("ny", 1)) if op["dim"] == 2 else 1))
         rc = lib().pexp_apply_operator(self.h, C.byref(make_operator(op)), C.c_void_p(X.data_ptr()),
                                        C.c_void_p(Y.data_ptr()), nvec, _dtype_code(X), int(transpose))
         if rc != OK:
             raise PexpError(rc, "pexp_apply_operator")
 
     def sai_solve(self, op: dict, gamma: float, X, Y):
-        nvec = X.shape[0] if X.dim() == 2 else 1
+        nvec = _check_vector_pair(X, Y, int(op["nx"]) * (int(op.get("ny", 1)) if op["dim"] == 2 else 1))
         rc = lib().pexp_sai_solve(self.h, C.byref(make_operator(op)), float(gamma), C.c_void_p(X.data_ptr()),
                                   C.c_void_p(Y.data_ptr()), nvec, _dtype_code(X))
         if rc != OK:
             raise PexpError(rc, "pexp_sai_solve")
 
+    def jacobian_sai_solve(self, op: dict, gamma: float, ubar, X, Y):
+        """Y = (I - gamma (A + J(ubar)))^{-1} X; ubar: (n,) FP64 CUDA tensor or None (J = 0)."""
+        import torch
+        nvec = _check_vector_pair(X, Y, int(op["nx"]))
+        if ubar is not None and (not ubar.is_cuda or ubar.dtype != torch.float64 or ubar.shape != (int(op["nx"]),)):
+            raise ValueError("ubar must be an FP64 CUDA tensor of shape (n,)")
+        rc = lib().pexp_jacobian_sai_solve(self.h, C.byref(make_operator(op)), float(gamma),
+                                           C.c_void_p(ubar.data_ptr()) if ubar is not None else None,
+                                           C.c_void_p(X.data_ptr()), C.c_void_p(Y.data_ptr()), nvec, _dtype_code(X))
+        if rc != OK:
+            raise PexpError(rc, "pexp_jacobian_sai_solve")
+
     def small_expm(self, M, E):
+        import torch
+        for t in (M, E):
+            if not t.is_cuda or not t.is_contiguous() or t.dtype != torch.float64 or t.dim() != 3:
+                raise ValueError("M and E must be contiguous CUDA FP64 tensors of shape (batch, N, N)")
+        if M.shape != E.shape or M.shape[1] != M.shape[2]:
+            raise ValueError("M and E must have the same shape (batch, N, N)")
         batch, N, _ = M.shape
         rc = lib().pexp_small_expm(self.h, C.c_void_p(M.data_ptr()), C.c_void_p(E.data_ptr()), N, batch)
         if rc != OK:
             raise PexpError(rc, "pexp_small_expm")
 
     def burgers_source(self, op: dict, U, G, form: int = 0):
-        rows = U.shape[0] if U.dim() == 2 else 1
+        rows = _check_vector_pair(U, G, int(op["nx"]))
         rc = lib().pexp_burgers_source(self.h, C.byref(make_operator(op)), C.c_void_p(U.data_ptr()),
                                        C.c_void_p(G.data_ptr()), rows, _dtype_code(U), form)
         if rc != OK:

@@ -53,7 +53,8 @@ class Problem:
 def default_opts(**kw) -> dict:
     o = dict(T=1.0, P=1, n_out=2, tol=1e-8, svd_tol=1e-12, max_rank=16,
              restart_len=20, max_restarts=0, krylov=1, sai_gamma=0.1,
-             precision=0, wr_max_iter=50, wr_tol=1e-6, burgers_form=0, diagnostics=0)
+             precision=0, wr_max_iter=50, wr_tol=1e-6, burgers_form=0, diagnostics=0, jacobian=0,
+             wr_diverge=3)
     o.update(kw)
     return o
 
@@ -171,11 +172,11 @@ def burgers_1d(n=65536, nu=5e-3, T=0.5, P=32, n_out=513, tol=1e-8, svd_tol=1e-8,
                    u0=u0, G=None)
 
 
-def batched_instance(i: int, n_min_log2=12, n_max_log2=18, tol=1e-7) -> Problem:
-    """Instance i of the batched workload: n log-uniform in [2^12, 2^18] rounded to a
-    multiple of 64, nu log-uniform in [1e-4, 1e-1], a uniform in [0.5, 2], a random
-    16-mode Fourier u0, P = 2^U{2..6}, T = 1, n_out = 16 P + 1,
-    g = gamma sin(4 pi x) cos(2 pi t) with gamma ~ U(0, 1)."""
+def batched_params(i: int, n_min_log2=12, n_max_log2=18) -> dict:
+    """The seeded draws of instance i of the batched workload: n log-uniform in
+    [2^n_min_log2, 2^n_max_log2] rounded to a multiple of 64, nu log-uniform in
+    [1e-4, 1e-1], a uniform in [0.5, 2], 16 Fourier amplitudes of u0 (cosine al, sine be,
+    each U(-1, 1)), P = 2^U{2..6}, source amplitude gamma ~ U(0, 1)."""
     rng = np.random.default_rng(SEED_BASE + i)
     n = int(round(2.0 ** rng.uniform(n_min_log2, n_max_log2) / 64.0)) * 64
     n = max(n, 64)
@@ -185,6 +186,16 @@ def batched_instance(i: int, n_min_log2=12, n_max_log2=18, tol=1e-7) -> Problem:
     be = rng.uniform(-1, 1, 16)
     P = 2 ** int(rng.integers(2, 7))
     gam = rng.uniform(0, 1)
+    return dict(n=n, nu=nu, a=a, al=al, be=be, P=P, gam=gam)
+
+
+def batched_instance(i: int, n_min_log2=12, n_max_log2=18, tol=1e-7, P_max: int | None = None) -> Problem:
+    """Instance i of the batched workload (batched_params): u0 = sum_k (al_k cos 2 pi k x +
+    be_k sin 2 pi k x) / k over k = 1..16, T = 1, n_out = 16 P + 1,
+    g = gamma sin(4 pi x) cos(2 pi t).  P_max caps P (small test sets)."""
+    d = batched_params(i, n_min_log2, n_max_log2)
+    n, nu, a, al, be, gam = d["n"], d["nu"], d["a"], d["al"], d["be"], d["gam"]
+    P = d["P"] if P_max is None else min(d["P"], P_max)
     x = grid_1d(n)
     k = np.arange(1, 17)[:, None]
     u0 = ((al[:, None] * np.cos(2 * np.pi * k * x) + be[:, None] * np.sin(2 * np.pi * k * x)) / k).sum(0)

@@ -116,10 +116,12 @@ int main(void) {
     memset(&r, 0, sizeof(r));
     memset(&op, 0, sizeof(op));
     pexp_default_options(&o);
-    if (o.restart_len != 20 || o.krylov != PEXP_KRYLOV_SAI) return 2;
+    if (o.restart_len != 20 || o.krylov != PEXP_KRYLOV_SAI || o.jacobian != 0 || o.wr_diverge != 3) return 2;
     if (strcmp(pexp_status_string(PEXP_OK), "ok") != 0) return 3;
     if (pexp_solve_linear(ctx, &op, &o, NULL, NULL, PEXP_F64, NULL, PEXP_F64, &r) != PEXP_ERR_INVALID_ARG) return 4;
-    printf("%d %d\n", o.P, PEXP_DIAG_KTIME | PEXP_DIAG_KTIME_CLASS(PEXP_KC_UPDATE) | PEXP_DIAG_KTIME_SAMPLE(2));
+    printf("%d %d %d %d %d %d\n", o.P, PEXP_DIAG_KTIME | PEXP_DIAG_KTIME_CLASS(PEXP_KC_UPDATE) | PEXP_DIAG_KTIME_SAMPLE(2),
+           (int)sizeof(pexp_operator), (int)sizeof(pexp_options), (int)sizeof(pexp_report), (int)sizeof(pexp_problem));
+    if (pexp_solve_batched(ctx, 1, NULL, NULL) != PEXP_ERR_INVALID_ARG) return 5;
     return 0;
 }
 """
@@ -145,4 +147,5 @@ def test_header_is_c99_and_links_from_plain_c(lib, tmp_path):
     assert r.returncode == 0, r.stderr
     run = subprocess.run([str(exe)], capture_output=True, text=True, timeout=60)
     assert run.returncode == 0, (run.returncode, run.stderr)
-    assert run.stdout.split() == ["1", str(2 | (1 << 11) | (2 << 16))]
+    sizes = [str(ctypes.sizeof(c)) for c in (pexp.Operator, pexp.Options, pexp.Report, pexp.Problem)]
+    assert run.stdout.split() == ["1", str(2 | (1 << 11) | (2 << 16))] + sizes

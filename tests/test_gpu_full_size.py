@@ -125,7 +125,9 @@ def test_full_size_vs_oracle_and_exact(c, exact, oracle_window1, precision, tol,
             "wall_s": round(wall, 2), "orth_max": rep["orth_max"], "rank_max": rep["rank_max"],
             "rel_err_exact": {str(k): f"{e:.2e}" for k, e in e_ex.items()},
             "rel_err_oracle_window1": {str(k): f"{e:.2e}" for k, e in e_or.items()},
-            "oracle_window1_vs_exact": {str(k): f"{e:.2e}" for k, e in e_oe.items()}}
+            "oracle_window1_vs_exact": {str(k): f"{e:.2e}" for k, e in e_oe.items()},
+            "max_rel_err_exact": f"{max(e_ex.values()):.3e}",
+            "margin_vs_gate": round((MIXED_TOL if precision else 3 * P * tol) / max(e_ex.values()), 3)}
     print(json.dumps(line))
     out = os.environ.get("PEXP_TEST_RECORD")
     if out:

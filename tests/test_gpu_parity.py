@@ -118,8 +118,9 @@ def test_invalid_arguments_are_rejected(c):
     for bad in (dict(P=9), dict(n_out=1), dict(tol=0.0), dict(restart_len=100), dict(krylov=5)):
         rep = c.solve_linear(pr.op, dict(pr.opts, **bad), y0, None, Y, check=False)
         assert rep["rc"] == pexp.ERR_INVALID_ARG, bad
-    op_d = dict(pr.op, bc=wl.BC_DIRICHLET0)
-    rep = c.solve_linear(op_d, dict(pr.opts, krylov=1), y0, None, Y, check=False)
+    # the shift-and-invert space needs a 1D operator (periodic or bounded)
+    op_2d = wl.make_op(8, 1e-2, 0.5, dim=2, ny=8)
+    rep = c.solve_linear(op_2d, dict(pr.opts, krylov=1), y0, None, Y, check=False)
     assert rep["rc"] == pexp.ERR_UNSUPPORTED
 
 

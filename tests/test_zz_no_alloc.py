@@ -3,18 +3,24 @@
 It shares the kernels of pexp_sai_solve but keeps its scratch in a fixed device
 array that every call reuses, so the GPU test makes two different calls in a row
 (the second one sees the first one's leftovers) and checks both against
-pexp_sai_solve through the C ABI.  Collected last, and passes alone or after the
-other tests.
+pexp_sai_solve through the C ABI and against the oracle's sparse-LU solve of
+(I - gamma A) x = b.  The device's free memory must not change across the second
+round of calls (the first call on a device may load the module and its array).
+Collected last, and passes alone or after the other tests.
 """
 import ctypes
 
 import numpy as np
 import pytest
 
+import oracle.pebk as ob
 from paper_1509_04567_gb300 import workloads as wl
 
 # tolerances of the SAI kernel tests: the FP64 parity gate and the FP32 solve bound
 TOL = {"f64": 1e-10, "f32": 2e-6}
+# against the sparse LU: cond(I - gamma A) is ~1e5 for these operators, so the FP64 bound
+# is cond * eps64 with margin; the FP32 output rounding dominates the FP32 bound
+LU_TOL = {"f64": 1e-9, "f32": 2e-6}
 
 
 @pytest.mark.gpu
@@ -34,17 +40,32 @@ def test_noalloc_matches_sai_solve_on_two_calls(dtype):
         op = wl.make_op(n, nu, a)
         X = torch.from_numpy(wl.random_block(n, nvec, n % 97).T.copy()).to("cuda:0", dt)
         Y = torch.full_like(X, float("nan"))
+        Y2 = torch.full_like(X, float("nan"))
+        outs.append((op, gamma, X, Y, Y2))
+    for op, gamma, X, Y, _ in outs:
         pexp.sai_solve_noalloc(op, gamma, X, Y)
-        outs.append((op, gamma, X, Y))
     torch.cuda.synchronize()
-    for op, gamma, X, Y in outs:
+    # a second round of the same calls, into fresh outputs: no device memory is taken
+    free0, _ = torch.cuda.mem_get_info()
+    for op, gamma, X, _, Y2 in outs:
+        pexp.sai_solve_noalloc(op, gamma, X, Y2)
+    torch.cuda.synchronize()
+    free1, _ = torch.cuda.mem_get_info()
+    assert free1 == free0, (free0, free1)
+    for op, gamma, X, Y, Y2 in outs:
         Yref = torch.empty_like(X)
         c.sai_solve(op, gamma, X, Yref)
         torch.cuda.synchronize()
-        got, ref = Y.double().cpu().numpy(), Yref.double().cpu().numpy()
+        got, got2, ref = Y.double().cpu().numpy(), Y2.double().cpu().numpy(), Yref.double().cpu().numpy()
         assert np.all(np.isfinite(got))
+        np.testing.assert_array_equal(got2, got)
+        kop = ob.KrylovOperator(op, ob.operator_matrix(op), ob.KRYLOV_SAI, gamma)
+        Xh = X.double().cpu().numpy()
         for r in range(X.shape[0]):
             assert np.linalg.norm(got[r] - ref[r]) <= TOL[dtype] * np.linalg.norm(ref[r]), (op["nx"], r)
+            # the oracle's sparse LU of (I - gamma A) on the same (rounded) input
+            lu = kop.build(Xh[r])
+            assert np.linalg.norm(got[r] - lu) <= LU_TOL[dtype] * np.linalg.norm(lu), (op["nx"], r)
 
 
 def test_noalloc_rejects_requests_beyond_its_scratch():
