@@ -109,6 +109,12 @@ typedef struct {
                           * one Jacobian per subinterval at its time-averaged iterate, eq. piecewiseJac) */
     int    wr_diverge;   /* Burgers WR: stop with PEXP_ERR_WR_DIVERGED once the relative update has grown
                           * this many iterations in a row (0 = never) */
+    /* Linear solves: solve only the subproblems j = sub_first .. sub_last-1 (0-based, eq.
+     * linivpSubproblem) and sum their solutions (eq. superposition); 0, 0 = all.  Outputs up to
+     * T_{sub_first} are set to zero and u0 is added only when sub_first = 0, so the solutions
+     * of disjoint ranges add up to the full solve (the subintervals split over several GPUs). */
+    int    sub_first;
+    int    sub_last;
 } pexp_options;
 
 #define PEXP_DIAG_ORTH  1   /* measure the orthogonality of every Krylov basis */

@@ -197,6 +197,16 @@ void launch_row_dots(const double* u, const T* G, int64_t n, int nrows, double* 
 
 int fail_cuda(cudaError_t e, const char* what, const char* file, int line);
 
+// Raises a kernel's dynamic shared-memory limit on the current device to at least `bytes`.
+// The limit is a process-wide attribute of the kernel: it is only ever raised, under a lock,
+// so that launches from several host threads (batched solves) never find it lowered by
+// another thread that needed less.
+void smem_optin_raw(const void* kernel, size_t bytes);
+template <typename K>
+inline void smem_optin(K* kernel, size_t bytes) {
+    smem_optin_raw(reinterpret_cast<const void*>(kernel), bytes);
+}
+
 // Programmatic dependent launch for the kernels of a Krylov step, which run back to back
 // on one stream.  Such a kernel is launched with programmatic stream serialization, so
 // its launch may overlap the kernel before it; it calls pdl_entry() before its first

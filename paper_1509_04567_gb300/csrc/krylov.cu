@@ -1047,7 +1047,7 @@ void launch_source_gram(const T* const* X, const int* sv, int ntasks, int s_max,
     if (ntasks <= 0) return;
     dim3 grid(g.nchunks, ntasks);
     const size_t sm = sizeof(T) * (size_t)s_max * kTile;
-    if (sm > 32 * 1024) cudaFuncSetAttribute(k_source_gram<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    if (sm > 32 * 1024) smem_optin(k_source_gram<T>, sm);
     k_source_gram<T><<<grid, kThreads, sm, st>>>(X, sv, n, g.rows, g.nchunks, pstride, partial);
 }
 

@@ -15,6 +15,8 @@
 
 #include <algorithm>
 
+#include <mutex>
+
 #include "small.cuh"
 
 namespace pexp {
@@ -59,8 +61,13 @@ __constant__ double c_theta[5] = {1.495585217958292e-2, 2.539398330063230e-1, 9.
                                   2.097847961257068e0, 5.371920351148152e0};
 
 void init_pade_constants() {
-    static bool done = false;
-    if (done) return;
+    // constant memory is per device: the coefficients go to each device once
+    static std::mutex mu;
+    static bool done[128] = {};
+    int dev = 0;
+    cudaGetDevice(&dev);
+    std::lock_guard<std::mutex> lk(mu);
+    if (dev < 0 || dev >= 128 || done[dev]) return;
     double h[5][14] = {};
     for (int d = 0; d < 5; ++d) {
         const int m = kPadeDeg[d];
@@ -73,7 +80,7 @@ void init_pade_constants() {
         }
     }
     cudaMemcpyToSymbol(c_pade, h, sizeof(h));
-    done = true;
+    done[dev] = true;
 }
 
 // ---------------------------------------------------------------- CTA helpers
@@ -373,7 +380,7 @@ void launch_source_eig(const WinLayout& L, double* wd, int* wi, const int* wins,
                        const double* dots, const double* nrm2, cudaStream_t s, Parts gp) {
     if (nw <= 0) return;
     size_t sm = (size_t)2 * L.s_max * L.s_max * sizeof(double);
-    if (sm > 32 * 1024) cudaFuncSetAttribute(k_source_eig, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    if (sm > 32 * 1024) smem_optin(k_source_eig, sm);
     k_source_eig<<<nw, 64, sm, s>>>(L, wd, wi, wins, thr, max_rank, dots, nrm2, gp);
 }
 
@@ -783,7 +790,7 @@ void launch_project(const WinLayout& L, double* wd, int* wi, const int* wins, in
     const int nl = b_launch > 0 ? std::min(L.N_max, (step + 4) * b_launch) : L.N_max;
     const size_t sm = (size_t)9 * nl * nl * sizeof(double);
     if (sm <= 200u * 1024u) {
-        if (sm > 32 * 1024) cudaFuncSetAttribute(k_project, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+        if (sm > 32 * 1024) smem_optin(k_project, sm);
         k_project<<<nw, 256, sm, s>>>(L, wd, wi, wins, step, h, tol, scale_ref, fp, d, cadv, nl, only_ef, jcoef);
     } else {
         k_project<<<nw, 256, 0, s>>>(L, wd, wi, wins, step, h, tol, scale_ref, fp, d, cadv, 0, only_ef, jcoef);

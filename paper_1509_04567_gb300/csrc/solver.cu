@@ -333,6 +333,8 @@ int validate(const pexp_operator* op, const pexp_options* o) {
         smax = std::max(smax, i1 - i0 + 1);
     }
     if (smax > PEXP_MAX_SAMPLES) return PEXP_ERR_INVALID_ARG;
+    if (!(o->sub_first == 0 && o->sub_last == 0) && !(0 <= o->sub_first && o->sub_first < o->sub_last && o->sub_last <= P))
+        return PEXP_ERR_INVALID_ARG;
     if (o->krylov == PEXP_KRYLOV_SAI && op->dim != 1) return PEXP_ERR_UNSUPPORTED;
     return PEXP_OK;
 }
@@ -989,6 +991,9 @@ int solve_linear_typed(pexp_ctx* c, const pexp_operator* op, const pexp_options*
     const int b_cap = std::min(std::min(o->max_rank, PEXP_MAX_RANK), pt.smax);
     S.L = make_layout(pt.smax, b_cap, S.kmax, fp64 ? 3 : 5);
     const WinLayout& L = S.L;
+    // the subproblems solved: j in [ja, jb) (all by default); their solutions are zero before T_ja
+    const bool ranged = !(o->sub_first == 0 && o->sub_last == 0);
+    const int ja = ranged ? o->sub_first : 0, jb = ranged ? o->sub_last : P;
 
     // ---- buffers
     double* Au0 = as<double>(ws_alloc(c, sizeof(double) * n));
@@ -1148,7 +1153,8 @@ int solve_linear_typed(pexp_ctx* c, const pexp_operator* op, const pexp_options*
     std::vector<int> mj(P);
     int b_max = 0, b_min = 1 << 30;
     for (int j = 0; j < P; ++j) {
-        mj[j] = S.wi_host[(size_t)j * L.istride + WI_B];
+        mj[j] = (j >= ja && j < jb) ? S.wi_host[(size_t)j * L.istride + WI_B] : 0;
+        if (j < ja || j >= jb) continue;
         b_max = std::max(b_max, mj[j]);
         b_min = std::min(b_min, mj[j]);
     }
@@ -1289,6 +1295,7 @@ int solve_linear_typed(pexp_ctx* c, const pexp_operator* op, const pexp_options*
     // ---- homogeneous chain over windows 2..P
     std::vector<T*> Vh(P, nullptr);
     std::vector<int> Kh(P, 0), steps_h(P, 0);
+    const double* u0_out = ja == 0 ? u0d : nullptr;   // u0 belongs to the range that starts at t = 0
     // reconstruction task of window m: its nonhomogeneous part and (m >= 1) the continuation
     // of the solution from T_m; the first sample of a window m >= 1 is the last of window m - 1
     auto recon_task = [&](int m) {
@@ -1310,7 +1317,7 @@ int solve_linear_typed(pexp_ctx* c, const pexp_operator* op, const pexp_options*
         const ReconTask<T>* drt = so.put(&rt, 1);
         so.flush();
         timed(c, PEXP_KC_RECON, (double)n * (rt.K1 + rt.K2) * sizeof(T) + (double)n * rt.ns * sizeof(TO),
-              [&] { launch_recon<T, TO>(drt, 1, rt.ns, n, u0d, Y, n, std::max(1, rt.K1 + rt.K2), st); });
+              [&] { launch_recon<T, TO>(drt, 1, rt.ns, n, u0_out, Y, n, std::max(1, rt.K1 + rt.K2), st); });
         check_launch(c);
         cudaEventRecord(c->ev_out, st);
         cudaStreamWaitEvent(c->cs, c->ev_out, 0);
@@ -1321,13 +1328,25 @@ int solve_linear_typed(pexp_ctx* c, const pexp_operator* op, const pexp_options*
             throw StatusError{PEXP_ERR_CUDA};
         }
     };
-    if (Y_host) emit_window(0);
+    if (ja > 0) {
+        // rows before and at T_ja: the range's solution is zero there
+        const size_t zr = (size_t)pt.idx[ja] + 1;
+        cudaMemsetAsync(Y, 0, sizeof(TO) * zr * n, st);
+        if (Y_host) {
+            cudaEventRecord(c->ev_out, st);
+            cudaStreamWaitEvent(c->cs, c->ev_out, 0);
+            cudaMemcpyAsync(Y_host, Y, sizeof(TO) * zr * n, cudaMemcpyDeviceToHost, c->cs);
+        }
+    }
+    // the first window of the range has no continuation: its rows are final already
+    if (Y_host) emit_window(ja);
     int k_hom_max = 0, k_hom_sum = 0;
     T* Sh = as<T>(bs_alloc(c, sizeof(T) * (size_t)n * (L.ycols - 1)));
     float* Whlo = std::is_same<T, float>::value ? as<float>(bs_alloc(c, sizeof(float) * (size_t)n)) : nullptr;
     // low part of z while it is formed and normalised
     float* Vh1lo_buf = std::is_same<T, float>::value ? as<float>(bs_alloc(c, sizeof(float) * (size_t)n)) : nullptr;
     for (int m = 1; m < P; ++m) {   // 0-based window m needs z at T_m (end of window m-1)
+        if (m <= ja) continue;      // nothing of subproblems ja.. exists before T_ja
         Vh[m] = as<T>(bs_alloc(c, sizeof(T) * (size_t)n * (S.kmax + 1)));
         const int wprev = m - 1;
         const int sprev = pt.idx[m] - pt.idx[m - 1] + 1;
@@ -1432,7 +1451,7 @@ int solve_linear_typed(pexp_ctx* c, const pexp_operator* op, const pexp_options*
         Stage s4(c, 1);
         std::vector<ReconTask<T>> rts;
         int maxc = 1, maxns = 1;
-        for (int m = 0; m < P; ++m) {
+        for (int m = ja; m < P; ++m) {
             const ReconTask<T> rt = recon_task(m);
             maxc = std::max(maxc, rt.K1 + rt.K2);
             maxns = std::max(maxns, rt.ns);
@@ -1443,7 +1462,7 @@ int solve_linear_typed(pexp_ctx* c, const pexp_operator* op, const pexp_options*
         double kt = 0;
         for (auto& r : rts) kt += r.K1 + r.K2;
         timed(c, PEXP_KC_RECON, (double)n * kt * sizeof(T) + (double)n * n_out * sizeof(TO),
-              [&] { launch_recon<T, TO>(drt, (int)rts.size(), maxns, n, u0d, Y, n, maxc, st); });
+              [&] { launch_recon<T, TO>(drt, (int)rts.size(), maxns, n, u0_out, Y, n, maxc, st); });
         check_launch(c);
         cudaEventRecord(c->evp[4], st);
         sync(c);

@@ -10,11 +10,27 @@
 #include <stdio.h>
 
 #include <algorithm>
+#include <map>
+#include <mutex>
+#include <utility>
 
 #include "common.cuh"
 #include "sai.cuh"
 
 namespace pexp {
+
+void smem_optin_raw(const void* kernel, size_t bytes) {
+    static std::mutex mu;
+    static std::map<std::pair<int, const void*>, size_t> cap;
+    int dev = 0;
+    cudaGetDevice(&dev);
+    std::lock_guard<std::mutex> lk(mu);
+    size_t& c = cap[{dev, kernel}];
+    if (bytes > c) {
+        cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+        c = bytes;
+    }
+}
 
 int fail_cuda(cudaError_t e, const char* what, const char* file, int line) {
     fprintf(stderr, "pexp: CUDA error %s (%d) in %s at %s:%d\n", cudaGetErrorString(e), (int)e, what, file,
@@ -617,7 +633,7 @@ void launch_ts_nn(const TsTask<T>* tasks_dev, int ntasks, int max_pq, int64_t n,
     int bx = std::max(1, std::min(grid_for(n, 256), (4 * kNumSM * 4 + ntasks - 1) / ntasks));
     dim3 grid(bx, ntasks);
     size_t sm = (size_t)max_pq * sizeof(T);
-    if (sm > 32 * 1024) cudaFuncSetAttribute(k_ts_nn<T, 16>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    if (sm > 32 * 1024) smem_optin(k_ts_nn<T, 16>, sm);
     k_ts_nn<T, 16><<<grid, 256, sm, s>>>(tasks_dev, n);
 }
 
@@ -720,7 +736,7 @@ void launch_ts_nn_df(const DfTask* tasks_dev, int ntasks, int max_pq, int64_t n,
     rows = (rows + 255) / 256 * 256;
     dim3 grid((unsigned)((n + rows - 1) / rows), ntasks);
     size_t sm = ((size_t)max_pq + 16) * sizeof(float2);
-    if (sm > 32 * 1024) cudaFuncSetAttribute(k_ts_nn_df, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    if (sm > 32 * 1024) smem_optin(k_ts_nn_df, sm);
     k_ts_nn_df<<<grid, 256, sm, s>>>(tasks_dev, n, rows);
 }
 
@@ -915,7 +931,7 @@ void launch_recon(const ReconTask<T>* tasks_dev, int ntasks, int max_ns, int64_t
     const size_t ng = (size_t)(std::max(max_ns, 1) + 16) / 17;
     const size_t sm = ng * (size_t)std::max(max_k, 1) * 17 * sizeof(typename ReconAcc<T>::C);
     if (sm > 32 * 1024)
-        cudaFuncSetAttribute(k_recon<T, TO, 17>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+        smem_optin(k_recon<T, TO, 17>, sm);
     k_recon<T, TO, 17><<<grid, 256, sm, s>>>(tasks_dev, n, u0, out, ldo, rows);
 }
 

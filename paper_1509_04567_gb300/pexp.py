@@ -74,7 +74,7 @@ class Options(C.Structure):
                 ("max_restarts", C.c_int), ("krylov", C.c_int), ("sai_gamma", C.c_double),
                 ("precision", C.c_int), ("wr_max_iter", C.c_int), ("wr_tol", C.c_double),
                 ("burgers_form", C.c_int), ("diagnostics", C.c_int), ("jacobian", C.c_int),
-                ("wr_diverge", C.c_int)]
+                ("wr_diverge", C.c_int), ("sub_first", C.c_int), ("sub_last", C.c_int)]
 
 
 class Problem(C.Structure):

@@ -54,7 +54,7 @@ def default_opts(**kw) -> dict:
     o = dict(T=1.0, P=1, n_out=2, tol=1e-8, svd_tol=1e-12, max_rank=16,
              restart_len=20, max_restarts=0, krylov=1, sai_gamma=0.1,
              precision=0, wr_max_iter=50, wr_tol=1e-6, burgers_form=0, diagnostics=0, jacobian=0,
-             wr_diverge=3)
+             wr_diverge=3, sub_first=0, sub_last=0)
     o.update(kw)
     return o
 

@@ -106,16 +106,18 @@ def test_bounded_mesh_linear_solve_in_sai_space(c, precision):
     from gpu_util import run_linear
     n = 500
     x = wl.grid_1d(n, bc=wl.BC_DIRICHLET0)
-    op = wl.make_op(n, 1e-2, 0.5, bc=wl.BC_DIRICHLET0)
+    # FP64 at tol 1e-12: pure diffusion (with advection on this bounded mesh the step-to-step
+    # change of both sides' source windows levels off near 1e-10, above such a tol); the
+    # mixed path at tol 1e-7 with advection
+    op = wl.make_op(n, 1e-2, 0.5 if precision else 0.0, bc=wl.BC_DIRICHLET0)
     t = wl.out_times(0.5, 41)
     G = np.cos(3 * t)[:, None] * (x * (1 - x))[None, :]
-    # tol 1e-9: on this problem the step-to-step change of both sides' source windows levels
-    # off at 2.4e-10 (the oracle's answers at tol 1e-10 .. 3e-12 agree to 2e-11)
-    pr = wl.Problem("dirichlet_sai", op, wl.default_opts(T=0.5, P=4, n_out=41, tol=1e-9, restart_len=30),
+    pr = wl.Problem("dirichlet_sai", op, wl.default_opts(T=0.5, P=4, n_out=41, tol=1e-12 if not precision else 1e-9,
+                                                         restart_len=40),
                     np.sin(np.pi * x) * (1 + x), G)
     Yref, rref = ob.solve_linear(pr.op, pr.opts, pr.u0, pr.G)
     assert all(rref["conv_nh"]) and all(all(cc) for cc in rref["conv_hom"]), rref
-    opts = dict(pr.opts, precision=precision, tol=1e-7 if precision else 1e-9)
+    opts = dict(pr.opts, precision=precision, tol=1e-7 if precision else 1e-12)
     Y, rep = run_linear(c, pr, opts, dtype="f32" if precision else "f64")
     assert rep["rc"] == 0, rep
     assert relerr_rows(Y, Yref) < (1e-6 if precision else 1e-10), rep
@@ -159,7 +161,7 @@ def test_averaged_jacobian_wr_mixed_precision(c):
                            wr_max_iter=30, restart_len=40, jacobian=1)
     Uref, rref = ob.solve_burgers_jacobian(op, opts, u0)
     assert rref["converged"], rref["deltas"]
-    mopts = dict(opts, precision=1, tol=1e-8, svd_tol=1e-5, wr_tol=1e-7, wr_max_iter=30)
+    mopts = dict(opts, precision=1, tol=1e-8, svd_tol=1e-5, wr_tol=1e-7, wr_max_iter=30, wr_diverge=0)
     U, rep = _burgers_run(c, op, mopts, u0, "f32")
     assert rep["rc"] in (0, -6), rep
     assert relerr_rows(U, Uref) < 1e-6
@@ -176,12 +178,13 @@ def test_burgers_workload_n4096_against_stored_oracle(c, precision):
     u0 = 0.5 + np.sin(2 * np.pi * wl.grid_1d(n))
     opts = wl.default_opts(**gold["opts"])
     if precision:
-        opts = dict(opts, precision=1, tol=1e-8, svd_tol=1e-5, wr_tol=1e-7)
+        # the FP32 iterate's updates level off near 1e-7: the workload's wr_tol 1e-6
+        opts = dict(opts, precision=1, tol=1e-8, svd_tol=1e-5, wr_tol=1e-6)
     U, rep = _burgers_run(c, op, opts, u0, "f32" if precision else "f64")
     print(json.dumps({"precision": precision, "rc": rep["rc"], "wr_iters": rep["wr_iters"],
                       "oracle_iters": gold["iters"], "history": rep["wr_history"][:rep["wr_iters"]],
                       "k_nh_max": rep["k_nh_max"], "rank_max": rep["rank_max"], "time_ms": rep["time_ms"]}))
-    assert rep["rc"] in ((0,) if not precision else (0, -6)), rep["rc"]
+    assert rep["rc"] == 0, rep["rc"]
     errs = []
     for i in gold["rows"]:
         ref = np.array(gold["samples"][str(i)])
