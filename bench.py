@@ -31,16 +31,27 @@ N, NU, A, P, NT, T = 1 << 20, 1e-3, 1.0, 64, 1025, 1.0
 WORKLOAD = "adv_diff_1d_n1048576_P64_nout1025"
 
 
-def opts_for(precision: int, diag: int = 0) -> dict:
+MIXED_TOL = 1e-7
+# FP64 Krylov tolerances tried, loosest first: the FP64 arm runs at the loosest one whose
+# answer is within the metric's 1e-6 of the tight FP64 reference solve (tol REF_TOL)
+FP64_TOLS = (1e-7, 1e-8, 1e-9, 1e-10)
+REF_TOL = 1e-11
+ERR_BAR = 1e-6
+HBM_CLASSES = ("sai", "proj", "update", "source", "recon")
+
+
+def opts_for(precision: int, diag: int = 0, tol: float | None = None) -> dict:
     from paper_1509_04567_gb300 import workloads as wl
-    return wl.default_opts(T=T, P=P, n_out=NT, tol=1e-7 if precision else 1e-8, svd_tol=1e-10, max_rank=8,
+    if tol is None:
+        tol = MIXED_TOL if precision else FP64_TOLS[1]
+    return wl.default_opts(T=T, P=P, n_out=NT, tol=tol, svd_tol=1e-10, max_rank=8,
                            precision=precision, diagnostics=diag)
 
 
 def config(precision: str, n: int = N) -> dict:
     wname = WORKLOAD if n == N else WORKLOAD.replace("n1048576", f"n{n}")
     return {"workload": wname, "n": n, "nu": NU, "a": A, "P": P, "n_out": NT, "T": T,
-            "precision": precision, "krylov": "shift-and-invert", "tol": 1e-7 if precision == "mixed" else 1e-8,
+            "precision": precision, "krylov": "shift-and-invert", "tol": MIXED_TOL if precision == "mixed" else FP64_TOLS[1],
             "l2": f"inputs larger than L2 (source {NT * n * 4 / 1e9:.1f} GB FP32 / {NT * n * 8 / 1e9:.1f} GB FP64, "
                   f"outputs {NT * n * 4 / 1e9:.1f} GB)"}
 
@@ -144,6 +155,95 @@ def cpu_sample(seconds_hint: float = 20.0) -> dict:
             "sample_seconds": t_nh + t_hom}
 
 
+def cpu_sample_single_thread() -> dict:
+    """The same bounded oracle sample in a child process limited to one BLAS/OpenMP thread."""
+    env = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1",
+               BLIS_NUM_THREADS="1", CUDA_VISIBLE_DEVICES="")
+    try:
+        r = subprocess.run([sys.executable, os.path.abspath(__file__), "--cpu-sample-only"], env=env,
+                           capture_output=True, text=True, timeout=600)
+        d = json.loads(r.stdout.strip().splitlines()[-1])
+        return {"single_thread_value": d["value"], "single_thread_sample_seconds": d["sample_seconds"]}
+    except Exception as e:  # reported, not fatal
+        return {"single_thread_value": None, "single_thread_error": str(e)[:200]}
+
+
+def burgers_leg(ctx, dev) -> dict:
+    """The viscous Burgers workload (n = 65536, nu = 5e-3, u0 = 0.5 + sin 2 pi x, T = 0.5,
+    P = 32, 513 samples) by the averaged-Jacobian waveform relaxation to a 1e-6 relative
+    update, mixed and FP64: one untimed and one timed solve each (CUDA events)."""
+    import numpy as np
+    import torch
+    from paper_1509_04567_gb300 import workloads as wl
+    n, nt = 65536, 513
+    op = wl.make_op(n, 5e-3, 0.0)
+    x = torch.arange(n, dtype=torch.float64, device=dev) / n
+    u0 = 0.5 + torch.sin(2 * np.pi * x)
+    out = {"workload": "burgers_1d_n65536_P32_nout513", "method": "averaged-Jacobian waveform relaxation",
+           "wr_tol": 1e-6}
+    res = {}
+    for prec, dt, tol, svd in ((1, torch.float32, 1e-7, 1e-5), (0, torch.float64, 1e-10, 1e-7)):
+        o = wl.default_opts(T=0.5, P=32, n_out=nt, tol=tol, svd_tol=svd, max_rank=16, restart_len=40, wr_tol=1e-6,
+                            wr_max_iter=40, jacobian=1, precision=prec)
+        U = torch.empty((nt, n), dtype=dt, device=dev)
+        ctx.solve_burgers(op, o, u0, U, check=False)
+        torch.cuda.synchronize(dev)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(torch.cuda.current_stream(dev))
+        rep = ctx.solve_burgers(op, o, u0, U, check=False)
+        e1.record(torch.cuda.current_stream(dev))
+        torch.cuda.synchronize(dev)
+        res[prec] = U
+        key = "mixed" if prec else "fp64"
+        out[key] = {"rc": rep["rc"], "s_per_solve": e0.elapsed_time(e1) / 1e3, "wr_iters": rep["wr_iters"],
+                    "wr_history": [round(v, 9) for v in rep["wr_history"][:rep["wr_iters"]]],
+                    "rank_max": rep["rank_max"], "k_nh_max": rep["k_nh_max"], "k_hom_max": rep["k_hom_max"],
+                    "tol": tol, "svd_tol": svd}
+    d = ((res[1].double() - res[0]).norm(dim=1) / res[0].norm(dim=1)).max().item()
+    out["rel_diff_mixed_vs_fp64"] = d
+    out["speedup_mixed_vs_fp64"] = out["fp64"]["s_per_solve"] / out["mixed"]["s_per_solve"]
+    return out
+
+
+def batched_leg(ctx, dev, count: int = 512) -> dict:
+    """The batched workload: `count` independent advection-diffusion problems of uneven size
+    (n log-uniform in [4096, 262144], nu, a, 16-mode u0, P in {4..64}, n_out = 16 P + 1),
+    mixed precision at tol 1e-7, through pexp_solve_batched; one untimed and one timed call."""
+    import numpy as np
+    import torch
+    from paper_1509_04567_gb300 import workloads as wl
+    items, npts = [], 0
+    k = torch.arange(1, 17, dtype=torch.float64, device=dev)[:, None]
+    for i in range(count):
+        d = wl.batched_params(i)
+        n, P = d["n"], d["P"]
+        nt = 16 * P + 1
+        x = torch.arange(n, dtype=torch.float64, device=dev) / n
+        al = torch.tensor(d["al"], dtype=torch.float64, device=dev)[:, None]
+        be = torch.tensor(d["be"], dtype=torch.float64, device=dev)[:, None]
+        u0 = ((al * torch.cos(2 * np.pi * k * x) + be * torch.sin(2 * np.pi * k * x)) / k).sum(0).contiguous()
+        t = torch.arange(nt, dtype=torch.float64, device=dev) / (nt - 1)
+        G = (d["gam"] * torch.cos(2 * np.pi * t)[:, None] * torch.sin(4 * np.pi * x)[None, :]).float().contiguous()
+        Y = torch.empty((nt, n), dtype=torch.float32, device=dev)
+        opts = wl.default_opts(T=1.0, P=P, n_out=nt, tol=1e-7, svd_tol=1e-10, max_rank=8, precision=1)
+        items.append((wl.make_op(n, d["nu"], d["a"]), opts, u0, G, Y))
+        npts += n
+    ctx.solve_batched(items, check=False)
+    torch.cuda.synchronize(dev)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(torch.cuda.current_stream(dev))
+    reps = ctx.solve_batched(items, check=False)
+    e1.record(torch.cuda.current_stream(dev))
+    torch.cuda.synchronize(dev)
+    s = e0.elapsed_time(e1) / 1e3
+    bad = sum(1 for r in reps if r["rc"] != 0)
+    del items
+    torch.cuda.empty_cache()
+    return {"workload": f"batched_{count}_adv_diff_1d_n4096_262144", "instances": count, "points_total": npts,
+            "precision": "mixed", "s_per_batch": s, "solves_per_s": count / s, "not_ok": bad,
+            "entry": "pexp_solve_batched"}
+
+
 def max_over_ranks(ms: float, dist, device) -> float:
     """The slowest rank's time per step: every rank calls this after its timed region
     (one process: the time itself)."""
@@ -169,7 +269,8 @@ def run_reference(args) -> None:
     for _ in range(min(args.warmup, 1)):
         cpu_sample()
     steps = [cpu_sample() for _ in range(args.steps)]
-    cb = steps[-1]
+    cb = dict(steps[-1])
+    cb.update(cpu_sample_single_thread())
     v = statistics.median(s["value"] for s in steps)
     line = {"impl": "reference", "metric": METRIC, "value": v, "unit": "solves/s", "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 / v, "higher_is_better": True,
@@ -190,7 +291,11 @@ def main() -> None:
     ap.add_argument("--n", type=int, default=N, help="grid points (profiling cases; the bench line uses 2^20)")
     ap.add_argument("--quick", action="store_true",
                     help="timed solves only: no precision comparison, end-to-end leg or CPU baseline")
+    ap.add_argument("--cpu-sample-only", action="store_true", help=argparse.SUPPRESS)
     args = ap.parse_args()
+    if args.cpu_sample_only:
+        print(json.dumps(cpu_sample()), flush=True)
+        return
     if args.impl == "reference":
         run_reference(args)
         return
@@ -255,54 +360,87 @@ def main() -> None:
     ms = max_over_ranks(ev0.elapsed_time(ev1) / args.steps, dist, dev)
     value = job_value(world, ms)
 
-    # the dominant kernel class, timed live over the timed region, sets the roofline line
+    # the dominant kernel class, timed live over the timed region, sets the roofline line;
+    # its achieved rate counts the algorithmic bytes (every array at its storage width);
+    # the bytes moved, with the low parts of the FP32 working block, are given beside it
     k_ms = np.sum([r["k_ms"] for r in reps], axis=0)
     k_n = np.sum([r["k_launches"] for r in reps], axis=0)
     k_b = np.sum([r["k_bytes"] for r in reps], axis=0)
+    k_a = np.sum([r["k_bytes_alg"] for r in reps], axis=0)
     peaks = read_peaks()
+    hbm = peaks.get("hbm_gbs", 6800.0)
+    peak_source = "measured" if "fallback" not in peaks else "fallback"
     if prec:
-        achieved = k_b[dom] / (k_ms[dom] * 1e-3) / 1e9
+        achieved = k_a[dom] / (k_ms[dom] * 1e-3) / 1e9
+        moved = k_b[dom] / (k_ms[dom] * 1e-3) / 1e9
         roof = {"bound": "hbm", "kernel_class": pexp.KC_NAMES[dom], "achieved": achieved,
-                "peak": peaks.get("hbm_gbs"), "unit": "GB/s",
-                "frac": achieved / peaks.get("hbm_gbs", 6800.0),
-                "traffic": profile_traffic(pexp.KC_NAMES[dom]),
-                "peak_source": "measured" if "fallback" not in peaks else "fallback",
+                "peak": peaks.get("hbm_gbs"), "unit": "GB/s", "frac": achieved / hbm,
+                "traffic": profile_traffic(pexp.KC_NAMES[dom]), "peak_source": peak_source,
+                "achieved_incl_low_parts": moved, "frac_incl_low_parts": moved / hbm,
+                "alg_bytes_per_launch": k_a[dom] / max(1, k_n[dom]),
                 "launches": int(k_n[dom]), "avg_launch_us": 1e3 * k_ms[dom] / max(1, k_n[dom]),
                 "sampled": f"1 in {1 << SAMPLE_LOG2} launches of the class, chosen by a fixed pseudo-random sequence"}
     else:
-        achieved = k_b[dom] / (k_ms[dom] * 1e-3) / 1e9
+        achieved = k_a[dom] / (k_ms[dom] * 1e-3) / 1e9
         roof = {"bound": "alu", "kernel_class": pexp.KC_NAMES[dom], "achieved": achieved, "unit": "GB/s",
                 "peak": None, "frac": None, "traffic": None,
                 "note": "FP64 path: bound by the FP64 FMA rate (1.01 TFLOP/s measured), not HBM"}
-    kernel_split = {pexp.KC_NAMES[i]: {"ms_per_step": wrep["k_ms"][i], "launches_per_step": wrep["k_launches"][i],
-                                        "GB_per_s": (wrep["k_bytes"][i] / (wrep["k_ms"][i] * 1e-3) / 1e9)
-                                        if wrep["k_ms"][i] > 0 else None}
-                    for i in range(8) if wrep["k_launches"][i] > 0}
+    # every HBM-bound class from the warm-up solve (all classes timed there)
+    kernel_split = {}
+    for i in range(8):
+        if wrep["k_launches"][i] <= 0:
+            continue
+        ent = {"ms_per_step": wrep["k_ms"][i], "launches_per_step": wrep["k_launches"][i]}
+        if wrep["k_ms"][i] > 0 and pexp.KC_NAMES[i] in HBM_CLASSES:
+            ga = wrep["k_bytes_alg"][i] / (wrep["k_ms"][i] * 1e-3) / 1e9
+            gm = wrep["k_bytes"][i] / (wrep["k_ms"][i] * 1e-3) / 1e9
+            ent.update({"GB_per_s": ga, "frac": ga / hbm, "GB_per_s_incl_low_parts": gm})
+        kernel_split[pexp.KC_NAMES[i]] = ent
+    roof["classes"] = {k: {"achieved": v["GB_per_s"], "frac": v["frac"]} for k, v in kernel_split.items()
+                       if "GB_per_s" in v}
     rep = reps[-1]
 
     extra = {}
-    if rank == 0 and not args.quick:
-        # accuracy and speed of the other precision on the same inputs
-        oth = 0 if prec else 1
-        ot = opts_for(oth)
-        Go = G.to(torch.float64 if oth == 0 else torch.float32).contiguous()
-        Yo = torch.empty((NT, n), dtype=Go.dtype, device=dev)
-        ctx.solve_linear(op, ot, u0, Go, Yo)
+    if rank == 0 and not args.quick and prec:
+        # the FP64 GPU path on the same inputs: a tight reference solve, then the loosest FP64
+        # tolerance whose answer is within 1e-6 of it, timed over the same number of solves
+        G64 = G.double().contiguous()
+        Yref = torch.empty((NT, n), dtype=torch.float64, device=dev)
+        ctx.solve_linear(op, dict(opts_for(0, tol=REF_TOL), restart_len=30), u0, G64, Yref)
+        refn = Yref.norm(dim=1)
+
+        def err_vs_ref(Yx):
+            return float(((Yx.double() - Yref).norm(dim=1) / refn).max().item())
+
+        err_mixed = err_vs_ref(Y)
+        Y64 = torch.empty_like(Yref)
+        tried = {}
+        tol64 = FP64_TOLS[-1]
+        for tl in FP64_TOLS:
+            ctx.solve_linear(op, opts_for(0, tol=tl), u0, G64, Y64)
+            torch.cuda.synchronize(dev)
+            tried[f"{tl:g}"] = err_vs_ref(Y64)
+            if tried[f"{tl:g}"] <= ERR_BAR:
+                tol64 = tl
+                break
+        o64 = opts_for(0, tol=tol64)
+        ctx.solve_linear(op, o64, u0, G64, Y64)
         torch.cuda.synchronize(dev)
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         e0.record(stream)
-        ctx.solve_linear(op, ot, u0, Go, Yo)
+        for _ in range(args.steps):
+            ctx.solve_linear(op, o64, u0, G64, Y64)
         e1.record(stream)
         torch.cuda.synchronize(dev)
-        ms_o = e0.elapsed_time(e1)
-        Yd = (Yo if oth == 0 else Y).double()
-        Ym = (Y if oth == 0 else Yo).double()
-        err = float(((Ym - Yd).norm(dim=1) / Yd.norm(dim=1)).max().item())
-        del Yd, Ym, Yo, Go
-        extra = {"fp64_ms_per_step": ms_o if prec else ms, "mixed_ms_per_step": ms if prec else ms_o,
-                 "speedup_mixed_vs_fp64": (ms_o / ms) if prec else (ms / ms_o),
-                 "rel_err_mixed_vs_fp64": err}
+        ms_o = e0.elapsed_time(e1) / args.steps
+        err64 = err_vs_ref(Y64)
+        del Yref, Y64, G64
+        extra = {"fp64_ms_per_step": ms_o, "mixed_ms_per_step": ms, "speedup_mixed_vs_fp64": ms_o / ms,
+                 "fp64_tol": tol64, "fp64_rel_err": err64, "mixed_rel_err": err_mixed,
+                 "fp64_tols_tried": tried, "rel_err_reference": f"FP64 GPU solve at tol {REF_TOL:g}",
+                 "rel_err_mixed_vs_fp64": err_mixed}
 
+    if rank == 0 and not args.quick:
         # end to end through the host-pointer entry: pinned host inputs/outputs, copies timed
         u0h = u0.cpu().numpy()
         Gh = torch.empty((NT, n), dtype=gdt, pin_memory=True)
@@ -322,9 +460,14 @@ def main() -> None:
                         "h2d_bytes_per_step": int(n * 8 + NT * n * el), "d2h_bytes_per_step": int(NT * n * el)}
         del Gh, Yh
 
+    if rank == 0 and not args.quick and prec and args.n == N:
+        extra["burgers"] = burgers_leg(ctx, dev)
+        extra["batched"] = batched_leg(ctx, dev)
+
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline and not args.quick:
         cpu = cpu_sample()
+        cpu.update(cpu_sample_single_thread())
 
     if rank == 0:
         line = {"metric": METRIC, "value": value, "unit": "solves/s", "n_gpus": world, "steps": args.steps,
