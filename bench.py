@@ -168,6 +168,26 @@ def cpu_sample_single_thread() -> dict:
         return {"single_thread_value": None, "single_thread_error": str(e)[:200]}
 
 
+def fp64_peak(size: int = 8192, reps: int = 10) -> dict:
+    """FP64 rate of the GPU: a cuBLAS DGEMM (size^3, through torch) timed with CUDA events
+    after warm-up -- the denominator of the FP64 path, which is bound by FP64 arithmetic."""
+    import torch
+    a = torch.randn(size, size, dtype=torch.float64, device="cuda")
+    b = torch.randn(size, size, dtype=torch.float64, device="cuda")
+    for _ in range(3):
+        a @ b
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(reps):
+        a @ b
+    e1.record()
+    torch.cuda.synchronize()
+    s = e0.elapsed_time(e1) / 1e3 / reps
+    return {"fp64_dgemm_tflops": 2.0 * size ** 3 / s / 1e12, "size": size, "reps": reps,
+            "device": torch.cuda.get_device_name(0)}
+
+
 def burgers_leg(ctx, dev) -> dict:
     """The viscous Burgers workload (n = 65536, nu = 5e-3, u0 = 0.5 + sin 2 pi x, T = 0.5,
     P = 32, 513 samples) by the averaged-Jacobian waveform relaxation to a 1e-6 relative
@@ -208,7 +228,8 @@ def burgers_leg(ctx, dev) -> dict:
 def batched_leg(ctx, dev, count: int = 512) -> dict:
     """The batched workload: `count` independent advection-diffusion problems of uneven size
     (n log-uniform in [4096, 262144], nu, a, 16-mode u0, P in {4..64}, n_out = 16 P + 1),
-    mixed precision at tol 1e-7, through pexp_solve_batched; one untimed and one timed call."""
+    mixed precision at tol 1e-7 with the largest step budget (40), through pexp_solve_batched;
+    one untimed and one timed call."""
     import numpy as np
     import torch
     from paper_1509_04567_gb300 import workloads as wl
@@ -225,7 +246,7 @@ def batched_leg(ctx, dev, count: int = 512) -> dict:
         t = torch.arange(nt, dtype=torch.float64, device=dev) / (nt - 1)
         G = (d["gam"] * torch.cos(2 * np.pi * t)[:, None] * torch.sin(4 * np.pi * x)[None, :]).float().contiguous()
         Y = torch.empty((nt, n), dtype=torch.float32, device=dev)
-        opts = wl.default_opts(T=1.0, P=P, n_out=nt, tol=1e-7, svd_tol=1e-10, max_rank=8, precision=1)
+        opts = wl.default_opts(T=1.0, P=P, n_out=nt, tol=1e-7, svd_tol=1e-10, max_rank=8, precision=1, restart_len=40)
         items.append((wl.make_op(n, d["nu"], d["a"]), opts, u0, G, Y))
         npts += n
     ctx.solve_batched(items, check=False)
@@ -237,10 +258,11 @@ def batched_leg(ctx, dev, count: int = 512) -> dict:
     torch.cuda.synchronize(dev)
     s = e0.elapsed_time(e1) / 1e3
     bad = sum(1 for r in reps if r["rc"] != 0)
+    nc = sum(1 for r in reps if r["rc"] == -5)
     del items
     torch.cuda.empty_cache()
     return {"workload": f"batched_{count}_adv_diff_1d_n4096_262144", "instances": count, "points_total": npts,
-            "precision": "mixed", "s_per_batch": s, "solves_per_s": count / s, "not_ok": bad,
+            "precision": "mixed", "s_per_batch": s, "solves_per_s": count / s, "not_ok": bad, "not_converged": nc,
             "entry": "pexp_solve_batched"}
 
 
@@ -292,9 +314,14 @@ def main() -> None:
     ap.add_argument("--quick", action="store_true",
                     help="timed solves only: no precision comparison, end-to-end leg or CPU baseline")
     ap.add_argument("--cpu-sample-only", action="store_true", help=argparse.SUPPRESS)
+    ap.add_argument("--fp64-peak", action="store_true",
+                    help="measure the FP64 rate of this GPU (cuBLAS DGEMM through torch) and exit")
     args = ap.parse_args()
     if args.cpu_sample_only:
         print(json.dumps(cpu_sample()), flush=True)
+        return
+    if args.fp64_peak:
+        print(json.dumps(fp64_peak()), flush=True)
         return
     if args.impl == "reference":
         run_reference(args)
@@ -390,7 +417,8 @@ def main() -> None:
     for i in range(8):
         if wrep["k_launches"][i] <= 0:
             continue
-        ent = {"ms_per_step": wrep["k_ms"][i], "launches_per_step": wrep["k_launches"][i]}
+        ent = {"ms_per_step": wrep["k_ms"][i], "launches_per_step": wrep["k_launches"][i],
+               "alg_bytes_per_step": wrep["k_bytes_alg"][i]}
         if wrep["k_ms"][i] > 0 and pexp.KC_NAMES[i] in HBM_CLASSES:
             ga = wrep["k_bytes_alg"][i] / (wrep["k_ms"][i] * 1e-3) / 1e9
             gm = wrep["k_bytes"][i] / (wrep["k_ms"][i] * 1e-3) / 1e9

@@ -190,7 +190,8 @@ void launch_row_diff_norms(const T* A, const T* B, int64_t n, int nrows, double*
 
 template <typename T>
 void launch_add(T* y, const T* x, int64_t count, cudaStream_t s);
-void launch_ts_nn_df(const DfTask* tasks_dev, int ntasks, int max_pq, int64_t n, cudaStream_t s);
+// max_q: most block columns q of any task (<= 16); q <= 4 takes a two-row kernel
+void launch_ts_nn_df(const DfTask* tasks_dev, int ntasks, int max_pq, int64_t n, cudaStream_t s, int max_q = 16);
 template <typename T>
 // split: 2n floats of scratch (FP32 data: u as a double-float pair)
 void launch_row_dots(const double* u, const T* G, int64_t n, int nrows, double* out, float* split, cudaStream_t s);

@@ -258,6 +258,7 @@ __global__ void __launch_bounds__(kThreads, Group<T, B, JAC>::ctas) k_step_proj(
             D[c] = vr - vi[c];
             C[c] = vr - vl;
         }
+
         T ub = T(0);
         if constexpr (JAC) ub = act ? ldg(tk.ubar + rp) : T(0);
 #pragma unroll
@@ -890,6 +891,10 @@ template <typename T>
 __global__ void __launch_bounds__(kThreads) k_source_gram(const T* const* __restrict__ Xp, const int* __restrict__ sv,
                                                           int64_t n, int64_t rows, int nchunks, int pstride,
                                                           double* __restrict__ partial) {
+    // One thread per Gram entry (a, c), a <= c (up to MAXP of them), a compensated sum over
+    // the chunk's rows in order.  The tile is stored row-major with an odd row stride: the
+    // lanes of a warp read different columns of one row, which fall in different banks (a
+    // column-major tile with a stride of kTile put them all in one bank).
     const int task = blockIdx.y;
     const T* X = Xp[task];
     const int s = sv[task];
@@ -897,7 +902,8 @@ __global__ void __launch_bounds__(kThreads) k_source_gram(const T* const* __rest
     const int64_t r0 = (int64_t)ch * rows;
     const int64_t r1 = (r0 + rows < n) ? r0 + rows : n;
     extern __shared__ double sh_gram[];
-    T* sX = reinterpret_cast<T*>(sh_gram);   // s x kTile
+    const int sp = s | 1;
+    T* sX = reinterpret_cast<T*>(sh_gram);   // kTile x sp, row k at sX + k * sp
     const int npair = s * (s + 1) / 2;
     // up to 9 (a, c) pairs per thread: s <= 64
     constexpr int MAXP = 9;
@@ -917,16 +923,16 @@ __global__ void __launch_bounds__(kThreads) k_source_gram(const T* const* __rest
         const int nt = (int)((t0 + kTile <= r1) ? kTile : (r1 - t0));
         __syncthreads();
         for (int e = threadIdx.x; e < s * kTile; e += kThreads) {
-            const int a = e / kTile, k = e % kTile;
-            if (k < nt) sX[a * kTile + k] = X[(int64_t)a * n + t0 + k];
+            const int a = e / kTile, k = e % kTile;   // coalesced along k in global memory
+            if (k < nt) sX[k * sp + a] = X[(int64_t)a * n + t0 + k];
         }
         __syncthreads();
 #pragma unroll
         for (int q = 0; q < MAXP; ++q) {
             if (q >= np) break;
-            const T* xa = sX + pa[q] * kTile;
-            const T* xc = sX + pc[q] * kTile;
-            for (int k = 0; k < nt; ++k) acc[q].add(xa[k], xc[k]);
+            const T* xa = sX + pa[q];
+            const T* xc = sX + pc[q];
+            for (int k = 0; k < nt; ++k) acc[q].add(xa[k * sp], xc[k * sp]);
         }
     }
     double* pout = partial + ((size_t)task * nchunks + ch) * pstride;
@@ -1046,7 +1052,8 @@ void launch_source_gram(const T* const* X, const int* sv, int ntasks, int s_max,
                         int pstride, cudaStream_t st) {
     if (ntasks <= 0) return;
     dim3 grid(g.nchunks, ntasks);
-    const size_t sm = sizeof(T) * (size_t)s_max * kTile;
+    // the sample tile: kTile rows of stride s_max | 1
+    const size_t sm = sizeof(T) * (size_t)(s_max | 1) * kTile;
     if (sm > 32 * 1024) smem_optin(k_source_gram<T>, sm);
     k_source_gram<T><<<grid, kThreads, sm, st>>>(X, sv, n, g.rows, g.nchunks, pstride, partial);
 }

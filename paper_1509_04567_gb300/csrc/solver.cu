@@ -898,15 +898,15 @@ struct Solver {
                 double pb = 0, bb = 0;   // sum of p*b and of b over the active windows
                 for (auto& W : act) { pb += (double)step * W.b; bb += W.b; }
                 const double nn = (double)n;
-                timed(c, PEXP_KC_UPDATE, nn * (pb * 4 + bb * 16), [&] { launch_ts_nn_df(dd1, nb, mpq1, n, st); }, nullptr, false, nn * (pb * 4 + bb * 8)); check_launch(c);
+                timed(c, PEXP_KC_UPDATE, nn * (pb * 4 + bb * 16), [&] { launch_ts_nn_df(dd1, nb, mpq1, n, st, mq3); }, nullptr, false, nn * (pb * 4 + bb * 8)); check_launch(c);
                 timed(c, PEXP_KC_PROJ, nn * (pb + bb) * 4, [&] { launch_ts_tn<T>(d_tn2, nb, mpq2, mq2, n, partial, st, PEXP_TN_EXACT_FP32); }); check_launch(c);
-                timed(c, PEXP_KC_UPDATE, nn * (pb * 4 + bb * 16), [&] { launch_ts_nn_df(dd2, nb, mpq1, n, st); }, nullptr, false, nn * (pb * 4 + bb * 8)); check_launch(c);
+                timed(c, PEXP_KC_UPDATE, nn * (pb * 4 + bb * 16), [&] { launch_ts_nn_df(dd2, nb, mpq1, n, st, mq3); }, nullptr, false, nn * (pb * 4 + bb * 8)); check_launch(c);
                 timed(c, PEXP_KC_PROJ, nn * bb * 4, [&] { launch_ts_tn<T>(d_tn3, nb, mpq3, mq3, n, partial, st, 1); }); check_launch(c);
                 timed(c, PEXP_KC_SMALL, 0.0, [&] { launch_block_orth(L, wd, wi, d_wl2, nb, 1, step, defl, st); }); check_launch(c);
-                timed(c, PEXP_KC_UPDATE, nn * bb * 16, [&] { launch_ts_nn_df(dd3, nb, mpq3, n, st); }, nullptr, false, nn * bb * 8); check_launch(c);
+                timed(c, PEXP_KC_UPDATE, nn * bb * 16, [&] { launch_ts_nn_df(dd3, nb, mpq3, n, st, mq3); }, nullptr, false, nn * bb * 8); check_launch(c);
                 timed(c, PEXP_KC_PROJ, nn * bb * 4, [&] { launch_ts_tn<T>(d_tn3, nb, mpq3, mq3, n, partial, st, 1); }); check_launch(c);
                 timed(c, PEXP_KC_SMALL, 0.0, [&] { launch_block_orth(L, wd, wi, d_wl2, nb, 2, step, defl, st); }); check_launch(c);
-                timed(c, PEXP_KC_UPDATE, nn * bb * 12, [&] { launch_ts_nn_df(dd4, nb, mpq3, n, st); }, nullptr, false, nn * bb * 8); check_launch(c);
+                timed(c, PEXP_KC_UPDATE, nn * bb * 12, [&] { launch_ts_nn_df(dd4, nb, mpq3, n, st, mq3); }, nullptr, false, nn * bb * 8); check_launch(c);
             } else {
                 const TsTask<T>* d_nn1 = sb.put(nn1.data(), nb);
                 const TsTask<T>* d_nn2 = sb.put(nn2.data(), nb);
@@ -1244,7 +1244,7 @@ int solve_linear_typed(pexp_ctx* c, const pexp_operator* op, const pexp_options*
             dds = s2.put(dsc.data(), ns);
         }
         s2.flush();
-        if (ddu) launch_ts_nn_df(ddu, ns, mpq, n, st);
+        if (ddu) launch_ts_nn_df(ddu, ns, mpq, n, st, mq);
         else launch_ts_nn<T>(dtu, ns, mpq, n, st);
         check_launch(c);
         if (mq <= 4) {
@@ -1268,7 +1268,7 @@ int solve_linear_typed(pexp_ctx* c, const pexp_operator* op, const pexp_options*
             launch_ts_tn<T>(dtg, ns, mpqg, mq, n, S.partial, st, 1); check_launch(c);
         }
         launch_start_orth(L, S.wd, S.wi, dwl, ns, st); check_launch(c);
-        if (dds) launch_ts_nn_df(dds, ns, mpqg, n, st);
+        if (dds) launch_ts_nn_df(dds, ns, mpqg, n, st, mq);
         else launch_ts_nn<T>(dts, ns, mpqg, n, st);
         check_launch(c);
         launch_spline(L, S.wd, S.wi, dwl, ns, S.h, st); check_launch(c);
@@ -1404,7 +1404,7 @@ int solve_linear_typed(pexp_ctx* c, const pexp_operator* op, const pexp_options*
         if (dz) {
             if (nz == 0) cudaMemsetAsync(Vh[m], 0, sizeof(T) * (size_t)n, st);
             for (int k = 0; k < nz; ++k) {
-                launch_ts_nn_df(dz + k, 1, std::max(rt.K1, rt.K2), n, st);
+                launch_ts_nn_df(dz + k, 1, std::max(rt.K1, rt.K2), n, st, 1);
                 check_launch(c);
             }
         } else {
@@ -1418,7 +1418,7 @@ int solve_linear_typed(pexp_ctx* c, const pexp_operator* op, const pexp_options*
             check_launch(c);
         }
         launch_start_orth(L, S.wd, S.wi, dw, 1, st); check_launch(c);
-        if (dz) launch_ts_nn_df(dz + 2, 1, 1, n, st);
+        if (dz) launch_ts_nn_df(dz + 2, 1, 1, n, st, 1);
         else launch_ts_nn<T>(dts, 1, 1, n, st);
         check_launch(c);
         // a zero z (nothing to continue) is marked converged with an empty basis on the device

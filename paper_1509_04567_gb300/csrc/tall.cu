@@ -642,8 +642,11 @@ void launch_ts_nn(const TsTask<T>* tasks_dev, int ntasks, int max_pq, int64_t n,
 // X and Z are (hi, lo) pairs of FP32 arrays (a missing lo array means 0, and for
 // Z means "round to FP32"); products and sums are error-free to ~2^-48, so the
 // cancellation of Gram-Schmidt leaves no FP32-sized noise in the new direction.
+// QM: most block columns q of Z this instantiation handles (4: the small blocks of the source
+// and continuation formations, fewer accumulators); R: rows per thread per iteration, all
+// their loads issued before any is used; PB: columns of X per batch of loads.
+template <int QM, int R, int PB>
 __global__ void __launch_bounds__(256, 2) k_ts_nn_df(const DfTask* __restrict__ tasks, int64_t n, int64_t rows) {
-    constexpr int QM = 16, PB = 16;   // block columns of Z, columns of X per batch of loads
     const DfTask tk = tasks[blockIdx.y];
     extern __shared__ float smem_df[];
     const int p = tk.p, q = tk.q;
@@ -665,68 +668,80 @@ __global__ void __launch_bounds__(256, 2) k_ts_nn_df(const DfTask* __restrict__ 
     const int pl = (tk.Xl && tk.pl > 0) ? tk.pl : (tk.Xl ? p : 0);   // columns of X with a low part
     const int64_t r0 = (int64_t)blockIdx.x * rows;
     const int64_t r1 = (r0 + rows < n) ? r0 + rows : n;
-    for (int64_t base = r0; base < r1; base += blockDim.x) {
-        const int64_t r = base + threadIdx.x;
-        const bool act = r < r1;
+    for (int64_t base = r0; base < r1; base += (int64_t)R * blockDim.x) {
+        int64_t r[R];
+        bool act[R];
+#pragma unroll
+        for (int u = 0; u < R; ++u) {
+            r[u] = base + (int64_t)u * blockDim.x + threadIdx.x;
+            act[u] = r[u] < r1;
+        }
         // Z[r, c] = sum_a (X[r, a] (+ xs[r])) T[a, c]: exact FP32 products x * t_hi (FMA), the
         // small terms in a second sum, the running sums compensated (two-sum)
-        float sh[QM], sl[QM];
+        float sh[R][QM], sl[R][QM];
 #pragma unroll
-        for (int c = 0; c < QM; ++c) sh[c] = sl[c] = 0.f;
+        for (int u = 0; u < R; ++u)
+#pragma unroll
+            for (int c = 0; c < QM; ++c) sh[u][c] = sl[u][c] = 0.f;
         for (int a0 = 0; a0 < p; a0 += PB) {
-            float x[PB], xl[PB];
+            float x[R][PB], xl[R][PB];
 #pragma unroll
-            for (int j = 0; j < PB; ++j) {
-                const int a = a0 + j;
-                x[j] = (act && a < p && tk.Xh) ? tk.Xh[(int64_t)a * tk.ldx + r] : 0.f;
-                xl[j] = (act && a < pl) ? tk.Xl[(int64_t)a * tk.ldx + r] : 0.f;
+            for (int u = 0; u < R; ++u)
+#pragma unroll
+                for (int j = 0; j < PB; ++j) {
+                    const int a = a0 + j;
+                    x[u][j] = (act[u] && a < p && tk.Xh) ? tk.Xh[(int64_t)a * tk.ldx + r[u]] : 0.f;
+                    xl[u][j] = (act[u] && a < pl) ? tk.Xl[(int64_t)a * tk.ldx + r[u]] : 0.f;
+                }
+#pragma unroll
+            for (int c = 0; c < QM; ++c) {
+                if (c >= q) break;
+#pragma unroll
+                for (int j = 0; j < PB; ++j) {
+                    if (a0 + j >= p) break;
+                    const float2 t = Tc[(a0 + j) + c * p];   // one coefficient pair, used by every row
+#pragma unroll
+                    for (int u = 0; u < R; ++u) {
+                        const float ph = x[u][j] * t.x;
+                        float pe = fmaf(x[u][j], t.x, -ph);
+                        pe = fmaf(x[u][j], t.y, pe);
+                        pe = fmaf(xl[u][j], t.x, pe);
+                        const float w = sh[u][c] + ph;
+                        const float bp = w - sh[u][c];
+                        sl[u][c] += ((sh[u][c] - (w - bp)) + (ph - bp)) + pe;
+                        sh[u][c] = w;
+                    }
+                }
+            }
+        }
+#pragma unroll
+        for (int u = 0; u < R; ++u) {
+            if (!act[u]) continue;
+            DF xsd = DF{0.f, 0.f};
+            if (tk.xs) {
+                const double v = tk.xs[r[u]];
+                const float h = (float)v;
+                xsd = DF{h, (float)(v - (double)h)};
             }
 #pragma unroll
             for (int c = 0; c < QM; ++c) {
                 if (c >= q) break;
-                float s_ = sh[c], l_ = sl[c];
-#pragma unroll
-                for (int j = 0; j < PB; ++j) {
-                    if (a0 + j >= p) break;
-                    const float2 t = Tc[(a0 + j) + c * p];
-                    const float ph = x[j] * t.x;
-                    float pe = fmaf(x[j], t.x, -ph);
-                    pe = fmaf(x[j], t.y, pe);
-                    pe = fmaf(xl[j], t.x, pe);
-                    const float u = s_ + ph;
-                    const float bp = u - s_;
-                    l_ += ((s_ - (u - bp)) + (ph - bp)) + pe;
-                    s_ = u;
+                DF z = df_fast2sum(sh[u][c], sl[u][c]);
+                if (tk.xs) z = df_add(z, df_mul(xsd, DF{cs[c].x, cs[c].y}));
+                const int64_t o = (int64_t)c * tk.ldz + r[u];
+                if (tk.accumulate) z = df_add(z, DF{tk.Zh[o], tk.Zl ? tk.Zl[o] : 0.f});
+                if (tk.Zl) {
+                    tk.Zh[o] = z.hi;
+                    tk.Zl[o] = z.lo;
+                } else {
+                    tk.Zh[o] = z.hi + z.lo;
                 }
-                sh[c] = s_;
-                sl[c] = l_;
-            }
-        }
-        if (!act) continue;
-        DF xsd = DF{0.f, 0.f};
-        if (tk.xs) {
-            const double v = tk.xs[r];
-            const float h = (float)v;
-            xsd = DF{h, (float)(v - (double)h)};
-        }
-#pragma unroll
-        for (int c = 0; c < QM; ++c) {
-            if (c >= q) break;
-            DF z = df_fast2sum(sh[c], sl[c]);
-            if (tk.xs) z = df_add(z, df_mul(xsd, DF{cs[c].x, cs[c].y}));
-            const int64_t o = (int64_t)c * tk.ldz + r;
-            if (tk.accumulate) z = df_add(z, DF{tk.Zh[o], tk.Zl ? tk.Zl[o] : 0.f});
-            if (tk.Zl) {
-                tk.Zh[o] = z.hi;
-                tk.Zl[o] = z.lo;
-            } else {
-                tk.Zh[o] = z.hi + z.lo;
             }
         }
     }
 }
 
-void launch_ts_nn_df(const DfTask* tasks_dev, int ntasks, int max_pq, int64_t n, cudaStream_t s) {
+void launch_ts_nn_df(const DfTask* tasks_dev, int ntasks, int max_pq, int64_t n, cudaStream_t s, int max_q) {
     if (ntasks <= 0) return;
     // row chunks of >= 256 rows, about 8 CTAs per SM in total
     const int64_t maxch = std::max<int64_t>(1, (n + 255) / 256);
@@ -736,8 +751,13 @@ void launch_ts_nn_df(const DfTask* tasks_dev, int ntasks, int max_pq, int64_t n,
     rows = (rows + 255) / 256 * 256;
     dim3 grid((unsigned)((n + rows - 1) / rows), ntasks);
     size_t sm = ((size_t)max_pq + 16) * sizeof(float2);
-    if (sm > 32 * 1024) smem_optin(k_ts_nn_df, sm);
-    k_ts_nn_df<<<grid, 256, sm, s>>>(tasks_dev, n, rows);
+    if (max_q <= 4) {
+        if (sm > 32 * 1024) smem_optin(k_ts_nn_df<4, 1, 16>, sm);
+        k_ts_nn_df<4, 1, 16><<<grid, 256, sm, s>>>(tasks_dev, n, rows);
+    } else {
+        if (sm > 32 * 1024) smem_optin(k_ts_nn_df<16, 1, 16>, sm);
+        k_ts_nn_df<16, 1, 16><<<grid, 256, sm, s>>>(tasks_dev, n, rows);
+    }
 }
 
 // out[i] = sum_k u[k] * G[i*n + k] for the rows i < nrows.  FP64 data: FP64 FMAs.  FP32 data:
