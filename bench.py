@@ -231,7 +231,7 @@ def burgers_leg(ctx, dev, n: int = 65536, precisions=(1, 0)) -> dict:
 def batched_leg(ctx, dev, count: int = 512) -> dict:
     """The batched workload: `count` independent advection-diffusion problems of uneven size
     (n log-uniform in [4096, 262144], nu, a, 16-mode u0, P in {4..64}, n_out = 16 P + 1),
-    mixed precision at tol 1e-7 with the largest step budget (40), through pexp_solve_batched;
+    mixed precision at tol 1e-7 with the largest step budget (64), through pexp_solve_batched;
     one untimed and one timed call."""
     import numpy as np
     import torch
@@ -249,7 +249,7 @@ def batched_leg(ctx, dev, count: int = 512) -> dict:
         t = torch.arange(nt, dtype=torch.float64, device=dev) / (nt - 1)
         G = (d["gam"] * torch.cos(2 * np.pi * t)[:, None] * torch.sin(4 * np.pi * x)[None, :]).float().contiguous()
         Y = torch.empty((nt, n), dtype=torch.float32, device=dev)
-        opts = wl.default_opts(T=1.0, P=P, n_out=nt, tol=1e-7, svd_tol=1e-10, max_rank=8, precision=1, restart_len=40)
+        opts = wl.default_opts(T=1.0, P=P, n_out=nt, tol=1e-7, svd_tol=1e-10, max_rank=8, precision=1, restart_len=64)
         items.append((wl.make_op(n, d["nu"], d["a"]), opts, u0, G, Y))
         npts += n
     ctx.solve_batched(items, check=False)

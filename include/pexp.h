@@ -141,8 +141,9 @@ typedef struct {
 #define PEXP_KC_COUNT   8
 
 #define PEXP_MAX_RANK   16    /* largest block width */
-#define PEXP_MAX_STEPS  40    /* largest Krylov step budget restart_len*(max_restarts+1) */
-#define PEXP_MAX_SAMPLES 64   /* largest number of samples in one subinterval */
+#define PEXP_MAX_STEPS  64    /* largest Krylov step budget restart_len*(max_restarts+1) */
+#define PEXP_MAX_SAMPLES 112  /* largest number of samples in one subinterval: the FP64 source
+                                 Gram tile, 8 (s|1) 256 bytes, fits one CTA's shared memory */
 #define PEXP_REPORT_SUBS 128  /* per-subinterval report entries (the first 128 subintervals) */
 #define PEXP_REPORT_WR   64   /* WR update history entries (the first 64 iterations) */
 

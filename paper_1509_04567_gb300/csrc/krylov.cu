@@ -887,7 +887,7 @@ __global__ void __launch_bounds__(kThreads) k_sum_parts(const double* __restrict
 // staged in shared memory; thread t owns entries (a, c), a <= c, and sums FP32
 // products with compensation; CTAs write partial Gram matrices (s x s, both halves).
 // =====================================================================================
-template <typename T>
+template <typename T, int MAXP>
 __global__ void __launch_bounds__(kThreads) k_source_gram(const T* const* __restrict__ Xp, const int* __restrict__ sv,
                                                           int64_t n, int64_t rows, int nchunks, int pstride,
                                                           double* __restrict__ partial) {
@@ -905,8 +905,7 @@ __global__ void __launch_bounds__(kThreads) k_source_gram(const T* const* __rest
     const int sp = s | 1;
     T* sX = reinterpret_cast<T*>(sh_gram);   // kTile x sp, row k at sX + k * sp
     const int npair = s * (s + 1) / 2;
-    // up to 9 (a, c) pairs per thread: s <= 64
-    constexpr int MAXP = 9;
+    // up to MAXP (a, c) pairs per thread: 9 for s <= 64, 25 for s <= 112 (npair <= MAXP kThreads)
     int pa[MAXP], pc[MAXP];
     int np = 0;
     for (int q = threadIdx.x; q < npair && np < MAXP; q += kThreads) {
@@ -1054,8 +1053,14 @@ void launch_source_gram(const T* const* X, const int* sv, int ntasks, int s_max,
     dim3 grid(g.nchunks, ntasks);
     // the sample tile: kTile rows of stride s_max | 1
     const size_t sm = sizeof(T) * (size_t)(s_max | 1) * kTile;
-    if (sm > 32 * 1024) smem_optin(k_source_gram<T>, sm);
-    k_source_gram<T><<<grid, kThreads, sm, st>>>(X, sv, n, g.rows, g.nchunks, pstride, partial);
+    static_assert(64 * 65 / 2 <= 9 * kThreads && 112 * 113 / 2 <= 25 * kThreads, "Gram pairs per thread");
+    if (s_max <= 64) {
+        if (sm > 32 * 1024) smem_optin(k_source_gram<T, 9>, sm);
+        k_source_gram<T, 9><<<grid, kThreads, sm, st>>>(X, sv, n, g.rows, g.nchunks, pstride, partial);
+    } else {
+        if (sm > 32 * 1024) smem_optin(k_source_gram<T, 25>, sm);
+        k_source_gram<T, 25><<<grid, kThreads, sm, st>>>(X, sv, n, g.rows, g.nchunks, pstride, partial);
+    }
 }
 
 #define PEXP_KRY_INST(T)                                                                                           \

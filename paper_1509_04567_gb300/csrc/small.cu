@@ -247,7 +247,10 @@ __device__ void cta_expm(double* A, int N, double* E, double* w) {
 // =====================================================================================
 // Source compression: Jacobi eigen-decomposition of the Gram matrix (Sec. 2.1)
 // =====================================================================================
-__global__ void __launch_bounds__(64) k_source_eig(WinLayout L, double* __restrict__ wd, int* __restrict__ wi,
+constexpr int kEigThreads = 64;
+constexpr int kEigRows = (PEXP_MAX_SAMPLES + kEigThreads - 1) / kEigThreads;   // rows per thread
+
+__global__ void __launch_bounds__(kEigThreads) k_source_eig(WinLayout L, double* __restrict__ wd, int* __restrict__ wi,
                                                    const int* __restrict__ wins, double thr, int max_rank,
                                                    const double* __restrict__ dots, const double* __restrict__ nrm2,
                                                    Parts gp) {
@@ -306,22 +309,32 @@ __global__ void __launch_bounds__(64) k_source_eig(WinLayout L, double* __restri
                 __syncthreads();
                 const double c = rot[0], sn = rot[1], t = rot[2];
                 if (sn != 0.0) {
-                    const int k = threadIdx.x;
-                    double akp = 0, akq = 0, zkp = 0, zkq = 0;
-                    if (k < s) {
-                        akp = A[k + p * s]; akq = A[k + q * s];
-                        zkp = Z[k + p * s]; zkq = Z[k + q * s];
+                    // rows k = threadIdx.x + kEigThreads u: all reads before the barrier, all writes after
+                    double akp[kEigRows], akq[kEigRows], zkp[kEigRows], zkq[kEigRows];
+#pragma unroll
+                    for (int u = 0; u < kEigRows; ++u) {
+                        const int k = threadIdx.x + kEigThreads * u;
+                        akp[u] = akq[u] = zkp[u] = zkq[u] = 0.0;
+                        if (k < s) {
+                            akp[u] = A[k + p * s]; akq[u] = A[k + q * s];
+                            zkp[u] = Z[k + p * s]; zkq[u] = Z[k + q * s];
+                        }
                     }
                     __syncthreads();
-                    if (k < s) {
-                        if (k != p && k != q) {
-                            const double np = c * akp - sn * akq, nq = sn * akp + c * akq;
-                            A[k + p * s] = np; A[p + k * s] = np;
-                            A[k + q * s] = nq; A[q + k * s] = nq;
+#pragma unroll
+                    for (int u = 0; u < kEigRows; ++u) {
+                        const int k = threadIdx.x + kEigThreads * u;
+                        if (k < s) {
+                            if (k != p && k != q) {
+                                const double np = c * akp[u] - sn * akq[u], nq = sn * akp[u] + c * akq[u];
+                                A[k + p * s] = np; A[p + k * s] = np;
+                                A[k + q * s] = nq; A[q + k * s] = nq;
+                            }
+                            Z[k + p * s] = c * zkp[u] - sn * zkq[u];
+                            Z[k + q * s] = sn * zkp[u] + c * zkq[u];
                         }
-                        Z[k + p * s] = c * zkp - sn * zkq;
-                        Z[k + q * s] = sn * zkp + c * zkq;
                     }
+                    const int k = threadIdx.x;
                     if (k == 0) {
                         const double apq = A[p + q * s];
                         A[p + p * s] -= t * apq;
@@ -381,7 +394,7 @@ void launch_source_eig(const WinLayout& L, double* wd, int* wi, const int* wins,
     if (nw <= 0) return;
     size_t sm = (size_t)2 * L.s_max * L.s_max * sizeof(double);
     if (sm > 32 * 1024) smem_optin(k_source_eig, sm);
-    k_source_eig<<<nw, 64, sm, s>>>(L, wd, wi, wins, thr, max_rank, dots, nrm2, gp);
+    k_source_eig<<<nw, kEigThreads, sm, s>>>(L, wd, wi, wins, thr, max_rank, dots, nrm2, gp);
 }
 
 // =====================================================================================
