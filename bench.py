@@ -231,8 +231,8 @@ def burgers_leg(ctx, dev, n: int = 65536, precisions=(1, 0)) -> dict:
 def batched_leg(ctx, dev, count: int = 512) -> dict:
     """The batched workload: `count` independent advection-diffusion problems of uneven size
     (n log-uniform in [4096, 262144], nu, a, 16-mode u0, P in {4..64}, n_out = 16 P + 1),
-    mixed precision at tol 1e-7 with the largest step budget (64), through pexp_solve_batched;
-    one untimed and one timed call."""
+    mixed precision at tol 1e-6 (the metric's accuracy) with the largest step budget (64), through
+    pexp_solve_batched; one untimed and one timed call."""
     import numpy as np
     import torch
     from paper_1509_04567_gb300 import workloads as wl
@@ -249,7 +249,7 @@ def batched_leg(ctx, dev, count: int = 512) -> dict:
         t = torch.arange(nt, dtype=torch.float64, device=dev) / (nt - 1)
         G = (d["gam"] * torch.cos(2 * np.pi * t)[:, None] * torch.sin(4 * np.pi * x)[None, :]).float().contiguous()
         Y = torch.empty((nt, n), dtype=torch.float32, device=dev)
-        opts = wl.default_opts(T=1.0, P=P, n_out=nt, tol=1e-7, svd_tol=1e-10, max_rank=8, precision=1, restart_len=64)
+        opts = wl.default_opts(T=1.0, P=P, n_out=nt, tol=1e-6, svd_tol=1e-10, max_rank=8, precision=1, restart_len=64)
         items.append((wl.make_op(n, d["nu"], d["a"]), opts, u0, G, Y))
         npts += n
     ctx.solve_batched(items, check=False)
@@ -265,7 +265,8 @@ def batched_leg(ctx, dev, count: int = 512) -> dict:
     del items
     torch.cuda.empty_cache()
     return {"workload": f"batched_{count}_adv_diff_1d_n4096_262144", "instances": count, "points_total": npts,
-            "precision": "mixed", "s_per_batch": s, "solves_per_s": count / s, "not_ok": bad, "not_converged": nc,
+            "precision": "mixed", "tol": 1e-6, "step_budget": 64, "s_per_batch": s, "solves_per_s": count / s,
+            "not_ok": bad, "not_converged": nc,
             "entry": "pexp_solve_batched"}
 
 
