@@ -119,6 +119,10 @@ typedef struct {
 
 #define PEXP_DIAG_ORTH  1   /* measure the orthogonality of every Krylov basis */
 #define PEXP_DIAG_KTIME 2   /* time kernel classes with CUDA events (report.k_*) */
+#define PEXP_DIAG_NOCOOP 4  /* launch every Krylov pass on its own: no cooperative launches (a
+                               single-column periodic window of up to 2^18 points otherwise runs
+                               its shift-and-invert passes, and its Gram-Schmidt passes, as one
+                               grid-synchronised launch each); the results are the same bit for bit */
 /* With PEXP_DIAG_KTIME, bits 8..15 of `diagnostics` choose the classes that are timed:
  * bit 8 + PEXP_KC_x times class x; no bit set times every class.  Each timed launch
  * costs two event records on the host, so timing one class perturbs a solve least. */

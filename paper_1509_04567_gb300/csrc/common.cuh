@@ -86,6 +86,13 @@ struct ReconTask {
     int64_t i0;
 };
 
+// Grid barrier words of cooperative launches (grid_bar below).
+struct GridBar {
+    unsigned* count;
+    unsigned* gen;
+    int* err;
+};
+
 struct SaiCoef {
     double alpha, beta, inv_c;   // (I - gamma A) = c (I - alpha S^{-1})(I - beta S)
     double alpha_n, beta_n;      // alpha^n, beta^n (circular closure)
@@ -173,6 +180,14 @@ void launch_sai_solve(const OpDesc& op, const SaiCoef& cf, const T* const* X, T*
 template <typename T>
 void launch_sai_solve_lo(const OpDesc& op, const SaiCoef& cf, const T* const* X, const T* const* Xlo, T* const* Y,
                          T* const* Ylo, int nvec, double* scratch, cudaStream_t s, const int* const* skip = nullptr);
+// The three passes of the solve of one vector (x: no low part) in one cooperative launch
+// with grid barriers between them; the same arithmetic as launch_sai_solve_lo, so the same
+// result.  Returns false (nothing launched) where a cooperative launch is not possible.
+template <typename T>
+bool launch_sai_coop(const OpDesc& op, const SaiCoef& cf, const T* x, T* y, T* ylo, double* scratch, const int* skip,
+                     GridBar bar, cudaStream_t s);
+// Largest grid (at most `want`) whose CTAs are all resident at once, 0 without cooperative launch.
+int coop_grid(const void* kernel, int threads, size_t smem, int want);
 template <typename T>
 void launch_ts_tn(const TsTask<T>* tasks_dev, int ntasks, int max_pq, int max_q, int64_t n, double* partial,
                   cudaStream_t s, int exact = 0);
@@ -217,6 +232,51 @@ inline void smem_optin(K* kernel, size_t bytes) {
 __device__ __forceinline__ void pdl_entry() {
     asm volatile("griddepcontrol.wait;" ::: "memory");
     asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+}
+
+// Grid-wide barrier for kernels launched cooperatively (every CTA resident at once):
+// an arrival counter and a generation word in global memory, shared by the launches of one
+// stream.  The wait is bounded: a CTA that sees no progress for 1 s sets *err and stops
+// waiting, and once *err is set every CTA skips the remaining barriers (and its callers the
+// remaining work), so a launch always ends.  The host resets the three words after an error.
+__device__ __forceinline__ unsigned long long global_ns() {
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+// Returns false (in every thread of the CTA) once the barrier has failed.
+__device__ __forceinline__ bool grid_bar(const GridBar& g) {
+    __shared__ int s_ok;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        volatile unsigned* vgen = g.gen;
+        volatile int* verr = g.err;
+        int ok = *verr == 0;
+        if (ok) {
+            const unsigned my = *vgen;
+            __threadfence();
+            const unsigned nb = gridDim.x * gridDim.y * gridDim.z;
+            if (atomicAdd(g.count, 1u) == nb - 1) {
+                atomicExch(g.count, 0u);
+                __threadfence();
+                atomicAdd(g.gen, 1u);
+            } else {
+                const unsigned long long t0 = global_ns();
+                while (*vgen == my && *verr == 0) {
+                    if (global_ns() - t0 > 1000000000ull) {
+                        atomicExch(g.err, 1);
+                        break;
+                    }
+                    __nanosleep(64);
+                }
+            }
+            __threadfence();
+            ok = *verr == 0;
+        }
+        s_ok = ok;
+    }
+    __syncthreads();
+    return s_ok != 0;
 }
 
 template <typename... KArgs, typename... Args>

@@ -396,21 +396,18 @@ template <int B>
 constexpr int kUpdCtas = B <= 2 ? 3 : 2;   // resident CTAs per SM the update kernels are built for
 
 template <typename T, int B>
-__global__ void __launch_bounds__(kThreads, kUpdCtas<B>) k_update0(const UpdTask<T>* __restrict__ tasks, int64_t n, int64_t rows,
-                                                         int nchunks, int pstride, double* __restrict__ partial) {
-    pdl_entry();
+__device__ __forceinline__ void k_update0_body(const UpdTask<T>& tk, int64_t n, int64_t rows, int nchunks, int pstride, double* __restrict__ partial, int bx, int by) {
+
     using CT = typename Coef<T>::type;
     constexpr int Q = kUpdQ, R = kUpdR;
     constexpr int NE = B * B;
     extern __shared__ double sh_dyn[];
     CT* sh = reinterpret_cast<CT*>(sh_dyn);
     __shared__ double sred[kWarps * NE];
-    const UpdTask<T> tk = tasks[blockIdx.y];
-    if (tk.conv && *tk.conv) return;
     const int p = tk.p;
     stage_coeffs<T>(tk, p, B, sh);
     const int64_t ld = tk.ld;
-    const int64_t r0 = (int64_t)blockIdx.x * rows;
+    const int64_t r0 = (int64_t)bx * rows;
     const int64_t r1 = (r0 + rows < n) ? r0 + rows : n;
     T g[B][B];
 #pragma unroll
@@ -471,8 +468,16 @@ __global__ void __launch_bounds__(kThreads, kUpdCtas<B>) k_update0(const UpdTask
 #pragma unroll
         for (int j = 0; j < B; ++j) warp_to_smem(g[i][j], sred, NE, i + j * B);
     __syncthreads();
-    double* pout = partial + ((size_t)blockIdx.y * nchunks + blockIdx.x) * pstride;
+    double* pout = partial + ((size_t)by * nchunks + bx) * pstride;
     for (int e = threadIdx.x; e < NE; e += kThreads) pout[e] = cta_entry(sred, NE, e);
+}
+
+template <typename T, int B>
+__global__ void __launch_bounds__(kThreads, kUpdCtas<B>) k_update0(const UpdTask<T>* __restrict__ tasks, int64_t n, int64_t rows,
+                                                         int nchunks, int pstride, double* __restrict__ partial) {    pdl_entry();
+    const UpdTask<T> tk = tasks[blockIdx.y];
+    if (tk.conv && *tk.conv) return;
+    k_update0_body<T, B>(tk, n, rows, nchunks, pstride, partial, blockIdx.x, blockIdx.y);
 }
 
 // W <- W T for one row (T: B x B FP64 in shared memory); FP32 data in double-float.
@@ -515,22 +520,18 @@ __device__ __forceinline__ void scale_row(double (&xh)[B], double (&)[B], const 
 // magnified by the block's conditioning.
 // =====================================================================================
 template <typename T, int B>
-__global__ void __launch_bounds__(kThreads, 2) k_scale_proj(const UpdTask<T>* __restrict__ tasks, int64_t n,
-                                                            int64_t rows, int nchunks, int pstride,
-                                                            double* __restrict__ partial) {
-    pdl_entry();
+__device__ __forceinline__ void k_scale_proj_body(const UpdTask<T>& tk, int64_t n, int64_t rows, int nchunks, int pstride, double* __restrict__ partial, int bx, int by) {
+
     constexpr int Q = kFuseP;
     constexpr int NE = Q * B;
     using CT = typename Coef<T>::type;
     __shared__ CT sT[B * B];
     __shared__ double sred[kWarps * NE];
-    const UpdTask<T> tk = tasks[blockIdx.y];
-    if (tk.conv && *tk.conv) return;
     const int p = tk.p;
     for (int e = threadIdx.x; e < B * B; e += kThreads) sT[e] = Coef<T>::make(tk.hm[(e % B) + (int64_t)(e / B) * tk.ldh]);
     __syncthreads();
     const int64_t ld = tk.ld;
-    const int64_t r0 = (int64_t)blockIdx.x * rows;
+    const int64_t r0 = (int64_t)bx * rows;
     const int64_t r1 = (r0 + rows < n) ? r0 + rows : n;
     T acc[Q][B];
 #pragma unroll
@@ -568,11 +569,20 @@ __global__ void __launch_bounds__(kThreads, 2) k_scale_proj(const UpdTask<T>* __
             for (int c = 0; c < B; ++c) warp_to_smem(acc[q][c], sred, NE, q + c * Q);
         }
     __syncthreads();
-    double* pout = partial + ((size_t)blockIdx.y * nchunks + blockIdx.x) * pstride;
+    double* pout = partial + ((size_t)by * nchunks + bx) * pstride;
     for (int e = threadIdx.x; e < NE; e += kThreads) {
         const int q = e % Q, c = e / Q;
         if (q < p) pout[q + c * p] = cta_entry(sred, NE, e);
     }
+}
+
+template <typename T, int B>
+__global__ void __launch_bounds__(kThreads, 2) k_scale_proj(const UpdTask<T>* __restrict__ tasks, int64_t n,
+                                                            int64_t rows, int nchunks, int pstride,
+                                                            double* __restrict__ partial) {    pdl_entry();
+    const UpdTask<T> tk = tasks[blockIdx.y];
+    if (tk.conv && *tk.conv) return;
+    k_scale_proj_body<T, B>(tk, n, rows, nchunks, pstride, partial, blockIdx.x, blockIdx.y);
 }
 
 // =====================================================================================
@@ -635,17 +645,13 @@ __global__ void __launch_bounds__(kThreads, 2) k_vtw(const UpdTask<T>* __restric
 // Loads as in k_update0: R rows per thread, W first, V in groups of Q columns.
 // =====================================================================================
 template <typename T, int B>
-__global__ void __launch_bounds__(kThreads, kUpdCtas<B>) k_update1(const UpdTask<T>* __restrict__ tasks, int64_t n, int64_t rows,
-                                                      int nchunks, int pstride, double* __restrict__ partial,
-                                                      const double* __restrict__ hpart, int hstride) {
-    pdl_entry();
+__device__ __forceinline__ void k_update1_body(const UpdTask<T>& tk, int64_t n, int64_t rows, int nchunks, int pstride, double* __restrict__ partial, const double* __restrict__ hpart, int hstride, int bx, int by) {
+
     constexpr int Q = kUpdQ, R = kUpdR;
     constexpr int NE = B * B;
     extern __shared__ double sh_dyn[];
     T* sh = reinterpret_cast<T*>(sh_dyn);
     __shared__ double sred[kWarps * NE];
-    const UpdTask<T> tk = tasks[blockIdx.y];
-    if (tk.conv && *tk.conv) return;
     const int p = tk.p;
     if (hpart) {
         // h2 straight from the chunk partials of k_scale_proj (p x B, column-major), summed
@@ -653,7 +659,7 @@ __global__ void __launch_bounds__(kThreads, kUpdCtas<B>) k_update1(const UpdTask
         // the same ones that a separate summing kernel would have stored
         const Parts hp{hpart, nchunks, hstride};
         for (int e = threadIdx.x >> 5; e < p * B; e += kWarps) {
-            const double v = parts_sum_warp(hp, blockIdx.y, e);
+            const double v = parts_sum_warp(hp, by, e);
             if ((threadIdx.x & 31) == 0) sh[e] = (T)v;
         }
     } else {
@@ -661,7 +667,7 @@ __global__ void __launch_bounds__(kThreads, kUpdCtas<B>) k_update1(const UpdTask
     }
     __syncthreads();
     const int64_t ld = tk.ld;
-    const int64_t r0 = (int64_t)blockIdx.x * rows;
+    const int64_t r0 = (int64_t)bx * rows;
     const int64_t r1 = (r0 + rows < n) ? r0 + rows : n;
     T g[B][B];
 #pragma unroll
@@ -727,8 +733,17 @@ __global__ void __launch_bounds__(kThreads, kUpdCtas<B>) k_update1(const UpdTask
 #pragma unroll
         for (int j = 0; j < B; ++j) warp_to_smem(g[i][j], sred, NE, i + j * B);
     __syncthreads();
-    double* pout = partial + ((size_t)blockIdx.y * nchunks + blockIdx.x) * pstride;
+    double* pout = partial + ((size_t)by * nchunks + bx) * pstride;
     for (int e = threadIdx.x; e < NE; e += kThreads) pout[e] = cta_entry(sred, NE, e);
+}
+
+template <typename T, int B>
+__global__ void __launch_bounds__(kThreads, kUpdCtas<B>) k_update1(const UpdTask<T>* __restrict__ tasks, int64_t n, int64_t rows,
+                                                      int nchunks, int pstride, double* __restrict__ partial,
+                                                      const double* __restrict__ hpart, int hstride) {    pdl_entry();
+    const UpdTask<T> tk = tasks[blockIdx.y];
+    if (tk.conv && *tk.conv) return;
+    k_update1_body<T, B>(tk, n, rows, nchunks, pstride, partial, hpart, hstride, blockIdx.x, blockIdx.y);
 }
 
 // =====================================================================================
@@ -737,21 +752,17 @@ __global__ void __launch_bounds__(kThreads, kUpdCtas<B>) k_update1(const UpdTask
 // Four rows per thread per iteration, loads first.
 // =====================================================================================
 template <typename T, int B>
-__global__ void __launch_bounds__(kThreads, 2) k_scale(const UpdTask<T>* __restrict__ tasks, int64_t n, int64_t rows,
-                                                       int nchunks, int gramflag, int pstride,
-                                                       double* __restrict__ partial) {
-    pdl_entry();
+__device__ __forceinline__ void k_scale_body(const UpdTask<T>& tk, int64_t n, int64_t rows, int nchunks, int gramflag, int pstride, double* __restrict__ partial, int bx, int by) {
+
     constexpr int U = 4;
     constexpr int NE = B * B;
     using CT = typename Coef<T>::type;
     __shared__ CT sT[B * B];
     __shared__ double sred[kWarps * NE];
-    const UpdTask<T> tk = tasks[blockIdx.y];
-    if (tk.conv && *tk.conv) return;
     for (int e = threadIdx.x; e < B * B; e += kThreads) sT[e] = Coef<T>::make(tk.hm[(e % B) + (int64_t)(e / B) * tk.ldh]);
     __syncthreads();
     const int64_t ld = tk.ld;
-    const int64_t r0 = (int64_t)blockIdx.x * rows;
+    const int64_t r0 = (int64_t)bx * rows;
     const int64_t r1 = (r0 + rows < n) ? r0 + rows : n;
     T g[B][B];
 #pragma unroll
@@ -801,9 +812,18 @@ __global__ void __launch_bounds__(kThreads, 2) k_scale(const UpdTask<T>* __restr
 #pragma unroll
             for (int j = 0; j < B; ++j) warp_to_smem(g[i][j], sred, NE, i + j * B);
         __syncthreads();
-        double* pout = partial + ((size_t)blockIdx.y * nchunks + blockIdx.x) * pstride;
+        double* pout = partial + ((size_t)by * nchunks + bx) * pstride;
         for (int e = threadIdx.x; e < NE; e += kThreads) pout[e] = cta_entry(sred, NE, e);
     }
+}
+
+template <typename T, int B>
+__global__ void __launch_bounds__(kThreads, 2) k_scale(const UpdTask<T>* __restrict__ tasks, int64_t n, int64_t rows,
+                                                       int nchunks, int gramflag, int pstride,
+                                                       double* __restrict__ partial) {    pdl_entry();
+    const UpdTask<T> tk = tasks[blockIdx.y];
+    if (tk.conv && *tk.conv) return;
+    k_scale_body<T, B>(tk, n, rows, nchunks, gramflag, pstride, partial, blockIdx.x, blockIdx.y);
 }
 
 // =====================================================================================
@@ -945,6 +965,73 @@ __global__ void __launch_bounds__(kThreads) k_source_gram(const T* const* __rest
 }
 
 // =====================================================================================
+// k_gs_coop: part B of a fused Krylov step (the four passes above and the two Cholesky QRs
+// between them) for one window in one cooperative launch.  CTAs take chunks blockIdx.x,
+// blockIdx.x + gridDim.x, ... of the same row geometry and meet at grid barriers, so every
+// partial sum, and every result, is the one the separate launches produce.  The Cholesky
+// QRs run in every CTA from the same fixed-order sums (CTA 0 alone writes the window's
+// state).  The partial sums of the three passes go to three separate regions of kp, since a
+// CTA may still be summing one pass's partials while another writes the next pass's.
+// The convergence flag is read once at entry: the projected solve on the other stream may
+// set it while this kernel runs, and every CTA must still reach every barrier.
+// =====================================================================================
+template <typename T, int B>
+__global__ void __launch_bounds__(kThreads, 3) k_gs_coop(UpdTask<T> u1, UpdTask<T> u3, UpdTask<T> u2, UpdTask<T> u4,
+                                                         int64_t n, int64_t rows, int nchunks, double* __restrict__ kp,
+                                                         int ps2, int psg, WinLayout L, double* __restrict__ wd,
+                                                         int* __restrict__ wi, int w, int step, double defl,
+                                                         GridBar bar) {
+    bool active = !(u1.conv && *(volatile const int*)u1.conv);
+    double* D = wd + (int64_t)w * L.stride;
+    int* I = wi + (int64_t)w * L.istride;
+    double* pg1 = kp;
+    double* ph2 = pg1 + (size_t)nchunks * psg;
+    double* pg2 = ph2 + (size_t)nchunks * ps2;
+    __shared__ double sG[B * B], sT1[B * B], sT2[B * B];
+    __shared__ int s_r;
+    // pass 1: W <- W - V h1 (h1 stored by the projection pass), Gram partials
+    if (active)
+        for (int ch = blockIdx.x; ch < nchunks; ch += gridDim.x) k_update0_body<T, B>(u1, n, rows, nchunks, psg, pg1, ch, 0);
+    if (!grid_bar(bar)) return;
+    if (active && threadIdx.x < 32) {
+        const int r = block_orth_body(L, D, I, 0, 1, step, defl, Parts{pg1, nchunks, psg}, -1, sG, sT1, blockIdx.x == 0);
+        if (threadIdx.x == 0) {
+            s_r = r;
+            if (blockIdx.x == 0)
+                for (int e = 0; e < B * B; ++e) D[L.off_T + e] = sT1[e];
+        }
+    }
+    __syncthreads();
+    const int r1 = active ? s_r : 0;
+    if (r1 == 0) active = false;   // no direction kept: CTA 0 marked the window converged
+    // W <- W T1, h2 partials
+    UpdTask<T> t3 = u3;
+    t3.hm = sT1;
+    t3.ldh = B;
+    if (active)
+        for (int ch = blockIdx.x; ch < nchunks; ch += gridDim.x) k_scale_proj_body<T, B>(t3, n, rows, nchunks, ps2, ph2, ch, 0);
+    if (!grid_bar(bar)) return;
+    // pass 2: W <- W - V h2 (h2 summed from the partials by every CTA), Gram partials
+    if (active)
+        for (int ch = blockIdx.x; ch < nchunks; ch += gridDim.x)
+            k_update1_body<T, B>(u2, n, rows, nchunks, psg, pg2, ph2, ps2, ch, 0);
+    if (!grid_bar(bar)) return;
+    if (active && threadIdx.x < 32) {
+        block_orth_body(L, D, I, 0, 2, step, defl, Parts{pg2, nchunks, psg}, r1, sG, sT2, blockIdx.x == 0);
+        if (threadIdx.x == 0 && blockIdx.x == 0)
+            for (int e = 0; e < B * B; ++e) D[L.off_T + e] = sT2[e];
+    }
+    __syncthreads();
+    // W T2 rounded into the basis slot
+    UpdTask<T> t4 = u4;
+    t4.hm = sT2;
+    t4.ldh = B;
+    if (active)
+        for (int ch = blockIdx.x; ch < nchunks; ch += gridDim.x)
+            k_scale_body<T, B>(t4, n, rows, nchunks, 0, psg, nullptr, ch, 0);
+}
+
+// =====================================================================================
 // launchers
 // =====================================================================================
 KGeom krylov_geom(int ntasks, int64_t n) {
@@ -1063,7 +1150,32 @@ void launch_source_gram(const T* const* X, const int* sv, int ntasks, int s_max,
     }
 }
 
+template <typename T>
+bool launch_gs_coop(const UpdTask<T>* u, int b, int p, int64_t n, KGeom g, double* kp, int ps2, int psg,
+                    const WinLayout& L, double* wd, int* wi, int w, int step, double defl, GridBar bar, cudaStream_t s) {
+    if (b != 1 || !proj_fused(p, b, sizeof(T))) return false;
+    constexpr int BB = 1;
+    const size_t sm = (size_t)p * BB * (sizeof(T) == 4 ? sizeof(float2) : sizeof(double)) + 16;
+    const void* fn = reinterpret_cast<const void*>(k_gs_coop<T, BB>);
+    const size_t sm_max = (size_t)kFuseP * BB * (sizeof(T) == 4 ? sizeof(float2) : sizeof(double)) + 16;
+    const int grid = coop_grid(fn, kThreads, sm_max, g.nchunks);
+    if (grid <= 0) return false;
+    UpdTask<T> u1 = u[0], u3 = u[1], u2 = u[2], u4 = u[3];
+    int64_t nn = n, rows = g.rows;
+    int nch = g.nchunks, a2 = ps2, ag = psg, ww = w, st = step;
+    WinLayout LL = L;
+    double dd = defl;
+    void* args[] = {&u1, &u3, &u2, &u4, &nn, &rows, &nch, &kp, &a2, &ag, &LL, &wd, &wi, &ww, &st, &dd, &bar};
+    if (cudaLaunchCooperativeKernel(fn, dim3(grid), dim3(kThreads), args, sm, s) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    return true;
+}
+
 #define PEXP_KRY_INST(T)                                                                                           \
+    template bool launch_gs_coop<T>(const UpdTask<T>*, int, int, int64_t, KGeom, double*, int, int, const WinLayout&, \
+                                    double*, int*, int, int, double, GridBar, cudaStream_t);               \
     template void launch_step_proj<T>(const StepTask<T>*, int, int, int, int64_t, int, KGeom, double*, int, cudaStream_t, bool); \
     template void launch_update<T>(const UpdTask<T>*, int, int, int, int64_t, int, KGeom, double*, int, cudaStream_t, \
                                    const double*, int);                                                             \

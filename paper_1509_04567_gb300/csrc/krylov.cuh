@@ -69,6 +69,15 @@ void launch_block_gram(const UpdTask<T>* tasks, int ntasks, int64_t n, KGeom g, 
 template <typename T>
 void launch_scale(const UpdTask<T>* tasks, int ntasks, int b, int64_t n, int gram, KGeom g, double* partial,
                   int pstride, cudaStream_t s);
+struct WinLayout;
+// Part B of a fused Krylov step (passes u[0..3]: update0, scale_proj, update1, scale, with the
+// two Cholesky QRs between them) for window w, block width b, in one cooperative launch:
+// the same arithmetic and results as the separate launches.  The partial sums take
+// g.nchunks * (2 psg + ps2) doubles of kp.  Returns false (nothing launched) for b != 1,
+// an unfused width p, or where a cooperative launch is not possible.
+template <typename T>
+bool launch_gs_coop(const UpdTask<T>* u, int b, int p, int64_t n, KGeom g, double* kp, int ps2, int psg,
+                    const WinLayout& L, double* wd, int* wi, int w, int step, double defl, GridBar bar, cudaStream_t s);
 constexpr int kKrylovMaxB = 4;   // block widths handled by the fused kernels
 // Sums the per-CTA partials of each task into wd + wins[task] * stride + off (ne entries).
 // Entries [e0, e0 + ne) of each partial go to entries [0, ne) of the output.

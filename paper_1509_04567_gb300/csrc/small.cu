@@ -480,81 +480,8 @@ __global__ void k_block_orth(WinLayout L, double* __restrict__ wd, int* __restri
     double* D = wd + (int64_t)w * L.stride;
     int* I = wi + (int64_t)w * L.istride;
     if (I[WI_CONV]) return;  // converged (at this step's projection, or earlier)
-    const int b = I[WI_B];
     __shared__ double sG[PEXP_MAX_RANK * PEXP_MAX_RANK];
-    if (gp.part) {
-        for (int e = 0; e < b * b; ++e) {
-            const double v = parts_sum_warp(gp, blockIdx.x, e);
-            if (threadIdx.x == 0) sG[e] = v;
-        }
-    }
-    __syncwarp();
-    if (threadIdx.x != 0) return;
-    const double* G0 = D + L.off_gw;
-    double G[PEXP_MAX_RANK * PEXP_MAX_RANK], R[PEXP_MAX_RANK * PEXP_MAX_RANK];
-    int perm[PEXP_MAX_RANK];
-    for (int e = 0; e < b * b; ++e) {
-        G[e] = gp.part ? sG[e] : G0[e];
-        R[e] = 0.0;
-    }
-    for (int k = 0; k < b; ++k) perm[k] = k;
-    double lim2;
-    int ncand = b;
-    if (pass == 1) {
-        // pre-Gram-Schmidt norms: diagonal of W^T W stored in out1 rows [step*b, step*b+b),
-        // in the last column block (fused path: b values after h1 at out1)
-        const int ldo = (step + 1) * b;
-        const double* o1 = D + L.off_out1;
-        const int wc = (L.ycols - 1) * b;
-        double pre = 0.0;
-        for (int c = 0; c < b; ++c)
-            pre = fmax(pre, gp.part ? o1[step * b * b + c] : o1[(step * b + c) + (wc + c) * ldo]);
-        lim2 = defl * defl * pre;
-        D[L.off_scal + WS_PRE] = sqrt(pre);
-    } else {
-        lim2 = 0.25;  // kept columns have unit norm after pass 1, dropped ones are zero
-        ncand = I[WI_KEPT];
-    }
-    int r = 0;
-    for (int k = 0; k < ncand; ++k) {
-        int j = k;
-        if (pass == 1) {
-            for (int l = k + 1; l < b; ++l)
-                if (G[l + l * b] > G[j + j * b]) j = l;
-        }
-        if (!(G[j + j * b] > lim2)) break;
-        if (j != k) {  // symmetric swap of rows/cols k and j, and of the R columns
-            for (int l = 0; l < b; ++l) { double t = G[k + l * b]; G[k + l * b] = G[j + l * b]; G[j + l * b] = t; }
-            for (int l = 0; l < b; ++l) { double t = G[l + k * b]; G[l + k * b] = G[l + j * b]; G[l + j * b] = t; }
-            for (int l = 0; l < k; ++l) { double t = R[l + k * b]; R[l + k * b] = R[l + j * b]; R[l + j * b] = t; }
-            int t = perm[k]; perm[k] = perm[j]; perm[j] = t;
-        }
-        const double rkk = sqrt(G[k + k * b]);
-        R[k + k * b] = rkk;
-        for (int l = k + 1; l < b; ++l) R[k + l * b] = G[k + l * b] / rkk;
-        for (int l = k + 1; l < b; ++l)
-            for (int l2 = k + 1; l2 < b; ++l2) G[l + l2 * b] -= R[k + l * b] * R[k + l2 * b];
-        ++r;
-    }
-    // T = P[:, 0:r] R[0:r, 0:r]^{-1}
-    double Ri[PEXP_MAX_RANK * PEXP_MAX_RANK];
-    for (int e = 0; e < b * b; ++e) Ri[e] = 0.0;
-    for (int j = 0; j < r; ++j) {
-        Ri[j + j * b] = 1.0 / R[j + j * b];
-        for (int i = j - 1; i >= 0; --i) {
-            double v = 0.0;
-            for (int k = i + 1; k <= j; ++k) v += R[i + k * b] * Ri[k + j * b];
-            Ri[i + j * b] = -v / R[i + i * b];
-        }
-    }
-    double* T = D + L.off_T;
-    for (int e = 0; e < b * b; ++e) T[e] = 0.0;
-    for (int k = 0; k < r; ++k)
-        for (int j = 0; j <= k; ++j) T[perm[j] + k * b] = Ri[j + k * b];
-    if (pass == 1) {
-        I[WI_KEPT] = r;
-        if (r == 0) I[WI_CONV] = 1;  // invariant subspace reached: the projection is exact
-    }
+    block_orth_body(L, D, I, blockIdx.x, pass, step, defl, gp, -1, sG, D + L.off_T, true);
 }
 
 void launch_block_orth(const WinLayout& L, double* wd, int* wi, const int* wins, int nw, int pass, int step,

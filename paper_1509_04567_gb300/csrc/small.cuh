@@ -59,6 +59,95 @@ __device__ __forceinline__ double parts_sum_warp(const Parts& p, int task, int e
     return s;
 }
 
+// Cholesky QR with diagonal pivoting and deflation of one new Krylov block (k_block_orth):
+//   pass 1: Gram G of W after Gram-Schmidt; columns whose remaining norm is below
+//           defl * (largest column norm of W before Gram-Schmidt) are dropped;
+//           T maps W to the kept orthonormal directions (columns 0..r-1), the rest 0.
+//   pass 2: re-orthonormalise the kept columns (Cholesky of their Gram).
+// Entered by warp 0 of the calling CTA (all lanes: the Gram may be summed from the chunk
+// partials gp of launch-list entry `task`); thread 0 factors, writes T (b x b, column-major)
+// to Tout and returns the kept count r (other threads return 0).  `kept`: pass 2's
+// candidate count (< 0: the window's WI_KEPT).  `owner`: also write the window's state (the
+// pre-Gram-Schmidt norm, WI_KEPT, and WI_CONV when the block is empty).  sG: b*b shared doubles.
+__device__ __forceinline__ int block_orth_body(const WinLayout& L, double* D, int* I, int task, int pass, int step,
+                                               double defl, Parts gp, int kept, double* sG, double* Tout, bool owner) {
+    const int b = I[WI_B];
+    if (gp.part) {
+        for (int e = 0; e < b * b; ++e) {
+            const double v = parts_sum_warp(gp, task, e);
+            if (threadIdx.x == 0) sG[e] = v;
+        }
+    }
+    __syncwarp();
+    if (threadIdx.x != 0) return 0;
+    const double* G0 = D + L.off_gw;
+    double G[PEXP_MAX_RANK * PEXP_MAX_RANK], R[PEXP_MAX_RANK * PEXP_MAX_RANK];
+    int perm[PEXP_MAX_RANK];
+    for (int e = 0; e < b * b; ++e) {
+        G[e] = gp.part ? sG[e] : G0[e];
+        R[e] = 0.0;
+    }
+    for (int k = 0; k < b; ++k) perm[k] = k;
+    double lim2;
+    int ncand = b;
+    if (pass == 1) {
+        // pre-Gram-Schmidt norms: diagonal of W^T W stored in out1 rows [step*b, step*b+b),
+        // in the last column block (fused path: b values after h1 at out1)
+        const int ldo = (step + 1) * b;
+        const double* o1 = D + L.off_out1;
+        const int wc = (L.ycols - 1) * b;
+        double pre = 0.0;
+        for (int c = 0; c < b; ++c)
+            pre = fmax(pre, gp.part ? o1[step * b * b + c] : o1[(step * b + c) + (wc + c) * ldo]);
+        lim2 = defl * defl * pre;
+        if (owner) D[L.off_scal + WS_PRE] = sqrt(pre);
+    } else {
+        lim2 = 0.25;  // kept columns have unit norm after pass 1, dropped ones are zero
+        ncand = kept >= 0 ? kept : I[WI_KEPT];
+    }
+    int r = 0;
+    for (int k = 0; k < ncand; ++k) {
+        int j = k;
+        if (pass == 1) {
+            for (int l = k + 1; l < b; ++l)
+                if (G[l + l * b] > G[j + j * b]) j = l;
+        }
+        if (!(G[j + j * b] > lim2)) break;
+        if (j != k) {  // symmetric swap of rows/cols k and j, and of the R columns
+            for (int l = 0; l < b; ++l) { double t = G[k + l * b]; G[k + l * b] = G[j + l * b]; G[j + l * b] = t; }
+            for (int l = 0; l < b; ++l) { double t = G[l + k * b]; G[l + k * b] = G[l + j * b]; G[l + j * b] = t; }
+            for (int l = 0; l < k; ++l) { double t = R[l + k * b]; R[l + k * b] = R[l + j * b]; R[l + j * b] = t; }
+            int t = perm[k]; perm[k] = perm[j]; perm[j] = t;
+        }
+        const double rkk = sqrt(G[k + k * b]);
+        R[k + k * b] = rkk;
+        for (int l = k + 1; l < b; ++l) R[k + l * b] = G[k + l * b] / rkk;
+        for (int l = k + 1; l < b; ++l)
+            for (int l2 = k + 1; l2 < b; ++l2) G[l + l2 * b] -= R[k + l * b] * R[k + l2 * b];
+        ++r;
+    }
+    // T = P[:, 0:r] R[0:r, 0:r]^{-1}
+    double Ri[PEXP_MAX_RANK * PEXP_MAX_RANK];
+    for (int e = 0; e < b * b; ++e) Ri[e] = 0.0;
+    for (int j = 0; j < r; ++j) {
+        Ri[j + j * b] = 1.0 / R[j + j * b];
+        for (int i = j - 1; i >= 0; --i) {
+            double v = 0.0;
+            for (int k = i + 1; k <= j; ++k) v += R[i + k * b] * Ri[k + j * b];
+            Ri[i + j * b] = -v / R[i + i * b];
+        }
+    }
+    double* T = Tout;
+    for (int e = 0; e < b * b; ++e) T[e] = 0.0;
+    for (int k = 0; k < r; ++k)
+        for (int j = 0; j <= k; ++j) T[perm[j] + k * b] = Ri[j + k * b];
+    if (pass == 1 && owner) {
+        I[WI_KEPT] = r;
+        if (r == 0) I[WI_CONV] = 1;  // invariant subspace reached: the projection is exact
+    }
+    return r;
+}
+
 // Launchers.  `wins` is a device array of window indices (nw entries).
 // The Gram matrix of the shifted samples G_hat = A u0 1^T + G is assembled from its
 // parts: off_gram holds G^T G, dots[i] = (A u0) . g(t_i) (NULL: no source),

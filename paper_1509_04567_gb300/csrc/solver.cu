@@ -112,6 +112,11 @@ struct pexp_ctx {
     size_t io_cap = 0;
     cudaStream_t cs = nullptr;
     cudaEvent_t ev_out = nullptr;
+    // grid-barrier words (count, generation, error) of the cooperative launches on `stream`
+    unsigned* bar = nullptr;
+    // cooperative launches allowed: not for the workers of a batched solve, whose solves run
+    // side by side (two grids that each fill the GPU must not wait on each other)
+    bool coop = true;
     // batched solves: worker contexts, each on a stream of its own
     std::vector<pexp_ctx*> workers;
     int batch_workers = 0;    // tuned count (0: default)
@@ -393,6 +398,31 @@ struct Solver {
     bool jac = false;                          // per-window Jacobian terms in the operator
     double inv2dx = 0.0;
     std::vector<int> wi_host;
+    bool coop_used = false;                    // a cooperative launch ran (check_coop reads its error word)
+
+    GridBar gbar() const { return GridBar{c->bar, c->bar + 1, reinterpret_cast<int*>(c->bar + 2)}; }
+    // A single window of one column (a link of the homogeneous chain) on a periodic constant-
+    // coefficient operator: the shift-and-invert passes and part B of each step run as one
+    // cooperative launch each (the same arithmetic, 2 launches instead of 9).  Only while the
+    // step's grids are under one wave (n <= 2^18): a grid barrier costs ~3.5 us, more than the
+    // launch gap that programmatic dependent launch leaves between full-size kernels (measured
+    // at 2^20 points: 164 ms per solve cooperative, 152 ms separate; 2^15: 24.5 vs 27.5 ms).
+    bool coop_ok(const std::vector<Win<T>>& act) const {
+        return c->coop && act.size() == 1 && act[0].b == 1 && !var && !jac && od.dim == 1 && od.x.periodic &&
+               o->krylov == PEXP_KRYLOV_SAI && !(o->diagnostics & PEXP_DIAG_NOCOOP) &&
+               krylov_geom(1, n).nchunks < 3 * kNumSM;
+    }
+    // after the cooperative launches: a bounded grid barrier that gave up ends the solve
+    void check_coop() {
+        if (!coop_used) return;
+        int err = 0;
+        d2h(c, &err, c->bar + 2, sizeof(int));
+        if (err) {
+            cudaMemsetAsync(c->bar, 0, 3 * sizeof(unsigned), st);
+            sync(c);
+            throw StatusError{PEXP_ERR_TIMEOUT};
+        }
+    }
 
     T* slot(const Win<T>& W, int blk) const { return W.V + (int64_t)blk * W.b * n; }
     double* D(int w) const { return wd + (int64_t)w * L.stride; }
@@ -452,6 +482,10 @@ struct Solver {
         for (int k = 0; k < kFlagBufs; ++k)
             if (!c->flag_ev[k]) cudaEventCreateWithFlags(&c->flag_ev[k], cudaEventDisableTiming);
         auto conv_of = [&](const Win<T>& W) { return wi + (size_t)W.w * L.istride + WI_CONV; };
+        // a cooperative step leaves its projected solve running on the second stream into the
+        // next step's shift-and-invert launch (which needs neither its result nor its buffers);
+        // the next projection pass, which reuses the partial sums it reads, waits for it
+        bool pj_pending = false;
         for (int step = 1; step <= kmax && !act.empty(); ++step) {
             const int na = (int)act.size();
             int bmax = 0;
@@ -495,11 +529,15 @@ struct Solver {
             const double w = sizeof(T);
             const double wout = std::is_same<T, float>::value ? 8.0 : w;
             if (o->krylov == PEXP_KRYLOV_SAI) {
+                bool one = false;
                 timed(c, PEXP_KC_SAI, (double)nv * n * (w + wout), [&] {
-                    if (var) launch_vsai_solve<T>(n, d_vcs, d_xin, nullptr, d_yout, d_ylo, nv, sai_scr, st, d_skip);
+                    if (coop_ok(act))
+                        one = launch_sai_coop<T>(od, sai, xin[0], yout[0], ylo[0], sai_scr, conv_of(act[0]), gbar(), st);
+                    if (one) coop_used = true;
+                    else if (var) launch_vsai_solve<T>(n, d_vcs, d_xin, nullptr, d_yout, d_ylo, nv, sai_scr, st, d_skip);
                     else launch_sai_solve_lo<T>(od, sai, d_xin, nullptr, d_yout, d_ylo, nv, sai_scr, st, d_skip);
                 }, nullptr, false, 2.0 * nv * n * w);
-                c->launches += 2;   // the solve is three kernels; check_launch below counts one
+                if (!one) c->launches += 2;   // the solve is three kernels; check_launch below counts one
             } else {
                 timed(c, PEXP_KC_STENCIL, (double)nv * n * (w + w), [&] { launch_stencil_ptrs<T>(od, d_xin, d_yout, nv, 0, st); });
                 for (const auto& W : act)
@@ -508,6 +546,10 @@ struct Solver {
             check_launch(c);
             double by1 = 0;
             for (auto& W : act) by1 += (double)n * (step + 1) * W.b * w;
+            if (pj_pending) {
+                cudaStreamWaitEvent(st, c->ev_pj, 0);
+                pj_pending = false;
+            }
             timed(c, PEXP_KC_PROJ, by1, [&] {
                 for (int a0 = 0; a0 < na;) {
                     int a1 = a0;
@@ -533,6 +575,10 @@ struct Solver {
                     a0 = a1;
                 }
             });
+            // a cooperative part B fills the GPU: queue it first, so that the projected solve
+            // starts beside the next step's shift-and-invert launch instead of holding back its grid
+            const bool coop_step = coop_ok(act);
+            if (coop_step && step < kmax) part_b(act, step);
             cudaStreamWaitEvent(c->s2, c->ev_sp, 0);
             timed(c, PEXP_KC_SMALL, 0.0, [&] {
                 launch_project(L, wd, wi, d_wl, na, step, h, o->tol, scale_ref, c->s2, Parts{kpart[0], g.nchunks, ps1},
@@ -540,15 +586,22 @@ struct Solver {
             }, c->s2, true);
             check_launch(c);
             cudaEventRecord(c->ev_pj, c->s2);
-            if (step < kmax) part_b(act, step);
-            // the step's projected solve must be done before its flags are read and before the
-            // next step's projections overwrite the partial sums it reads
-            cudaStreamWaitEvent(st, c->ev_pj, 0);
-            // flags of this step, read back without waiting; then those of the step kLookahead
-            // before, so that the host prepares the next launches while the device runs this step
+            if (!coop_step && step < kmax) part_b(act, step);
             int* fl = c->flags_h + (size_t)(step % kFlagBufs) * nint;
-            cudaMemcpyAsync(fl, wi, sizeof(int) * nint, cudaMemcpyDeviceToHost, st);
-            cudaEventRecord(c->flag_ev[step % kFlagBufs], st);
+            if (coop_step) {
+                // the flags of this step go back behind its projected solve, on its stream
+                cudaMemcpyAsync(fl, wi, sizeof(int) * nint, cudaMemcpyDeviceToHost, c->s2);
+                cudaEventRecord(c->flag_ev[step % kFlagBufs], c->s2);
+                pj_pending = true;
+            } else {
+                // the step's projected solve must be done before its flags are read and before the
+                // next step's projections overwrite the partial sums it reads
+                cudaStreamWaitEvent(st, c->ev_pj, 0);
+                // flags of this step, read back without waiting; then those of the step kLookahead
+                // before, so that the host prepares the next launches while the device runs this step
+                cudaMemcpyAsync(fl, wi, sizeof(int) * nint, cudaMemcpyDeviceToHost, st);
+                cudaEventRecord(c->flag_ev[step % kFlagBufs], st);
+            }
             if (step > kLookahead) {
                 const int old = (step - kLookahead) % kFlagBufs;
                 cudaEventSynchronize(c->flag_ev[old]);
@@ -559,6 +612,7 @@ struct Solver {
                 act.swap(next);
             }
         }
+        if (pj_pending) cudaStreamWaitEvent(st, c->ev_pj, 0);
         d2h(c, wi_host.data(), wi, sizeof(int) * nint);
         for (auto& W : ws) {
             const int* I = &wi_host[(size_t)W.w * L.istride];
@@ -573,6 +627,45 @@ struct Solver {
     // All its partial sums go through kpart[1]: kpart[0] holds the step projections, which
     // the projected solve on the second stream may still be reading.
     void part_b(const std::vector<Win<T>>& act, int step) {
+        if (coop_ok(act)) {
+            // the same four passes and two QRs as below, for the single window, in one launch
+            const Win<T>& W = act[0];
+            T* Wn = slot(W, step);
+            const int p = step * W.b;
+            UpdTask<T> u[4];
+            memset(u, 0, sizeof(u));
+            UpdTask<T> t;
+            memset(&t, 0, sizeof(t));
+            t.V = W.V; t.Wh = Wn; t.Wl = W.Wlo; t.ld = n; t.p = p;
+            t.conv = wi + (size_t)W.w * L.istride + WI_CONV;
+            t.hm = D(W.w) + L.off_out1; t.ldh = p;   // h1 from the projection pass
+            u[0] = t;
+            t.hm = nullptr; t.ldh = W.b;              // W <- W T1 (T1 from the first QR), h2 = V^T W
+            u[1] = t;
+            u[2] = t;                                 // W <- W - V h2 (h2 summed from the partials)
+            memset(&t, 0, sizeof(t));
+            t.Wh = Wn; t.Wl = W.Wlo; t.ld = n; t.p = W.b; t.ldh = W.b;
+            t.conv = wi + (size_t)W.w * L.istride + WI_CONV;
+            t.out = Wn;                               // W T2 rounded into the slot
+            u[3] = t;
+            const KGeom gb = krylov_geom(1, n);
+            const double w = sizeof(T);
+            const double wl_ = std::is_same<T, float>::value ? 8.0 : w;
+            const double pb = (double)p, bb = (double)W.b;
+            const double bytes = 2.0 * n * (pb * w + 2 * bb * wl_) + (double)n * (pb * w + 2 * bb * wl_) +
+                                 (double)n * bb * (wl_ + w);
+            const double alg = 3.0 * n * (pb * w + 2 * bb * w) + 2.0 * n * bb * w;
+            bool one = false;
+            timed(c, PEXP_KC_UPDATE, bytes, [&] {
+                one = launch_gs_coop<T>(u, W.b, p, n, gb, kpart[1], p * W.b, W.b * W.b, L, wd, wi, W.w, step, defl,
+                                        gbar(), st);
+            }, nullptr, false, alg);
+            if (one) {
+                coop_used = true;
+                ++c->launches;
+                return;
+            }
+        }
         {
             const double w = sizeof(T);
             const int nb = (int)act.size();
@@ -1435,6 +1528,7 @@ int solve_linear_typed(pexp_ctx* c, const pexp_operator* op, const pexp_options*
         steps_h[m] = kh;
         if (Y_host) emit_window(m);
     }
+    S.check_coop();
 
     cudaEventRecord(c->evp[3], st);
     if (Y_host) {
@@ -1640,6 +1734,10 @@ int pexp_create(pexp_ctx** out, int device, void* stream) {
     cudaEventCreate(&c->ev0);
     cudaEventCreate(&c->ev1);
     for (int k = 0; k < 5; ++k) cudaEventCreate(&c->evp[k]);
+    if (cudaMalloc(&c->bar, 256) != cudaSuccess || cudaMemset(c->bar, 0, 256) != cudaSuccess) {
+        pexp_destroy(c);
+        return PEXP_ERR_OOM;
+    }
     init_pade_constants();
     *out = c;
     return PEXP_OK;
@@ -1657,6 +1755,7 @@ int pexp_destroy(pexp_ctx* c) {
     }
     if (c->ws) cudaFree(c->ws);
     if (c->bs) cudaFree(c->bs);
+    if (c->bar) cudaFree(c->bar);
     for (int h = 0; h < 2; ++h) {
         if (c->stage_h[h]) cudaFreeHost(c->stage_h[h]);
         if (c->stage_d[h]) cudaFree(c->stage_d[h]);
@@ -1795,6 +1894,7 @@ int ensure_workers(pexp_ctx* c, int k) {
             return r;
         }
         w->owns_stream = true;
+        w->coop = false;
         c->workers.push_back(w);
     }
     return PEXP_OK;

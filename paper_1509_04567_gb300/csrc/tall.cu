@@ -32,6 +32,26 @@ void smem_optin_raw(const void* kernel, size_t bytes) {
     }
 }
 
+int coop_grid(const void* kernel, int threads, size_t smem, int want) {
+    static std::mutex mu;
+    static std::map<std::pair<int, const void*>, int> cap;
+    int dev = 0;
+    cudaGetDevice(&dev);
+    std::lock_guard<std::mutex> lk(mu);
+    auto it = cap.find({dev, kernel});
+    if (it == cap.end()) {
+        int coop = 0, sms = 0, per = 0;
+        cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, dev);
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        if (coop && cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, kernel, threads, smem) != cudaSuccess) {
+            cudaGetLastError();
+            per = 0;
+        }
+        it = cap.emplace(std::make_pair(dev, kernel), coop ? per * sms : 0).first;
+    }
+    return it->second <= 0 ? 0 : std::min(want, it->second);
+}
+
 int fail_cuda(cudaError_t e, const char* what, const char* file, int line) {
     fprintf(stderr, "pexp: CUDA error %s (%d) in %s at %s:%d\n", cudaGetErrorString(e), (int)e, what, file,
             line);
@@ -257,21 +277,13 @@ size_t sai_scratch_doubles(int64_t n, int nvec) {
     return (size_t)4 * nch * nvec;
 }
 
-// Pass 1: chunk summaries of the forward recurrence with zero carry-in.
+// Pass 1: chunk summaries of the forward recurrence with zero carry-in (chunk ch of vector v).
 template <typename T>
-__global__ void __launch_bounds__(kSaiThreads) k_sai_fwd_ends(int64_t n, int nch, double alpha,
-                                                              const T* const* __restrict__ Xp,
-                                                              const T* const* __restrict__ Xlo,
-                                                              double* __restrict__ ends,
-                                                              double* __restrict__ decays,
-                                                              const int* const* __restrict__ skip) {
-    pdl_entry();
+__device__ __forceinline__ void sai_fwd_ends_body(int64_t n, int nch, double alpha, const T* x, const T* xl,
+                                                  double* __restrict__ ends, double* __restrict__ decays, int v,
+                                                  int ch) {
     using R = typename SaiR<T>::R;
     __shared__ R sa[kSaiThreads], sb[kSaiThreads];
-    const int v = blockIdx.y, ch = blockIdx.x;
-    if (skip && skip[v] && *skip[v]) return;
-    const T* x = Xp[v];
-    const T* xl = Xlo ? Xlo[v] : nullptr;
     const int64_t start = (int64_t)ch * kSaiChunk + (int64_t)threadIdx.x * kSaiPer;
     T vals[kSaiPer], lows[kSaiPer];
     const int cnt = sai_load(x, n, start, vals);
@@ -293,26 +305,17 @@ __global__ void __launch_bounds__(kSaiThreads) k_sai_fwd_ends(int64_t n, int nch
 // Pass 2: forward values with carries (kept in registers) -> summaries of the
 // backward recurrence of w with zero carry from the right.
 template <typename T>
-__global__ void __launch_bounds__(kSaiThreads) k_sai_fwd_apply(int64_t n, int nch, double alpha, double beta,
-                                                               double alpha_n, const T* const* __restrict__ Xp,
-                                                               const T* const* __restrict__ Xlo,
-                                                               const double* __restrict__ fends,
-                                                               const double* __restrict__ fdecays,
-                                                               double* __restrict__ bends,
-                                                               double* __restrict__ bdecays,
-                                                               const int* const* __restrict__ skip) {
-    pdl_entry();
+__device__ __forceinline__ void sai_fwd_apply_body(int64_t n, int nch, double alpha, double beta, double alpha_n,
+                                                   const T* x, const T* xl, const double* __restrict__ fends,
+                                                   const double* __restrict__ fdecays, double* __restrict__ bends,
+                                                   double* __restrict__ bdecays, int v, int ch) {
     using R = typename SaiR<T>::R;
     __shared__ R sa[kSaiThreads], sb[kSaiThreads];
     __shared__ double carry_in;
-    const int v = blockIdx.y, ch = blockIdx.x;
-    if (skip && skip[v] && *skip[v]) return;
     if (threadIdx.x < 32) {
         const double cv = sai_carry_warp(fends + (int64_t)v * nch, fdecays + (int64_t)v * nch, nch, ch, +1, alpha_n);
         if (threadIdx.x == 0) carry_in = cv;
     }
-    const T* x = Xp[v];
-    const T* xl = Xlo ? Xlo[v] : nullptr;
     const int64_t start = (int64_t)ch * kSaiChunk + (int64_t)threadIdx.x * kSaiPer;
     T vals[kSaiPer], lows[kSaiPer];
     const int cnt = sai_load(x, n, start, vals);
@@ -337,22 +340,15 @@ __global__ void __launch_bounds__(kSaiThreads) k_sai_fwd_apply(int64_t n, int nc
 // Pass 3: the forward values again (same inputs and arithmetic as pass 2, so the
 // same w), then the backward recurrence with carries, scaled by 1/c, into Y.
 template <typename T>
-__global__ void __launch_bounds__(kSaiThreads) k_sai_bwd_apply(int64_t n, int nch, double alpha, double alpha_n,
-                                                               double beta, double beta_n, double inv_c,
-                                                               const T* const* __restrict__ Xp,
-                                                               const T* const* __restrict__ Xlo,
-                                                               T* const* __restrict__ Yp, T* const* __restrict__ Ylo,
-                                                               const double* __restrict__ fends,
-                                                               const double* __restrict__ fdecays,
-                                                               const double* __restrict__ bends,
-                                                               const double* __restrict__ bdecays,
-                                                               const int* const* __restrict__ skip) {
-    pdl_entry();
+__device__ __forceinline__ void sai_bwd_apply_body(int64_t n, int nch, double alpha, double alpha_n, double beta,
+                                                   double beta_n, double inv_c, const T* x, const T* xl, T* y, T* ylo,
+                                                   const double* __restrict__ fends,
+                                                   const double* __restrict__ fdecays,
+                                                   const double* __restrict__ bends,
+                                                   const double* __restrict__ bdecays, int v, int ch) {
     using R = typename SaiR<T>::R;
     __shared__ R sa[kSaiThreads], sb[kSaiThreads];
     __shared__ double carry_f, carry_b;
-    const int v = blockIdx.y, ch = blockIdx.x;
-    if (skip && skip[v] && *skip[v]) return;
     if (threadIdx.x < 32) {
         const double cf = sai_carry_warp(fends + (int64_t)v * nch, fdecays + (int64_t)v * nch, nch, ch, +1, alpha_n);
         const double cb = sai_carry_warp(bends + (int64_t)v * nch, bdecays + (int64_t)v * nch, nch, ch, -1, beta_n);
@@ -361,10 +357,6 @@ __global__ void __launch_bounds__(kSaiThreads) k_sai_bwd_apply(int64_t n, int nc
             carry_b = cb;
         }
     }
-    const T* x = Xp[v];
-    const T* xl = Xlo ? Xlo[v] : nullptr;
-    T* y = Yp[v];
-    T* ylo = Ylo ? Ylo[v] : nullptr;
     const int64_t start = (int64_t)ch * kSaiChunk + (int64_t)threadIdx.x * kSaiPer;
     T vals[kSaiPer], lows[kSaiPer];
     const int cnt = sai_load(x, n, start, vals);
@@ -397,6 +389,80 @@ __global__ void __launch_bounds__(kSaiThreads) k_sai_bwd_apply(int64_t n, int nc
 }
 
 template <typename T>
+__global__ void __launch_bounds__(kSaiThreads) k_sai_fwd_ends(int64_t n, int nch, double alpha,
+                                                              const T* const* __restrict__ Xp,
+                                                              const T* const* __restrict__ Xlo,
+                                                              double* __restrict__ ends,
+                                                              double* __restrict__ decays,
+                                                              const int* const* __restrict__ skip) {
+    pdl_entry();
+    const int v = blockIdx.y;
+    if (skip && skip[v] && *skip[v]) return;
+    sai_fwd_ends_body<T>(n, nch, alpha, Xp[v], Xlo ? Xlo[v] : nullptr, ends, decays, v, blockIdx.x);
+}
+
+template <typename T>
+__global__ void __launch_bounds__(kSaiThreads) k_sai_fwd_apply(int64_t n, int nch, double alpha, double beta,
+                                                               double alpha_n, const T* const* __restrict__ Xp,
+                                                               const T* const* __restrict__ Xlo,
+                                                               const double* __restrict__ fends,
+                                                               const double* __restrict__ fdecays,
+                                                               double* __restrict__ bends,
+                                                               double* __restrict__ bdecays,
+                                                               const int* const* __restrict__ skip) {
+    pdl_entry();
+    const int v = blockIdx.y;
+    if (skip && skip[v] && *skip[v]) return;
+    sai_fwd_apply_body<T>(n, nch, alpha, beta, alpha_n, Xp[v], Xlo ? Xlo[v] : nullptr, fends, fdecays, bends, bdecays, v,
+                          blockIdx.x);
+}
+
+template <typename T>
+__global__ void __launch_bounds__(kSaiThreads) k_sai_bwd_apply(int64_t n, int nch, double alpha, double alpha_n,
+                                                               double beta, double beta_n, double inv_c,
+                                                               const T* const* __restrict__ Xp,
+                                                               const T* const* __restrict__ Xlo,
+                                                               T* const* __restrict__ Yp, T* const* __restrict__ Ylo,
+                                                               const double* __restrict__ fends,
+                                                               const double* __restrict__ fdecays,
+                                                               const double* __restrict__ bends,
+                                                               const double* __restrict__ bdecays,
+                                                               const int* const* __restrict__ skip) {
+    pdl_entry();
+    const int v = blockIdx.y;
+    if (skip && skip[v] && *skip[v]) return;
+    sai_bwd_apply_body<T>(n, nch, alpha, alpha_n, beta, beta_n, inv_c, Xp[v], Xlo ? Xlo[v] : nullptr, Yp[v],
+                          Ylo ? Ylo[v] : nullptr, fends, fdecays, bends, bdecays, v, blockIdx.x);
+}
+
+// The three passes of one vector's solve in one cooperative launch: CTAs take chunks
+// ch = blockIdx.x, blockIdx.x + gridDim.x, ... in every pass, with the same arithmetic as the
+// three kernels above (so the same result), and meet at a grid barrier between passes.
+// `skip`: the window's convergence flag, read once at entry (the whole solve is skipped).
+template <typename T>
+__global__ void __launch_bounds__(kSaiThreads) k_sai_coop(int64_t n, int nch, SaiCoef cf, const T* __restrict__ x,
+                                                          T* __restrict__ y, T* __restrict__ ylo,
+                                                          double* __restrict__ scr, const int* __restrict__ skip,
+                                                          GridBar bar) {
+    const bool active = !(skip && *(volatile const int*)skip);
+    double* fends = scr;
+    double* fdec = fends + nch;
+    double* bends = fdec + nch;
+    double* bdec = bends + nch;
+    if (active)
+        for (int ch = blockIdx.x; ch < nch; ch += gridDim.x) sai_fwd_ends_body<T>(n, nch, cf.alpha, x, nullptr, fends, fdec, 0, ch);
+    if (!grid_bar(bar)) return;
+    if (active)
+        for (int ch = blockIdx.x; ch < nch; ch += gridDim.x)
+            sai_fwd_apply_body<T>(n, nch, cf.alpha, cf.beta, cf.alpha_n, x, nullptr, fends, fdec, bends, bdec, 0, ch);
+    if (!grid_bar(bar)) return;
+    if (active)
+        for (int ch = blockIdx.x; ch < nch; ch += gridDim.x)
+            sai_bwd_apply_body<T>(n, nch, cf.alpha, cf.alpha_n, cf.beta, cf.beta_n, cf.inv_c, x, nullptr, y, ylo, fends,
+                                  fdec, bends, bdec, 0, ch);
+}
+
+template <typename T>
 void launch_sai_solve(const OpDesc& op, const SaiCoef& cf, const T* const* X, T* const* Y, T* const* Ylo, int nvec,
                       double* scratch, cudaStream_t s) {
     launch_sai_solve_lo<T>(op, cf, X, nullptr, Y, Ylo, nvec, scratch, s, nullptr);
@@ -419,6 +485,23 @@ void launch_sai_solve_lo(const OpDesc& op, const SaiCoef& cf, const T* const* X,
     launch_pdl(k_sai_bwd_apply<T>, g, dim3(kSaiThreads), 0, s, n, nch, cf.alpha, cf.alpha_n, cf.beta, cf.beta_n,
                cf.inv_c, X, Xlo, Y, Ylo, (const double*)fends, (const double*)fdec, (const double*)bends,
                (const double*)bdec, skip);
+}
+
+template <typename T>
+bool launch_sai_coop(const OpDesc& op, const SaiCoef& cf, const T* x, T* y, T* ylo, double* scratch, const int* skip,
+                     GridBar bar, cudaStream_t s) {
+    int64_t n = op.n;
+    int nch = (int)((n + kSaiChunk - 1) / kSaiChunk);
+    const int g = coop_grid(reinterpret_cast<const void*>(k_sai_coop<T>), kSaiThreads, 0, nch);
+    if (g <= 0) return false;
+    SaiCoef c = cf;
+    void* args[] = {&n, &nch, &c, &x, &y, &ylo, &scratch, &skip, &bar};
+    if (cudaLaunchCooperativeKernel(reinterpret_cast<const void*>(k_sai_coop<T>), dim3(g), dim3(kSaiThreads), args, 0,
+                                    s) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    return true;
 }
 
 // =====================================================================================
@@ -1025,6 +1108,8 @@ void launch_row_diff_norms(const T* A, const T* B, int64_t n, int nrows, double*
                                       int, double*, cudaStream_t);                                        \
     template void launch_sai_solve_lo<T>(const OpDesc&, const SaiCoef&, const T* const*, const T* const*,       \
                                          T* const*, T* const*, int, double*, cudaStream_t, const int* const*); \
+    template bool launch_sai_coop<T>(const OpDesc&, const SaiCoef&, const T*, T*, T*, double*, const int*, GridBar, \
+                                     cudaStream_t);                                                          \
     template void launch_ts_tn<T>(const TsTask<T>*, int, int, int, int64_t, double*, cudaStream_t, int);   \
     template void launch_ts_nn<T>(const TsTask<T>*, int, int, int64_t, cudaStream_t);                     \
     template void launch_recon<T, float>(const ReconTask<T>*, int, int, int64_t, const double*, float*,    \

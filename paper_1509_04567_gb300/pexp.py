@@ -35,6 +35,7 @@ KRYLOV_POLY = 0
 KRYLOV_SAI = 1
 DIAG_ORTH = 1
 DIAG_KTIME = 2
+DIAG_NOCOOP = 4
 
 
 def DIAG_KTIME_CLASS(cls: int) -> int:
