@@ -334,6 +334,15 @@ int pexp_burgers_source(pexp_ctx* ctx, const pexp_operator* op, const void* U_de
 int pexp_sai_solve_noalloc(const pexp_operator* op, double gamma, const void* X_dev, void* Y_dev,
                            int nvec, int dtype, void* cuda_stream);
 
+/* Self-test of the bounded wait of the grid barriers that the cooperative launches use
+ * (no counterpart in the paper; it checks this library's own synchronisation).  Launches a
+ * small cooperative grid on the context's stream whose CTAs pass four barriers; with
+ * absent_cta >= 0 that CTA leaves at once, so the others' wait expires after about 1 s.
+ * Blocks until the launch ends.  Returns PEXP_OK when every barrier completed,
+ * PEXP_ERR_TIMEOUT when a wait expired (the barrier words are then reset and the context
+ * stays usable), PEXP_ERR_UNSUPPORTED where a cooperative launch is not possible. */
+int pexp_selftest_barrier(pexp_ctx* ctx, int absent_cta);
+
 #ifdef __cplusplus
 }
 #endif

@@ -188,6 +188,9 @@ bool launch_sai_coop(const OpDesc& op, const SaiCoef& cf, const T* x, T* y, T* y
                      GridBar bar, cudaStream_t s);
 // Largest grid (at most `want`) whose CTAs are all resident at once, 0 without cooperative launch.
 int coop_grid(const void* kernel, int threads, size_t smem, int want);
+// Cooperative launch of up to 64 CTAs passing 4 barriers; CTA `absent` (>= 0) skips them.
+// Returns the grid size, 0 where a cooperative launch is not possible.
+int launch_bar_selftest(GridBar bar, int absent, cudaStream_t s);
 template <typename T>
 void launch_ts_tn(const TsTask<T>* tasks_dev, int ntasks, int max_pq, int max_q, int64_t n, double* partial,
                   cudaStream_t s, int exact = 0);

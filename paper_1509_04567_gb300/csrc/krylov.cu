@@ -393,7 +393,9 @@ __device__ __forceinline__ void sub_vh(const double (&x)[Q], const double* sh, i
 constexpr int kUpdQ = 8;   // columns of V per load group of the update kernels
 constexpr int kUpdR = 2;   // rows per thread per iteration of the update kernels
 template <int B>
-constexpr int kUpdCtas = B <= 2 ? 3 : 2;   // resident CTAs per SM the update kernels are built for
+constexpr int kUpdCtas = B <= 2 ? 4 : 2;   // resident CTAs per SM the update kernels are built for
+template <int B>
+constexpr int kScaleProjCtas = B == 1 ? 3 : 2;   // and the scale-projection kernel
 
 template <typename T, int B>
 __device__ __forceinline__ void k_update0_body(const UpdTask<T>& tk, int64_t n, int64_t rows, int nchunks, int pstride, double* __restrict__ partial, int bx, int by) {
@@ -577,7 +579,7 @@ __device__ __forceinline__ void k_scale_proj_body(const UpdTask<T>& tk, int64_t 
 }
 
 template <typename T, int B>
-__global__ void __launch_bounds__(kThreads, 2) k_scale_proj(const UpdTask<T>* __restrict__ tasks, int64_t n,
+__global__ void __launch_bounds__(kThreads, kScaleProjCtas<B>) k_scale_proj(const UpdTask<T>* __restrict__ tasks, int64_t n,
                                                             int64_t rows, int nchunks, int pstride,
                                                             double* __restrict__ partial) {    pdl_entry();
     const UpdTask<T> tk = tasks[blockIdx.y];

@@ -1842,6 +1842,22 @@ int pexp_solve_linear(pexp_ctx* c, const pexp_operator* op, const pexp_options* 
     return solve_linear_entry(c, op, o, y0_dev, G_dev, g_dtype, Y_dev, y_dtype, rep, nullptr);
 }
 
+int pexp_selftest_barrier(pexp_ctx* c, int absent_cta) {
+    if (!c) return PEXP_ERR_INVALID_ARG;
+    cudaSetDevice(c->device);
+    const GridBar bar{c->bar, c->bar + 1, reinterpret_cast<int*>(c->bar + 2)};
+    if (launch_bar_selftest(bar, absent_cta, c->stream) <= 0) return PEXP_ERR_UNSUPPORTED;
+    int err = 0;
+    PEXP_CUDA_TRY(cudaMemcpyAsync(&err, c->bar + 2, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
+    PEXP_CUDA_TRY(cudaStreamSynchronize(c->stream));
+    if (err) {
+        PEXP_CUDA_TRY(cudaMemsetAsync(c->bar, 0, 3 * sizeof(unsigned), c->stream));
+        PEXP_CUDA_TRY(cudaStreamSynchronize(c->stream));
+        return PEXP_ERR_TIMEOUT;
+    }
+    return PEXP_OK;
+}
+
 int pexp_solve_linear_host(pexp_ctx* c, const pexp_operator* op, const pexp_options* o, const void* y0_host,
                            const void* G_host, int g_dtype, void* Y_host, int y_dtype, pexp_report* rep) {
     if (!c || !y0_host || !Y_host) return PEXP_ERR_INVALID_ARG;

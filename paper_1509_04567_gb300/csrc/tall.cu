@@ -277,6 +277,10 @@ size_t sai_scratch_doubles(int64_t n, int nvec) {
     return (size_t)4 * nch * nvec;
 }
 
+// Resident CTAs per SM the three passes are built for (48 registers): their CTA scans are
+// latency-bound, so more CTAs in flight hide more of it.
+constexpr int kSaiCtas = 5;
+
 // Pass 1: chunk summaries of the forward recurrence with zero carry-in (chunk ch of vector v).
 template <typename T>
 __device__ __forceinline__ void sai_fwd_ends_body(int64_t n, int nch, double alpha, const T* x, const T* xl,
@@ -389,7 +393,7 @@ __device__ __forceinline__ void sai_bwd_apply_body(int64_t n, int nch, double al
 }
 
 template <typename T>
-__global__ void __launch_bounds__(kSaiThreads) k_sai_fwd_ends(int64_t n, int nch, double alpha,
+__global__ void __launch_bounds__(kSaiThreads, kSaiCtas) k_sai_fwd_ends(int64_t n, int nch, double alpha,
                                                               const T* const* __restrict__ Xp,
                                                               const T* const* __restrict__ Xlo,
                                                               double* __restrict__ ends,
@@ -402,7 +406,7 @@ __global__ void __launch_bounds__(kSaiThreads) k_sai_fwd_ends(int64_t n, int nch
 }
 
 template <typename T>
-__global__ void __launch_bounds__(kSaiThreads) k_sai_fwd_apply(int64_t n, int nch, double alpha, double beta,
+__global__ void __launch_bounds__(kSaiThreads, kSaiCtas) k_sai_fwd_apply(int64_t n, int nch, double alpha, double beta,
                                                                double alpha_n, const T* const* __restrict__ Xp,
                                                                const T* const* __restrict__ Xlo,
                                                                const double* __restrict__ fends,
@@ -418,7 +422,7 @@ __global__ void __launch_bounds__(kSaiThreads) k_sai_fwd_apply(int64_t n, int nc
 }
 
 template <typename T>
-__global__ void __launch_bounds__(kSaiThreads) k_sai_bwd_apply(int64_t n, int nch, double alpha, double alpha_n,
+__global__ void __launch_bounds__(kSaiThreads, kSaiCtas) k_sai_bwd_apply(int64_t n, int nch, double alpha, double alpha_n,
                                                                double beta, double beta_n, double inv_c,
                                                                const T* const* __restrict__ Xp,
                                                                const T* const* __restrict__ Xlo,
@@ -502,6 +506,28 @@ bool launch_sai_coop(const OpDesc& op, const SaiCoef& cf, const T* x, T* y, T* y
         return false;
     }
     return true;
+}
+
+// Self-test of the bounded grid barrier: the CTAs of a cooperative launch pass `rounds`
+// barriers, except CTA `absent` (>= 0), which leaves at once, so that the others' wait runs
+// out after its time limit and sets the error word.
+__global__ void k_bar_selftest(GridBar bar, int rounds, int absent) {
+    if ((int)blockIdx.x == absent) return;
+    for (int i = 0; i < rounds; ++i)
+        if (!grid_bar(bar)) return;
+}
+
+int launch_bar_selftest(GridBar bar, int absent, cudaStream_t s) {
+    const int g = coop_grid(reinterpret_cast<const void*>(k_bar_selftest), 256, 0, 64);
+    if (g <= 0) return 0;
+    int rounds = 4;
+    void* args[] = {&bar, &rounds, &absent};
+    if (cudaLaunchCooperativeKernel(reinterpret_cast<const void*>(k_bar_selftest), dim3(g), dim3(256), args, 0, s) !=
+        cudaSuccess) {
+        cudaGetLastError();
+        return 0;
+    }
+    return g;
 }
 
 // =====================================================================================

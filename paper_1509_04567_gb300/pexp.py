@@ -60,7 +60,7 @@ F32 = 1
 EXPORTS = ["pexp_create", "pexp_destroy", "pexp_set_stream", "pexp_default_options", "pexp_status_string",
            "pexp_solve_linear", "pexp_solve_linear_host", "pexp_solve_burgers", "pexp_apply_operator",
            "pexp_sai_solve", "pexp_small_expm", "pexp_burgers_source", "pexp_sai_solve_noalloc",
-           "pexp_jacobian_sai_solve", "pexp_solve_batched", "pexp_autotune"]
+           "pexp_jacobian_sai_solve", "pexp_solve_batched", "pexp_autotune", "pexp_selftest_barrier"]
 
 
 class Operator(C.Structure):
@@ -124,6 +124,7 @@ def lib() -> C.CDLL:
         L.pexp_solve_linear.argtypes = [vp, C.POINTER(Operator), C.POINTER(Options), vp, vp, i, vp, i,
                                         C.POINTER(Report)]
         L.pexp_solve_linear_host.argtypes = L.pexp_solve_linear.argtypes
+        L.pexp_selftest_barrier.argtypes = [C.c_void_p, C.c_int]
         L.pexp_solve_burgers.argtypes = [vp, C.POINTER(Operator), C.POINTER(Options), vp, vp, vp, vp, i,
                                          C.POINTER(Report)]
         L.pexp_apply_operator.argtypes = [vp, C.POINTER(Operator), vp, vp, i, i, i]
@@ -332,6 +333,12 @@ class Context:
             d["rc"] = r.status
             out.append(d)
         return out
+
+    def selftest_barrier(self, absent_cta: int = -1) -> int:
+        """pexp_selftest_barrier: a small cooperative launch through the bounded grid barrier;
+        with absent_cta >= 0 one CTA never arrives and the wait must expire (ERR_TIMEOUT).
+        Returns the status code."""
+        return lib().pexp_selftest_barrier(self.h, int(absent_cta))
 
     def autotune(self, items, path: str | None = None) -> None:
         """Tunes the batched solve on these problems (pexp_autotune); the table goes to `path`."""

@@ -49,3 +49,24 @@ def test_cooperative_chain_is_bitwise_the_separate_launches(c, prec, n, P, tol):
     # each chain step: 2 launches instead of 9
     assert r1["launches"] < r2["launches"] - 4 * r1["k_hom_sum"], (r1["launches"], r2["launches"], r1["k_hom_sum"])
     assert np.isfinite(Y1.double().numpy()).all()
+
+
+def test_grid_barrier_wait_is_bounded_and_the_context_survives(c):
+    """The barrier of the cooperative launches gives up after about 1 s when a CTA never
+    arrives (here one CTA of a self-test launch leaves at once): the call returns
+    ERR_TIMEOUT, the kernel ends, and the same context then solves as before."""
+    import time
+    import torch
+    assert c.selftest_barrier(-1) == pexp.OK
+    t0 = time.time()
+    rc = c.selftest_barrier(3)
+    dt = time.time() - t0
+    assert rc == pexp.ERR_TIMEOUT, rc
+    assert dt < 10.0, dt
+    assert c.selftest_barrier(-1) == pexp.OK   # the barrier words were reset
+    pr = wl.adv_diff_1d(n=1 << 14, nu=1e-3, a=1.0, T=1.0, P=8, n_out=65, tol=1e-7, svd_tol=1e-10, max_rank=8,
+                        restart_len=30)
+    opts = dict(pr.opts, precision=1)
+    Y1, r1 = _solve(c, pr, opts, 1)
+    Y2, r2 = _solve(c, pr, dict(opts, diagnostics=pexp.DIAG_NOCOOP), 1)
+    assert r1["rc"] == 0 and torch.equal(Y1, Y2)
