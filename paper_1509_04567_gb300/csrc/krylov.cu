@@ -967,6 +967,95 @@ __global__ void __launch_bounds__(kThreads) k_source_gram(const T* const* __rest
 }
 
 // =====================================================================================
+// Part B of a fused step with its small steps folded in (separate launches):
+//   k_update0_h:     k_update0 with h1 summed by every CTA from the projection pass's
+//                    partials (entries hoff + [0, p B) of its task);
+//   k_scale_proj_qr: the first Cholesky QR (k_block_orth pass 1, with the pre-Gram-Schmidt
+//                    norms from the projection partials) in every CTA, then k_scale_proj;
+//   k_scale_qr:      the second Cholesky QR in every CTA, then k_scale (rounded into the slot).
+// The sums run in the fixed order of parts_sum_warp, so every CTA gets the values that the
+// separate summing and QR kernels store, and the results are the same bit for bit.  CTA 0
+// of each window writes the window's state (the QR's T, kept count, convergence).
+// =====================================================================================
+constexpr int kH1Max = PEXP_MAX_STEPS * kKrylovMaxB * kKrylovMaxB;   // p B <= 64 * 4 * 4
+template <typename T, int B>
+__global__ void __launch_bounds__(kThreads, kUpdCtas<B>) k_update0_h(const UpdTask<T>* __restrict__ tasks, int64_t n,
+                                                                     int64_t rows, int nchunks, int pstride,
+                                                                     double* __restrict__ partial,
+                                                                     const double* __restrict__ hpart, int hstride,
+                                                                     int hoff) {
+    pdl_entry();
+    __shared__ double sH[kH1Max];
+    const UpdTask<T> tk0 = tasks[blockIdx.y];
+    if (tk0.conv && *tk0.conv) return;
+    const int p = tk0.p;
+    const Parts hp{hpart, nchunks, hstride};
+    for (int e = threadIdx.x >> 5; e < p * B; e += kWarps) {
+        const double v = parts_sum_warp(hp, blockIdx.y, hoff + e);
+        if ((threadIdx.x & 31) == 0) sH[e] = v;
+    }
+    __syncthreads();
+    UpdTask<T> tk = tk0;
+    tk.hm = sH;
+    tk.ldh = p;
+    k_update0_body<T, B>(tk, n, rows, nchunks, pstride, partial, blockIdx.x, blockIdx.y);
+}
+
+template <typename T, int B>
+__global__ void __launch_bounds__(kThreads, kScaleProjCtas<B>) k_scale_proj_qr(
+    const UpdTask<T>* __restrict__ tasks, int64_t n, int64_t rows, int nchunks, int pstride, double* __restrict__ partial,
+    WinLayout L, double* __restrict__ wd, int* __restrict__ wi, const int* __restrict__ wins, int step, double defl,
+    const double* __restrict__ gpart, int gstride, const double* __restrict__ ppart, int ppstride, int pre_off) {
+    pdl_entry();
+    const UpdTask<T> tk0 = tasks[blockIdx.y];
+    if (tk0.conv && *tk0.conv) return;
+    __shared__ double sG[B * B], sT[B * B], spre[B];
+    __shared__ int s_r;
+    const int w = wins[blockIdx.y];
+    double* D = wd + (int64_t)w * L.stride;
+    int* I = wi + (int64_t)w * L.istride;
+    if (threadIdx.x < 32) {
+        const int r = block_orth_body<B>(L, D, I, blockIdx.y, 1, step, defl, Parts{gpart, nchunks, gstride}, -1, sG, sT,
+                                      blockIdx.x == 0, Parts{ppart, nchunks, ppstride}, pre_off, spre);
+        if (threadIdx.x == 0) {
+            s_r = r;
+            if (blockIdx.x == 0)
+                for (int e = 0; e < B * B; ++e) D[L.off_T + e] = sT[e];
+        }
+    }
+    __syncthreads();
+    if (s_r == 0) return;   // no direction kept: CTA 0 marked the window converged
+    UpdTask<T> tk = tk0;
+    tk.hm = sT;
+    tk.ldh = B;
+    k_scale_proj_body<T, B>(tk, n, rows, nchunks, pstride, partial, blockIdx.x, blockIdx.y);
+}
+
+template <typename T, int B>
+__global__ void __launch_bounds__(kThreads, 2) k_scale_qr(const UpdTask<T>* __restrict__ tasks, int64_t n, int64_t rows,
+                                                         int nchunks, WinLayout L, double* __restrict__ wd,
+                                                         int* __restrict__ wi, const int* __restrict__ wins, int step,
+                                                         double defl, const double* __restrict__ gpart, int gstride) {
+    pdl_entry();
+    const UpdTask<T> tk0 = tasks[blockIdx.y];
+    if (tk0.conv && *tk0.conv) return;
+    __shared__ double sG[B * B], sT[B * B];
+    const int w = wins[blockIdx.y];
+    double* D = wd + (int64_t)w * L.stride;
+    int* I = wi + (int64_t)w * L.istride;
+    if (threadIdx.x < 32) {
+        block_orth_body<B>(L, D, I, blockIdx.y, 2, step, defl, Parts{gpart, nchunks, gstride}, -1, sG, sT, blockIdx.x == 0);
+        if (threadIdx.x == 0 && blockIdx.x == 0)
+            for (int e = 0; e < B * B; ++e) D[L.off_T + e] = sT[e];
+    }
+    __syncthreads();
+    UpdTask<T> tk = tk0;
+    tk.hm = sT;
+    tk.ldh = B;
+    k_scale_body<T, B>(tk, n, rows, nchunks, 0, 0, nullptr, blockIdx.x, blockIdx.y);
+}
+
+// =====================================================================================
 // k_gs_coop: part B of a fused Krylov step (the four passes above and the two Cholesky QRs
 // between them) for one window in one cooperative launch.  CTAs take chunks blockIdx.x,
 // blockIdx.x + gridDim.x, ... of the same row geometry and meet at grid barriers, so every
@@ -996,7 +1085,7 @@ __global__ void __launch_bounds__(kThreads, 3) k_gs_coop(UpdTask<T> u1, UpdTask<
         for (int ch = blockIdx.x; ch < nchunks; ch += gridDim.x) k_update0_body<T, B>(u1, n, rows, nchunks, psg, pg1, ch, 0);
     if (!grid_bar(bar)) return;
     if (active && threadIdx.x < 32) {
-        const int r = block_orth_body(L, D, I, 0, 1, step, defl, Parts{pg1, nchunks, psg}, -1, sG, sT1, blockIdx.x == 0);
+        const int r = block_orth_body<B>(L, D, I, 0, 1, step, defl, Parts{pg1, nchunks, psg}, -1, sG, sT1, blockIdx.x == 0);
         if (threadIdx.x == 0) {
             s_r = r;
             if (blockIdx.x == 0)
@@ -1019,7 +1108,7 @@ __global__ void __launch_bounds__(kThreads, 3) k_gs_coop(UpdTask<T> u1, UpdTask<
             k_update1_body<T, B>(u2, n, rows, nchunks, psg, pg2, ph2, ps2, ch, 0);
     if (!grid_bar(bar)) return;
     if (active && threadIdx.x < 32) {
-        block_orth_body(L, D, I, 0, 2, step, defl, Parts{pg2, nchunks, psg}, r1, sG, sT2, blockIdx.x == 0);
+        block_orth_body<B>(L, D, I, 0, 2, step, defl, Parts{pg2, nchunks, psg}, r1, sG, sT2, blockIdx.x == 0);
         if (threadIdx.x == 0 && blockIdx.x == 0)
             for (int e = 0; e < B * B; ++e) D[L.off_T + e] = sT2[e];
     }
@@ -1153,6 +1242,37 @@ void launch_source_gram(const T* const* X, const int* sv, int ntasks, int s_max,
 }
 
 template <typename T>
+void launch_update0_h(const UpdTask<T>* tasks, int ntasks, int b, int p, int64_t n, KGeom g, double* partial,
+                      int pstride, const double* hpart, int hstride, int hoff, cudaStream_t s) {
+    if (ntasks <= 0) return;
+    dim3 grid(g.nchunks, ntasks);
+    const size_t sm = (size_t)p * b * (sizeof(T) == 4 ? sizeof(float2) : sizeof(double)) + 16;
+    PEXP_B_DISPATCH(b, (launch_pdl(k_update0_h<T, BB>, grid, dim3(kThreads), sm, s, tasks, n, g.rows, g.nchunks, pstride,
+                                   partial, hpart, hstride, hoff)));
+}
+
+template <typename T>
+void launch_scale_proj_qr(const UpdTask<T>* tasks, int ntasks, int b, int64_t n, KGeom g, double* partial, int pstride,
+                          const WinLayout& L, double* wd, int* wi, const int* wins, int step, double defl,
+                          const double* gpart, int gstride, const double* ppart, int ppstride, int pre_off,
+                          cudaStream_t s) {
+    if (ntasks <= 0) return;
+    dim3 grid(g.nchunks, ntasks);
+    PEXP_B_DISPATCH(b, (launch_pdl(k_scale_proj_qr<T, BB>, grid, dim3(kThreads), 0, s, tasks, n, g.rows, g.nchunks,
+                                   pstride, partial, L, wd, wi, wins, step, defl, gpart, gstride, ppart, ppstride,
+                                   pre_off)));
+}
+
+template <typename T>
+void launch_scale_qr(const UpdTask<T>* tasks, int ntasks, int b, int64_t n, KGeom g, const WinLayout& L, double* wd,
+                     int* wi, const int* wins, int step, double defl, const double* gpart, int gstride, cudaStream_t s) {
+    if (ntasks <= 0) return;
+    dim3 grid(g.nchunks, ntasks);
+    PEXP_B_DISPATCH(b, (launch_pdl(k_scale_qr<T, BB>, grid, dim3(kThreads), 0, s, tasks, n, g.rows, g.nchunks, L, wd, wi,
+                                   wins, step, defl, gpart, gstride)));
+}
+
+template <typename T>
 bool launch_gs_coop(const UpdTask<T>* u, int b, int p, int64_t n, KGeom g, double* kp, int ps2, int psg,
                     const WinLayout& L, double* wd, int* wi, int w, int step, double defl, GridBar bar, cudaStream_t s) {
     if (b != 1 || !proj_fused(p, b, sizeof(T))) return false;
@@ -1176,6 +1296,13 @@ bool launch_gs_coop(const UpdTask<T>* u, int b, int p, int64_t n, KGeom g, doubl
 }
 
 #define PEXP_KRY_INST(T)                                                                                           \
+    template void launch_update0_h<T>(const UpdTask<T>*, int, int, int, int64_t, KGeom, double*, int, const double*, int, \
+                                      int, cudaStream_t);                                                          \
+    template void launch_scale_proj_qr<T>(const UpdTask<T>*, int, int, int64_t, KGeom, double*, int, const WinLayout&,   \
+                                          double*, int*, const int*, int, double, const double*, int, const double*, int, \
+                                          int, cudaStream_t);                                                      \
+    template void launch_scale_qr<T>(const UpdTask<T>*, int, int, int64_t, KGeom, const WinLayout&, double*, int*,       \
+                                     const int*, int, double, const double*, int, cudaStream_t);                    \
     template bool launch_gs_coop<T>(const UpdTask<T>*, int, int, int64_t, KGeom, double*, int, int, const WinLayout&, \
                                     double*, int*, int, int, double, GridBar, cudaStream_t);               \
     template void launch_step_proj<T>(const StepTask<T>*, int, int, int, int64_t, int, KGeom, double*, int, cudaStream_t, bool); \

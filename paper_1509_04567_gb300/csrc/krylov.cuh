@@ -70,6 +70,9 @@ template <typename T>
 void launch_scale(const UpdTask<T>* tasks, int ntasks, int b, int64_t n, int gram, KGeom g, double* partial,
                   int pstride, cudaStream_t s);
 struct WinLayout;
+// The scale and second projection pass fuse into one kernel (k_scale_proj) for a basis of p
+// columns and block width b with elements of tsize bytes.
+bool proj_fused(int p, int b, size_t tsize);
 // Part B of a fused Krylov step (passes u[0..3]: update0, scale_proj, update1, scale, with the
 // two Cholesky QRs between them) for window w, block width b, in one cooperative launch:
 // the same arithmetic and results as the separate launches.  The partial sums take
@@ -78,6 +81,22 @@ struct WinLayout;
 template <typename T>
 bool launch_gs_coop(const UpdTask<T>* u, int b, int p, int64_t n, KGeom g, double* kp, int ps2, int psg,
                     const WinLayout& L, double* wd, int* wi, int w, int step, double defl, GridBar bar, cudaStream_t s);
+// Part B of a fused step with the partial-sum and Cholesky-QR kernels folded into the passes
+// (bitwise the same results as update + sum + block_orth + scale_proj + ... launched apart):
+// update0 summing h1 from the projection partials (entries hoff + [0, p b)); scale_proj after
+// the first QR (Gram partials gpart, pre-Gram-Schmidt norms at entry pre_off of the projection
+// partials ppart); scale after the second QR.  wins: the window of each task.
+template <typename T>
+void launch_update0_h(const UpdTask<T>* tasks, int ntasks, int b, int p, int64_t n, KGeom g, double* partial,
+                      int pstride, const double* hpart, int hstride, int hoff, cudaStream_t s);
+template <typename T>
+void launch_scale_proj_qr(const UpdTask<T>* tasks, int ntasks, int b, int64_t n, KGeom g, double* partial, int pstride,
+                          const WinLayout& L, double* wd, int* wi, const int* wins, int step, double defl,
+                          const double* gpart, int gstride, const double* ppart, int ppstride, int pre_off,
+                          cudaStream_t s);
+template <typename T>
+void launch_scale_qr(const UpdTask<T>* tasks, int ntasks, int b, int64_t n, KGeom g, const WinLayout& L, double* wd,
+                     int* wi, const int* wins, int step, double defl, const double* gpart, int gstride, cudaStream_t s);
 constexpr int kKrylovMaxB = 4;   // block widths handled by the fused kernels
 // Sums the per-CTA partials of each task into wd + wins[task] * stride + off (ne entries).
 // Entries [e0, e0 + ne) of each partial go to entries [0, ne) of the output.

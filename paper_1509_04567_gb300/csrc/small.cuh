@@ -69,8 +69,15 @@ __device__ __forceinline__ double parts_sum_warp(const Parts& p, int task, int e
 // to Tout and returns the kept count r (other threads return 0).  `kept`: pass 2's
 // candidate count (< 0: the window's WI_KEPT).  `owner`: also write the window's state (the
 // pre-Gram-Schmidt norm, WI_KEPT, and WI_CONV when the block is empty).  sG: b*b shared doubles.
+// pp (pass 1): the pre-Gram-Schmidt norms summed from the projection pass's partials (entries
+// pre_off + c of launch-list entry `task`) into spre (b shared doubles) instead of read from
+// the window's state.
+// BM: the largest block width b the caller passes (sizes the factorisation's local arrays).
+template <int BM = PEXP_MAX_RANK>
 __device__ __forceinline__ int block_orth_body(const WinLayout& L, double* D, int* I, int task, int pass, int step,
-                                               double defl, Parts gp, int kept, double* sG, double* Tout, bool owner) {
+                                               double defl, Parts gp, int kept, double* sG, double* Tout, bool owner,
+                                               Parts pp = Parts{nullptr, 0, 0}, int pre_off = 0,
+                                               double* spre = nullptr) {
     const int b = I[WI_B];
     if (gp.part) {
         for (int e = 0; e < b * b; ++e) {
@@ -78,11 +85,17 @@ __device__ __forceinline__ int block_orth_body(const WinLayout& L, double* D, in
             if (threadIdx.x == 0) sG[e] = v;
         }
     }
+    if (pass == 1 && pp.part) {
+        for (int c = 0; c < b; ++c) {
+            const double v = parts_sum_warp(pp, task, pre_off + c);
+            if (threadIdx.x == 0) spre[c] = v;
+        }
+    }
     __syncwarp();
     if (threadIdx.x != 0) return 0;
     const double* G0 = D + L.off_gw;
-    double G[PEXP_MAX_RANK * PEXP_MAX_RANK], R[PEXP_MAX_RANK * PEXP_MAX_RANK];
-    int perm[PEXP_MAX_RANK];
+    double G[BM * BM], R[BM * BM];
+    int perm[BM];
     for (int e = 0; e < b * b; ++e) {
         G[e] = gp.part ? sG[e] : G0[e];
         R[e] = 0.0;
@@ -98,7 +111,7 @@ __device__ __forceinline__ int block_orth_body(const WinLayout& L, double* D, in
         const int wc = (L.ycols - 1) * b;
         double pre = 0.0;
         for (int c = 0; c < b; ++c)
-            pre = fmax(pre, gp.part ? o1[step * b * b + c] : o1[(step * b + c) + (wc + c) * ldo]);
+            pre = fmax(pre, pp.part ? spre[c] : gp.part ? o1[step * b * b + c] : o1[(step * b + c) + (wc + c) * ldo]);
         lim2 = defl * defl * pre;
         if (owner) D[L.off_scal + WS_PRE] = sqrt(pre);
     } else {
@@ -127,7 +140,7 @@ __device__ __forceinline__ int block_orth_body(const WinLayout& L, double* D, in
         ++r;
     }
     // T = P[:, 0:r] R[0:r, 0:r]^{-1}
-    double Ri[PEXP_MAX_RANK * PEXP_MAX_RANK];
+    double Ri[BM * BM];
     for (int e = 0; e < b * b; ++e) Ri[e] = 0.0;
     for (int j = 0; j < r; ++j) {
         Ri[j + j * b] = 1.0 / R[j + j * b];

@@ -412,6 +412,17 @@ struct Solver {
                o->krylov == PEXP_KRYLOV_SAI && !(o->diagnostics & PEXP_DIAG_NOCOOP) &&
                krylov_geom(1, n).nchunks < 3 * kNumSM;
     }
+    // Separate launches with the partial-sum and Cholesky-QR kernels folded into the passes of
+    // part B (update0 sums h1, scale_proj and scale factor their QRs): a single window (a link
+    // of the chain, where 3 fewer launches per step pay; in the batched phase every CTA re-summing
+    // the partials costs more than the launches it saves: 2^20 points, 152.4 against 150.0 ms),
+    // its basis in the fused width range, and the step not cooperative
+    bool fold_ok(const std::vector<Win<T>>& act, int step) const {
+        if (act.size() != 1 || coop_ok(act)) return false;
+        for (const auto& W : act)
+            if (!proj_fused(step * W.b, W.b, sizeof(T))) return false;
+        return true;
+    }
     // after the cooperative launches: a bounded grid barrier that gave up ends the solve
     void check_coop() {
         if (!coop_used) return;
@@ -564,7 +575,7 @@ struct Solver {
             // Galerkin matrix, its exponential, the convergence test) runs on the second stream
             // beside them: it is FP64-bound on one SM per window, the passes are HBM-bound
             cudaEventRecord(c->ev_sp, st);
-            timed(c, PEXP_KC_SMALL, 0.0, [&] {
+            if (!fold_ok(act, step)) timed(c, PEXP_KC_SMALL, 0.0, [&] {
                 for (int a0 = 0; a0 < na;) {
                     int a1 = a0;
                     while (a1 < na && act[a1].b == act[a0].b) ++a1;
@@ -715,8 +726,47 @@ struct Solver {
                     a0 = a1;
                 }
             };
-            // pass 1: W <- W - V h1 (Gram of the result), Cholesky QR with deflation
             const double alg_upd = (double)n * (pb * w + 2 * bb * w);
+            if (fold_ok(act, step)) {
+                // partial sums: Gram of pass 1 | h2 | Gram of pass 2, each pass's in its own
+                // region (a kernel reads one pass's partials while writing the next one's)
+                const size_t rg = (size_t)nb * gb.nchunks * psg, rh = (size_t)nb * gb.nchunks * ps2;
+                double* pg1 = kpart[1];
+                double* ph2 = pg1 + rg;
+                double* pg2 = ph2 + rh;
+                const int ps1 = (jac ? 5 : 3) * step * bmb * bmb + bmb;   // projection partial stride
+                timed(c, PEXP_KC_UPDATE, (double)n * (pb * w + 2 * bb * wl_), [&] {
+                    groups([&](int a0, int a1, int b) {
+                        launch_update0_h<T>(d1 + a0, a1 - a0, b, step * b, n, gb, pg1 + (size_t)a0 * gb.nchunks * psg, psg,
+                                            kpart[0] + (size_t)a0 * gb.nchunks * ps1, ps1, 2 * step * b * b, st);
+                        check_launch(c);
+                    });
+                }, nullptr, false, alg_upd);
+                timed(c, PEXP_KC_UPDATE, (double)n * (pb * w + 2 * bb * wl_), [&] {
+                    groups([&](int a0, int a1, int b) {
+                        launch_scale_proj_qr<T>(d3 + a0, a1 - a0, b, n, gb, ph2 + (size_t)a0 * gb.nchunks * ps2, ps2, L, wd, wi,
+                                                d_wl2 + a0, step, defl, pg1 + (size_t)a0 * gb.nchunks * psg, psg,
+                                                kpart[0] + (size_t)a0 * gb.nchunks * ps1, ps1, 3 * step * b * b, st);
+                        check_launch(c);
+                    });
+                }, nullptr, false, alg_upd);
+                timed(c, PEXP_KC_UPDATE, (double)n * (pb * w + 2 * bb * wl_), [&] {
+                    groups([&](int a0, int a1, int b) {
+                        launch_update<T>(d2 + a0, a1 - a0, b, step * b, n, 1, gb, pg2 + (size_t)a0 * gb.nchunks * psg, psg, st,
+                                         ph2 + (size_t)a0 * gb.nchunks * ps2, ps2);
+                        check_launch(c);
+                    });
+                }, nullptr, false, alg_upd);
+                timed(c, PEXP_KC_UPDATE, (double)n * bb * (wl_ + w), [&] {
+                    groups([&](int a0, int a1, int b) {
+                        launch_scale_qr<T>(d4 + a0, a1 - a0, b, n, gb, L, wd, wi, d_wl2 + a0, step, defl,
+                                           pg2 + (size_t)a0 * gb.nchunks * psg, psg, st);
+                        check_launch(c);
+                    });
+                }, nullptr, false, 2.0 * n * bb * w);
+                return;
+            }
+            // pass 1: W <- W - V h1 (Gram of the result), Cholesky QR with deflation
             timed(c, PEXP_KC_UPDATE, (double)n * (pb * w + 2 * bb * wl_), [&] {
                 groups([&](int a0, int a1, int b) {
                     launch_update<T>(d1 + a0, a1 - a0, b, step * b, n, 0, gb, kpart[1] + (size_t)a0 * gb.nchunks * psg, psg, st);

@@ -2,7 +2,8 @@
 
 A single-column window on a periodic operator (every link of the homogeneous chain) runs its
 three shift-and-invert passes as one grid-synchronised launch, and the four Gram-Schmidt
-passes with their two Cholesky QRs as another.  They keep the chunking and the fixed-order
+passes with their two Cholesky QRs as another (the separate launches fold the QRs and the
+h1 sums into the passes, 4 launches).  They keep the chunking and the fixed-order
 partial sums of the separate kernels, so the outputs must agree bit for bit with the run
 that PEXP_DIAG_NOCOOP forces onto the separate launches; the launch count shows that the
 cooperative path ran.
@@ -46,8 +47,8 @@ def test_cooperative_chain_is_bitwise_the_separate_launches(c, prec, n, P, tol):
     assert r1["rc"] == 0 and r2["rc"] == 0, (r1["rc"], r2["rc"])
     assert torch.equal(Y1, Y2)
     assert r1["k_hom_sum"] == r2["k_hom_sum"] and r1["k_nh_max"] == r2["k_nh_max"]
-    # each chain step: 2 launches instead of 9
-    assert r1["launches"] < r2["launches"] - 4 * r1["k_hom_sum"], (r1["launches"], r2["launches"], r1["k_hom_sum"])
+    # each chain step: 5 launches instead of 9 (SAI 1 + 3, part B 1 + 4)
+    assert r1["launches"] <= r2["launches"] - 3 * r1["k_hom_sum"], (r1["launches"], r2["launches"], r1["k_hom_sum"])
     assert np.isfinite(Y1.double().numpy()).all()
 
 
