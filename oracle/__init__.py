@@ -11,12 +11,12 @@ arXiv:1509.04567) it follows.  Library primitives (sparse LU, Householder QR,
 SVD, cubic spline, dense expm) serve as single steps; nothing is blocked,
 fused or reordered beyond what the paper states.
 """
-from .pebk import (operator_matrix, apply_A, partition, compress_source, spline_segments,
+from .pebk import (operator_matrix, apply_A, partition, sample_partition, compress_source, spline_segments,
                    KrylovOperator, block_krylov_step, projected_source_window,
                    projected_homogeneous, ebk_nonhomogeneous, ebk_homogeneous,
                    solve_linear, burgers_source, solve_burgers)
 
-__all__ = ["operator_matrix", "apply_A", "partition", "compress_source", "spline_segments",
+__all__ = ["operator_matrix", "apply_A", "partition", "sample_partition", "compress_source", "spline_segments",
            "KrylovOperator", "block_krylov_step", "projected_source_window",
            "projected_homogeneous", "ebk_nonhomogeneous", "ebk_homogeneous", "solve_linear",
            "burgers_source", "solve_burgers"]

@@ -12,6 +12,12 @@ Readings of points the paper leaves open:
     spline through the samples of each subinterval (a line / parabola for 2 / 3
     samples);
   * subinterval boundaries snap to the output grid: T_j = t_floor(j (n_out-1) / P);
+  * source samples: by default the output times inside each subinterval; with
+    nodes=1 the s = n_samp Chebyshev points of each subinterval (Sec. 3), read as the
+    Chebyshev extrema T_{j-1} + dT_j (1 - cos(pi i/(s-1)))/2, i = 0..s-1, so that both
+    ends are samples (shared by neighbouring subintervals) and the cubic spline through
+    them covers the whole subinterval; the projected solution is then evaluated at the
+    output times, from the state at the knot before each one;
   * the Krylov space is either the polynomial block Krylov space of eq.
     blockKrylovSubspace (krylov=0) or its shift-and-invert form (krylov=1,
     Sec. 2.1, the acceleration the paper cites);
@@ -30,9 +36,15 @@ Readings of points the paper leaves open:
     max_i ||u_{k+1}(t_i) - u_k(t_i)|| / max_i ||u_{k+1}(t_i)|| <= wr_tol, or once that
     update has grown in wr_diverge (default 3) successive iterations (divergence; the
     paper states no rule for it).
-  * restarting after restart_len block steps is not carried out: the Krylov
-    space grows up to restart_len * (max_restarts + 1) block steps and a
-    subproblem that has not converged by then is reported as such;
+  * restarting ("restarted every 20 iterations", Sec. 3): with max_restarts = 0 the Krylov
+    space grows up to restart_len block steps; with max_restarts > 0 a subproblem that has
+    not converged after restart_len block steps of a cycle starts a new cycle that solves
+    for the error of the cycles so far.  That error e obeys e' = A e + r(t) with the
+    residual r(t) = (A V_c - V_c H_c) y_c(t) of the cycle's Galerkin solution, whose spatial
+    factor (I - V_c V_c^T) A V_c has rank b (the block width): the new cycle's Krylov space
+    starts from its range, and its projected problem is coupled to the previous cycle's
+    through Q^T A V_c, so that all cycles together form one block lower-triangular projected
+    system, solved exactly as one (restart_len (max_restarts + 1) block steps at most);
   * the averaged-Jacobian waveform relaxation (eq. ivp4 with the per-subinterval
     average of eq. piecewiseJac) averages over each subinterval by the trapezoidal
     rule on its samples; the Jacobian is linear in the state for the quadratic
@@ -58,6 +70,8 @@ BC_PERIODIC = 0
 BC_DIRICHLET0 = 1
 KRYLOV_POLY = 0
 KRYLOV_SAI = 1
+NODES_UNIFORM = 0
+NODES_CHEBYSHEV = 1
 
 
 # --------------------------------------------------------------------------------------
@@ -117,6 +131,33 @@ def partition(n_out: int, P: int) -> list[int]:
     idx = [(j * (n_out - 1)) // P for j in range(P + 1)]
     assert all(idx[j + 1] > idx[j] for j in range(P))
     return idx
+
+
+def sample_partition(opts: dict):
+    """Source sample times of the subintervals (Sec. 2.2, Sec. 3).
+
+    Returns (ts, sidx): subinterval j's samples are ts[sidx[j-1] : sidx[j]+1] (both ends
+    included, an end shared with the neighbour).  nodes=0 (default): the output times,
+    sidx = partition(n_out, P).  nodes=1: s = n_samp Chebyshev extrema per subinterval
+    [T_{j-1}, T_j], tau_i = dT_j (1 - cos(pi i / (s-1))) / 2, sidx[j] = j (s-1); "the sample
+    points per subinterval are Chebyshev nodes" (Sec. 3).  The boundaries T_j are those of
+    partition() in both cases."""
+    T, P, n_out = opts["T"], opts["P"], opts["n_out"]
+    t = np.arange(n_out) * (T / (n_out - 1))
+    idx = partition(n_out, P)
+    if opts.get("nodes", NODES_UNIFORM) == NODES_UNIFORM:
+        return t, idx
+    s = int(opts["n_samp"])
+    if s < 2:
+        raise ValueError("need n_samp >= 2")
+    ts = np.zeros(P * (s - 1) + 1)
+    for j in range(1, P + 1):
+        a, b = t[idx[j - 1]], t[idx[j]]
+        tau = (b - a) * (1.0 - np.cos(np.pi * np.arange(s) / (s - 1))) / 2.0
+        ts[(j - 1) * (s - 1):j * (s - 1) + 1] = a + tau
+        ts[(j - 1) * (s - 1)] = a
+        ts[j * (s - 1)] = b
+    return ts, [j * (s - 1) for j in range(P + 1)]
 
 
 def compress_source(Ghat: np.ndarray, svd_tol: float, max_rank: int):
@@ -207,6 +248,49 @@ def block_krylov_step(kop: KrylovOperator, V: np.ndarray, last: np.ndarray, defl
 # --------------------------------------------------------------------------------------
 # Projected problems
 # --------------------------------------------------------------------------------------
+def _cubic_step(H: np.ndarray, B: np.ndarray, y: np.ndarray, h: float, c: np.ndarray) -> np.ndarray:
+    """y(theta = h) for y' = H y + B sum_l c_l theta^l from y(0) = y: the augmented-matrix
+    exponential of projected_source_window over one step of length h."""
+    K = H.shape[0]
+    m = B.shape[1]
+    M = np.zeros((K + 4 * m, K + 4 * m))
+    M[:K, :K] = h * H
+    M[:K, K:K + m] = h * B
+    for l in range(3):
+        M[K + l * m:K + (l + 1) * m, K + (l + 1) * m:K + (l + 2) * m] = np.eye(m)
+    E = sla.expm(M)
+    ynew = E[:K, :K] @ y
+    for l in range(4):
+        ynew = ynew + math.factorial(l) * h ** l * (E[:K, K + l * m:K + (l + 1) * m] @ c[l])
+    return ynew
+
+
+def projected_source_at(H: np.ndarray, B: np.ndarray, knots: np.ndarray, coef: np.ndarray,
+                        t_eval: np.ndarray) -> np.ndarray:
+    """Exact solution of y' = H y + B p(t), y(knots_0) = 0, at the times t_eval (offsets in
+    [knots_0, knots_-1]), for a cubic spline p with arbitrary knots (Chebyshev samples).
+
+    The state is carried from knot to knot (one augmented-matrix exponential per knot
+    interval, as in projected_source_window); a time inside a knot interval is reached from
+    the state at the knot before it with that interval's cubic.  Returns (len(t_eval), K)."""
+    K = H.shape[0]
+    s = knots.size
+    ys = [np.zeros(K)]
+    for r in range(s - 1):
+        ys.append(_cubic_step(H, B, ys[r], knots[r + 1] - knots[r], coef[r]))
+    Y = np.zeros((t_eval.size, K))
+    scale = knots[-1] - knots[0]
+    for q, te in enumerate(t_eval):
+        # the knot interval [knots_r, knots_{r+1}) holding te; te at a knot takes its state
+        r = int(np.searchsorted(knots, te, side="right")) - 1
+        r = min(max(r, 0), s - 1)
+        if abs(te - knots[r]) <= 1e-14 * scale:
+            Y[q] = ys[r]
+        else:
+            Y[q] = _cubic_step(H, B, ys[r], te - knots[r], coef[min(r, s - 2)])
+    return Y
+
+
 def projected_source_window(H: np.ndarray, B: np.ndarray, tau: np.ndarray, coef: np.ndarray) -> np.ndarray:
     """Exact solution of y' = H y + B p(t), y(tau_0) = 0 at the sample times tau.
 
@@ -254,23 +338,89 @@ def _grow(kop, V, AV, new):
     return V, AV
 
 
+def restart_block(Vc: np.ndarray, AVc: np.ndarray, width: int, rank_tol: float = 1e-10) -> np.ndarray:
+    """First block of the next restart cycle (Sec. 2.1, Sec. 3 "restarted every 20
+    iterations"; the residual-correction reading of the module docstring).
+
+    The Galerkin solution V_c y_c(t) of a cycle leaves the residual r(t) = Z y_c(t) with
+    Z = A V_c - V_c (V_c^T A V_c) = (I - V_c V_c^T) A V_c, of rank <= the block width in exact
+    arithmetic.  Returns an orthonormal basis of its range: the left singular vectors of Z
+    whose singular values exceed rank_tol * sigma_1, at most `width` of them."""
+    Z = AVc - Vc @ (Vc.T @ AVc)
+    Uz, sz, _ = np.linalg.svd(Z, full_matrices=False)
+    if sz.size == 0 or sz[0] == 0.0:
+        return Vc[:, :0]
+    r = min(int(np.sum(sz > rank_tol * sz[0])), width)
+    return Uz[:, :r]
+
+
+def coupled_galerkin(V: np.ndarray, AV: np.ndarray, cyc: list, first: list) -> np.ndarray:
+    """Projected matrix of the restarted method: the Galerkin blocks V_c^T A V_c of every
+    cycle c on the diagonal, and the coupling Q_{c+1}^T A V_c of cycle c+1's first block
+    (the range of cycle c's residual) to cycle c below it; zero elsewhere.
+    cyc[i]: cycle of column i; first[i]: column i is in the first block of a cycle > 0."""
+    H = V.T @ AV
+    c = np.asarray(cyc)
+    f = np.asarray(first, dtype=bool)
+    keep = (c[:, None] == c[None, :]) | (f[:, None] & (c[:, None] == c[None, :] + 1))
+    return np.where(keep, H, 0.0)
+
+
+class _Cycles:
+    """Column bookkeeping of the restart cycles of one Krylov solve."""
+
+    def __init__(self, width: int, restart_len: int | None):
+        self.restart_len = restart_len
+        self.cyc = [0] * width
+        self.first = [False] * width
+        self.c = 0          # current cycle
+        self.k0 = 0         # its first column
+        self.blocks = 1     # its blocks so far
+
+    def restart_due(self) -> bool:
+        return self.restart_len is not None and self.blocks >= self.restart_len
+
+    def add(self, width: int, restart: bool):
+        if restart:
+            self.c += 1
+            self.k0 = len(self.cyc)
+            self.blocks = 0
+        self.cyc += [self.c] * width
+        self.first += [restart] * width
+        self.blocks += 1
+
+    def H(self, V, AV):
+        if self.restart_len is None:
+            return V.T @ AV
+        return coupled_galerkin(V, AV, self.cyc, self.first)
+
+
 def ebk_nonhomogeneous(kop: KrylovOperator, U: np.ndarray, tau: np.ndarray, coef: np.ndarray,
-                       tol: float, scale_ref: float, kmax: int, defl_tol: float = 1e-10):
+                       tol: float, scale_ref: float, kmax: int, defl_tol: float = 1e-10,
+                       t_eval: np.ndarray | None = None, restart_len: int | None = None):
     """EBK for v' = A v + U p(t), v(tau_0) = 0 on one window (Sec. 2.1).
 
     Grows the block Krylov basis V (V_1 = U) one block step at a time, projects
     (H = V^T A V, B = V^T U), solves the projected problem exactly at the window's
-    sample times and stops when the change since the previous step is within tolerance.
-    Returns (V, Y) with v(tau_i) ~ V Y[i], and an info dict."""
+    sample times (or at t_eval, when the samples are not the output times) and stops when
+    the change since the previous step is within tolerance.  With restart_len, a cycle of
+    restart_len blocks that has not converged is followed by a restart cycle (restart_block,
+    coupled_galerkin); the source enters the first cycle only.
+    Returns (V, Y) with v(tau_i) ~ V Y[i] (v(t_eval_i) with t_eval), and an info dict."""
     V = U.copy()
     AV = kop.A @ V
     last = U
     prev = None
-    info = dict(steps=0, converged=False, est=np.inf, dims=[])
+    cy = _Cycles(U.shape[1], restart_len)
+    info = dict(steps=0, converged=False, est=np.inf, dims=[], restarts=0)
     for k in range(1, kmax + 1):
-        H = V.T @ AV
+        H = cy.H(V, AV)
         B = V.T @ U
-        Y = projected_source_window(H, B, tau, coef)
+        B[np.asarray(cy.cyc) > 0] = 0.0
+        if t_eval is None:
+            Y = projected_source_window(H, B, tau, coef)
+        else:
+            Y = projected_source_at(H, B, tau, coef, t_eval)
         scale = max(scale_ref, float(np.max(np.linalg.norm(Y, axis=1))))
         info["steps"] = k
         info["dims"].append(V.shape[1])
@@ -285,30 +435,39 @@ def ebk_nonhomogeneous(kop: KrylovOperator, U: np.ndarray, tau: np.ndarray, coef
         prev = Y
         if k == kmax:
             break
-        new = block_krylov_step(kop, V, last, defl_tol)
+        restart = cy.restart_due()
+        if restart:
+            new = restart_block(V[:, cy.k0:], AV[:, cy.k0:], last.shape[1])
+            info["restarts"] += 1
+        else:
+            new = block_krylov_step(kop, V[:, cy.k0:], last, defl_tol)
         if new.shape[1] == 0:  # invariant subspace: the projection is exact
             info["converged"] = True
             info["est"] = 0.0
             return V, Y, info
         V, AV = _grow(kop, V, AV, new)
+        cy.add(new.shape[1], restart)
         last = new
     return V, prev, info
 
 
 def ebk_homogeneous(kop: KrylovOperator, w: np.ndarray, tau: np.ndarray, tol: float, scale_ref: float,
-                    kmax: int, defl_tol: float = 1e-10):
+                    kmax: int, defl_tol: float = 1e-10, restart_len: int | None = None):
     """EBK for v' = A v, v(tau_0) = w on one window: single-vector Krylov space of w,
-    projected solution exp(tau H) ||w|| e_1, same stopping rule as the source part."""
+    projected solution exp(tau H) ||w|| e_1, same stopping rule and restarts as the source
+    part."""
     beta = float(np.linalg.norm(w))
     if beta == 0.0:
-        return w[:, None] * 0.0, np.zeros((tau.size, 1)), dict(steps=0, converged=True, est=0.0, dims=[])
+        return w[:, None] * 0.0, np.zeros((tau.size, 1)), dict(steps=0, converged=True, est=0.0, dims=[],
+                                                               restarts=0)
     V = (w / beta)[:, None]
     AV = kop.A @ V
     last = V
     prev = None
-    info = dict(steps=0, converged=False, est=np.inf, dims=[])
+    cy = _Cycles(1, restart_len)
+    info = dict(steps=0, converged=False, est=np.inf, dims=[], restarts=0)
     for k in range(1, kmax + 1):
-        H = V.T @ AV
+        H = cy.H(V, AV)
         Y = projected_homogeneous(H, beta, tau)
         scale = max(scale_ref, float(np.max(np.linalg.norm(Y, axis=1))))
         info["steps"] = k
@@ -324,12 +483,18 @@ def ebk_homogeneous(kop: KrylovOperator, w: np.ndarray, tau: np.ndarray, tol: fl
         prev = Y
         if k == kmax:
             break
-        new = block_krylov_step(kop, V, last, defl_tol)
+        restart = cy.restart_due()
+        if restart:
+            new = restart_block(V[:, cy.k0:], AV[:, cy.k0:], last.shape[1])
+            info["restarts"] += 1
+        else:
+            new = block_krylov_step(kop, V[:, cy.k0:], last, defl_tol)
         if new.shape[1] == 0:
             info["converged"] = True
             info["est"] = 0.0
             return V, Y, info
         V, AV = _grow(kop, V, AV, new)
+        cy.add(new.shape[1], restart)
         last = new
     return V, prev, info
 
@@ -346,30 +511,36 @@ def solve_linear(op: dict, opts: dict, u0: np.ndarray, G: np.ndarray | None,
     (eq. linivpSubproblem) solve the nonhomogeneous part on [T_{j-1}, T_j] and the
     homogeneous part on [T_j, T]; sum the subsolutions (eq. superposition).
 
-    G: (n_out, n) samples g(t_i) or None.  Returns Y (n_out, n) with Y[i] ~ u(t_i)
-    and a report.  `subintervals` restricts the sum to the given j (1-based) -- used
+    G: (n_out, n) samples g(t_i) or None; with Chebyshev samples (nodes=1) G holds g at the
+    sample times of sample_partition, shape (P (n_samp-1) + 1, n).  Returns Y (n_out, n)
+    with Y[i] ~ u(t_i) and a report.  `subintervals` restricts the sum to the given j (1-based) -- used
     to time a bounded sample and by superposition tests; u0 is then left out."""
     n = u0.size
     T, P, n_out = opts["T"], opts["P"], opts["n_out"]
     t = np.arange(n_out) * (T / (n_out - 1))
     idx = partition(n_out, P)
+    ts, sidx = sample_partition(opts)
+    cheb = opts.get("nodes", NODES_UNIFORM) != NODES_UNIFORM
     A = operator_matrix(op)
     Au0 = A @ u0
     kmax = opts["restart_len"] * (opts.get("max_restarts", 0) + 1)
+    rlen = opts["restart_len"] if opts.get("max_restarts", 0) > 0 else None
     tol = opts["tol"]
     scale_ref = float(np.linalg.norm(u0))
     js = list(range(1, P + 1)) if subintervals is None else list(subintervals)
     Y = np.zeros((n_out, n)) if subintervals is not None else np.tile(u0, (n_out, 1))
-    rep = dict(m=[], sigma_ratio=[], k_nh=[], est_nh=[], conv_nh=[], k_hom=[], conv_hom=[], boundaries=idx)
+    rep = dict(m=[], sigma_ratio=[], k_nh=[], est_nh=[], conv_nh=[], k_hom=[], conv_hom=[], boundaries=idx,
+               restarts_nh=[], restarts_hom=[])
     parts = {}
     # one shift-and-invert pole for all windows: gamma = sai_gamma * T / P
     kop = KrylovOperator(op, A, opts["krylov"], opts.get("sai_gamma", 0.1) * T / P)
     for j in js:
         i0, i1 = idx[j - 1], idx[j]
-        tau = t[i0:i1 + 1] - t[i0]
-        Ghat = np.tile(Au0[:, None], (1, i1 - i0 + 1))
+        s0, s1 = sidx[j - 1], sidx[j]
+        tau = ts[s0:s1 + 1] - ts[s0]
+        Ghat = np.tile(Au0[:, None], (1, s1 - s0 + 1))
         if G is not None:
-            Ghat = Ghat + G[i0:i1 + 1].T
+            Ghat = Ghat + G[s0:s1 + 1].T
         U, C, sig = compress_source(Ghat, opts["svd_tol"], opts["max_rank"])
         m = U.shape[1]
         rep["m"].append(m)
@@ -378,23 +549,26 @@ def solve_linear(op: dict, opts: dict, u0: np.ndarray, G: np.ndarray | None,
         if m == 0:
             rep["k_nh"].append(0); rep["est_nh"].append(0.0); rep["conv_nh"].append(True)
             rep["k_hom"].append([]); rep["conv_hom"].append([])
+            rep["restarts_nh"].append(0); rep["restarts_hom"].append([])
             parts[j] = vj
             continue
         coef = spline_segments(tau, C)
-        V, Yp, info = ebk_nonhomogeneous(kop, U, tau, coef, tol, scale_ref, kmax)
+        V, Yp, info = ebk_nonhomogeneous(kop, U, tau, coef, tol, scale_ref, kmax,
+                                         t_eval=(t[i0:i1 + 1] - t[i0]) if cheb else None, restart_len=rlen)
         rep["k_nh"].append(info["steps"]); rep["est_nh"].append(info["est"]); rep["conv_nh"].append(info["converged"])
+        rep["restarts_nh"].append(info["restarts"])
         vj[i0:i1 + 1] = Yp @ V.T
         w = vj[i1].copy()
-        khs, chs = [], []
+        khs, chs, rhs = [], [], []
         for mm in range(j + 1, P + 1):
             a0, a1 = idx[mm - 1], idx[mm]
             tau_h = t[a0:a1 + 1] - t[a0]
-            Vh, Yh, ih = ebk_homogeneous(kop, w, tau_h, tol, scale_ref, kmax)
-            khs.append(ih["steps"]); chs.append(ih["converged"])
+            Vh, Yh, ih = ebk_homogeneous(kop, w, tau_h, tol, scale_ref, kmax, restart_len=rlen)
+            khs.append(ih["steps"]); chs.append(ih["converged"]); rhs.append(ih["restarts"])
             seg = Yh @ Vh.T
             vj[a0 + 1:a1 + 1] = seg[1:]
             w = seg[-1].copy()
-        rep["k_hom"].append(khs); rep["conv_hom"].append(chs)
+        rep["k_hom"].append(khs); rep["conv_hom"].append(chs); rep["restarts_hom"].append(rhs)
         parts[j] = vj
         Y += vj
     if return_parts:
@@ -418,6 +592,7 @@ def solve_linear_piecewise(A_list: list, opts: dict, u0: np.ndarray, G_list: lis
     t = np.arange(n_out) * (T / (n_out - 1))
     idx = partition(n_out, P)
     kmax = opts["restart_len"] * (opts.get("max_restarts", 0) + 1)
+    rlen = opts["restart_len"] if opts.get("max_restarts", 0) > 0 else None
     tol = opts["tol"]
     scale_ref = float(np.linalg.norm(u0))
     gamma = opts.get("sai_gamma", 0.1) * T / P
@@ -433,14 +608,16 @@ def solve_linear_piecewise(A_list: list, opts: dict, u0: np.ndarray, G_list: lis
         if U.shape[1] == 0:
             rep["k_nh"].append(0); rep["conv_nh"].append(True); rep["k_hom"].append([]); rep["conv_hom"].append([])
             continue
-        V, Yp, info = ebk_nonhomogeneous(kops[j - 1], U, tau, spline_segments(tau, C), tol, scale_ref, kmax)
+        V, Yp, info = ebk_nonhomogeneous(kops[j - 1], U, tau, spline_segments(tau, C), tol, scale_ref, kmax,
+                                         restart_len=rlen)
         rep["k_nh"].append(info["steps"]); rep["conv_nh"].append(info["converged"])
         Y[i0:i1 + 1] += Yp @ V.T
         w = V @ Yp[-1]
         khs, chs = [], []
         for mm in range(j + 1, P + 1):
             a0, a1 = idx[mm - 1], idx[mm]
-            Vh, Yh, ih = ebk_homogeneous(kops[mm - 1], w, t[a0:a1 + 1] - t[a0], tol, scale_ref, kmax)
+            Vh, Yh, ih = ebk_homogeneous(kops[mm - 1], w, t[a0:a1 + 1] - t[a0], tol, scale_ref, kmax,
+                                         restart_len=rlen)
             khs.append(ih["steps"]); chs.append(ih["converged"])
             seg = Yh @ Vh.T
             Y[a0 + 1:a1 + 1] += seg[1:]

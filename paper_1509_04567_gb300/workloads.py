@@ -54,7 +54,7 @@ def default_opts(**kw) -> dict:
     o = dict(T=1.0, P=1, n_out=2, tol=1e-8, svd_tol=1e-12, max_rank=16,
              restart_len=20, max_restarts=0, krylov=1, sai_gamma=0.1,
              precision=0, wr_max_iter=50, wr_tol=1e-6, burgers_form=0, diagnostics=0, jacobian=0,
-             wr_diverge=3, sub_first=0, sub_last=0)
+             wr_diverge=3, sub_first=0, sub_last=0, nodes=0, n_samp=0)
     o.update(kw)
     return o
 
@@ -76,14 +76,31 @@ def out_times(T: float, n_out: int) -> np.ndarray:
     return np.arange(n_out, dtype=np.float64) * (T / (n_out - 1))
 
 
+def chebyshev_sample_times(T: float, P: int, n_out: int, n_samp: int) -> np.ndarray:
+    """Where a caller samples the source for Chebyshev sampling (Sec. 3): n_samp Chebyshev
+    extrema in each subinterval [T_{j-1}, T_j], both ends included and shared with the
+    neighbour, P (n_samp - 1) + 1 times in all.  The boundaries are output times,
+    T_j = t_floor(j (n_out-1)/P); subinterval j's i-th sample is
+    T_{j-1} + (T_j - T_{j-1}) (1 - cos(pi i / (n_samp - 1))) / 2."""
+    t = out_times(T, n_out)
+    bnd = [t[(j * (n_out - 1)) // P] for j in range(P + 1)]
+    i = np.arange(n_samp - 1, dtype=np.float64)
+    ts = [bnd[j] + (bnd[j + 1] - bnd[j]) * 0.5 * (1.0 - np.cos(np.pi * i / (n_samp - 1))) for j in range(P)]
+    return np.concatenate(ts + [np.array([bnd[P]])])
+
+
 def adv_diff_1d(n=1024, nu=1e-2, a=1.0, T=1.0, P=8, n_out=101, tol=1e-8,
                 svd_tol=1e-12, max_rank=16, with_source=True, **kw) -> Problem:
     """1D periodic advection-diffusion, u0 = sin(2 pi x) + exp(-100 (x-0.5)^2),
     g(x,t) = sin(4 pi x) cos(2 pi t).  At n=1024, nu=1e-2, P=8, n_out=101 this is
-    the small case; at n=2^20, nu=1e-3, P=64, n_out=1025 the large one."""
+    the small case; at n=2^20, nu=1e-3, P=64, n_out=1025 the large one.  With
+    nodes=1, n_samp=s the source is sampled at s Chebyshev points per subinterval
+    (chebyshev_sample_times) instead of at the output times."""
     x = grid_1d(n)
     u0 = np.sin(2 * np.pi * x) + np.exp(-100.0 * (x - 0.5) ** 2)
     t = out_times(T, n_out)
+    if kw.get("nodes", 0) == 1:
+        t = chebyshev_sample_times(T, P, n_out, kw["n_samp"])
     G = None
     if with_source:
         G = np.cos(2 * np.pi * t)[:, None] * np.sin(4 * np.pi * x)[None, :]

@@ -639,3 +639,128 @@ def test_picard_divergence_is_detected():
     d = rp["deltas"]
     assert rp["diverged"] and not rp["converged"] and len(d) < 30, d
     assert d[-1] > d[-2] > d[-3] > d[-4]
+
+
+# ---------------------------------------------------------------- Chebyshev sample nodes (Sec. 3)
+def test_chebyshev_samples_are_the_extrema_of_the_chebyshev_polynomial():
+    """The sample times of nodes=1: per subinterval, the ends and the zeros of T'_{s-1} (the
+    extrema of the Chebyshev polynomial) mapped onto [T_{j-1}, T_j]; the caller's sampling
+    (workloads) and the oracle's agree."""
+    from numpy.polynomial import chebyshev as npc
+    P, n_out, s = 3, 13, 7
+    opts = wl.default_opts(T=0.6, P=P, n_out=n_out, nodes=1, n_samp=s)
+    ts, sidx = ob.sample_partition(opts)
+    assert sidx == [0, 6, 12, 18] and ts.size == P * (s - 1) + 1
+    np.testing.assert_allclose(ts, wl.chebyshev_sample_times(0.6, P, n_out, s), rtol=0, atol=1e-15)
+    t = wl.out_times(0.6, n_out)
+    ext = np.sort(npc.Chebyshev.basis(s - 1).deriv().roots().real)   # interior extrema in (-1, 1)
+    for j, (i0, i1) in enumerate(zip(ob.partition(n_out, P)[:-1], ob.partition(n_out, P)[1:])):
+        a, b = t[i0], t[i1]
+        w = ts[sidx[j]:sidx[j + 1] + 1]
+        assert w[0] == a and w[-1] == b
+        # x = -cos(pi i/(s-1)) runs from -1 to 1: t = a + (b - a)(x + 1)/2
+        np.testing.assert_allclose(np.sort(2 * (w[1:-1] - a) / (b - a) - 1), ext, atol=1e-13)
+
+
+def _cubic_in_time_case(s):
+    n, nu, a = 256, 1e-2, 1.0
+    x = wl.grid_1d(n)
+    u0 = np.sin(2 * np.pi * x)
+    v = np.sin(4 * np.pi * x)
+    fc = np.array([1.0, 2.0, -3.0, 1.5])          # f(t) = sum_l fc_l t^l
+    opts = wl.default_opts(T=0.6, P=3, n_out=13, tol=1e-13, restart_len=40, nodes=1, n_samp=s)
+    ts, _ = ob.sample_partition(opts)
+    f = sum(fc[l] * ts ** l for l in range(4))
+    G = f[:, None] * v[None, :]
+    return n, nu, a, u0, v, fc, opts, G
+
+
+@pytest.mark.parametrize("s", [4, 7, 9])
+def test_chebyshev_samples_reproduce_a_cubic_source_exactly(s):
+    """A source cubic in time is its own spline on any knots, so with Chebyshev samples the
+    method is exact up to the Krylov tolerance: per Fourier mode,
+    u(t) = e^{lam t} u0 + sum_l l! fc_l t^{l+1} phi_{l+1}(lam t) v (the outputs lie between
+    the knots, so this pins the evaluation inside a knot interval)."""
+    n, nu, a, u0, v, fc, opts, G = _cubic_in_time_case(s)
+    Y, rep = ob.solve_linear(wl.make_op(n, nu, a), opts, u0, G)
+    assert all(rep["conv_nh"])
+    lam = cf.circulant_eigs(n, a, nu)
+    u0h, vh = np.fft.fft(u0), np.fft.fft(v)
+    for i, tt in enumerate(wl.out_times(0.6, 13)):
+        ph = cf.phi_functions(lam * tt)
+        yh = ph[0] * u0h + sum(math.factorial(l) * fc[l] * tt ** (l + 1) * ph[l + 1] * vh for l in range(4))
+        ref = np.real(np.fft.ifft(yh))
+        assert np.linalg.norm(Y[i] - ref) <= 1e-11 * np.linalg.norm(ref), i
+
+
+def test_chebyshev_samples_with_the_true_source():
+    """g = sin(4 pi x) cos(2 pi t) sampled at Chebyshev points: the solution stays within the
+    spline's time error of the exact semi-discrete one (per mode,
+    int_0^t e^{lam (t-s)} cos(w s) ds in closed form); samples taken at other times than the
+    solver assumes would be O(1e-2) off."""
+    n, nu, a, T, P, n_out, s = 512, 1e-2, 1.0, 1.0, 8, 101, 13
+    pr = wl.adv_diff_1d(n=n, nu=nu, a=a, T=T, P=P, n_out=n_out, tol=1e-12, restart_len=30, nodes=1, n_samp=s)
+    Y, rep = ob.solve_linear(pr.op, pr.opts, pr.u0, pr.G)
+    assert all(rep["conv_nh"])
+    x = wl.grid_1d(n)
+    lam = cf.circulant_eigs(n, a, nu)
+    u0h, gh = np.fft.fft(pr.u0), np.fft.fft(np.sin(4 * np.pi * x))
+    w = 2 * np.pi
+    err = 0.0
+    for i, tt in enumerate(wl.out_times(T, n_out)):
+        el = np.exp(lam * tt)
+        I = 0.5 * ((np.exp(1j * w * tt) - el) / (1j * w - lam) + (np.exp(-1j * w * tt) - el) / (-1j * w - lam))
+        ref = np.real(np.fft.ifft(el * u0h + I * gh))
+        err = max(err, np.linalg.norm(Y[i] - ref) / np.linalg.norm(ref))
+    assert err < 1e-6, err
+
+
+# ---------------------------------------------------------------- restarting (Sec. 2.1, Sec. 3)
+def _restart_err(krylov, n, nu, P, n_out, T, rl, mr):
+    pr = wl.adv_diff_1d(n=n, nu=nu, P=P, n_out=n_out, T=T, tol=1e-12, restart_len=rl, max_restarts=mr,
+                        krylov=krylov)
+    Y, rep = ob.solve_linear(pr.op, pr.opts, pr.u0, pr.G)
+    t, wins = cf.fourier_windows_from_oracle_model(pr.op, pr.opts, pr.u0, pr.G, ob.compress_source,
+                                                   ob.spline_segments, ob.partition)
+    Yx = cf.exact_piecewise_cubic(cf.circulant_eigs(n, 1.0, nu), pr.u0, t, wins)
+    return float(np.max(np.linalg.norm(Y - Yx, axis=1) / np.linalg.norm(Yx, axis=1))), rep
+
+
+def test_restarted_polynomial_krylov_matches_the_closed_form():
+    """Restart cycles of 4 and 6 block steps in the polynomial space: every subproblem restarts
+    and still converges to the exact solution with the same source model, in about as many
+    block steps in all as without restarts (the cycle's residual lies in the next block)."""
+    e0, r0 = _restart_err(0, 128, 1e-3, 4, 33, 0.25, 40, 0)
+    for rl, mr in ((4, 20), (6, 10)):
+        e, rep = _restart_err(0, 128, 1e-3, 4, 33, 0.25, rl, mr)
+        assert all(rep["conv_nh"]) and all(all(c) for c in rep["conv_hom"])
+        assert min(rep["restarts_nh"]) >= 2
+        assert e < 1e-11, (rl, e)
+        assert max(rep["k_nh"]) <= max(r0["k_nh"]) + 2
+
+
+def test_restarted_shift_and_invert_krylov_matches_the_closed_form():
+    """Restart cycles of 8 block steps in the shift-and-invert space, on a case that needs 24
+    steps without restarts: the restarted solve converges to the exact solution."""
+    e, rep = _restart_err(1, 1024, 1e-2, 4, 41, 1.0, 8, 10)
+    assert all(rep["conv_nh"]) and all(all(c) for c in rep["conv_hom"])
+    assert min(rep["restarts_nh"]) >= 2 and max(max(r) for r in rep["restarts_hom"] if r) >= 2
+    assert e < 1e-10, e
+
+
+@pytest.mark.parametrize("krylov", [0, 1])
+def test_restart_residual_has_the_block_rank(krylov):
+    """The residual factor (I - V V^T) A V of a block Krylov basis has rank b: its singular
+    values beyond the block width are at round-off level (what restart_block relies on)."""
+    n, b = 256, 2
+    pr = wl.adv_diff_1d(n=n, nu=1e-2, P=1, n_out=5)
+    A = ob.operator_matrix(pr.op)
+    kop = ob.KrylovOperator(pr.op, A, krylov, 0.01)
+    V, _ = np.linalg.qr(np.column_stack([pr.u0, np.sin(4 * np.pi * wl.grid_1d(n))]))
+    last = V
+    for _ in range(4):
+        new = ob.block_krylov_step(kop, V, last)
+        V, last = np.hstack([V, new]), new
+    Z = A @ V - V @ (V.T @ (A @ V))
+    sv = np.linalg.svd(Z, compute_uv=False)
+    assert sv[b] < 1e-8 * sv[0], sv[:b + 2]
