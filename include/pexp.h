@@ -74,6 +74,9 @@ extern "C" {
 #define PEXP_F64 0
 #define PEXP_F32 1
 
+#define PEXP_NODES_UNIFORM   0   /* source sampled at the output times (Sec. 4's uniform samples) */
+#define PEXP_NODES_CHEBYSHEV 1   /* source sampled at n_samp Chebyshev points per subinterval (Sec. 3) */
+
 /* ---------------------------------------------------------------- descriptors */
 /* The operator A of eq. ivp2: second-order central differences of
  * -a u_x + nu u_xx (Sec. 3.1), per dimension; 2D is the sum A_x + A_y.
@@ -92,12 +95,19 @@ typedef struct {
 typedef struct {
     double T;            /* final time */
     int    P;            /* number of subintervals, 1 <= P <= n_out-1 (Sec. 2.2) */
-    int    n_out;        /* number of output (= source sample) times, >= 2 */
+    int    n_out;        /* number of output times, >= 2 (the source sample times unless nodes = 1) */
     double tol;          /* relative tolerance of each EBK subproblem (Sec. 3, "tol") */
     double svd_tol;      /* keep singular values sigma_i > svd_tol*sigma_1 (Sec. 2.1) */
     int    max_rank;     /* cap on the retained rank m = block width, <= PEXP_MAX_RANK */
     int    restart_len;  /* block steps per Krylov cycle (Sec. 3: 20) */
-    int    max_restarts; /* extra cycles; the step budget is restart_len*(max_restarts+1) */
+    int    max_restarts; /* restart cycles after the first (Sec. 2.1, Sec. 3); the step budget is
+                          * restart_len*(max_restarts+1) <= PEXP_MAX_STEPS.  0: one cycle that may grow to
+                          * restart_len steps.  > 0: a subproblem not converged after restart_len steps of
+                          * a cycle starts a new cycle for the error of the cycles so far, from the range
+                          * of the cycle's rank-b residual (I - V V^T) A V, coupled to the previous cycle
+                          * in one block lower-triangular projected problem; each cycle orthogonalises
+                          * against its own blocks only.  Restarted solves run the dense-projection
+                          * driver (not the fused kernels); report.sub_restarts counts the cycles. */
     int    krylov;       /* PEXP_KRYLOV_* */
     double sai_gamma;    /* SAI pole gamma = sai_gamma * T / P (nominal subinterval length) */
     int    precision;    /* PEXP_FP64 or PEXP_MIXED */
@@ -115,6 +125,16 @@ typedef struct {
      * of disjoint ranges add up to the full solve (the subintervals split over several GPUs). */
     int    sub_first;
     int    sub_last;
+    /* Linear solves: where the source is sampled (Sec. 3: "the sample points per subinterval
+     * are Chebyshev nodes").  PEXP_NODES_UNIFORM (default): at the output times, G has n_out
+     * rows.  PEXP_NODES_CHEBYSHEV: at n_samp (2 .. PEXP_MAX_SAMPLES) Chebyshev extrema of every
+     * subinterval [T_{j-1}, T_j], the i-th at T_{j-1} + (T_j - T_{j-1}) (1 - cos(pi i/(n_samp-1)))/2,
+     * both ends included and shared with the neighbour: G has P*(n_samp-1)+1 rows, subinterval
+     * j's (1-based) at rows (j-1)*(n_samp-1) .. j*(n_samp-1).  The cubic spline of the source
+     * model runs through these samples and the outputs stay at the uniform times.  Not for
+     * pexp_solve_burgers (PEXP_ERR_UNSUPPORTED), whose source samples are its iterate's. */
+    int    nodes;
+    int    n_samp;
 } pexp_options;
 
 #define PEXP_DIAG_ORTH  1   /* measure the orthogonality of every Krylov basis */
@@ -203,7 +223,8 @@ const char* pexp_status_string(int status);
  *   y0_dev: n FP64 values (always FP64: the shift g_hat = A u0 + g of eq. linivp_shift
  *   multiplies the rounding error of u0 by ||A||, up to ~4e9 on fine meshes, so u0 must
  *   carry full precision whatever the precision of the solve).  G_dev: n_out*n source samples g(t_i)
- *   (time-major, dtype g_dtype) or NULL for g = 0.  Y_dev: n_out*n outputs
+ *   (time-major, dtype g_dtype; with opts->nodes = PEXP_NODES_CHEBYSHEV, P*(n_samp-1)+1 samples at
+ *   the Chebyshev points) or NULL for g = 0.  Y_dev: n_out*n outputs
  *   u(t_i) (time-major, dtype y_dtype); must not overlap G_dev or y0_dev.
  * Returns PEXP_ERR_NOT_CONVERGED (outputs still written) when a Krylov solve missed tol. */
 int pexp_solve_linear(pexp_ctx* ctx, const pexp_operator* op, const pexp_options* opts,

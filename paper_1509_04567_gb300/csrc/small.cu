@@ -47,6 +47,7 @@ WinLayout make_layout(int s_max, int b_max, int kmax, int ycols) {
     L.off_Yp = take((int64_t)s_max * L.K_max);
     L.off_scal = take(WS_COUNT);
     L.off_scr = take((int64_t)9 * L.N_max * L.N_max);
+    L.off_yk = take((int64_t)2 * L.K_max);
     L.stride = o;
     L.istride = WI_COUNT;
     return L;
@@ -498,6 +499,70 @@ void launch_block_orth(const WinLayout& L, double* wd, int* wi, const int* wins,
 // with sigma_0, sigma_{s-1} eliminated by the not-a-knot conditions
 // (continuous third derivative at tau_1 and tau_{s-2}).
 // =====================================================================================
+// Chebyshev knots of a window of length dT: tau_i = dT (1 - cos(pi i/(s-1))) / 2 (both ends exact).
+__device__ __forceinline__ double cheb_knot(int i, int s, double dT) {
+    if (i <= 0) return 0.0;
+    if (i >= s - 1) return dT;
+    return 0.5 * dT * (1.0 - cospi((double)i / (double)(s - 1)));
+}
+
+// The same not-a-knot spline through s samples at the Chebyshev knots of a window of length dT
+// (spacings h_r = tau_{r+1} - tau_r):
+//   h_{i-1} sigma_{i-1} + 2 (h_{i-1} + h_i) sigma_i + h_i sigma_{i+1}
+//       = 6 ((y_{i+1} - y_i)/h_i - (y_i - y_{i-1})/h_{i-1}),  i = 1 .. s-2,
+// with sigma_0 = sigma_1 + (h_0/h_1)(sigma_1 - sigma_2) and
+// sigma_{s-1} = sigma_{s-2} + (h_{s-2}/h_{s-3})(sigma_{s-2} - sigma_{s-3}) (not-a-knot) substituted
+// into the first and last rows; a line for 2 samples, the parabola through 3.
+template <typename Y, typename Put>
+__device__ void spline_knots(int s, double dT, Y y, Put put) {
+    double hk[PEXP_MAX_SAMPLES];
+    for (int r = 0; r + 1 < s; ++r) hk[r] = cheb_knot(r + 1, s, dT) - cheb_knot(r, s, dT);
+    if (s == 2) {
+        put(0, y(0), (y(1) - y(0)) / hk[0], 0.0, 0.0);
+        return;
+    }
+    if (s == 3) {
+        const double f01 = (y(1) - y(0)) / hk[0], f12 = (y(2) - y(1)) / hk[1];
+        const double f012 = (f12 - f01) / (hk[0] + hk[1]);
+        put(0, y(0), f01 - f012 * hk[0], f012, 0.0);
+        put(1, y(1), f01 + f012 * hk[0], f012, 0.0);
+        return;
+    }
+    double sig[PEXP_MAX_SAMPLES], cp[PEXP_MAX_SAMPLES];
+    const int nI = s - 2;
+    for (int i = 1; i <= nI; ++i) {
+        const double h0 = hk[i - 1], h1 = hk[i];
+        const double rhs = 6.0 * ((y(i + 1) - y(i)) / h1 - (y(i) - y(i - 1)) / h0);
+        double a = h0, d = 2.0 * (h0 + h1), c = h1;
+        if (i == 1) {   // sigma_0 eliminated
+            d += h0 * (1.0 + h0 / h1);
+            c -= h0 * h0 / h1;
+            a = 0.0;
+        }
+        if (i == nI) {  // sigma_{s-1} eliminated
+            d += h1 * (1.0 + h1 / h0);
+            a -= h1 * h1 / h0;
+            c = 0.0;
+        }
+        if (i == 1) {
+            cp[i] = c / d;
+            sig[i] = rhs / d;
+        } else {
+            const double m = d - a * cp[i - 1];
+            cp[i] = c / m;
+            sig[i] = (rhs - a * sig[i - 1]) / m;
+        }
+    }
+    for (int i = nI - 1; i >= 1; --i) sig[i] -= cp[i] * sig[i + 1];
+    sig[0] = sig[1] + hk[0] / hk[1] * (sig[1] - sig[2]);
+    sig[s - 1] = sig[s - 2] + hk[s - 2] / hk[s - 3] * (sig[s - 2] - sig[s - 3]);
+    for (int r = 0; r < s - 1; ++r) {
+        const double hr = hk[r];
+        const double c1 = (y(r + 1) - y(r)) / hr - hr * (2.0 * sig[r] + sig[r + 1]) / 6.0;
+        put(r, y(r), c1, 0.5 * sig[r], (sig[r + 1] - sig[r]) / (6.0 * hr));
+    }
+}
+
 __global__ void k_spline(WinLayout L, double* __restrict__ wd, int* __restrict__ wi, const int* __restrict__ wins,
                          double h) {
     const int w = wins[blockIdx.x];
@@ -515,6 +580,10 @@ __global__ void k_spline(WinLayout L, double* __restrict__ wd, int* __restrict__
         cf[(r * 4 + 2) * L.b_max + k] = c2;
         cf[(r * 4 + 3) * L.b_max + k] = c3;
     };
+    if (I[WI_CHEB]) {
+        spline_knots(s, (I[WI_SOUT] - 1) * h, y, put);
+        return;
+    }
     if (s == 2) {
         put(0, y(0), (y(1) - y(0)) / h, 0.0, 0.0);
         return;
@@ -574,10 +643,95 @@ void launch_spline(const WinLayout& L, double* wd, int* wi, const int* wins, int
 //   4. est = max_r ||y_step(tau_r) - y_{step-1}(tau_r)||, converged when
 //      step >= 2 and est <= tol * max(scale_ref, max_r ||y(tau_r)||).
 // =====================================================================================
+// One step of length hh of the projected source problem from the state yin: the exponential of
+// the augmented matrix M(hh) (as in k_project), then
+//   yout = e^{hh H} yin + sum_l l! hh^l [hh phi_{l+1}(hh H) E_1] c_{r,l}
+// with the cubic coefficients of knot interval r.  yout: K_max entries (zero beyond K).
+__device__ void project_step(const WinLayout& L, const double* D, const double* H, int K, int b, int N, double hh,
+                             int r, const double* yin, double* yout, double* M, double* E, double* work) {
+    const int KM = L.K_max;
+    for (int e = threadIdx.x; e < N * N; e += blockDim.x) {
+        const int i = e % N, j = e / N;
+        double v = 0.0;
+        if (i < K && j < K) v = hh * H[i + j * KM];
+        else if (i < b && j >= K && j < K + b && (j - K) == i) v = hh;
+        else if (i >= K && j >= K) {
+            const int bi = (i - K) / b, bj = (j - K) / b;
+            if (bj == bi + 1 && (i - K) % b == (j - K) % b) v = 1.0;
+        }
+        M[e] = v;
+    }
+    __syncthreads();
+    cta_expm(M, N, E, work);
+    const double* cf = D + L.off_coef;
+    for (int a = threadIdx.x; a < KM; a += blockDim.x) {
+        double v = 0.0;
+        if (a < K) {
+            for (int j = 0; j < K; ++j) v = fma(E[a + j * N], yin[j], v);
+            double f = 1.0, hl = 1.0;
+            for (int l = 0; l < 4; ++l) {
+                double t = 0.0;
+                for (int k = 0; k < b; ++k) t = fma(E[a + (K + l * b + k) * N], cf[(r * 4 + l) * L.b_max + k], t);
+                v = fma(f * hl, t, v);
+                hl *= hh;
+                f *= (double)(l + 1);
+            }
+        }
+        yout[a] = v;
+    }
+    __syncthreads();
+}
+
+// Projected source problem of a window sampled at its s Chebyshev knots (the spline's knots),
+// solved at its srow output times q h, q = 0 .. srow-1: the state is carried from knot to
+// knot, and an output time inside a knot interval is reached from the state at the knot
+// before it with that interval's cubic (output times at a knot take its state).  Y's rows
+// are the output times; the previous step's rows go to Yp first.
+__device__ void project_cheb(const WinLayout& L, double* D, const double* H, int K, int b, int N, int s, int srow,
+                             double h, double* M, double* E, double* work) {
+    const int KM = L.K_max;
+    double* Y = D + L.off_Y;
+    double* Yp = D + L.off_Yp;
+    const int Kp = K - b;
+    for (int e = threadIdx.x; e < srow * KM; e += blockDim.x) {
+        const int a = e % KM;
+        Yp[e] = (a < Kp) ? Y[e] : 0.0;
+    }
+    __syncthreads();
+    double* yc = D + L.off_yk;   // state at the current knot
+    double* yn = yc + KM;
+    for (int a = threadIdx.x; a < KM; a += blockDim.x) Y[a] = yc[a] = 0.0;
+    __syncthreads();
+    const double dT = (srow - 1) * h;
+    const double eps = 1e-14 * dT;
+    int q = 1;
+    for (int r = 0; r + 1 < s; ++r) {
+        const double ta = cheb_knot(r, s, dT), tb = cheb_knot(r + 1, s, dT);
+        for (; q < srow && q * h < tb - eps; ++q) {
+            double* yq = Y + (int64_t)q * KM;
+            const double th = q * h - ta;
+            if (th <= eps) {
+                for (int a = threadIdx.x; a < KM; a += blockDim.x) yq[a] = yc[a];
+                __syncthreads();
+            } else {
+                project_step(L, D, H, K, b, N, th, r, yc, yq, M, E, work);
+            }
+        }
+        project_step(L, D, H, K, b, N, tb - ta, r, yc, yn, M, E, work);
+        for (int a = threadIdx.x; a < KM; a += blockDim.x) yc[a] = yn[a];
+        __syncthreads();
+        for (; q < srow && fabs(q * h - tb) <= eps; ++q) {
+            double* yq = Y + (int64_t)q * KM;
+            for (int a = threadIdx.x; a < KM; a += blockDim.x) yq[a] = yc[a];
+            __syncthreads();
+        }
+    }
+}
+
 __global__ void __launch_bounds__(256) k_project(WinLayout L, double* __restrict__ wd, int* __restrict__ wi,
                                                  const int* __restrict__ wins, int step, double h, double tol,
                                                  double scale_ref, Parts fp, double dcoef, double ccoef, int nsm,
-                                                 int only_ef, double jcoef) {
+                                                 int only_ef, double jcoef, int rc0, int rc0p) {
     extern __shared__ double sm_proj[];   // 9 nsm^2 doubles when nsm > 0
     const int w = wins[blockIdx.x];
     double* D = wd + (int64_t)w * L.stride;
@@ -627,17 +781,22 @@ __global__ void __launch_bounds__(256) k_project(WinLayout L, double* __restrict
             if (a < (step - 1) * b) H[((step - 1) * b + c) + a * KM] = -dcoef * Es[e] + ccoef * Fs[e] + jb;
         }
     } else {
+        // restart cycles (rc0: first block of the current cycle, rc0p: of the previous one):
+        // the new block couples to its own cycle, and as the first block of a cycle also
+        // through its row to the previous cycle (the residual's range); other entries are 0
+        const int k0 = rc0 * b, k0p = rc0p * b;
+        const bool first = rc0 > 0 && step - 1 == rc0;
         for (int e = threadIdx.x; e < K * b; e += blockDim.x) {
             const int a = e % K, c = e / K;
             double v = o1[a + c * ldo];
             if (lo) v += o1[a + (2 * b + c) * ldo];
-            H[a + ((step - 1) * b + c) * KM] = v;
+            H[a + ((step - 1) * b + c) * KM] = (a >= k0) ? v : 0.0;
         }
         for (int e = threadIdx.x; e < (step - 1) * b * b; e += blockDim.x) {
             const int a = e % ((step - 1) * b), c = e / ((step - 1) * b);
             double v = o1[a + (b + c) * ldo];
             if (lo) v += o1[a + (3 * b + c) * ldo];
-            H[((step - 1) * b + c) + a * KM] = v;
+            H[((step - 1) * b + c) + a * KM] = (a >= k0 || (first && a >= k0p)) ? v : 0.0;
         }
     }
     __syncthreads();
@@ -648,6 +807,14 @@ __global__ void __launch_bounds__(256) k_project(WinLayout L, double* __restrict
     double* M = nsm > 0 ? sm_proj : D + L.off_scr;
     double* E = M + mstride;
     double* work = E + mstride;
+    // Chebyshev samples: the knots are not the output times (one exponential per step, below)
+    const bool cheb = kind == KIND_SOURCE && I[WI_CHEB];
+    const int srow = cheb ? I[WI_SOUT] : s;   // rows of Y: the window's output times
+    double* Y = D + L.off_Y;
+    double* Yp = D + L.off_Yp;
+    if (cheb) {
+        project_cheb(L, D, H, K, b, N, s, srow, h, M, E, work);
+    } else {
     for (int e = threadIdx.x; e < N * N; e += blockDim.x) {
         const int i = e % N, j = e / N;
         double v = 0.0;
@@ -663,8 +830,6 @@ __global__ void __launch_bounds__(256) k_project(WinLayout L, double* __restrict
     }
     __syncthreads();
     cta_expm(M, N, E, work);
-    double* Y = D + L.off_Y;
-    double* Yp = D + L.off_Yp;
     const int Kp = K - b;
     for (int e = threadIdx.x; e < s * KM; e += blockDim.x) {
         const int a = e % KM;
@@ -698,16 +863,19 @@ __global__ void __launch_bounds__(256) k_project(WinLayout L, double* __restrict
         }
         __syncthreads();
     }
+    }
     double dmax = 0.0, nmax = 0.0;
-    for (int r = threadIdx.x; r < s; r += blockDim.x) {
-        double dd = 0.0, nn = 0.0;
+    for (int r = threadIdx.x; r < srow; r += blockDim.x) {
+        double dd = 0.0, nn = 0.0, cc = 0.0;
         for (int a = 0; a < K; ++a) {
             const double y = Y[(int64_t)r * KM + a];
             const double df = y - Yp[(int64_t)r * KM + a];
             dd = fma(df, df, dd);
             nn = fma(y, y, nn);
+            if (rc0 > 0 && a >= rc0 * b) cc = fma(y, y, cc);
         }
-        dmax = fmax(dmax, sqrt(dd));
+        // in a restart cycle the estimate also covers the cycle's own part of the solution
+        dmax = fmax(dmax, sqrt(fmax(dd, cc)));
         nmax = fmax(nmax, sqrt(nn));
     }
     dmax = cta_max(dmax, red);
@@ -718,22 +886,25 @@ __global__ void __launch_bounds__(256) k_project(WinLayout L, double* __restrict
         D[L.off_scal + WS_SCALE] = scale;
         I[WI_STEPS] = step;
         I[WI_K] = K;
-        if (step >= 2 && dmax <= tol * scale) I[WI_CONV] = 1;
+        // no stop at the first step of a restart cycle: the new direction alone barely moves
+        // the solution, and the estimate is far below the error there
+        if (step >= 2 && dmax <= tol * scale && (rc0 == 0 || step - rc0 >= 2)) I[WI_CONV] = 1;
     }
 }
 
 void launch_project(const WinLayout& L, double* wd, int* wi, const int* wins, int nw, int step, double h, double tol,
                     double scale_ref, cudaStream_t s, Parts fp, double d, double cadv, int b_launch, int only_ef,
-                    double jcoef) {
+                    double jcoef, int rc0, int rc0p) {
     if (nw <= 0) return;
     // largest augmented matrix of this launch: step * b + 4 b (source windows)
     const int nl = b_launch > 0 ? std::min(L.N_max, (step + 4) * b_launch) : L.N_max;
     const size_t sm = (size_t)9 * nl * nl * sizeof(double);
     if (sm <= 200u * 1024u) {
         if (sm > 32 * 1024) smem_optin(k_project, sm);
-        k_project<<<nw, 256, sm, s>>>(L, wd, wi, wins, step, h, tol, scale_ref, fp, d, cadv, nl, only_ef, jcoef);
+        k_project<<<nw, 256, sm, s>>>(L, wd, wi, wins, step, h, tol, scale_ref, fp, d, cadv, nl, only_ef, jcoef, rc0,
+                                      rc0p);
     } else {
-        k_project<<<nw, 256, 0, s>>>(L, wd, wi, wins, step, h, tol, scale_ref, fp, d, cadv, 0, only_ef, jcoef);
+        k_project<<<nw, 256, 0, s>>>(L, wd, wi, wins, step, h, tol, scale_ref, fp, d, cadv, 0, only_ef, jcoef, rc0, rc0p);
     }
 }
 

@@ -27,11 +27,15 @@ struct WinLayout {
     int64_t off_Yp;    // s_max x K_max     previous step's projected solution
     int64_t off_scal;  // 16 scalars
     int64_t off_scr;   // 9 N_max^2 scratch (augmented matrix, exponential, Pade work)
+    int64_t off_yk;    // 2 x K_max         projected state at two knots (Chebyshev samples)
     int istride;
 };
 
 // int fields
-enum { WI_B = 0, WI_CONV, WI_STEPS, WI_S, WI_KIND, WI_KEPT, WI_STATUS, WI_K, WI_I0, WI_COUNT = 16 };
+// WI_S: source samples of a source window (output times of a homogeneous one); WI_SOUT: output
+// times of a source window whose samples are not its output times (0: the same as WI_S);
+// WI_CHEB: the source samples are the window's Chebyshev points (knots of the spline).
+enum { WI_B = 0, WI_CONV, WI_STEPS, WI_S, WI_KIND, WI_KEPT, WI_STATUS, WI_K, WI_I0, WI_SOUT, WI_CHEB, WI_COUNT = 16 };
 // double scalars at off_scal
 enum { WS_BETA = 0, WS_EST, WS_SCALE, WS_SIGRATIO, WS_H, WS_PRE, WS_COUNT = 16 };
 
@@ -171,6 +175,8 @@ void launch_source_eig(const WinLayout& L, double* wd, int* wi, const int* wins,
 void launch_start_orth(const WinLayout& L, double* wd, int* wi, const int* wins, int nw, cudaStream_t s);
 void launch_block_orth(const WinLayout& L, double* wd, int* wi, const int* wins, int nw, int pass, int step,
                        double defl, cudaStream_t s, Parts gp = Parts{nullptr, 0, 0});
+// h: the output spacing; a window with WI_CHEB set takes its knots at its Chebyshev points
+// (WI_S of them over (WI_SOUT - 1) h), otherwise at the multiples of h.
 void launch_spline(const WinLayout& L, double* wd, int* wi, const int* wins, int nw, double h, cudaStream_t s);
 // With fused partials (E, F, h1, pre of the step) and the operator coefficients d, c:
 // H[a, i] = -d E - c F, H[i, a] = -d E + c F; h1 and pre are stored at out1.
@@ -180,9 +186,13 @@ void launch_spline(const WinLayout& L, double* wd, int* wi, const int* wins, int
 // jcoef != 0 (fused partials): the partials also hold the Jacobian sums Ja, Jb of
 // launch_step_proj, and H gets jcoef * Ja in its new column and jcoef * Jb in its new row
 // (jcoef = 1/(2 dx): the Jacobian of the conservative Burgers term).
+// rc0, rc0p (dense projections only): first blocks of the current and the previous restart
+// cycle; the new block's H entries outside its cycle are set to 0, except the row of a cycle's
+// first block over the previous cycle (0, 0: no restarts).
 void launch_project(const WinLayout& L, double* wd, int* wi, const int* wins, int nw, int step, double h,
                     double tol, double scale_ref, cudaStream_t s, Parts fp = Parts{nullptr, 0, 0}, double d = 0.0,
-                    double cadv = 0.0, int b_launch = 0, int only_ef = 0, double jcoef = 0.0);
+                    double cadv = 0.0, int b_launch = 0, int only_ef = 0, double jcoef = 0.0, int rc0 = 0,
+                    int rc0p = 0);
 void launch_small_expm_batch(const double* M, double* E, int N, int batch, double* scratch, cudaStream_t s);
 size_t small_expm_scratch_doubles(int N);
 void init_pade_constants();

@@ -338,6 +338,8 @@ int validate(const pexp_operator* op, const pexp_options* o) {
         smax = std::max(smax, i1 - i0 + 1);
     }
     if (smax > PEXP_MAX_SAMPLES) return PEXP_ERR_INVALID_ARG;
+    if (o->nodes != PEXP_NODES_UNIFORM && o->nodes != PEXP_NODES_CHEBYSHEV) return PEXP_ERR_INVALID_ARG;
+    if (o->nodes == PEXP_NODES_CHEBYSHEV && (o->n_samp < 2 || o->n_samp > PEXP_MAX_SAMPLES)) return PEXP_ERR_INVALID_ARG;
     if (!(o->sub_first == 0 && o->sub_last == 0) && !(0 <= o->sub_first && o->sub_first < o->sub_last && o->sub_last <= P))
         return PEXP_ERR_INVALID_ARG;
     if (o->krylov == PEXP_KRYLOV_SAI && op->dim != 1) return PEXP_ERR_UNSUPPORTED;
@@ -398,6 +400,7 @@ struct Solver {
     bool jac = false;                          // per-window Jacobian terms in the operator
     double inv2dx = 0.0;
     std::vector<int> wi_host;
+    std::vector<int> restarts;                 // restart cycles begun, per window
     bool coop_used = false;                    // a cooperative launch ran (check_coop reads its error word)
 
     GridBar gbar() const { return GridBar{c->bar, c->bar + 1, reinterpret_cast<int*>(c->bar + 2)}; }
@@ -439,6 +442,16 @@ struct Solver {
     double* D(int w) const { return wd + (int64_t)w * L.stride; }
 
     // max |V^T V - I| over the first K columns of V (diagnostic, one pass over V per 48 columns).
+    // Restart cycles are orthonormal each, not to one another: the defect is taken per cycle
+    // (restart_len blocks of b columns).
+    double orth_defect_cycles(const T* V, int K, int b) {
+        if (o->max_restarts <= 0 || b <= 0) return orth_defect(V, K);
+        const int cw = o->restart_len * b;
+        double m = 0.0;
+        for (int k0 = 0; k0 < K; k0 += cw) m = std::max(m, orth_defect(V + (int64_t)k0 * n, std::min(cw, K - k0)));
+        return m;
+    }
+
     double orth_defect(const T* V, int K) {
         if (K <= 0) return 0.0;
         std::vector<double> G((size_t)K * K);
@@ -814,6 +827,10 @@ struct Solver {
         int notconv = 0;
         *max_steps = 0;
         std::vector<Win<T>> act = ws;
+        // restart cycles (max_restarts > 0): every window starts together, so the cycles of all
+        // active windows begin at the same block: c0 (current cycle), c0p (previous cycle)
+        const int rlen = o->max_restarts > 0 ? o->restart_len : 0;
+        int c0 = 0, c0p = 0;
         for (int step = 1; step <= kmax && !act.empty(); ++step) {
             const int na = (int)act.size();
             // ---- part A: operator applications, projections, projected solve
@@ -942,7 +959,10 @@ struct Solver {
                     check_launch(c);
                 });
             }
-            timed(c, PEXP_KC_SMALL, 0.0, [&] { launch_project(L, wd, wi, d_wl, na, step, h, o->tol, scale_ref, st); });
+            timed(c, PEXP_KC_SMALL, 0.0, [&] {
+                launch_project(L, wd, wi, d_wl, na, step, h, o->tol, scale_ref, st, Parts{nullptr, 0, 0}, 0.0, 0.0, 0, 0,
+                               0.0, c0, c0p);
+            });
             check_launch(c);
             // ---- convergence flags
             d2h(c, wi_host.data(), wi, sizeof(int) * wi_host.size());
@@ -964,22 +984,25 @@ struct Solver {
             std::vector<TsTask<T>> nn1(nb), tn2(nb), nn2(nb), tn3(nb), nn3(nb);
             std::vector<int> wl2(nb);
             int mpq1 = 0, mpq2 = 0, mq2 = 0, mpq3 = 0, mq3 = 0;
+            // the block made at this step starts the next restart cycle
+            const bool restart = rlen > 0 && step - c0 == rlen;
             for (int a = 0; a < nb; ++a) {
                 const Win<T>& W = act[a];
                 T* Wn = slot(W, step);
-                const int b = W.b, p = step * b, ldo = (step + 1) * b;
+                // Gram-Schmidt against the blocks of the current cycle, columns [k0, k0 + p)
+                const int b = W.b, k0 = c0 * W.b, p = (step - c0) * b, ldo = (step + 1) * b;
                 TsTask<T> t;
                 memset(&t, 0, sizeof(t));
-                // W -= V_{1:step} h1, h1 = out1[0:p, 2b:3b]
-                t.X = W.V; t.ldx = n; t.p = p; t.q = b;
+                // W -= V_{cycle} h1, h1 = out1[k0:k0+p, 2b:3b]
+                t.X = W.V + (int64_t)k0 * n; t.ldx = n; t.p = p; t.q = b;
                 t.Z = Wn; t.ldz = n;
-                t.Tm = D(W.w) + L.off_out1 + (int64_t)2 * b * ldo; t.ldt = ldo;
+                t.Tm = D(W.w) + L.off_out1 + (int64_t)2 * b * ldo + k0; t.ldt = ldo;
                 t.alpha = -1.0; t.beta = 1.0;
                 nn1[a] = t;
                 mpq1 = std::max(mpq1, p * b);
                 // h2 = V^T W
                 memset(&t, 0, sizeof(t));
-                t.X = W.V; t.ldx = n; t.p = p;
+                t.X = W.V + (int64_t)k0 * n; t.ldx = n; t.p = p;
                 t.Y = Wn; t.ldy = n; t.q = b; t.q1 = b;
                 t.out = D(W.w) + L.off_h2;
                 tn2[a] = t;
@@ -1017,11 +1040,11 @@ struct Solver {
                 for (int a = 0; a < nb; ++a) {
                     const Win<T>& W = act[a];
                     float* Wn = slot(W, step);
-                    const int b = W.b, p = step * b, ldo = (step + 1) * b;
+                    const int b = W.b, k0 = c0 * W.b, p = (step - c0) * b, ldo = (step + 1) * b;
                     DfTask t;
                     memset(&t, 0, sizeof(t));
-                    t.Xh = W.V; t.ldx = n; t.Zh = Wn; t.Zl = W.Wlo; t.ldz = n;
-                    t.Tm = D(W.w) + L.off_out1 + (int64_t)(L.ycols - 1) * b * ldo; t.ldt = ldo;
+                    t.Xh = W.V + (int64_t)k0 * n; t.ldx = n; t.Zh = Wn; t.Zl = W.Wlo; t.ldz = n;
+                    t.Tm = D(W.w) + L.off_out1 + (int64_t)(L.ycols - 1) * b * ldo + k0; t.ldt = ldo;
                     t.p = p; t.q = b; t.alpha = -1.0; t.accumulate = 1;
                     d1[a] = t;
                     t.Tm = D(W.w) + L.off_h2; t.ldt = p;
@@ -1030,7 +1053,9 @@ struct Solver {
                     t.Xh = Wn; t.Xl = W.Wlo; t.ldx = n; t.Zh = Wn; t.Zl = W.Wlo; t.ldz = n;
                     t.Tm = D(W.w) + L.off_T; t.ldt = b; t.p = b; t.q = b; t.alpha = 1.0; t.accumulate = 0;
                     d3[a] = t;
-                    t.Zl = nullptr;
+                    // a block that starts a shift-and-invert restart cycle keeps its low part
+                    // for the residual direction formed from it below
+                    if (!(restart && o->krylov == PEXP_KRYLOV_SAI)) t.Zl = nullptr;
                     d4[a] = t;
                 }
                 const DfTask* dd1 = sb.put(d1.data(), nb);
@@ -1039,14 +1064,17 @@ struct Solver {
                 const DfTask* dd4 = sb.put(d4.data(), nb);
                 sb.flush();
                 double pb = 0, bb = 0;   // sum of p*b and of b over the active windows
-                for (auto& W : act) { pb += (double)step * W.b; bb += W.b; }
+                for (auto& W : act) { pb += (double)(step - c0) * W.b; bb += W.b; }
                 const double nn = (double)n;
+                // pass 1, Cholesky QR of the result, then the second pass on the normalised block
+                // (as the fused kernels do): second-pass coefficients taken from the block before
+                // normalisation carry its conditioning into the basis's orthogonality
                 timed(c, PEXP_KC_UPDATE, nn * (pb * 4 + bb * 16), [&] { launch_ts_nn_df(dd1, nb, mpq1, n, st, mq3); }, nullptr, false, nn * (pb * 4 + bb * 8)); check_launch(c);
-                timed(c, PEXP_KC_PROJ, nn * (pb + bb) * 4, [&] { launch_ts_tn<T>(d_tn2, nb, mpq2, mq2, n, partial, st, PEXP_TN_EXACT_FP32); }); check_launch(c);
-                timed(c, PEXP_KC_UPDATE, nn * (pb * 4 + bb * 16), [&] { launch_ts_nn_df(dd2, nb, mpq1, n, st, mq3); }, nullptr, false, nn * (pb * 4 + bb * 8)); check_launch(c);
                 timed(c, PEXP_KC_PROJ, nn * bb * 4, [&] { launch_ts_tn<T>(d_tn3, nb, mpq3, mq3, n, partial, st, 1); }); check_launch(c);
                 timed(c, PEXP_KC_SMALL, 0.0, [&] { launch_block_orth(L, wd, wi, d_wl2, nb, 1, step, defl, st); }); check_launch(c);
                 timed(c, PEXP_KC_UPDATE, nn * bb * 16, [&] { launch_ts_nn_df(dd3, nb, mpq3, n, st, mq3); }, nullptr, false, nn * bb * 8); check_launch(c);
+                timed(c, PEXP_KC_PROJ, nn * (pb + bb) * 4, [&] { launch_ts_tn<T>(d_tn2, nb, mpq2, mq2, n, partial, st, PEXP_TN_EXACT_FP32); }); check_launch(c);
+                timed(c, PEXP_KC_UPDATE, nn * (pb * 4 + bb * 16), [&] { launch_ts_nn_df(dd2, nb, mpq1, n, st, mq3); }, nullptr, false, nn * (pb * 4 + bb * 8)); check_launch(c);
                 timed(c, PEXP_KC_PROJ, nn * bb * 4, [&] { launch_ts_tn<T>(d_tn3, nb, mpq3, mq3, n, partial, st, 1); }); check_launch(c);
                 timed(c, PEXP_KC_SMALL, 0.0, [&] { launch_block_orth(L, wd, wi, d_wl2, nb, 2, step, defl, st); }); check_launch(c);
                 timed(c, PEXP_KC_UPDATE, nn * bb * 12, [&] { launch_ts_nn_df(dd4, nb, mpq3, n, st, mq3); }, nullptr, false, nn * bb * 8); check_launch(c);
@@ -1056,7 +1084,7 @@ struct Solver {
                 const TsTask<T>* d_nn3 = sb.put(nn3.data(), nb);
                 sb.flush();
                 double pb = 0, bb = 0;
-                for (auto& W : act) { pb += (double)step * W.b; bb += W.b; }
+                for (auto& W : act) { pb += (double)(step - c0) * W.b; bb += W.b; }
                 const double nn = (double)n * 8.0;
                 timed(c, PEXP_KC_UPDATE, nn * (pb + 2 * bb), [&] { launch_ts_nn<T>(d_nn1, nb, mpq1, n, st); }); check_launch(c);
                 timed(c, PEXP_KC_PROJ, nn * (pb + bb), [&] { launch_ts_tn<T>(d_tn2, nb, mpq2, mq2, n, partial, st, 0); }); check_launch(c);
@@ -1068,8 +1096,156 @@ struct Solver {
                 timed(c, PEXP_KC_SMALL, 0.0, [&] { launch_block_orth(L, wd, wi, d_wl2, nb, 2, step, defl, st); }); check_launch(c);
                 timed(c, PEXP_KC_UPDATE, nn * 2 * bb, [&] { launch_ts_nn<T>(d_nn3, nb, mpq3, n, st); }); check_launch(c);
             }
+            if (restart) {
+                if (o->krylov == PEXP_KRYLOV_SAI) restart_block(act, step, c0);
+                for (auto& W : act) ++restarts[W.w];
+                c0p = c0;
+                c0 = step;
+            }
         }
         return notconv;
+    }
+
+    // First block of a restart cycle in the shift-and-invert space.  After `step` blocks of the
+    // cycle that starts at block c0, the Galerkin solution V_c y_c(t) leaves the residual
+    // (I - V_c V_c^T) A V_c y_c(t), of rank b: with M = (I - gamma A)^{-1}, the cycle's Arnoldi
+    // relation M V_c = V_c Ht + V' h E^T (V' the block just made in slot `step`) gives
+    //     (I - V_c V_c^T) A V_c = q h E^T Ht^{-1} / gamma,   q = V' - gamma (I - V_c V_c^T) A V'.
+    // The next cycle's space starts from q, orthonormalised (two Cholesky QRs) into the slot.
+    // FP32 data: V' is the double-float block (slot, Wlo), so that gamma A V' carries no
+    // amplified rounding of a stored vector.  (In the polynomial space the range is V' itself.)
+    void restart_block(const std::vector<Win<T>>& act, int step, int c0) {
+        const int nb = (int)act.size();
+        const double gamma = o->sai_gamma * o->T / (double)o->P;
+        int bmax = 0;
+        for (auto& W : act) bmax = std::max(bmax, W.b);
+        std::vector<double> mg((size_t)bmax * bmax, 0.0);   // -gamma I
+        for (int i = 0; i < bmax; ++i) mg[(size_t)i * bmax + i] = -gamma;
+        Stage sr(c, 1);
+        const double* d_mg = sr.put(mg.data(), mg.size());
+        std::vector<const T*> xin;
+        std::vector<const float*> xlo;
+        std::vector<T*> yav, yavl;
+        std::vector<TsTask<T>> th(nb), tq(nb), tg(nb), ts(nb);
+        std::vector<DfTask> da(nb), dh(nb), dl(nb), d3(nb), d4(nb);
+        std::vector<int> wl(nb);
+        int mpq = 0;
+        for (int a = 0; a < nb; ++a) {
+            const Win<T>& W = act[a];
+            T* Wn = slot(W, step);
+            const int b = W.b, k0 = c0 * b, p = (step - c0) * b;
+            for (int cc = 0; cc < b; ++cc) {
+                xin.push_back(Wn + (int64_t)cc * n);
+                xlo.push_back(W.Wlo ? W.Wlo + (int64_t)cc * n : nullptr);
+                yav.push_back(W.S + (int64_t)cc * n);
+                yavl.push_back(W.S + (int64_t)(2 * b + cc) * n);
+            }
+            TsTask<T> t;
+            // h = V_c^T (A V') (FP32 data: the high and the low part of A V' side by side)
+            memset(&t, 0, sizeof(t));
+            t.X = W.V + (int64_t)k0 * n; t.ldx = n; t.p = p;
+            t.Y = W.S; t.ldy = n; t.q1 = b; t.q = b;
+            if (W.Wlo) { t.Y2 = W.S + (int64_t)2 * b * n; t.ldy2 = n; t.q = 2 * b; }
+            t.out = D(W.w) + L.off_h2;
+            th[a] = t;
+            mpq = std::max(mpq, p * t.q);
+            // FP64: q = V' - gamma A V' + gamma V_c h
+            memset(&t, 0, sizeof(t));
+            t.X = W.S; t.ldx = n; t.p = b; t.q = b; t.Z = Wn; t.ldz = n; t.Tm = d_mg; t.ldt = bmax;
+            t.alpha = 1.0; t.beta = 1.0;
+            tq[a] = t;
+            memset(&t, 0, sizeof(t));
+            t.X = W.V + (int64_t)k0 * n; t.ldx = n; t.p = p; t.q = b; t.Z = Wn; t.ldz = n;
+            t.Tm = D(W.w) + L.off_h2; t.ldt = p; t.alpha = gamma; t.beta = 1.0;
+            tg[a] = t;
+            // Gram of the block and its scaling (Cholesky QR)
+            memset(&t, 0, sizeof(t));
+            t.X = Wn; t.ldx = n; t.p = b; t.Y = Wn; t.ldy = n; t.q = b; t.q1 = b; t.out = D(W.w) + L.off_gw;
+            ts[a] = t;
+            if constexpr (std::is_same<T, float>::value) {
+                DfTask d;
+                memset(&d, 0, sizeof(d));
+                d.Xh = W.S; d.Xl = W.S + (int64_t)2 * b * n; d.ldx = n; d.Zh = Wn; d.Zl = W.Wlo; d.ldz = n;
+                d.Tm = d_mg; d.ldt = bmax; d.p = b; d.q = b; d.alpha = 1.0; d.accumulate = 1;
+                da[a] = d;
+                memset(&d, 0, sizeof(d));
+                d.Xh = W.V + (int64_t)k0 * n; d.ldx = n; d.Zh = Wn; d.Zl = W.Wlo; d.ldz = n;
+                d.Tm = D(W.w) + L.off_h2; d.ldt = p; d.p = p; d.q = b; d.alpha = gamma; d.accumulate = 1;
+                dh[a] = d;
+                d.Tm = D(W.w) + L.off_h2 + (int64_t)p * b;   // the low part's products
+                dl[a] = d;
+                memset(&d, 0, sizeof(d));
+                d.Xh = Wn; d.Xl = W.Wlo; d.ldx = n; d.Zh = Wn; d.Zl = W.Wlo; d.ldz = n;
+                d.Tm = D(W.w) + L.off_T; d.ldt = b; d.p = b; d.q = b; d.alpha = 1.0; d.accumulate = 0;
+                d3[a] = d;
+                d.Zl = nullptr;
+                d4[a] = d;
+            }
+            wl[a] = W.w;
+        }
+        const int nv = (int)xin.size();
+        const T* const* d_xin = sr.put(xin.data(), nv);
+        T* const* d_yav = sr.put(yav.data(), nv);
+        const float* const* d_xlo = std::is_same<T, float>::value ? sr.put(xlo.data(), nv) : nullptr;
+        T* const* d_yavl = std::is_same<T, float>::value ? sr.put(yavl.data(), nv) : nullptr;
+        const TsTask<T>* d_th = sr.put(th.data(), nb);
+        const TsTask<T>* d_tq = sr.put(tq.data(), nb);
+        const TsTask<T>* d_tg = sr.put(tg.data(), nb);
+        const TsTask<T>* d_ts = sr.put(ts.data(), nb);
+        const DfTask* d_da = std::is_same<T, float>::value ? sr.put(da.data(), nb) : nullptr;
+        const DfTask* d_dh = std::is_same<T, float>::value ? sr.put(dh.data(), nb) : nullptr;
+        const DfTask* d_dl = std::is_same<T, float>::value ? sr.put(dl.data(), nb) : nullptr;
+        const DfTask* d_d3 = std::is_same<T, float>::value ? sr.put(d3.data(), nb) : nullptr;
+        const DfTask* d_d4 = std::is_same<T, float>::value ? sr.put(d4.data(), nb) : nullptr;
+        const int* d_wl = sr.put(wl.data(), nb);
+        sr.flush();
+        int bm = 0;
+        for (auto& W : act) bm = std::max(bm, W.b);
+        // A V' (FP32 data: of the double-float pair, as a double-float pair)
+        if constexpr (std::is_same<T, float>::value) {
+            launch_stencil_df(od, reinterpret_cast<const float* const*>(d_xin), d_xlo,
+                              reinterpret_cast<float* const*>(d_yav), reinterpret_cast<float* const*>(d_yavl), nv, 0, st);
+        } else {
+            launch_stencil_ptrs<T>(od, d_xin, d_yav, nv, 0, st);
+        }
+        check_launch(c);
+        launch_ts_tn<T>(d_th, nb, mpq, std::is_same<T, float>::value ? 2 * bm : bm, n, partial, st,
+                        std::is_same<T, float>::value ? 1 : 0);
+        check_launch(c);
+        if constexpr (std::is_same<T, float>::value) {
+            launch_ts_nn_df(d_da, nb, bm * bm, n, st, bm); check_launch(c);
+            launch_ts_nn_df(d_dh, nb, mpq, n, st, bm); check_launch(c);
+            launch_ts_nn_df(d_dl, nb, mpq, n, st, bm); check_launch(c);
+        } else {
+            launch_ts_nn<T>(d_tq, nb, bm * bm, n, st); check_launch(c);
+            launch_ts_nn<T>(d_tg, nb, mpq, n, st); check_launch(c);
+        }
+        // two Cholesky QRs of q (deflation relative to this step's pre-Gram-Schmidt norms)
+        for (int pass = 1; pass <= 2; ++pass) {
+            launch_ts_tn<T>(d_ts, nb, bm * bm, bm, n, partial, st, std::is_same<T, float>::value ? 1 : 0);
+            check_launch(c);
+            launch_block_orth(L, wd, wi, d_wl, nb, pass, step, defl, st);
+            check_launch(c);
+            if constexpr (std::is_same<T, float>::value) {
+                launch_ts_nn_df(pass == 1 ? d_d3 : d_d4, nb, bm * bm, n, st, bm);
+            } else {
+                // W <- W T in place, as the final scaling of a step
+                std::vector<TsTask<T>> sc(nb);
+                for (int a = 0; a < nb; ++a) {
+                    TsTask<T> t;
+                    memset(&t, 0, sizeof(t));
+                    T* Wn = slot(act[a], step);
+                    t.X = Wn; t.ldx = n; t.p = act[a].b; t.q = act[a].b; t.Z = Wn; t.ldz = n;
+                    t.Tm = D(act[a].w) + L.off_T; t.ldt = act[a].b; t.alpha = 1.0; t.beta = 0.0;
+                    sc[a] = t;
+                }
+                Stage sq(c, 0);
+                const TsTask<T>* d_sc = sq.put(sc.data(), nb);
+                sq.flush();
+                launch_ts_nn<T>(d_sc, nb, bm * bm, n, st);
+            }
+            check_launch(c);
+        }
     }
 };
 
@@ -1088,6 +1264,33 @@ Partition make_partition(int n_out, int P) {
     return r;
 }
 
+// Source samples of the subintervals: the output times (nodes = PEXP_NODES_UNIFORM), or n_samp
+// Chebyshev points per subinterval sharing the ends (Sec. 3), rows j (n_samp - 1) .. of G.
+struct SrcPartition {
+    bool cheb = false;
+    std::vector<int> idx;   // P+1 first rows: subinterval j's samples are rows idx[j] .. idx[j+1]
+    int smax = 0;           // largest sample count of a subinterval
+    int rows = 0;           // rows of G
+};
+SrcPartition make_src_partition(const pexp_options* o, const Partition& pt) {
+    SrcPartition r;
+    r.cheb = o->nodes == PEXP_NODES_CHEBYSHEV;
+    if (!r.cheb) {
+        r.idx = pt.idx;
+        r.smax = pt.smax;
+        r.rows = o->n_out;
+        return r;
+    }
+    r.idx.resize(o->P + 1);
+    for (int j = 0; j <= o->P; ++j) r.idx[j] = j * (o->n_samp - 1);
+    r.smax = o->n_samp;
+    r.rows = o->P * (o->n_samp - 1) + 1;
+    return r;
+}
+int src_rows_of(const pexp_options* o) {
+    return o->nodes == PEXP_NODES_CHEBYSHEV ? o->P * (o->n_samp - 1) + 1 : o->n_out;
+}
+
 size_t align_up(size_t x) { return (x + kAlign - 1) / kAlign * kAlign; }
 
 // Upper bound of the workspace a linear solve needs (bytes).
@@ -1095,18 +1298,20 @@ template <typename T>
 size_t linear_workspace_bytes(int64_t n, const pexp_options* o, int g_conv, int b_cap) {
     const int P = o->P;
     Partition pt = make_partition(o->n_out, P);
+    const SrcPartition sp = make_src_partition(o, pt);
+    const int smax = std::max(pt.smax, sp.smax);
     const int kmax = o->restart_len * (o->max_restarts + 1);
-    WinLayout L = make_layout(pt.smax, b_cap, kmax, sizeof(T) == 8 ? 3 : 5);
+    WinLayout L = make_layout(smax, b_cap, kmax, sizeof(T) == 8 ? 3 : 5);
     size_t s = 0;
     s += align_up(sizeof(double) * n * 2);                                  // u0, A u0
-    if (g_conv) s += align_up(sizeof(T) * (size_t)n * o->n_out);           // converted G
+    if (g_conv) s += align_up(sizeof(T) * (size_t)n * sp.rows);            // converted G
     s += align_up(sizeof(double) * L.stride * 2 * P);                       // window state
     s += align_up(sizeof(int) * L.istride * 2 * P);
-    s += align_up(sizeof(double) * (ts_tn_partial_doubles(P, std::max(std::max(pt.smax * pt.smax, 48 * (L.K_max + b_cap)), 48 * L.K_max), n) + 512));
+    s += align_up(sizeof(double) * (ts_tn_partial_doubles(P, std::max(std::max(smax * smax, 48 * (L.K_max + b_cap)), 48 * L.K_max), n) + 512));
     s += align_up(sizeof(double) * (size_t)L.K_max * 48);                   // orthogonality diagnostic
-    s += 2 * align_up(sizeof(double) * kpart_doubles(P, n, kmax, b_cap, pt.smax));
+    s += 2 * align_up(sizeof(double) * kpart_doubles(P, n, kmax, b_cap, smax));
     s += align_up(sizeof(double) * sai_scratch_doubles(n, P * b_cap) + 64);
-    s += align_up(sizeof(double) * (o->n_out + P));                         // (A u0) . g(t_i)
+    s += align_up(sizeof(double) * (sp.rows + P));                          // (A u0) . g(t_i)
     s += align_up(sizeof(double) * 3 * (size_t)n) + kAlign;                 // bounded-mesh SAI factors
     if (sizeof(T) == 4) s += align_up(sizeof(float) * n * 2);               // A u0 as a double-float pair
     s += (size_t)(4 * P + 32) * kAlign;   // alignment of the per-window allocations
@@ -1126,13 +1331,16 @@ int solve_linear_typed(pexp_ctx* c, const pexp_operator* op, const pexp_options*
     S.n = n;
     const int P = o->P, n_out = o->n_out;
     Partition pt = make_partition(n_out, P);
+    // source samples: the output times, or each subinterval's Chebyshev points
+    const SrcPartition sp = make_src_partition(o, pt);
+    const int smax = std::max(pt.smax, sp.smax);
     S.kmax = o->restart_len * (o->max_restarts + 1);
     S.h = o->T / (double)(n_out - 1);
     const bool fp64 = sizeof(T) == 8;
     S.defl = fp64 ? PEXP_DEFL_FP64 : PEXP_DEFL_FP32;
     const double svd_floor = fp64 ? 1e-7 : 1e-5;
-    const int b_cap = std::min(std::min(o->max_rank, PEXP_MAX_RANK), pt.smax);
-    S.L = make_layout(pt.smax, b_cap, S.kmax, fp64 ? 3 : 5);
+    const int b_cap = std::min(std::min(o->max_rank, PEXP_MAX_RANK), sp.smax);
+    S.L = make_layout(smax, b_cap, S.kmax, fp64 ? 3 : 5);
     const WinLayout& L = S.L;
     // the subproblems solved: j in [ja, jb) (all by default); their solutions are zero before T_ja
     const bool ranged = !(o->sub_first == 0 && o->sub_last == 0);
@@ -1146,9 +1354,9 @@ int solve_linear_typed(pexp_ctx* c, const pexp_operator* op, const pexp_options*
         if (same) {
             G = reinterpret_cast<const T*>(G_dev);
         } else {
-            T* Gc = as<T>(ws_alloc(c, sizeof(T) * (size_t)n * n_out));
-            if (g_dtype == PEXP_F64) launch_convert<double, T>(reinterpret_cast<const double*>(G_dev), Gc, n * n_out, st);
-            else launch_convert<float, T>(reinterpret_cast<const float*>(G_dev), Gc, n * n_out, st);
+            T* Gc = as<T>(ws_alloc(c, sizeof(T) * (size_t)n * sp.rows));
+            if (g_dtype == PEXP_F64) launch_convert<double, T>(reinterpret_cast<const double*>(G_dev), Gc, n * sp.rows, st);
+            else launch_convert<float, T>(reinterpret_cast<const float*>(G_dev), Gc, n * sp.rows, st);
             check_launch(c);
             G = Gc;
         }
@@ -1157,11 +1365,12 @@ int solve_linear_typed(pexp_ctx* c, const pexp_operator* op, const pexp_options*
     // row idx_j + j, and the shift by A u0 is already in them
     const T* Gw = wo ? wo->Gwin : nullptr;
     const bool have_src = G || Gw;
-    const int src_rows = Gw ? n_out + P - 1 : n_out;
+    const int src_rows = Gw ? n_out + P - 1 : sp.rows;
     auto src_first = [&](int j) -> const T* {
         if (Gw) return Gw + (int64_t)(pt.idx[j] + j) * n;
-        return G ? G + (int64_t)pt.idx[j] * n : nullptr;
+        return G ? G + (int64_t)sp.idx[j] * n : nullptr;
     };
+    auto src_count = [&](int j) { return sp.idx[j + 1] - sp.idx[j] + 1; };
     // a bounded mesh with the shift-and-invert space: one factored operator for all windows
     WinOps<T> wo_bounded;
     if (!wo && o->krylov == PEXP_KRYLOV_SAI && !S.od.x.periodic) {
@@ -1196,23 +1405,28 @@ int solve_linear_typed(pexp_ctx* c, const pexp_operator* op, const pexp_options*
     const int nwin = 2 * P;   // [0, P): source windows j=1..P; [P, 2P): homogeneous windows m=1..P
     S.wd = as<double>(ws_alloc(c, sizeof(double) * L.stride * nwin));
     S.wi = as<int>(ws_alloc(c, sizeof(int) * L.istride * nwin));
-    const size_t part_n = ts_tn_partial_doubles(P, std::max(std::max(pt.smax * pt.smax, 48 * (L.K_max + b_cap)), 48 * L.K_max), n) + 512;
+    const size_t part_n = ts_tn_partial_doubles(P, std::max(std::max(smax * smax, 48 * (L.K_max + b_cap)), 48 * L.K_max), n) + 512;
     S.partial = as<double>(ws_alloc(c, sizeof(double) * part_n));
     S.diag = as<double>(ws_alloc(c, sizeof(double) * (size_t)L.K_max * 48));
-    const size_t kpart_n = kpart_doubles(P, n, S.kmax, b_cap, pt.smax);
+    const size_t kpart_n = kpart_doubles(P, n, S.kmax, b_cap, smax);
     for (int k = 0; k < 2; ++k) S.kpart[k] = as<double>(ws_alloc(c, sizeof(double) * kpart_n));
     S.sai_scr = as<double>(ws_alloc(c, sizeof(double) * (sai_scratch_doubles(n, P * b_cap) + 64)));
     // one pole for every window: gamma = sai_gamma * T / P (the nominal subinterval length)
     if (o->krylov == PEXP_KRYLOV_SAI && !S.var) S.sai = sai_coefficients(S.od, o->sai_gamma * o->T / (double)P);
     S.wi_host.assign((size_t)L.istride * nwin, 0);
+    S.restarts.assign(nwin, 0);
 
     // ---- initial window state
     {
         std::vector<int> wih((size_t)L.istride * nwin, 0);
         for (int j = 0; j < P; ++j) {
-            wih[(size_t)j * L.istride + WI_S] = pt.idx[j + 1] - pt.idx[j] + 1;
+            wih[(size_t)j * L.istride + WI_S] = src_count(j);
             wih[(size_t)j * L.istride + WI_KIND] = KIND_SOURCE;
-            wih[(size_t)j * L.istride + WI_I0] = Gw ? pt.idx[j] + j : pt.idx[j];
+            wih[(size_t)j * L.istride + WI_I0] = Gw ? pt.idx[j] + j : sp.idx[j];
+            if (sp.cheb) {
+                wih[(size_t)j * L.istride + WI_SOUT] = pt.idx[j + 1] - pt.idx[j] + 1;
+                wih[(size_t)j * L.istride + WI_CHEB] = 1;
+            }
             wih[(size_t)(P + j) * L.istride + WI_S] = pt.idx[j + 1] - pt.idx[j] + 1;
             wih[(size_t)(P + j) * L.istride + WI_KIND] = KIND_HOM;
             wih[(size_t)(P + j) * L.istride + WI_B] = 1;
@@ -1246,7 +1460,7 @@ int solve_linear_typed(pexp_ctx* c, const pexp_operator* op, const pexp_options*
         launch_ts_tn<double>(dt, 2, 1, 1, n, S.partial, st, 0);
         check_launch(c);
         if (G && !Gw) {
-            launch_row_dots<T>(Au0, G, n, n_out, dots, au0_split, st);
+            launch_row_dots<T>(Au0, G, n, sp.rows, dots, au0_split, st);
             check_launch(c);
         }
         double nn = 0;
@@ -1264,7 +1478,7 @@ int solve_linear_typed(pexp_ctx* c, const pexp_operator* op, const pexp_options*
         for (int j = 0; j < P; ++j) {
             TsTask<T> t;
             memset(&t, 0, sizeof(t));
-            const int s = pt.idx[j + 1] - pt.idx[j] + 1;
+            const int s = src_count(j);
             t.X = src_first(j);
             t.ldx = n; t.p = s;
             t.Y = t.X; t.ldy = n; t.q = s; t.q1 = s;
@@ -1275,17 +1489,17 @@ int solve_linear_typed(pexp_ctx* c, const pexp_operator* op, const pexp_options*
         std::vector<int> gs(P);
         for (int j = 0; j < P; ++j) {
             gx[j] = src_first(j);
-            gs[j] = pt.idx[j + 1] - pt.idx[j] + 1;
+            gs[j] = src_count(j);
         }
         const T* const* dgx = s1.put(gx.data(), P);
         const int* dgs = s1.put(gs.data(), P);
         const int* dall = s1.put(all.data(), P);
         s1.flush();
         const KGeom gg = krylov_geom(P, n);
-        const int psg = pt.smax * pt.smax;
+        const int psg = sp.smax * sp.smax;
         if (have_src) {
             timed(c, PEXP_KC_SOURCE, (double)n * src_rows * sizeof(T),
-                  [&] { launch_source_gram<T>(dgx, dgs, P, pt.smax, n, gg, S.kpart[0], psg, st); });
+                  [&] { launch_source_gram<T>(dgx, dgs, P, sp.smax, n, gg, S.kpart[0], psg, st); });
             check_launch(c);
         }
         launch_source_eig(L, S.wd, S.wi, dall, P, std::max(o->svd_tol, svd_floor), b_cap, dots, nrm + 1, st,
@@ -1301,7 +1515,8 @@ int solve_linear_typed(pexp_ctx* c, const pexp_operator* op, const pexp_options*
         b_max = std::max(b_max, mj[j]);
         b_min = std::min(b_min, mj[j]);
     }
-    S.fused = (S.od.dim == 1) && (b_max <= kKrylovMaxB);
+    // restart cycles run in the dense-projection driver
+    S.fused = (S.od.dim == 1) && (b_max <= kKrylovMaxB) && o->max_restarts == 0;
     // bases laid out with the actual widths, in the basis pool
     {
         size_t need = 0;
@@ -1338,7 +1553,7 @@ int solve_linear_typed(pexp_ctx* c, const pexp_operator* op, const pexp_options*
         for (int a = 0; a < ns; ++a) {
             const Win<T>& W = src[a];
             const int j = W.w;
-            const int s = pt.idx[j + 1] - pt.idx[j] + 1;
+            const int s = src_count(j);
             TsTask<T> t;
             memset(&t, 0, sizeof(t));
             t.X = src_first(j); t.ldx = n; t.xs = Au0; t.p = s; t.q = W.b;
@@ -1431,7 +1646,7 @@ int solve_linear_typed(pexp_ctx* c, const pexp_operator* op, const pexp_options*
     if (o->diagnostics & PEXP_DIAG_ORTH) {
         orth_max = 0.0;
         for (int j = 0; j < P; ++j)
-            if (Vnh[j]) orth_max = std::max(orth_max, S.orth_defect(Vnh[j], Knh[j]));
+            if (Vnh[j]) orth_max = std::max(orth_max, S.orth_defect_cycles(Vnh[j], Knh[j], mj[j]));
     }
 
     cudaEventRecord(c->evp[2], st);
@@ -1572,7 +1787,7 @@ int solve_linear_typed(pexp_ctx* c, const pexp_operator* op, const pexp_options*
         notconv += S.run(one, KIND_HOM, &kh);
         const int kk = S.wi_host[(size_t)(P + m) * L.istride + WI_K];   // state after the last step
         Kh[m] = kk;
-        if (o->diagnostics & PEXP_DIAG_ORTH) orth_max = std::max(orth_max, S.orth_defect(Vh[m], kk));
+        if (o->diagnostics & PEXP_DIAG_ORTH) orth_max = std::max(orth_max, S.orth_defect_cycles(Vh[m], kk, 1));
         k_hom_max = std::max(k_hom_max, kh);
         k_hom_sum += kh;
         steps_h[m] = kh;
@@ -1640,7 +1855,7 @@ int solve_linear_typed(pexp_ctx* c, const pexp_operator* op, const pexp_options*
             rep->sub_rank[j] = mj[j];
             rep->sub_steps[j] = mj[j] > 0 ? S.wi_host[(size_t)j * L.istride + WI_STEPS] : 0;
             rep->sub_hom_steps[j] = steps_h[j];
-            rep->sub_restarts[j] = 0;
+            rep->sub_restarts[j] = S.restarts[j];
         }
         const double w = (double)sizeof(T);
         double bytes = 0;
@@ -1650,7 +1865,7 @@ int solve_linear_typed(pexp_ctx* c, const pexp_operator* op, const pexp_options*
         // over k steps) and ~14 column passes of the working block; the homogeneous chain
         // likewise; the reconstruction below
         for (int j = 0; j < P; ++j) {
-            const int s = pt.idx[j + 1] - pt.idx[j] + 1;
+            const int s = src_count(j);
             bytes += 2.0 * n * s * w + (double)n * mj[j] * w;
             const double k = Knh[j] / std::max(1, mj[j]);
             bytes += (double)n * mj[j] * w * (2.0 * k * (k + 1) + 14.0 * k);
@@ -1670,7 +1885,7 @@ int solve_linear_dispatch(pexp_ctx* c, const pexp_operator* op, const pexp_optio
     const int64_t n = od.n;
     const bool fp64 = o->precision == PEXP_FP64;
     Partition pt = make_partition(o->n_out, o->P);
-    const int b_cap = std::min(std::min(o->max_rank, PEXP_MAX_RANK), pt.smax);
+    const int b_cap = std::min(std::min(o->max_rank, PEXP_MAX_RANK), make_src_partition(o, pt).smax);
     const int g_conv = G_dev && ((g_dtype == PEXP_F64) != fp64);
     size_t need = keep_top +
                   (fp64 ? linear_workspace_bytes<double>(n, o, g_conv, b_cap)
@@ -1916,7 +2131,8 @@ int pexp_solve_linear_host(pexp_ctx* c, const pexp_operator* op, const pexp_opti
     const OpDesc od = make_opdesc(*op);
     const size_t n = (size_t)od.n;
     const size_t ys = (y_dtype == PEXP_F64) ? 8 : 4, gs = (g_dtype == PEXP_F64) ? 8 : 4;
-    const size_t bytes = align_up(n * 8) + (G_host ? align_up(n * o->n_out * gs) : 0) + align_up(n * o->n_out * ys);
+    const size_t grows = (size_t)src_rows_of(o);
+    const size_t bytes = align_up(n * 8) + (G_host ? align_up(n * grows * gs) : 0) + align_up(n * o->n_out * ys);
     cudaSetDevice(c->device);
     if (bytes > c->io_cap) {
         if (c->io_d) cudaFree(c->io_d);
@@ -1929,10 +2145,10 @@ int pexp_solve_linear_host(pexp_ctx* c, const pexp_operator* op, const pexp_opti
     void* y0d = p;
     p += align_up(n * 8);
     void* Gd = nullptr;
-    if (G_host) { Gd = p; p += align_up(n * o->n_out * gs); }
+    if (G_host) { Gd = p; p += align_up(n * grows * gs); }
     void* Yd = p;
     PEXP_CUDA_TRY(cudaMemcpyAsync(y0d, y0_host, n * 8, cudaMemcpyHostToDevice, c->stream));
-    if (G_host) PEXP_CUDA_TRY(cudaMemcpyAsync(Gd, G_host, n * o->n_out * gs, cudaMemcpyHostToDevice, c->stream));
+    if (G_host) PEXP_CUDA_TRY(cudaMemcpyAsync(Gd, G_host, n * grows * gs, cudaMemcpyHostToDevice, c->stream));
     // the outputs leave window by window on the copy stream while the continuation chain runs
     return solve_linear_entry(c, op, o, y0d, Gd, g_dtype, Yd, y_dtype, rep, Y_host);
 }
@@ -2099,6 +2315,8 @@ int pexp_solve_burgers(pexp_ctx* c, const pexp_operator* op, const pexp_options*
     if (o->jacobian != 0 && o->jacobian != 1) return PEXP_ERR_INVALID_ARG;
     int v = validate(op, o);
     if (v) return v;
+    // the source samples of waveform relaxation are the iterate's, at the output times
+    if (o->nodes != PEXP_NODES_UNIFORM) return PEXP_ERR_UNSUPPORTED;
     // the averaged Jacobian: conservative form, shift-and-invert space, iterates in the
     // solver's own precision
     if (o->jacobian && (o->burgers_form != 0 || o->krylov != PEXP_KRYLOV_SAI ||

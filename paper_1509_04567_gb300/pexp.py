@@ -55,6 +55,8 @@ FP64 = 0
 MIXED = 1
 F64 = 0
 F32 = 1
+NODES_UNIFORM = 0
+NODES_CHEBYSHEV = 1
 
 # Symbols declared in include/pexp.h (checked by the CPU tests).
 EXPORTS = ["pexp_create", "pexp_destroy", "pexp_set_stream", "pexp_default_options", "pexp_status_string",
@@ -75,7 +77,8 @@ class Options(C.Structure):
                 ("max_restarts", C.c_int), ("krylov", C.c_int), ("sai_gamma", C.c_double),
                 ("precision", C.c_int), ("wr_max_iter", C.c_int), ("wr_tol", C.c_double),
                 ("burgers_form", C.c_int), ("diagnostics", C.c_int), ("jacobian", C.c_int),
-                ("wr_diverge", C.c_int), ("sub_first", C.c_int), ("sub_last", C.c_int)]
+                ("wr_diverge", C.c_int), ("sub_first", C.c_int), ("sub_last", C.c_int),
+                ("nodes", C.c_int), ("n_samp", C.c_int)]
 
 
 class Problem(C.Structure):
@@ -194,6 +197,29 @@ def make_options(opts: dict) -> Options:
     return o
 
 
+def source_rows(opts: dict) -> int:
+    """Rows of the source samples G of a linear solve: n_out (samples at the output times), or
+    P (n_samp - 1) + 1 with Chebyshev samples (nodes = NODES_CHEBYSHEV)."""
+    if int(opts.get("nodes", NODES_UNIFORM)) == NODES_CHEBYSHEV:
+        return int(opts["P"]) * (int(opts["n_samp"]) - 1) + 1
+    return int(opts["n_out"])
+
+
+def _check_series_shapes(op: dict, opts: dict, y0, G, Y) -> None:
+    """A valid solve reads n values of y0 and source_rows(opts) * n of G and writes n_out * n of
+    Y: check that the arrays hold at least that before passing their pointers (invalid options
+    are left to the library, which rejects them before touching any buffer)."""
+    n = int(op["nx"]) * (int(op.get("ny", 1)) if op["dim"] == 2 else 1)
+    if tuple(y0.shape) != (n,):
+        raise ValueError(f"y0 must have shape ({n},), got {tuple(y0.shape)}")
+    for name, a, rows in (("Y", Y, int(opts["n_out"])), ("G", G, source_rows(opts))):
+        if a is None:
+            continue
+        count = a.numel() if hasattr(a, "numel") else a.size
+        if a.shape[-1] != n or count < max(rows, 0) * n:
+            raise ValueError(f"{name} must hold ({rows}, {n}) values, got shape {tuple(a.shape)}")
+
+
 def _dtype_code(t) -> int:
     import torch
     if t.dtype == torch.float64:
@@ -246,12 +272,14 @@ class Context:
 
     # ---------------------------------------------------------------- solvers
     def solve_linear(self, op: dict, opts: dict, y0, G, Y, check: bool = True) -> dict:
-        """Paraexp-EBK solve: y0 (n,) FP64, G (n_out, n) or None, Y (n_out, n) -- CUDA tensors."""
+        """Paraexp-EBK solve: y0 (n,) FP64, G (source_rows(opts), n) or None, Y (n_out, n) --
+        CUDA tensors."""
         import torch
         for t in (y0, Y) + ((G,) if G is not None else ()):
             assert t.is_cuda and t.is_contiguous()
         if y0.dtype != torch.float64:
             raise TypeError("the initial condition must be FP64")
+        _check_series_shapes(op, opts, y0, G, Y)
         rep = Report()
         o = make_options(opts)
         rc = lib().pexp_solve_linear(self.h, C.byref(make_operator(op)), C.byref(o), C.c_void_p(y0.data_ptr()),
@@ -271,6 +299,7 @@ class Context:
             assert isinstance(a, np.ndarray) and a.flags["C_CONTIGUOUS"]
         if y0.dtype != np.float64:
             raise TypeError("the initial condition must be FP64")
+        _check_series_shapes(op, opts, y0, G, Y)
         rep = Report()
         rc = lib().pexp_solve_linear_host(self.h, C.byref(make_operator(op)), C.byref(make_options(opts)),
                                           C.c_void_p(y0.ctypes.data),

@@ -90,3 +90,54 @@ def test_travelling_sawtooth_error_is_second_order_in_dx(c):
         floors.append(float(np.max(np.linalg.norm(U - ex, axis=1) / np.linalg.norm(ex, axis=1))))
     assert 3.2 < floors[0] / floors[1] < 5.0, floors
     assert 3.2 < floors[1] / floors[2] < 5.0, floors
+
+
+def _multiscale(n, k0, P=2, s=33, T=0.2):
+    """Sec. 4 multiscale example (eq. multiscale_solution) with the forcing built from the
+    discrete operators, f = u_t - A u - g(u) at the grid points (the oracle's A and g, on the
+    host), so that the semi-discrete solution is the exact one."""
+    n_out = P * (s - 1) + 1
+    t = wl.out_times(T, n_out)
+    x = wl.grid_1d(n)
+    op = wl.make_op(n, 1e-2, 0.0)
+    A = ob.operator_matrix(op)
+    U = np.zeros((n_out, n))
+    F = np.zeros((n_out, n))
+    for i, tt in enumerate(t):
+        u, ut = wl.multiscale_solution(x, tt, k0)
+        U[i] = u
+        F[i] = ut - A @ u - ob.burgers_source(op, u, 0)
+    return op, t, U, F
+
+
+def _relerr_max(U, Uref):
+    """max_i ||U_i - Uref_i|| / max_i ||Uref_i|| (the norm of the WR update; the solution is
+    zero at t = 0, so row-wise relative errors are not defined there)."""
+    return float(np.max(np.linalg.norm(U - Uref, axis=1)) / np.max(np.linalg.norm(Uref, axis=1)))
+
+
+@pytest.mark.parametrize("k0", [4, 16])
+def test_multiscale_burgers_matches_oracle_and_exact(c, k0):
+    """The multiscale case on the GPU (averaged-Jacobian WR, FP64): after 4 iterations the
+    iterate equals the oracle's (both at Krylov tol 1e-12 and svd_tol 1e-7, the FP64 path's
+    singular-value floor), and after 8 its error against the exact solution is at the
+    time-integration floor (< 1e-5, no spatial error), for the wide spectrum (k0 = 16) as
+    for the narrow one."""
+    import torch
+    op, t, Uex, F = _multiscale(128, k0)
+    opts = wl.default_opts(T=0.2, P=2, n_out=t.size, tol=1e-12, svd_tol=1e-7, max_rank=12, wr_tol=1e-14,
+                           wr_max_iter=4, restart_len=40, jacobian=1, wr_diverge=0)
+    Ft = torch.from_numpy(F).cuda()
+    u0 = torch.from_numpy(Uex[0].copy()).cuda()
+    U = torch.zeros((t.size, 128), dtype=torch.float64, device="cuda")
+    rep = c.solve_burgers(op, opts, u0, U, forcing=Ft)
+    torch.cuda.synchronize()
+    assert rep["wr_iters"] == 4, rep
+    Uo, ro = ob.solve_burgers_jacobian(op, opts, Uex[0].copy(), forcing=F)
+    np.testing.assert_allclose(rep["wr_history"][:4], ro["deltas"], rtol=1e-6)
+    assert _relerr_max(U.cpu().numpy(), Uo) < 1e-9
+    opts8 = dict(opts, tol=1e-8, svd_tol=1e-10, wr_max_iter=8)
+    rep = c.solve_burgers(op, opts8, u0, U, forcing=Ft)
+    torch.cuda.synchronize()
+    err = _relerr_max(U.cpu().numpy(), Uex)
+    assert err < 1e-5, err

@@ -728,15 +728,15 @@ def _restart_err(krylov, n, nu, P, n_out, T, rl, mr):
 
 def test_restarted_polynomial_krylov_matches_the_closed_form():
     """Restart cycles of 4 and 6 block steps in the polynomial space: every subproblem restarts
-    and still converges to the exact solution with the same source model, in about as many
-    block steps in all as without restarts (the cycle's residual lies in the next block)."""
+    and still converges to the exact solution with the same source model, in at most one cycle
+    more than without restarts (the cycle's residual lies in the next block)."""
     e0, r0 = _restart_err(0, 128, 1e-3, 4, 33, 0.25, 40, 0)
     for rl, mr in ((4, 20), (6, 10)):
         e, rep = _restart_err(0, 128, 1e-3, 4, 33, 0.25, rl, mr)
         assert all(rep["conv_nh"]) and all(all(c) for c in rep["conv_hom"])
         assert min(rep["restarts_nh"]) >= 2
         assert e < 1e-11, (rl, e)
-        assert max(rep["k_nh"]) <= max(r0["k_nh"]) + 2
+        assert max(rep["k_nh"]) <= max(r0["k_nh"]) + rl   # at most one cycle more
 
 
 def test_restarted_shift_and_invert_krylov_matches_the_closed_form():
@@ -764,3 +764,18 @@ def test_restart_residual_has_the_block_rank(krylov):
     Z = A @ V - V @ (V.T @ (A @ V))
     sv = np.linalg.svd(Z, compute_uv=False)
     assert sv[b] < 1e-8 * sv[0], sv[:b + 2]
+
+
+def test_restarted_solve_stops_within_its_tolerance():
+    """At tol 1e-7 with cycles of 4 and 8 blocks the restarted solve ends within 10 tol of the
+    closed form: a restart cycle is not tested for convergence at its first step, where the
+    step-to-step change is far below the error."""
+    for rl, mr in ((4, 15), (8, 7)):
+        pr = wl.adv_diff_1d(n=1024, nu=1e-2, P=4, n_out=41, T=1.0, tol=1e-7, restart_len=rl, max_restarts=mr)
+        Y, rep = ob.solve_linear(pr.op, pr.opts, pr.u0, pr.G)
+        assert all(rep["conv_nh"]) and min(rep["restarts_nh"]) >= 1
+        t, wins = cf.fourier_windows_from_oracle_model(pr.op, pr.opts, pr.u0, pr.G, ob.compress_source,
+                                                       ob.spline_segments, ob.partition)
+        Yx = cf.exact_piecewise_cubic(cf.circulant_eigs(1024, 1.0, 1e-2), pr.u0, t, wins)
+        err = float(np.max(np.linalg.norm(Y - Yx, axis=1) / np.linalg.norm(Yx, axis=1)))
+        assert err < 1e-6, (rl, err)
