@@ -107,11 +107,12 @@ __device__ __forceinline__ void cta_affine_scan(R a, R b, bool reverse, R* sa, R
     }
     __syncthreads();
     if (warp == 0) {
-        // exclusive scan of the warp totals (NW <= 32) in virtual warp order
+        // exclusive scan of the warp totals (NW <= 32) in virtual warp order; lanes < NW only
+        // read lanes < NW, so log2(NW) shuffle rounds give them their full prefixes
         R wa = lane < NW ? sa[lane] : rfrom<R>(1.0);
         R wb = lane < NW ? sb[lane] : rfrom<R>(0.0);
 #pragma unroll
-        for (int d = 1; d < 32; d <<= 1) {
+        for (int d = 1; d < NW; d <<= 1) {
             const R pa = rshfl_up(wa, d), pb = rshfl_up(wb, d);
             if (lane >= d) {
                 wb = rfma(wa, pb, wb);
@@ -268,10 +269,12 @@ __device__ __forceinline__ double sai_carry_warp(const double* ends, const doubl
 }
 
 // Forward values w of this thread's elements (cnt of them, registers): the local maps
-// composed over the CTA and the circular carry into the chunk.  Contains barriers.
+// composed over the CTA and the circular carry into the chunk.  Contains barriers.  The carry
+// is read from shared memory after the CTA scan, so the warp that computes it may write it
+// up to the scan's first barrier: its computation overlaps the other warps' local work.
 template <typename T, typename R>
 __device__ __forceinline__ void sai_forward_values(const T* vals, const T* lows, bool has_lo, int cnt, R al,
-                                                   double carry, R* sa, R* sb, R* wv) {
+                                                   const double* carry_sm, R* sa, R* sb, R* wv) {
     R b = rfrom<R>(0.0);
 #pragma unroll
     for (int j = 0; j < kSaiPer; ++j)
@@ -279,7 +282,7 @@ __device__ __forceinline__ void sai_forward_values(const T* vals, const T* lows,
     R a = ipow(al, cnt);
     R ea, eb, ta, tb;
     cta_affine_scan<R>(a, b, false, sa, sb, ea, eb, ta, tb);
-    R w = rfma(ea, rfrom<R>(carry), eb);
+    R w = rfma(ea, rfrom<R>(*carry_sm), eb);
 #pragma unroll
     for (int j = 0; j < kSaiPer; ++j) {
         if (j < cnt) w = rfma(al, w, load_r<T, R>(vals[j], has_lo ? lows[j] : T(0)));

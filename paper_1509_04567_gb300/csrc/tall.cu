@@ -316,17 +316,17 @@ __device__ __forceinline__ void sai_fwd_apply_body(int64_t n, int nch, double al
     using R = typename SaiR<T>::R;
     __shared__ R sa[kSaiThreads], sb[kSaiThreads];
     __shared__ double carry_in;
-    if (threadIdx.x < 32) {
-        const double cv = sai_carry_warp(fends + (int64_t)v * nch, fdecays + (int64_t)v * nch, nch, ch, +1, alpha_n);
-        if (threadIdx.x == 0) carry_in = cv;
-    }
     const int64_t start = (int64_t)ch * kSaiChunk + (int64_t)threadIdx.x * kSaiPer;
     T vals[kSaiPer], lows[kSaiPer];
     const int cnt = sai_load(x, n, start, vals);
     if (xl) sai_load(xl, n, start, lows);
-    __syncthreads();   // carry_in
+    // warp 0 computes the carry while the loads are in flight; it is read after the first scan
+    if (threadIdx.x < 32) {
+        const double cv = sai_carry_warp(fends + (int64_t)v * nch, fdecays + (int64_t)v * nch, nch, ch, +1, alpha_n);
+        if (threadIdx.x == 0) carry_in = cv;
+    }
     R wv[kSaiPer];
-    sai_forward_values<T, R>(vals, lows, xl != nullptr, cnt, rfrom<R>(alpha), carry_in, sa, sb, wv);
+    sai_forward_values<T, R>(vals, lows, xl != nullptr, cnt, rfrom<R>(alpha), &carry_in, sa, sb, wv);
     const R be = rfrom<R>(beta);
     R gb = rfrom<R>(0.0);
 #pragma unroll
@@ -353,21 +353,21 @@ __device__ __forceinline__ void sai_bwd_apply_body(int64_t n, int nch, double al
     using R = typename SaiR<T>::R;
     __shared__ R sa[kSaiThreads], sb[kSaiThreads];
     __shared__ double carry_f, carry_b;
-    if (threadIdx.x < 32) {
-        const double cf = sai_carry_warp(fends + (int64_t)v * nch, fdecays + (int64_t)v * nch, nch, ch, +1, alpha_n);
-        const double cb = sai_carry_warp(bends + (int64_t)v * nch, bdecays + (int64_t)v * nch, nch, ch, -1, beta_n);
-        if (threadIdx.x == 0) {
-            carry_f = cf;
-            carry_b = cb;
-        }
-    }
     const int64_t start = (int64_t)ch * kSaiChunk + (int64_t)threadIdx.x * kSaiPer;
     T vals[kSaiPer], lows[kSaiPer];
     const int cnt = sai_load(x, n, start, vals);
     if (xl) sai_load(xl, n, start, lows);
-    __syncthreads();   // carry_f, carry_b
+    // the two carries side by side while the loads are in flight: warp 0 the forward one (read
+    // after the first scan), warp 1 the backward one (read after the second)
+    if (threadIdx.x < 32) {
+        const double cf = sai_carry_warp(fends + (int64_t)v * nch, fdecays + (int64_t)v * nch, nch, ch, +1, alpha_n);
+        if (threadIdx.x == 0) carry_f = cf;
+    } else if (threadIdx.x < 64) {
+        const double cb = sai_carry_warp(bends + (int64_t)v * nch, bdecays + (int64_t)v * nch, nch, ch, -1, beta_n);
+        if (threadIdx.x == 32) carry_b = cb;
+    }
     R wv[kSaiPer];
-    sai_forward_values<T, R>(vals, lows, xl != nullptr, cnt, rfrom<R>(alpha), carry_f, sa, sb, wv);
+    sai_forward_values<T, R>(vals, lows, xl != nullptr, cnt, rfrom<R>(alpha), &carry_f, sa, sb, wv);
     const R be = rfrom<R>(beta);
     R gb = rfrom<R>(0.0);
 #pragma unroll
@@ -456,14 +456,20 @@ __global__ void __launch_bounds__(kSaiThreads) k_sai_coop(int64_t n, int nch, Sa
     if (active)
         for (int ch = blockIdx.x; ch < nch; ch += gridDim.x) sai_fwd_ends_body<T>(n, nch, cf.alpha, x, nullptr, fends, fdec, 0, ch);
     if (!grid_bar(bar)) return;
+    // a CTA's chunks run one after another: a barrier between them keeps the next chunk's
+    // carries (written by warps 0 and 1) from overtaking the reads of the last chunk's
     if (active)
-        for (int ch = blockIdx.x; ch < nch; ch += gridDim.x)
+        for (int ch = blockIdx.x; ch < nch; ch += gridDim.x) {
             sai_fwd_apply_body<T>(n, nch, cf.alpha, cf.beta, cf.alpha_n, x, nullptr, fends, fdec, bends, bdec, 0, ch);
+            __syncthreads();
+        }
     if (!grid_bar(bar)) return;
     if (active)
-        for (int ch = blockIdx.x; ch < nch; ch += gridDim.x)
+        for (int ch = blockIdx.x; ch < nch; ch += gridDim.x) {
             sai_bwd_apply_body<T>(n, nch, cf.alpha, cf.alpha_n, cf.beta, cf.beta_n, cf.inv_c, x, nullptr, y, ylo, fends,
                                   fdec, bends, bdec, 0, ch);
+            __syncthreads();
+        }
 }
 
 template <typename T>
