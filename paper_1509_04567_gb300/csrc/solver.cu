@@ -30,6 +30,8 @@
 #include <type_traits>
 #include <vector>
 
+#include <nvtx3/nvToolsExt.h>
+
 #include "common.cuh"
 #include "krylov.cuh"
 #include "small.cuh"
@@ -149,6 +151,21 @@ constexpr int kFlagBufs = 4;                 // pinned copies of the window flag
 constexpr int kLookahead = 1;                // steps between queueing a step and reading its flags
 static_assert(kLookahead + 1 <= kFlagBufs, "a flag copy is read before its buffer is reused");
 static_assert(std::extent<decltype(pexp_ctx::flag_ev)>::value == kFlagBufs, "one event per flag copy");
+
+// NVTX ranges of a solve's phases, shown by profilers (ncu, nsys) on the host timeline: one
+// range at a time, the next phase closing the current one; the destructor closes the last
+// (also when a phase throws).
+struct NvtxPhases {
+    bool open = false;
+    void next(const char* name) {
+        if (open) nvtxRangePop();
+        nvtxRangePushA(name);
+        open = true;
+    }
+    ~NvtxPhases() {
+        if (open) nvtxRangePop();
+    }
+};
 
 struct OomError {};
 struct StatusError {
@@ -1436,6 +1453,8 @@ int solve_linear_typed(pexp_ctx* c, const pexp_operator* op, const pexp_options*
         sync(c);   // wih goes out of scope
     }
 
+    NvtxPhases nvtx;
+    nvtx.next("pexp: shift and source compression");
     cudaEventRecord(c->evp[0], st);
     // ---- shift: A u0, ||u0||, ||A u0||^2, (A u0) . g(t_i)
     double* nrm = S.partial + part_n - 8;   // [0] = ||u0||^2, [1] = ||A u0||^2
@@ -1633,6 +1652,7 @@ int solve_linear_typed(pexp_ctx* c, const pexp_operator* op, const pexp_options*
         sync(c);   // staging half 1 is reused by the Krylov loop
     }
 
+    nvtx.next("pexp: nonhomogeneous block Krylov");
     cudaEventRecord(c->evp[1], st);
     // the Krylov steps take the rounded start block (see the note on the solve's input)
     for (auto& W : src) W.V1lo = nullptr;
@@ -1649,6 +1669,7 @@ int solve_linear_typed(pexp_ctx* c, const pexp_operator* op, const pexp_options*
             if (Vnh[j]) orth_max = std::max(orth_max, S.orth_defect_cycles(Vnh[j], Knh[j], mj[j]));
     }
 
+    nvtx.next("pexp: homogeneous chain");
     cudaEventRecord(c->evp[2], st);
     // ---- homogeneous chain over windows 2..P
     std::vector<T*> Vh(P, nullptr);
@@ -1795,6 +1816,7 @@ int solve_linear_typed(pexp_ctx* c, const pexp_operator* op, const pexp_options*
     }
     S.check_coop();
 
+    nvtx.next("pexp: reconstruction");
     cudaEventRecord(c->evp[3], st);
     if (Y_host) {
         // every window has been reconstructed and is on its way to the host
