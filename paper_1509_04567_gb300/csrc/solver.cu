@@ -629,20 +629,17 @@ struct Solver {
             cudaEventRecord(c->ev_pj, c->s2);
             if (!coop_step && step < kmax) part_b(act, step);
             int* fl = c->flags_h + (size_t)(step % kFlagBufs) * nint;
-            if (coop_step) {
-                // the flags of this step go back behind its projected solve, on its stream
-                cudaMemcpyAsync(fl, wi, sizeof(int) * nint, cudaMemcpyDeviceToHost, c->s2);
-                cudaEventRecord(c->flag_ev[step % kFlagBufs], c->s2);
-                pj_pending = true;
-            } else {
-                // the step's projected solve must be done before its flags are read and before the
-                // next step's projections overwrite the partial sums it reads
-                cudaStreamWaitEvent(st, c->ev_pj, 0);
-                // flags of this step, read back without waiting; then those of the step kLookahead
-                // before, so that the host prepares the next launches while the device runs this step
-                cudaMemcpyAsync(fl, wi, sizeof(int) * nint, cudaMemcpyDeviceToHost, st);
-                cudaEventRecord(c->flag_ev[step % kFlagBufs], st);
-            }
+            // The flags of this step go back behind its projected solve, on its stream, so that
+            // no copy and no wait sit between the main stream's kernels (programmatic dependent
+            // launch chains part B into the next step's shift-and-invert passes, which need
+            // neither the projected solve's results nor its buffers; a window it marks converged
+            // costs them one step of work that is never used).  The next projection pass, which
+            // overwrites the partial sums the projected solve reads, waits for it.  The host
+            // reads the flags of the step kLookahead before, so that it prepares the next
+            // launches while the device runs this step.
+            cudaMemcpyAsync(fl, wi, sizeof(int) * nint, cudaMemcpyDeviceToHost, c->s2);
+            cudaEventRecord(c->flag_ev[step % kFlagBufs], c->s2);
+            pj_pending = true;
             if (step > kLookahead) {
                 const int old = (step - kLookahead) % kFlagBufs;
                 cudaEventSynchronize(c->flag_ev[old]);

@@ -149,3 +149,24 @@ def test_header_is_c99_and_links_from_plain_c(lib, tmp_path):
     assert run.returncode == 0, (run.returncode, run.stderr)
     sizes = [str(ctypes.sizeof(c)) for c in (pexp.Operator, pexp.Options, pexp.Report, pexp.Problem)]
     assert run.stdout.split() == ["1", str(2 | (1 << 11) | (2 << 16))] + sizes
+
+
+def test_binding_checks_the_series_it_passes():
+    """The binding checks, before a solve's pointers go to the library, that y0, G and Y hold
+    what a valid solve reads and writes: G has n_out rows, or P (n_samp - 1) + 1 with
+    Chebyshev samples; invalid options are left to the library (no buffer check fails)."""
+    import numpy as np
+    from paper_1509_04567_gb300 import pexp
+    op = dict(dim=1, nx=64, ny=1, bc=0, ax=1.0, ay=0.0, nu=1e-2, Lx=1.0, Ly=1.0)
+    opts = dict(n_out=9, P=4)
+    cheb = dict(n_out=9, P=4, nodes=pexp.NODES_CHEBYSHEV, n_samp=13)
+    assert pexp.source_rows(opts) == 9 and pexp.source_rows(cheb) == 49
+    y0, Y = np.zeros(64), np.zeros((9, 64))
+    pexp._check_series_shapes(op, opts, y0, np.zeros((9, 64)), Y)
+    pexp._check_series_shapes(op, cheb, y0, np.zeros((49, 64)), Y)
+    pexp._check_series_shapes(op, dict(opts, n_out=1), y0, None, Y)   # invalid: the library says so
+    for bad in ((cheb, np.zeros((9, 64)), Y), (opts, np.zeros((9, 32)), Y), (opts, None, np.zeros((8, 64)))):
+        with pytest.raises(ValueError):
+            pexp._check_series_shapes(op, bad[0], y0, bad[1], bad[2])
+    with pytest.raises(ValueError):
+        pexp._check_series_shapes(op, opts, np.zeros(63), None, Y)
