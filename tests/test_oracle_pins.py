@@ -779,3 +779,29 @@ def test_restarted_solve_stops_within_its_tolerance():
         Yx = cf.exact_piecewise_cubic(cf.circulant_eigs(1024, 1.0, 1e-2), pr.u0, t, wins)
         err = float(np.max(np.linalg.norm(Y - Yx, axis=1) / np.linalg.norm(Yx, axis=1)))
         assert err < 1e-6, (rl, err)
+
+
+def test_shift_and_invert_arnoldi_relation_gives_the_residual_range():
+    """The GPU starts a restart cycle from q = V' - gamma (I - V V^T) A V' (V' the block that
+    the cycle's next step would add), by the cycle's Arnoldi relation for (I - gamma A)^{-1};
+    the oracle from an SVD of (I - V V^T) A V.  Both are the same subspace."""
+    n, b, gamma = 512, 2, 0.02
+    pr = wl.adv_diff_1d(n=n, nu=1e-2, P=1, n_out=5)
+    A = ob.operator_matrix(pr.op)
+    kop = ob.KrylovOperator(pr.op, A, ob.KRYLOV_SAI, gamma)
+    x = wl.grid_1d(n)
+    V, _ = np.linalg.qr(np.column_stack([pr.u0, np.exp(-50 * (x - 0.3) ** 2)]))
+    last = V
+    for _ in range(3):
+        new = ob.block_krylov_step(kop, V, last)
+        assert new.shape[1] == b
+        V, last = np.hstack([V, new]), new
+    Vn = ob.block_krylov_step(kop, V, last)          # V'
+    AVn = A @ Vn
+    q = Vn - gamma * (AVn - V @ (V.T @ AVn))
+    Q = np.linalg.qr(q)[0]
+    R = ob.restart_block(V, A @ V, b)
+    assert R.shape[1] == b
+    # the two orthonormal bases span the same space: singular values of Q^T R are all 1
+    sv = np.linalg.svd(Q.T @ R, compute_uv=False)
+    np.testing.assert_allclose(sv, 1.0, atol=1e-9)
