@@ -65,15 +65,19 @@ def read_peaks() -> dict:
 
 
 def profile_traffic(kernel_class: str):
-    """Per-launch DRAM bytes of a kernel class from the committed ncu summary, or None."""
+    """Per-launch DRAM bytes of a kernel class from the committed ncu summary, or None (also
+    when the summary says that the class's kernels have changed since its capture)."""
     p = os.path.join(ROOT, "profiles", f"{kernel_class}_traffic.txt")
     try:
+        value = None
         for line in open(p):
+            if line.startswith("stale:"):
+                return None
             if line.startswith("traffic_bytes_per_launch:"):
-                return float(line.split(":")[1])
+                value = float(line.split(":")[1])
+        return value
     except Exception:
-        pass
-    return None
+        return None
 
 
 class Clocks:
